@@ -1,0 +1,288 @@
+"""Seeded, synthetic initial data for the Active Flux solver and its oracle.
+
+This module only defines initial conditions and turns them into the
+method's degrees of freedom (cell averages of the conserved variables by a
+5x5 Gauss-Legendre rule per cell, and point values at vertices and edge
+midpoints).  It holds none of the method's own arithmetic, so both the CUDA
+path and the FP64 oracle can take their inputs from it.
+
+Problems (paper sections in brackets):
+  * ``gaussian_pulse``  -- Example 1, 1D density/pressure pulse [Sec. 2]
+  * ``compact_vortex``  -- Example 2, compactly supported travelling vortex
+    [Sec. 2]; the velocity profile is read as 1024 (1-r)^6 r^6, the only
+    profile whose pressure balance gives the printed p(r)
+  * ``shu_vortex``      -- isentropic vortex on a periodic box; strength,
+    centre and box are parameters (not from the paper; a standard smooth test)
+  * ``four_quadrant``   -- four constant states meeting at (0.5, 0.5), as in
+    the 2D Riemann problems of Sec. 4.1; states drawn from a seed
+  * ``double_rarefaction`` -- two states moving apart at x = 0.5, cf.
+    Example 4 (double rarefaction), with the stated near-vacuum data
+  * ``kelvin_helmholtz`` -- the shear-layer data of Sec. 4.2
+  * ``fourier_smooth``  -- seeded smooth periodic field used for parity tests
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Callable, Optional
+
+import numpy as np
+
+GAMMA = 1.4
+PERIODIC, TRANSMISSIVE, REFLECTING = 0, 1, 2
+
+# 5-point Gauss-Legendre on [0, 1]
+_GLX, _GLW = np.polynomial.legendre.leggauss(5)
+_GLX = 0.5 * (_GLX + 1.0)
+_GLW = 0.5 * _GLW
+
+Field = Callable[[np.ndarray, np.ndarray], tuple]
+
+
+@dataclasses.dataclass
+class Problem:
+    name: str
+    nx: int
+    ny: int
+    x0: float
+    y0: float
+    lx: float
+    ly: float
+    bc: tuple  # (xlo, xhi, ylo, yhi)
+    field: Field  # (x, y) -> (rho, u, v, p), vectorised
+    t_end: float
+    cfl: float = 0.3
+    gamma: float = GAMMA
+    options: dict = dataclasses.field(default_factory=dict)
+    exact: Optional[Callable[[float], Field]] = None
+
+    @property
+    def dx(self):
+        return self.lx / self.nx
+
+    @property
+    def dy(self):
+        return self.ly / self.ny
+
+    @property
+    def bc_code(self):
+        a, b, c, d = self.bc
+        return a | (b << 8) | (c << 16) | (d << 24)
+
+
+def conserved(U, gamma=GAMMA):
+    """Conserved variables (rho, rho u, rho v, E) of primitive (rho, u, v, p)."""
+    r, u, v, p = U
+    return np.stack([r, r * u, r * v, p / (gamma - 1.0) + 0.5 * r * (u * u + v * v)])
+
+
+def _eval(field, x, y):
+    return np.stack([np.broadcast_to(np.asarray(c, dtype=np.float64), np.broadcast(x, y).shape)
+                     for c in field(x, y)])
+
+
+def discretise(prob: Problem, field: Optional[Field] = None):
+    """Degrees of freedom of ``field`` (default: the problem's initial data).
+
+    Returns float64 arrays avg (4,ny,nx) conservative, vtx (4,ny+1,nx+1),
+    xe (4,ny,nx+1), ye (4,ny+1,nx) primitive.  On periodic axes the last node
+    line is an exact copy of the first one.
+    """
+    f = field or prob.field
+    nx, ny, dx, dy = prob.nx, prob.ny, prob.dx, prob.dy
+    xn = prob.x0 + dx * np.arange(nx + 1)
+    yn = prob.y0 + dy * np.arange(ny + 1)
+    xc = prob.x0 + dx * (np.arange(nx) + 0.5)
+    yc = prob.y0 + dy * (np.arange(ny) + 0.5)
+    vtx = _eval(f, xn[None, :], yn[:, None])
+    xe = _eval(f, xn[None, :], yc[:, None])
+    ye = _eval(f, xc[None, :], yn[:, None])
+    avg = np.zeros((4, ny, nx))
+    for a, wa in zip(_GLX, _GLW):
+        for b, wb in zip(_GLX, _GLW):
+            X = prob.x0 + dx * (np.arange(nx)[None, :] + a)
+            Y = prob.y0 + dy * (np.arange(ny)[:, None] + b)
+            avg += wa * wb * conserved(_eval(f, X, Y), prob.gamma)
+    if prob.bc[0] == PERIODIC:
+        vtx[:, :, nx] = vtx[:, :, 0]
+        xe[:, :, nx] = xe[:, :, 0]
+    if prob.bc[2] == PERIODIC:
+        vtx[:, ny, :] = vtx[:, 0, :]
+        ye[:, ny, :] = ye[:, 0, :]
+    return avg, vtx, xe, ye
+
+
+def to_f32(state):
+    """Round a state to FP32 (the GPU's storage) and back to float64."""
+    return tuple(np.asarray(a, dtype=np.float32).astype(np.float64) for a in state)
+
+
+def _wrap(d, period):
+    return d - period * np.floor(d / period + 0.5)
+
+
+# ----------------------------------------------------------------- problems
+def shu_vortex(n=32, eps=5.0, xc=5.0, yc=5.0, L=10.0, t_end=10.0, ny=None, cfl=0.3):
+    """Isentropic vortex of strength eps on the periodic box [0,L]^2 moving
+    with (1,1) through the background rho = u = v = p = 1 (minimum-image
+    distance to the centre, so the data are single valued on the torus)."""
+    g = GAMMA
+
+    def at(t):
+        cx, cy = xc + t, yc + t
+
+        def f(x, y):
+            X = _wrap(x - cx, L)
+            Y = _wrap(y - cy, L)
+            r2 = X * X + Y * Y
+            e = np.exp(0.5 * (1.0 - r2))
+            T = 1.0 - (g - 1.0) * eps * eps / (8.0 * g * np.pi ** 2) * e * e
+            rho = T ** (1.0 / (g - 1.0))
+            return rho, 1.0 - eps / (2 * np.pi) * e * Y, 1.0 + eps / (2 * np.pi) * e * X, rho ** g
+
+        return f
+
+    return Problem("shu_vortex", n, ny or n, 0.0, 0.0, L, L, (0, 0, 0, 0), at(0.0), t_end,
+                   cfl=cfl, exact=at)
+
+
+def shu_vortex_seeded(n, seed=2508, t_end=2.0):
+    """Vortex with centre in [3,6]^2 and strength in [3,6] drawn from ``seed``."""
+    rng = np.random.default_rng(seed)
+    xc, yc = rng.uniform(3.0, 6.0, size=2)
+    eps = rng.uniform(3.0, 6.0)
+    p = shu_vortex(n, eps=eps, xc=xc, yc=yc, t_end=t_end)
+    p.name = f"shu_vortex_seed{seed}"
+    return p
+
+
+_EX2_P = np.array([1 / 72, -6 / 35, 15 / 17, -74 / 33, 57 / 32, 174 / 31, -269 / 15, 450 / 29,
+                   153 / 8, -1564 / 27, 510 / 13, 204 / 5, -1473 / 16, 1014 / 23, 1053 / 22,
+                   -558 / 7, 783 / 20, 54 / 19, -38 / 9, -222 / 17, 609 / 32, -184 / 15, 9 / 2,
+                   -12 / 13, 1 / 12])  # coefficients of r^36 ... r^12, Example 2
+
+
+def ex2_pressure(r):
+    """p(r) of Example 2 (coefficients of r^36 down to r^12, times 1024^2)."""
+    r = np.asarray(r, dtype=np.float64)
+    s = np.zeros_like(r)
+    for k, c in enumerate(_EX2_P):
+        s = s * r + c
+    return 1024.0 ** 2 * s * r ** 12
+
+
+def compact_vortex(n=32, t_end=1.0, cfl=0.3):
+    """Example 2 on [0,1]^2, periodic, translating with (1,1); the exact
+    solution at integer times equals the initial data."""
+    rc, uc, vc, pc, R = 0.5, 1.0, 1.0, 0.1, 0.4
+    p1 = float(ex2_pressure(1.0))
+
+    def at(t):
+        def f(x, y):
+            X = _wrap(x - 0.5 - uc * t, 1.0)
+            Y = _wrap(y - 0.5 - vc * t, 1.0)
+            d = np.sqrt(X * X + Y * Y)
+            r = d / R
+            inside = r < 1.0
+            safe = np.where(d > 0, d, 1.0)
+            prof = 1024.0 * (1.0 - r) ** 6 * r ** 6
+            rho = np.where(inside, rc + 0.5 * (1.0 - r * r) ** 6, rc)
+            u = np.where(inside, uc - prof * Y / safe, uc)
+            v = np.where(inside, vc + prof * X / safe, vc)
+            p = np.where(inside, pc + ex2_pressure(np.minimum(r, 1.0)) - p1, pc)
+            return rho, u, v, p
+
+        return f
+
+    return Problem("compact_vortex", n, n, 0.0, 0.0, 1.0, 1.0, (0, 0, 0, 0), at(0.0), t_end,
+                   cfl=cfl, exact=at)
+
+
+def gaussian_pulse(nx=32, ny=8, t_end=0.25, cfl=0.3):
+    """Example 1: rho = p = 1 + exp(-80 (x-1/2)^2)/2, u = v = 0 on x in
+    [0,1]; ``ny`` square cells in y, periodic both ways."""
+
+    def f(x, y):
+        g = 1.0 + 0.5 * np.exp(-80.0 * (x - 0.5) ** 2) + 0.0 * y
+        return g, 0.0 * g, 0.0 * g, g
+
+    dx = 1.0 / nx
+    return Problem("gaussian_pulse", nx, ny, 0.0, 0.0, 1.0, ny * dx, (0, 0, 0, 0), f, t_end,
+                   cfl=cfl)
+
+
+def _piecewise(states, xs, ys):
+    """Four quadrant states (ll, lr, ul, ur) meeting at (xs, ys); points on a
+    dividing line take the mean of the adjacent states (the corner the mean of
+    all four)."""
+    S = np.asarray(states, dtype=np.float64)  # (4 quadrants, 4 vars)
+
+    def f(x, y):
+        x, y = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
+        wx_r = np.where(x > xs, 1.0, np.where(x == xs, 0.5, 0.0))
+        wy_u = np.where(y > ys, 1.0, np.where(y == ys, 0.5, 0.0))
+        w = [(1 - wx_r) * (1 - wy_u), wx_r * (1 - wy_u), (1 - wx_r) * wy_u, wx_r * wy_u]
+        return tuple(sum(w[q] * S[q, k] for q in range(4)) for k in range(4))
+
+    return f
+
+
+def four_quadrant(n=64, seed=0, t_end=0.25, cfl=0.3):
+    """Four-quadrant Riemann data on [0,1]^2 split at (0.5,0.5), outflow
+    boundaries; rho in [0.1,1.5], p in [0.01,1.5], u, v in [-1.2,1.2]."""
+    rng = np.random.default_rng(seed)
+    st = np.stack([rng.uniform(0.1, 1.5, 4), rng.uniform(-1.2, 1.2, 4),
+                   rng.uniform(-1.2, 1.2, 4), rng.uniform(0.01, 1.5, 4)], axis=1)
+    p = Problem(f"four_quadrant_seed{seed}", n, n, 0.0, 0.0, 1.0, 1.0, (1, 1, 1, 1),
+                _piecewise(st, 0.5, 0.5), t_end, cfl=cfl, options={"tsw": 1, "limiter": 1})
+    p.states = st
+    return p
+
+
+def double_rarefaction(n=64, t_end=0.25, cfl=0.3, rho=1.0, p=0.4, speed=2.0):
+    """rho = 1, p = 0.4, u = -2 for x < 0.5 and +2 for x > 0.5 (u = 0 on the
+    line), v = 0; outflow at x = 0, 1 and solid walls at y = 0, 1."""
+    st = [(rho, -speed, 0.0, p), (rho, speed, 0.0, p), (rho, -speed, 0.0, p), (rho, speed, 0.0, p)]
+    return Problem("double_rarefaction", n, n, 0.0, 0.0, 1.0, 1.0, (1, 1, 2, 2),
+                   _piecewise(st, 0.5, -1.0), t_end, cfl=cfl, options={"limiter": 1})
+
+
+def kelvin_helmholtz(n=64, t_end=1.0, cfl=0.3):
+    """Sec. 4.2: shear layer on [-1/2,1/2]^2, periodic; nodes on |y| = 1/4
+    take the mean of the two layers."""
+
+    def f(x, y):
+        x, y = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
+        inner = np.where(np.abs(y) < 0.25, 1.0, np.where(np.abs(y) == 0.25, 0.5, 0.0))
+        rho = 1.0 + inner
+        u = 0.5 - inner
+        v = 1e-2 * np.sin(2 * np.pi * x)
+        return rho, u, v, 2.5 + 0.0 * x
+
+    return Problem("kelvin_helmholtz", n, n, -0.5, -0.5, 1.0, 1.0, (0, 0, 0, 0), f, t_end,
+                   cfl=cfl, options={"limiter": 1})
+
+
+def fourier_smooth(nx=32, ny=32, seed=1, amp=0.15, lx=1.0, ly=1.0, modes=3):
+    """Smooth periodic field: every primitive variable is a background value
+    plus a few seeded Fourier modes (used for parity tests)."""
+    rng = np.random.default_rng(seed)
+    base = np.array([1.0, 0.3, -0.2, 1.0])
+    coef = rng.normal(size=(4, modes, modes, 2)) * amp / modes
+
+    def f(x, y):
+        out = []
+        for k in range(4):
+            s = base[k] + 0.0 * (x + y)
+            for a in range(modes):
+                for b in range(modes):
+                    ph = 2 * np.pi * (a * x / lx + b * y / ly)
+                    s = s + coef[k, a, b, 0] * np.cos(ph) + coef[k, a, b, 1] * np.sin(ph)
+            out.append(s)
+        return tuple(out)
+
+    return Problem(f"fourier_smooth_seed{seed}", nx, ny, 0.0, 0.0, lx, ly, (0, 0, 0, 0), f, 1.0)
+
+
+def cell_mean_exact(prob: Problem, field: Field):
+    """Cell averages of the conserved variables of ``field`` (5x5 Gauss)."""
+    return discretise(prob, field)[0]
