@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Throughput of the fully discrete third-order Active Flux step on GB300.
+
+One benchmark step = one time step of the whole hot path (ghost fill, cell
+prep, point values at t^{n+1/2} and t^{n+1} with the correction term and the
+bound-preserving limiter, Simpson fluxes and the finite-volume update, plus
+the max-speed reduction that sets dt) over the 8192 x 8192 isentropic-vortex
+grid on the periodic box [0,10]^2, centre and strength drawn from seed 2508.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (launched by torch.distributed.run)
+every rank advances its own independent grid (replicas, weak scaling).  The
+reference arm (--impl reference) times the FP64 CPU oracle on the host cores
+on a bounded window of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell updates/s (FP32 plain vs MLP-surrogate+fallback) at stated L1 error vs FP64 oracle"
+UNIT = "cell updates/s"
+SEED = 2508
+# FP32 operations of the point-value stage per cell update (one vertex and two
+# edge midpoints, two time levels; subsonic linearisation: 4 arcs per vertex,
+# 2 per edge), counted from the kernel source; see the design doc.
+PV_FLOP_PER_CELL = 12900
+# algorithmic HBM bytes of the flux/update kernel per cell: 3 levels x 3 node
+# arrays read (144 B), averages hi/lo read and written (64 B)
+FLUX_BYTES_PER_CELL = 208
+
+
+# ------------------------------------------------------------ distributed
+def dist_setup(backend=None):
+    """(rank, world, local_rank); initialises torch.distributed when WORLD_SIZE > 1."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def reduce_max(x, world, device=None):
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(cells_per_rank, steps, world, max_seconds):
+    """Whole-job cell updates per second: all ranks' work over the slowest rank's time."""
+    return cells_per_rank * steps * world / max_seconds
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=None):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu is not None:
+            cmd += ["-i", str(self.gpu)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ helpers
+def workload(n, rank=0):
+    from paper_2508_06273_gb300 import workloads as W
+
+    return W.shu_vortex_seeded(n, seed=SEED + rank)
+
+
+def workload_name(n):
+    return (f"isentropic vortex, periodic [0,10]^2, {n}x{n} cells, centre and strength "
+            f"in [3,6] from seed {SEED}, CFL 0.3, one time step per bench step")
+
+
+class OracleWindow:
+    """FP64 oracle on a window of the workload around the vortex (outflow
+    ghosts at its edge), on all host cores; one call = one time step
+    (max-speed reduction + step)."""
+
+    def __init__(self, n, window=128):
+        import numpy as np
+
+        import oracle
+        from paper_2508_06273_gb300 import workloads as W
+
+        prob = workload(n)
+        xc, yc = np.random.default_rng(SEED).uniform(3.0, 6.0, size=2)
+        i0 = max(0, min(n - window, int(xc / prob.dx) - window // 2))
+        j0 = max(0, min(n - window, int(yc / prob.dy) - window // 2))
+        self.sub = W.subproblem(prob, i0, j0, window, window)
+        self.cells = window * window
+        self.window = window
+        self.o = oracle.Oracle(self.sub.nx, self.sub.ny, self.sub.dx, self.sub.dy, self.sub.gamma,
+                               self.sub.bc)
+        self.threads = len(os.sched_getaffinity(0))
+        self.o.set_option(oracle.OPT_THREADS, self.threads)
+        self.o.set_state(*W.to_f32(W.discretise(self.sub)))
+
+    def step(self):
+        self.o.step(self.sub.cfl * self.sub.dx / self.o.max_speed())
+
+    def describe(self, n, steps):
+        return (f"FP64 oracle on a {self.window}x{self.window}-cell window of the {n}^2 workload "
+                f"around the vortex, {steps} steps (max-speed reduction + step), "
+                f"{self.threads} OpenMP threads")
+
+
+def cpu_sample(n, min_seconds=10.0, window=128, max_steps=200):
+    """(cell updates/s, threads, description, seconds) of the oracle window."""
+    w = OracleWindow(n, window)
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        w.step()
+        steps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    el = time.perf_counter() - t0
+    return w.cells * steps / el, w.threads, w.describe(n, steps), el
+
+
+def fp32_peak_tflops(sm_count, mhz):
+    """FP32 (non-tensor) peak: SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------ arms
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2508_06273_gb300 import af
+    from paper_2508_06273_gb300 import workloads as W
+
+    n = args.n
+    prob = workload(n, rank)
+    cells = n * n
+    dev = W.discretise_torch(prob, "cuda")
+    s = af.Solver(n, n, prob.dx, prob.dy, prob.gamma, prob.bc)
+    s.set_state(*dev)
+    pinned = None
+    if args.e2e_steps > 0:
+        pinned = [torch.empty(a.shape, dtype=torch.float32, pin_memory=True) for a in dev]
+        for p, a in zip(pinned, dev):
+            p.copy_(a)
+    del dev
+    torch.cuda.empty_cache()
+
+    def one_step():
+        dt = prob.cfl * prob.dx / s.max_speed()
+        s.step(dt)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if s.status() != 0:
+        raise SystemExit("warm-up steps raised device status bits")
+    s.set_option("profile", 1)
+    s.profile(reset=True)
+    clocks = ClockSampler(local).start() if rank == 0 else None
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if clocks else None
+    status = s.status()
+    stage_ms, launches = s.profile()
+    s.set_option("profile", 0)
+    max_s = reduce_max(ms / 1e3, world, device="cuda")
+    value = aggregate_value(cells, args.steps, world, max_s)
+
+    # end to end through the C ABI with host buffers: H2D of the step's inputs
+    # from pinned memory, the step, D2H of its result, every step
+    e2e = None
+    if pinned is not None:
+        h2d = sum(p.numel() * 4 for p in pinned)
+        outs = [np.empty(p.shape, dtype=np.float32) for p in pinned]
+        host_in = [p.numpy() for p in pinned]
+        s.set_state(*host_in)
+        one_step()
+        s.get_state_host(outs)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            s.set_state(*host_in)
+            one_step()
+            s.get_state_host(outs)
+        torch.cuda.synchronize()
+        el = reduce_max(time.perf_counter() - t0, world, device="cuda")
+        e2e = {"value": aggregate_value(cells, args.e2e_steps, world, el), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d, "steps": args.e2e_steps}
+    s.close()
+
+    if rank != 0:
+        return
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    pv_ms = stage_ms["pointvalue"] / args.steps
+    pv_tflops = PV_FLOP_PER_CELL * cells / (pv_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops(sms, max_mhz)
+    flux_ms = stage_ms["flux"] / args.steps
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm = float(peaks["hbm_gbs"])
+        hbm_src = "measured"
+    except (OSError, KeyError, ValueError):
+        hbm, hbm_src = 6800.0, "fallback"
+    flux_gbs = FLUX_BYTES_PER_CELL * cells / (flux_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(n), "cells": cells, "grid": [n, n],
+                   "method": "Alg. 1 step, averaged linearisation, correction on, Alg. 3 limiter on",
+                   "l2": "inputs larger than L2 (about 15 GB of state per grid)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "node_updates_per_s": 3 * value,
+        "status": status,
+        "roofline": {"bound": "alu", "kernel": "point-value stage (3 launches: vertices, x-edges, y-edges)",
+                     "achieved": pv_tflops, "peak": peak, "unit": "TFLOP/s", "frac": pv_tflops / peak,
+                     "traffic": None, "flop_per_cell": PV_FLOP_PER_CELL,
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (max clock)",
+                     "frac_at_median_clock": (pv_tflops / fp32_peak_tflops(sms, clk["sm_mhz"])
+                                              if clk else None),
+                     "ms_per_launch": pv_ms},
+        "roofline_flux": {"bound": "hbm", "kernel": "Simpson flux + FP64 update", "achieved": flux_gbs,
+                          "peak": hbm, "unit": "GB/s", "frac": flux_gbs / hbm, "peak_source": hbm_src,
+                          "bytes_per_cell": FLUX_BYTES_PER_CELL, "ms_per_launch": flux_ms},
+        "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+        "gpu_launches": int(sum(launches.values())),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu:
+        v, threads, desc, _ = cpu_sample(n, min_seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup()
+    if rank != 0:
+        return
+    n = args.n
+    w = OracleWindow(n)
+    for _ in range(args.warmup):
+        w.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        w.step()
+    el = time.perf_counter() - t0
+    value = w.cells * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name(n), "cells": n * n, "grid": [n, n]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": w.threads, "kind": "oracle",
+                         "sample": w.describe(n, args.steps) + ", one step per bench step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=8192, help="cells per side (default: 8192)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

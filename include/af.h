@@ -1,0 +1,139 @@
+/*
+ * af.h -- C ABI of the GB300 (sm_103a) library for the fully discrete,
+ * third-order Active Flux method for the 2D Euler equations
+ * (E. Chudzik, C. Helzel, A. Porfetye, arXiv 2508.06273).
+ *
+ * One handle (af_ctx) holds one Cartesian grid of nx x ny cells, its state
+ * in device memory (FP32 storage, cell averages with an FP32 low word), and
+ * a CUDA stream.  Every numerical step runs in the library's CUDA kernels.
+ *
+ * Degrees of freedom (Sec. 2 of the paper, "Let (x_{i-1/2}, x_{i+1/2}) x
+ * (y_{j-1/2}, y_{j+1/2}) be the grid cell (i,j)..."):
+ *   cell averages of the conserved variables (rho, rho u, rho v, E),
+ *   point values of the primitive variables (rho, u, v, p) at the vertices
+ *   (x_{i-1/2}, y_{j-1/2}), the x-edge midpoints (x_{i-1/2}, y_j) and the
+ *   y-edge midpoints (x_i, y_{j-1/2}).
+ * External layout: variable-major, row-major FP32 arrays
+ *   avg [4][ny][nx], vtx [4][ny+1][nx+1], xe [4][ny][nx+1], ye [4][ny+1][nx].
+ * On a periodic axis the last node line duplicates the first one; the
+ * library checks this on input and keeps it on output.
+ * Ideal gas, E = p/(gamma-1) + rho (u^2+v^2)/2 (Sec. 2, eq. (2.2)).
+ *
+ * Errors: functions return 0 (AF_OK) or a negative AF_ERR_* code;
+ * af_last_error() gives a message for the calling thread.  af_step and
+ * af_run are asynchronous; conditions detected on the device accumulate in
+ * a status word that af_status() returns (AF_ST_* bits).
+ * Threading: one handle must not be used by two host threads at once.
+ */
+#ifndef AF_H
+#define AF_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct af_ctx af_ctx;
+
+/* boundary kinds (Sec. 4.3): periodic; outflow (piecewise-constant, mirror
+ * copy into ghost cells); solid wall (mirror copy with negated normal
+ * velocity).  bc = xlo | xhi << 8 | ylo << 16 | yhi << 24; periodic must
+ * be given on both sides of an axis. */
+enum { AF_BC_PERIODIC = 0, AF_BC_TRANSMISSIVE = 1, AF_BC_REFLECTING = 2 };
+
+enum {
+  AF_OK = 0,
+  AF_ERR_ARG = -1,   /* bad argument (size, pointer kind, option, periodic duplicate) */
+  AF_ERR_CUDA = -2,  /* a CUDA runtime call failed */
+  AF_ERR_ALLOC = -3, /* device or host allocation failed */
+  AF_ERR_STATE = -4  /* no state has been set */
+};
+
+/* device status bits returned by af_status */
+enum {
+  AF_ST_CFL = 1,        /* a Mach-cone base left the node's cell block: dt too large */
+  AF_ST_AVG_NONPOS = 2, /* a cell average with rho <= 0 or p <= 0 after the update */
+  AF_ST_NONFINITE = 4,  /* a non-finite point value or cell average */
+  AF_ST_KEPT = 8        /* Alg. 3's Lax-Friedrichs value was not admissible in FP32;
+                           the node kept its old value */
+};
+
+/* option keys for af_set_option */
+enum {
+  AF_OPT_LIN_MODE = 0,   /* half-step linearisation: 0 averaged Ubar (eq. (Un+1/2), default),
+                            1 node value (eq. (1stStep)), 2 Algorithm 1 (EG2 over dt/4) */
+  AF_OPT_TSW = 1,        /* 1: Algorithm 2 switch for the full step near transonic shocks */
+  AF_OPT_LIMITER = 2,    /* 1 (default): Algorithm 3 bound-preserving point values */
+  AF_OPT_CORRECTION = 3, /* 1 (default): Corollary 1 correction term */
+  AF_OPT_FORCE_LO = 4,   /* test hook, single steps only: 1 EG1 at every node, 2 LF at every node */
+  AF_OPT_PROFILE = 5     /* 1: time every stage of af_step with CUDA events (see af_profile) */
+};
+
+/* stages reported by af_profile */
+enum { AF_STAGE_PREP = 0, AF_STAGE_POINTVALUE = 1, AF_STAGE_FLUX = 2, AF_STAGE_REDUCE = 3 };
+
+/* Create a grid of nx x ny cells of size dx x dy (nx, ny >= 2).  Allocates
+ * the device state on the current device.  NULL on error (af_last_error). */
+af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t bc);
+/* Free everything the handle owns.  NULL-safe. */
+void af_destroy(af_ctx *h);
+/* Message of the last error on this host thread (static storage). */
+const char *af_last_error(void);
+
+/* Stream all later work of the handle is enqueued on (cudaStream_t; NULL =
+ * the handle's own stream). */
+int af_set_stream(af_ctx *h, void *stream);
+int af_set_option(af_ctx *h, int key, double value);
+int af_get_option(af_ctx *h, int key, double *value);
+
+/* Copy a state from caller-owned DEVICE memory (FP32, layout above) into
+ * the handle; the low words of the averages are cleared.  Ordered after
+ * prior work on `stream` (may be NULL) and the handle's stream.  Returns
+ * AF_ERR_ARG for host pointers or non-matching periodic duplicates. */
+int af_set_state(af_ctx *h, const float *avg, const float *vtx, const float *xe,
+                 const float *ye, void *stream);
+/* Same from HOST memory (pageable or pinned); synchronous. */
+int af_set_state_host(af_ctx *h, const float *avg, const float *vtx, const float *xe,
+                      const float *ye);
+/* Copy the current state into caller-owned DEVICE memory (any pointer may
+ * be NULL to skip that array).  Ordered before later work on `stream`. */
+int af_get_state(af_ctx *h, float *avg, float *vtx, float *xe, float *ye, void *stream);
+/* Same into HOST memory; synchronous. */
+int af_get_state_host(af_ctx *h, float *avg, float *vtx, float *xe, float *ye);
+/* FP32 low words of the cell averages [4][ny][nx] (device / host memory). */
+int af_get_avg_lo(af_ctx *h, float *avg_lo, void *stream);
+int af_set_avg_lo(af_ctx *h, const float *avg_lo, void *stream);
+/* Point values at t^{n+1/2} computed by the last step (device memory). */
+int af_get_half(af_ctx *h, float *vtx, float *xe, float *ye, void *stream);
+
+/* One time step of size dt (Alg. 1 with the options above): ghost fill,
+ * cell prep, point values at t^{n+1/2} and t^{n+1} by EG2 plus the
+ * correction term with Alg. 3 limiting, Simpson fluxes and the
+ * finite-volume update (eq. (2dfvm)).  Asynchronous. */
+int af_step(af_ctx *h, double dt);
+/* nsteps steps of fixed size dt, enqueued back to back.  Asynchronous. */
+int af_run(af_ctx *h, int nsteps, double dt);
+
+/* Synchronise the handle's stream; return the accumulated AF_ST_* bits
+ * (>= 0) and clear them, or a negative AF_ERR_* code. */
+int af_status(af_ctx *h);
+/* Counters of the last step (synchronises): EG1 fallbacks, LF fallbacks,
+ * kept values, vertices flagged by Alg. 2. */
+int af_counters(af_ctx *h, int64_t out[4]);
+/* dx dy * sum of the cell averages per conserved variable, FP64 with the
+ * low words, fixed-order (deterministic) reduction; synchronises. */
+int af_conserved_totals(af_ctx *h, double out[4]);
+/* max over cell averages and owned point values of max(|u|,|v|) + c, the
+ * speed in the paper's CFL number (Sec. 2); synchronises. */
+int af_max_speed(af_ctx *h, float *out);
+
+/* Per-stage device time in ms (ghost fill + cell prep, point values, flux
+ * update, reductions), accumulated with CUDA events on the handle's stream
+ * while AF_OPT_PROFILE is 1, and the number of kernels each stage launched
+ * (always counted).  Synchronises; reset != 0 clears both afterwards. */
+int af_profile(af_ctx *h, double ms[4], int64_t launches[4], int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

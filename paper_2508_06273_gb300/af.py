@@ -1,0 +1,200 @@
+"""Thin ctypes binding of the C ABI in include/af.h (argument marshalling only).
+
+Every numerical step runs in the CUDA kernels of libaf.so; this module only
+passes pointers, sizes and streams.  PyTorch provides device memory and the
+current CUDA stream.  The library must have been built
+(``__graft_entry__.build()``); if it is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libaf.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING = 0, 1, 2
+OPT = {"lin_mode": 0, "tsw": 1, "limiter": 2, "correction": 3, "force_lo": 4, "profile": 5}
+STAGES = ("prep", "pointvalue", "flux", "reduce")
+ST_CFL, ST_AVG_NONPOS, ST_NONFINITE, ST_KEPT = 1, 2, 4, 8
+EXPORTS = [
+    "af_create", "af_destroy", "af_last_error", "af_set_stream", "af_set_option",
+    "af_get_option", "af_set_state", "af_set_state_host", "af_get_state", "af_get_state_host",
+    "af_get_avg_lo", "af_set_avg_lo", "af_get_half", "af_step", "af_run", "af_status",
+    "af_counters", "af_conserved_totals", "af_max_speed", "af_profile",
+]
+
+
+class AFError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libaf.so (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            if not os.path.exists(LIB_PATH):
+                raise AFError(f"{LIB_PATH} is missing: build the CUDA library first "
+                              "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = C.CDLL(LIB_PATH)
+            vp, i, d, fp = C.c_void_p, C.c_int, C.c_double, C.c_void_p
+            sig = {
+                "af_create": (vp, [i, i, d, d, d, C.c_uint32]),
+                "af_destroy": (None, [vp]),
+                "af_last_error": (C.c_char_p, []),
+                "af_set_stream": (i, [vp, vp]),
+                "af_set_option": (i, [vp, i, d]),
+                "af_get_option": (i, [vp, i, C.POINTER(C.c_double)]),
+                "af_set_state": (i, [vp, fp, fp, fp, fp, vp]),
+                "af_set_state_host": (i, [vp, fp, fp, fp, fp]),
+                "af_get_state": (i, [vp, fp, fp, fp, fp, vp]),
+                "af_get_state_host": (i, [vp, fp, fp, fp, fp]),
+                "af_get_avg_lo": (i, [vp, fp, vp]),
+                "af_set_avg_lo": (i, [vp, fp, vp]),
+                "af_get_half": (i, [vp, fp, fp, fp, vp]),
+                "af_step": (i, [vp, d]),
+                "af_run": (i, [vp, i, d]),
+                "af_status": (i, [vp]),
+                "af_counters": (i, [vp, C.POINTER(C.c_int64)]),
+                "af_conserved_totals": (i, [vp, C.POINTER(C.c_double)]),
+                "af_max_speed": (i, [vp, C.POINTER(C.c_float)]),
+                "af_profile": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def _check(rc):
+    if rc < 0:
+        raise AFError(f"af error {rc}: {lib().af_last_error().decode()}")
+    return rc
+
+
+def bc_code(bc):
+    if isinstance(bc, int):
+        return bc
+    a, b, c, d = bc
+    return a | (b << 8) | (c << 16) | (d << 24)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One grid on one GPU (an af_ctx).  Work is enqueued on ``stream``
+    (default: PyTorch's current stream at construction)."""
+
+    def __init__(self, nx, ny, dx, dy, gamma=1.4, bc=(0, 0, 0, 0), stream=None, options=None):
+        import torch
+
+        self.torch = torch
+        self.L = lib()
+        self.nx, self.ny, self.dx, self.dy, self.gamma = nx, ny, dx, dy, gamma
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.h = self.L.af_create(nx, ny, dx, dy, gamma, bc_code(bc))
+        if not self.h:
+            raise AFError(self.L.af_last_error().decode())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        _check(self.L.af_set_stream(self.h, C.c_void_p(self.stream.cuda_stream)))
+        for k, v in (options or {}).items():
+            self.set_option(k, v)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.af_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def shapes(self):
+        nx, ny = self.nx, self.ny
+        return (4, ny, nx), (4, ny + 1, nx + 1), (4, ny, nx + 1), (4, ny + 1, nx)
+
+    def _s(self):
+        return C.c_void_p(self.stream.cuda_stream)
+
+    def set_option(self, key, value):
+        _check(self.L.af_set_option(self.h, OPT[key] if isinstance(key, str) else key, float(value)))
+
+    def set_state(self, avg, vtx, xe, ye):
+        """State from CUDA float32 tensors (device) or numpy arrays (host)."""
+        arrs = (avg, vtx, xe, ye)
+        if all(isinstance(a, np.ndarray) for a in arrs):
+            hs = [np.ascontiguousarray(a, dtype=np.float32) for a in arrs]
+            for a, s in zip(hs, self.shapes()):
+                if a.shape != s:
+                    raise ValueError(f"shape {a.shape} != {s}")
+            _check(self.L.af_set_state_host(self.h, *[C.c_void_p(a.ctypes.data) for a in hs]))
+            return
+        ts = []
+        for a, s in zip(arrs, self.shapes()):
+            if tuple(a.shape) != s or a.dtype != self.torch.float32 or not a.is_cuda:
+                raise ValueError(f"need CUDA float32 tensors of shape {s}")
+            ts.append(a.contiguous())
+        _check(self.L.af_set_state(self.h, *[_ptr(t) for t in ts], self._s()))
+
+    def get_state(self):
+        """Current state as CUDA float32 tensors."""
+        out = [self.torch.empty(s, dtype=self.torch.float32, device=self.device) for s in self.shapes()]
+        _check(self.L.af_get_state(self.h, *[_ptr(t) for t in out], self._s()))
+        return tuple(out)
+
+    def get_state_host(self, out=None):
+        """Current state copied into host numpy arrays (optionally pre-allocated)."""
+        out = out or [np.empty(s, dtype=np.float32) for s in self.shapes()]
+        _check(self.L.af_get_state_host(self.h, *[C.c_void_p(a.ctypes.data) for a in out]))
+        return tuple(out)
+
+    def get_avg_lo(self):
+        t = self.torch.empty(self.shapes()[0], dtype=self.torch.float32, device=self.device)
+        _check(self.L.af_get_avg_lo(self.h, _ptr(t), self._s()))
+        return t
+
+    def set_avg_lo(self, t):
+        _check(self.L.af_set_avg_lo(self.h, _ptr(t.contiguous()), self._s()))
+
+    def get_half(self):
+        out = [self.torch.empty(s, dtype=self.torch.float32, device=self.device) for s in self.shapes()[1:]]
+        _check(self.L.af_get_half(self.h, *[_ptr(t) for t in out], self._s()))
+        return tuple(out)
+
+    def step(self, dt):
+        _check(self.L.af_step(self.h, float(dt)))
+
+    def run(self, nsteps, dt):
+        _check(self.L.af_run(self.h, int(nsteps), float(dt)))
+
+    def status(self):
+        return _check(self.L.af_status(self.h))
+
+    def counters(self):
+        out = (C.c_int64 * 4)()
+        _check(self.L.af_counters(self.h, out))
+        return list(out)
+
+    def totals(self):
+        out = (C.c_double * 4)()
+        _check(self.L.af_conserved_totals(self.h, out))
+        return np.array(list(out))
+
+    def profile(self, reset=False):
+        """(ms per stage, kernel launches per stage) since the last reset."""
+        ms, n = (C.c_double * 4)(), (C.c_int64 * 4)()
+        _check(self.L.af_profile(self.h, ms, n, 1 if reset else 0))
+        return dict(zip(STAGES, list(ms))), dict(zip(STAGES, list(n)))
+
+    def max_speed(self):
+        out = C.c_float()
+        _check(self.L.af_max_speed(self.h, C.byref(out)))
+        return out.value

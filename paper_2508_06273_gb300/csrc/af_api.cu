@@ -1,0 +1,566 @@
+// af_api.cu -- the C ABI of include/af.h: handle, device state, transfers,
+// step sequencing and reductions.  All numerical work is in the kernels of
+// af_misc.cu, af_pointvalue.cu and af_flux.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/af.h"
+#include "af_common.cuh"
+#include "af_kernels.h"
+
+using namespace af;
+
+static thread_local char g_err[512] = "";
+
+static int fail(int code, const char *fmt, const char *detail = nullptr) {
+  std::snprintf(g_err, sizeof(g_err), fmt, detail ? detail : "");
+  return code;
+}
+static int cuda_fail(cudaError_t e, const char *where) {
+  std::snprintf(g_err, sizeof(g_err), "%s: %s", where, cudaGetErrorString(e));
+  return AF_ERR_CUDA;
+}
+#define CK(call, where)                         \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+struct af_ctx {
+  Grid g;
+  double dx, dy;
+  Options opt;
+  int device;
+  cudaStream_t own_stream, stream;
+  float *base;  // all planes in one allocation
+  float *hi, *lo, *uc, *ub;
+  NodeSet lev[3];  // 0: t^n, 1: t^{n+1/2}, 2: t^{n+1}
+  // small device buffers
+  void *small;
+  int *d_status, *d_bad;
+  unsigned *d_speed;
+  unsigned long long *d_counters;
+  double *d_partials, *d_totals;
+  float *staging;  // host-transfer staging (lazily allocated)
+  size_t staging_floats;
+  bool has_state;
+  cudaEvent_t ev_in, ev_out;
+  // profiling: events around each stage of the last step, accumulated times
+  int profile;
+  cudaEvent_t ev_stage[5];
+  bool stage_pending;
+  double stage_ms[4];
+  long long launches[4];
+};
+
+namespace {
+
+struct DeviceGuard {
+  int old = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&old) == cudaSuccess && old != dev) cudaSetDevice(dev);
+    else old = -1;
+  }
+  ~DeviceGuard() {
+    if (old >= 0) cudaSetDevice(old);
+  }
+};
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// make the handle's stream wait for `user`, or the reverse
+void order_after(af_ctx *h, cudaStream_t user) {
+  if (!user || user == h->stream) return;
+  cudaEventRecord(h->ev_in, user);
+  cudaStreamWaitEvent(h->stream, h->ev_in, 0);
+}
+void order_before(af_ctx *h, cudaStream_t user) {
+  if (!user || user == h->stream) return;
+  cudaEventRecord(h->ev_out, h->stream);
+  cudaStreamWaitEvent(user, h->ev_out, 0);
+}
+
+// external array extents of the four state arrays
+void extents(const af_ctx *h, int which, int &ni, int &nj) {
+  const int nx = h->g.nx, ny = h->g.ny;
+  switch (which) {
+    case 0: ni = nx; nj = ny; break;          // averages
+    case 1: ni = nx + 1; nj = ny + 1; break;  // vertices
+    case 2: ni = nx + 1; nj = ny; break;      // x-edges
+    default: ni = nx; nj = ny + 1; break;     // y-edges
+  }
+}
+
+int ensure_staging(af_ctx *h) {
+  size_t need = (size_t)NV * (h->g.nx + 1) * (h->g.ny + 1);
+  if (h->staging && h->staging_floats >= need) return AF_OK;
+  if (h->staging) cudaFree(h->staging);
+  h->staging = nullptr;
+  CK(cudaMalloc(&h->staging, need * sizeof(float)), "cudaMalloc(staging)");
+  h->staging_floats = need;
+  return AF_OK;
+}
+
+// device external arrays -> padded planes (after the periodic-duplicate check)
+int load_state(af_ctx *h, const float *const src[4]) {
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(h->d_bad, 0, sizeof(int), s), "memset");
+  for (int w = 1; w < 4; w++) {
+    int ni, nj;
+    extents(h, w, ni, nj);
+    const int dup_x = h->g.per_x && (w == 1 || w == 2), dup_y = h->g.per_y && (w == 1 || w == 3);
+    if (dup_x || dup_y) CK(launch_check_dup(src[w], ni, nj, dup_x, dup_y, h->d_bad, s), "check_dup");
+  }
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, s), "memcpy");
+  CK(cudaStreamSynchronize(s), "sync");
+  if (bad) return fail(AF_ERR_ARG, "periodic state: the duplicated last node line differs from the first%s");
+  float *dst[4] = {h->hi, h->lev[0].k[VTX], h->lev[0].k[XE], h->lev[0].k[YE]};
+  for (int w = 0; w < 4; w++) {
+    int ni, nj;
+    extents(h, w, ni, nj);
+    CK(launch_pack(h->g, src[w], dst[w], ni, nj, true, s), "pack");
+  }
+  CK(cudaMemsetAsync(h->lo, 0, sizeof(float) * NV * h->g.plane, s), "memset lo");
+  CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), s), "memset status");
+  h->has_state = true;
+  return AF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *af_last_error(void) { return g_err; }
+
+af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t bc) {
+  if (nx < 2 || ny < 2 || !(dx > 0) || !(dy > 0) || !(gamma > 1.0) || !std::isfinite(dx) ||
+      !std::isfinite(dy)) {
+    fail(AF_ERR_ARG, "af_create: need nx, ny >= 2, dx, dy > 0 and gamma > 1%s");
+    return nullptr;
+  }
+  int b[4];
+  for (int k = 0; k < 4; k++) {
+    b[k] = (int)((bc >> (8 * k)) & 0xffu);
+    if (b[k] > AF_BC_REFLECTING) {
+      fail(AF_ERR_ARG, "af_create: unknown boundary kind%s");
+      return nullptr;
+    }
+  }
+  if ((b[0] == AF_BC_PERIODIC) != (b[1] == AF_BC_PERIODIC) ||
+      (b[2] == AF_BC_PERIODIC) != (b[3] == AF_BC_PERIODIC)) {
+    fail(AF_ERR_ARG, "af_create: periodic must be set on both sides of an axis%s");
+    return nullptr;
+  }
+  if ((long long)nx * ny > (1LL << 31)) {
+    fail(AF_ERR_ARG, "af_create: grid too large%s");
+    return nullptr;
+  }
+  af_ctx *h = new (std::nothrow) af_ctx();
+  if (!h) {
+    fail(AF_ERR_ALLOC, "af_create: out of host memory%s");
+    return nullptr;
+  }
+  Grid &g = h->g;
+  g.nx = nx;
+  g.ny = ny;
+  g.P = ((nx + OX + G + 1) + 31) / 32 * 32;
+  g.H = ny + OY + G + 1;
+  g.plane = (long long)g.P * g.H;
+  g.per_x = b[0] == AF_BC_PERIODIC;
+  g.per_y = b[2] == AF_BC_PERIODIC;
+  g.nxv = g.per_x ? nx : nx + 1;
+  g.nyv = g.per_y ? ny : ny + 1;
+  for (int k = 0; k < 4; k++) g.bc[k] = b[k];
+  g.dx = (float)dx;
+  g.dy = (float)dy;
+  g.idx = (float)(1.0 / dx);
+  g.idy = (float)(1.0 / dy);
+  g.gamma = (float)gamma;
+  h->dx = dx;
+  h->dy = dy;
+  cudaGetDevice(&h->device);
+  // hi, lo, U_c, Ubar and 3 levels x 3 node kinds: 13 arrays of 4 planes
+  const size_t state_bytes = 13 * (size_t)NV * (size_t)g.plane * sizeof(float);
+  cudaError_t e = cudaMalloc(&h->base, state_bytes);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "af_create: cudaMalloc(state)");
+    delete h;
+    return nullptr;
+  }
+  float *p = h->base;
+  auto take = [&]() {
+    float *q = p;
+    p += (size_t)NV * g.plane;
+    return q;
+  };
+  h->hi = take();
+  h->lo = take();
+  h->uc = take();
+  h->ub = take();
+  for (int l = 0; l < 3; l++)
+    for (int k = 0; k < 3; k++) h->lev[l].k[k] = take();
+  const size_t small = 64 + 64 + 64 + 64 + sizeof(double) * (TOTALS_BLOCKS * NV + NV);
+  e = cudaMalloc(&h->small, small);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+  for (int k = 0; k < 5 && e == cudaSuccess; k++) e = cudaEventCreate(&h->ev_stage[k]);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "af_create");
+    if (h->small) cudaFree(h->small);
+    cudaFree(h->base);
+    delete h;
+    return nullptr;
+  }
+  char *sp = (char *)h->small;
+  h->d_status = (int *)sp;
+  h->d_bad = (int *)(sp + 64);
+  h->d_speed = (unsigned *)(sp + 128);
+  h->d_counters = (unsigned long long *)(sp + 192);
+  h->d_totals = (double *)(sp + 256);
+  h->d_partials = h->d_totals + NV;
+  h->stream = h->own_stream;
+  // the whole state starts zeroed, ghosts included
+  cudaMemsetAsync(h->base, 0, state_bytes, h->stream);
+  cudaMemsetAsync(h->small, 0, small, h->stream);
+  cudaStreamSynchronize(h->stream);
+  return h;
+}
+
+void af_destroy(af_ctx *h) {
+  if (!h) return;
+  DeviceGuard dg(h->device);
+  cudaStreamSynchronize(h->stream);
+  if (h->staging) cudaFree(h->staging);
+  cudaFree(h->small);
+  cudaFree(h->base);
+  cudaEventDestroy(h->ev_in);
+  cudaEventDestroy(h->ev_out);
+  for (int k = 0; k < 5; k++) cudaEventDestroy(h->ev_stage[k]);
+  cudaStreamDestroy(h->own_stream);
+  delete h;
+}
+
+int af_set_stream(af_ctx *h, void *stream) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  cudaStream_t s = stream ? (cudaStream_t)stream : h->own_stream;
+  if (s != h->stream) {
+    DeviceGuard dg(h->device);
+    order_after(h, s);  // new stream starts after everything queued so far
+    cudaStream_t old = h->stream;
+    h->stream = s;
+    order_after(h, old);
+  }
+  return AF_OK;
+}
+
+int af_set_option(af_ctx *h, int key, double value) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  const int iv = (int)value;
+  switch (key) {
+    case AF_OPT_LIN_MODE:
+      if (iv < 0 || iv > 2) return fail(AF_ERR_ARG, "lin_mode must be 0, 1 or 2%s");
+      h->opt.lin_mode = iv;
+      return AF_OK;
+    case AF_OPT_TSW: h->opt.tsw = iv != 0; return AF_OK;
+    case AF_OPT_LIMITER: h->opt.limiter = iv != 0; return AF_OK;
+    case AF_OPT_CORRECTION: h->opt.correction = iv != 0; return AF_OK;
+    case AF_OPT_FORCE_LO:
+      if (iv < 0 || iv > 2) return fail(AF_ERR_ARG, "force_lo must be 0, 1 or 2%s");
+      h->opt.force_lo = iv;
+      return AF_OK;
+    case AF_OPT_PROFILE: h->profile = iv != 0; return AF_OK;
+    default: return fail(AF_ERR_ARG, "unknown option%s");
+  }
+}
+
+int af_get_option(af_ctx *h, int key, double *value) {
+  if (!h || !value) return fail(AF_ERR_ARG, "null argument%s");
+  switch (key) {
+    case AF_OPT_LIN_MODE: *value = h->opt.lin_mode; return AF_OK;
+    case AF_OPT_TSW: *value = h->opt.tsw; return AF_OK;
+    case AF_OPT_LIMITER: *value = h->opt.limiter; return AF_OK;
+    case AF_OPT_CORRECTION: *value = h->opt.correction; return AF_OK;
+    case AF_OPT_FORCE_LO: *value = h->opt.force_lo; return AF_OK;
+    case AF_OPT_PROFILE: *value = h->profile; return AF_OK;
+    default: return fail(AF_ERR_ARG, "unknown option%s");
+  }
+}
+
+int af_set_state(af_ctx *h, const float *avg, const float *vtx, const float *xe, const float *ye,
+                 void *stream) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  DeviceGuard dg(h->device);
+  const float *src[4] = {avg, vtx, xe, ye};
+  for (int w = 0; w < 4; w++)
+    if (!is_device_ptr(src[w])) return fail(AF_ERR_ARG, "af_set_state: arrays must be device memory%s");
+  order_after(h, (cudaStream_t)stream);
+  int rc = load_state(h, src);
+  order_before(h, (cudaStream_t)stream);
+  return rc;
+}
+
+int af_set_state_host(af_ctx *h, const float *avg, const float *vtx, const float *xe,
+                      const float *ye) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (!avg || !vtx || !xe || !ye) return fail(AF_ERR_ARG, "af_set_state_host: null array%s");
+  DeviceGuard dg(h->device);
+  int rc = ensure_staging(h);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  const float *src[4] = {avg, vtx, xe, ye};
+  float *dst[4] = {h->hi, h->lev[0].k[VTX], h->lev[0].k[XE], h->lev[0].k[YE]};
+  CK(cudaMemsetAsync(h->d_bad, 0, sizeof(int), s), "memset");
+  for (int w = 0; w < 4; w++) {
+    int ni, nj;
+    extents(h, w, ni, nj);
+    CK(cudaMemcpyAsync(h->staging, src[w], sizeof(float) * NV * ni * nj, cudaMemcpyHostToDevice, s),
+       "af_set_state_host: H2D");
+    const int dup_x = h->g.per_x && (w == 1 || w == 2), dup_y = h->g.per_y && (w == 1 || w == 3);
+    if (dup_x || dup_y) CK(launch_check_dup(h->staging, ni, nj, dup_x, dup_y, h->d_bad, s), "check_dup");
+    CK(launch_pack(h->g, h->staging, dst[w], ni, nj, true, s), "pack");
+  }
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, s), "memcpy");
+  CK(cudaMemsetAsync(h->lo, 0, sizeof(float) * NV * h->g.plane, s), "memset lo");
+  CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), s), "memset status");
+  CK(cudaStreamSynchronize(s), "sync");
+  if (bad) {
+    h->has_state = false;
+    return fail(AF_ERR_ARG, "periodic state: the duplicated last node line differs from the first%s");
+  }
+  h->has_state = true;
+  return AF_OK;
+}
+
+static int get_arrays(af_ctx *h, NodeSet &ns, const float *avgsrc, float *dst[4], bool host,
+                      cudaStream_t user) {
+  const float *src[4] = {avgsrc, ns.k[VTX], ns.k[XE], ns.k[YE]};
+  cudaStream_t s = h->stream;
+  if (!host) {
+    for (int w = 0; w < 4; w++)
+      if (dst[w] && !is_device_ptr(dst[w])) return fail(AF_ERR_ARG, "arrays must be device memory%s");
+    order_after(h, user);
+  } else {
+    int rc = ensure_staging(h);
+    if (rc) return rc;
+  }
+  for (int w = 0; w < 4; w++) {
+    if (!dst[w] || !src[w]) continue;
+    int ni, nj;
+    extents(h, w, ni, nj);
+    if (!host) {
+      CK(launch_pack(h->g, src[w], dst[w], ni, nj, false, s), "pack");
+    } else {
+      CK(launch_pack(h->g, src[w], h->staging, ni, nj, false, s), "pack");
+      CK(cudaMemcpyAsync(dst[w], h->staging, sizeof(float) * NV * ni * nj, cudaMemcpyDeviceToHost, s),
+         "D2H");
+      CK(cudaStreamSynchronize(s), "sync");
+    }
+  }
+  if (!host) order_before(h, user);
+  return AF_OK;
+}
+
+int af_get_state(af_ctx *h, float *avg, float *vtx, float *xe, float *ye, void *stream) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  DeviceGuard dg(h->device);
+  float *dst[4] = {avg, vtx, xe, ye};
+  return get_arrays(h, h->lev[0], h->hi, dst, false, (cudaStream_t)stream);
+}
+
+int af_get_state_host(af_ctx *h, float *avg, float *vtx, float *xe, float *ye) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  DeviceGuard dg(h->device);
+  float *dst[4] = {avg, vtx, xe, ye};
+  return get_arrays(h, h->lev[0], h->hi, dst, true, nullptr);
+}
+
+int af_get_half(af_ctx *h, float *vtx, float *xe, float *ye, void *stream) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  DeviceGuard dg(h->device);
+  float *dst[4] = {nullptr, vtx, xe, ye};
+  return get_arrays(h, h->lev[1], nullptr, dst, false, (cudaStream_t)stream);
+}
+
+int af_get_avg_lo(af_ctx *h, float *avg_lo, void *stream) {
+  if (!h || !is_device_ptr(avg_lo)) return fail(AF_ERR_ARG, "af_get_avg_lo: need a device array%s");
+  DeviceGuard dg(h->device);
+  order_after(h, (cudaStream_t)stream);
+  CK(launch_pack(h->g, h->lo, avg_lo, h->g.nx, h->g.ny, false, h->stream), "pack");
+  order_before(h, (cudaStream_t)stream);
+  return AF_OK;
+}
+
+int af_set_avg_lo(af_ctx *h, const float *avg_lo, void *stream) {
+  if (!h || !is_device_ptr(avg_lo)) return fail(AF_ERR_ARG, "af_set_avg_lo: need a device array%s");
+  if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  DeviceGuard dg(h->device);
+  order_after(h, (cudaStream_t)stream);
+  CK(launch_pack(h->g, avg_lo, h->lo, h->g.nx, h->g.ny, true, h->stream), "pack");
+  order_before(h, (cudaStream_t)stream);
+  return AF_OK;
+}
+
+// fold the stage times of the previous profiled step into the totals
+static void collect_stages(af_ctx *h) {
+  if (!h->stage_pending) return;
+  cudaEventSynchronize(h->ev_stage[4]);
+  // events: 0 | prep | 1 | point values | 2 | (none) | 3 | flux | 4
+  const int from[3] = {0, 1, 3}, to[3] = {1, 2, 4};
+  for (int k = 0; k < 3; k++) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, h->ev_stage[from[k]], h->ev_stage[to[k]]) == cudaSuccess) h->stage_ms[k] += ms;
+  }
+  h->stage_pending = false;
+}
+
+static int enqueue_step(af_ctx *h, double dt) {
+  cudaStream_t s = h->stream;
+  const bool prof = h->profile != 0;
+  if (prof) {
+    collect_stages(h);
+    cudaEventRecord(h->ev_stage[0], s);
+  }
+  CK(launch_ghost_fill(h->g, h->hi, h->lo, h->lev[0], s), "ghost fill");
+  CK(launch_prep(h->g, h->hi, h->lev[0], h->uc, h->ub, s), "prep");
+  h->launches[AF_STAGE_PREP] += 2;
+  CK(cudaMemsetAsync(h->d_counters, 0, 4 * sizeof(unsigned long long), s), "memset counters");
+  if (prof) cudaEventRecord(h->ev_stage[1], s);
+  CK(launch_pointvalue(h->g, h->lev[0], h->uc, h->ub, h->lev[1], h->lev[2], (float)dt, h->opt,
+                       h->d_status, h->d_counters, s),
+     "point values");
+  h->launches[AF_STAGE_POINTVALUE] += 3;
+  if (prof) {
+    cudaEventRecord(h->ev_stage[2], s);
+    cudaEventRecord(h->ev_stage[3], s);
+  }
+  CK(launch_flux_update(h->g, h->lev[0], h->lev[1], h->lev[2], h->hi, h->lo, dt / h->dx, dt / h->dy,
+                        h->d_status, s),
+     "flux update");
+  h->launches[AF_STAGE_FLUX] += 1;
+  if (prof) {
+    cudaEventRecord(h->ev_stage[4], s);
+    h->stage_pending = true;
+  }
+  NodeSet t = h->lev[0];
+  h->lev[0] = h->lev[2];
+  h->lev[2] = t;
+  return AF_OK;
+}
+
+int af_step(af_ctx *h, double dt) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(AF_ERR_ARG, "af_step: dt must be positive%s");
+  if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  DeviceGuard dg(h->device);
+  return enqueue_step(h, dt);
+}
+
+int af_run(af_ctx *h, int nsteps, double dt) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(AF_ERR_ARG, "af_run: bad arguments%s");
+  if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  DeviceGuard dg(h->device);
+  for (int k = 0; k < nsteps; k++) {
+    int rc = enqueue_step(h, dt);
+    if (rc) return rc;
+  }
+  return AF_OK;
+}
+
+int af_status(af_ctx *h) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  DeviceGuard dg(h->device);
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status");
+  CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream), "status");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  return st;
+}
+
+int af_counters(af_ctx *h, int64_t out[4]) {
+  if (!h || !out) return fail(AF_ERR_ARG, "null argument%s");
+  DeviceGuard dg(h->device);
+  unsigned long long c[4];
+  CK(cudaMemcpyAsync(c, h->d_counters, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "counters");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  for (int k = 0; k < 4; k++) out[k] = (int64_t)c[k];
+  return AF_OK;
+}
+
+int af_conserved_totals(af_ctx *h, double out[4]) {
+  if (!h || !out) return fail(AF_ERR_ARG, "null argument%s");
+  if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  DeviceGuard dg(h->device);
+  CK(launch_totals(h->g, h->hi, h->lo, h->d_partials, h->d_totals, h->stream), "totals");
+  h->launches[AF_STAGE_REDUCE] += 2;
+  double t[4];
+  CK(cudaMemcpyAsync(t, h->d_totals, sizeof(t), cudaMemcpyDeviceToHost, h->stream), "totals");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  for (int v = 0; v < 4; v++) out[v] = t[v] * h->dx * h->dy;
+  return AF_OK;
+}
+
+int af_max_speed(af_ctx *h, float *out) {
+  if (!h || !out) return fail(AF_ERR_ARG, "null argument%s");
+  if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  DeviceGuard dg(h->device);
+  cudaEvent_t e0 = h->ev_in, e1 = h->ev_out;
+  if (h->profile) {
+    collect_stages(h);
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    cudaEventRecord(e0, h->stream);
+  }
+  CK(launch_max_speed(h->g, h->hi, h->lev[0], h->d_speed, h->d_bad, h->stream), "max speed");
+  h->launches[AF_STAGE_REDUCE] += 1;
+  if (h->profile) cudaEventRecord(e1, h->stream);
+  unsigned bits = 0;
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bits, h->d_speed, sizeof(bits), cudaMemcpyDeviceToHost, h->stream), "speed");
+  CK(cudaMemcpyAsync(&bad, h->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "speed");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  if (h->profile) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) h->stage_ms[AF_STAGE_REDUCE] += ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  float m;
+  std::memcpy(&m, &bits, sizeof(m));
+  *out = bad ? NAN : m;
+  return AF_OK;
+}
+
+int af_profile(af_ctx *h, double ms[4], int64_t launches[4], int reset) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  DeviceGuard dg(h->device);
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  collect_stages(h);
+  for (int k = 0; k < 4; k++) {
+    if (ms) ms[k] = h->stage_ms[k];
+    if (launches) launches[k] = h->launches[k];
+    if (reset) {
+      h->stage_ms[k] = 0.0;
+      h->launches[k] = 0;
+    }
+  }
+  return AF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,56 @@
+// af_common.cuh -- layout of the device state and small shared helpers.
+//
+// Every array is a set of 4 FP32 planes (one per variable) with a common
+// padded layout: interior index (i, j) of a cell, a vertex (i-1/2, j-1/2),
+// an x-edge midpoint (i-1/2, j) or a y-edge midpoint (i, j-1/2) lives at
+// row j + OY, column i + OX of its plane.  The pitch is a multiple of 32
+// floats, so rows start on 128-byte boundaries and interior column 0 on a
+// 16-byte boundary.  G = 2 ghost layers surround the interior on every side.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace af {
+
+constexpr int NV = 4;
+constexpr int G = 2;
+constexpr int OX = 4;
+constexpr int OY = 2;
+
+enum NodeKind { VTX = 0, XE = 1, YE = 2 };
+enum BcKind { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTING = 2 };
+enum StatusBits { ST_CFL = 1, ST_AVG_NONPOS = 2, ST_NONFINITE = 4, ST_KEPT = 8 };
+enum Counter { CNT_EG1 = 0, CNT_LF = 1, CNT_KEPT = 2, CNT_TSW = 3 };
+
+struct Grid {
+  int nx, ny;         // cells
+  int P, H;           // pitch (floats) and rows of a plane
+  long long plane;    // P * H
+  int per_x, per_y;   // periodic axes
+  int nxv, nyv;       // owned node lines along x / y: n on a periodic axis, n + 1 otherwise
+  int bc[4];          // xlo, xhi, ylo, yhi
+  float dx, dy, idx, idy;
+  float gamma;
+};
+
+__host__ __device__ __forceinline__ long long at(const Grid &g, int v, int i, int j) {
+  return (long long)v * g.plane + (long long)(j + OY) * g.P + (i + OX);
+}
+
+// primitive -> conservative (Sec. 2: q = (rho, rho u, rho v, E))
+__device__ __forceinline__ void p2c(const float U[4], float gm1i, float Q[4]) {
+  Q[0] = U[0];
+  Q[1] = U[0] * U[1];
+  Q[2] = U[0] * U[2];
+  Q[3] = U[3] * gm1i + 0.5f * U[0] * (U[1] * U[1] + U[2] * U[2]);
+}
+__device__ __forceinline__ void c2p(const float Q[4], float gm1, float U[4]) {
+  float ir = 1.0f / Q[0];
+  U[0] = Q[0];
+  U[1] = Q[1] * ir;
+  U[2] = Q[2] * ir;
+  U[3] = gm1 * (Q[3] - 0.5f * (Q[1] * Q[1] + Q[2] * Q[2]) * ir);
+}
+__device__ __forceinline__ bool admissible(const float U[4]) { return U[0] > 0.0f && U[3] > 0.0f; }
+
+}  // namespace af

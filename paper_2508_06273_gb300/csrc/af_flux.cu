@@ -1,0 +1,151 @@
+// af_flux.cu -- Simpson fluxes and the finite-volume update of the cell
+// averages, eqs. (F) and (2dfvm).
+//
+// A block owns a TX x TY tile of cells.  It first integrates f (and g) in
+// time at every node of the tile's faces with Simpson weights (1, 4, 1) over
+// t^n, t^{n+1/2}, t^{n+1}, then forms each face flux once with the weights
+// (1, 4, 1) along the face and 1/36, and finally updates every cell in FP64
+// on its FP32 (hi, lo) pair.  A face on a tile boundary is computed by both
+// tiles with the same instructions from the same inputs, so the two cells
+// sharing it see bit-identical fluxes and the update conserves to round-off.
+#include "af_common.cuh"
+#include "af_kernels.h"
+
+namespace af {
+
+namespace {
+
+constexpr int TX = 32, TY = 8;
+
+struct Args {
+  Grid g;
+  const float *__restrict__ n[3][3];  // [level][kind]
+  float *hi, *lo;
+  double lamx, lamy;
+  int *status;
+};
+
+// f (dir 0) or g (dir 1) of the conservative form at primitive U
+__device__ __forceinline__ void phys_flux(const float U[4], float gm1i, int dir, float F[4]) {
+  const float r = U[0], u = U[1], v = U[2], p = U[3];
+  const float un = dir == 0 ? u : v;
+  const float E = p * gm1i + 0.5f * r * (u * u + v * v);
+  F[0] = r * un;
+  F[1] = r * u * un + (dir == 0 ? p : 0.0f);
+  F[2] = r * v * un + (dir == 1 ? p : 0.0f);
+  F[3] = un * (E + p);
+}
+
+// Simpson in time at one node: f(U^n) + 4 f(U^{n+1/2}) + f(U^{n+1})
+__device__ __forceinline__ void time_flux(const Args &A, int kind, int i, int j, int dir, float gm1i,
+                                          float F[4]) {
+  F[0] = F[1] = F[2] = F[3] = 0.0f;
+#pragma unroll
+  for (int l = 0; l < 3; l++) {
+    float U[4], f[4];
+#pragma unroll
+    for (int v = 0; v < NV; v++) U[v] = __ldg(A.n[l][kind] + at(A.g, v, i, j));
+    phys_flux(U, gm1i, dir, f);
+    const float w = l == 1 ? 4.0f : 1.0f;
+#pragma unroll
+    for (int v = 0; v < NV; v++) F[v] += w * f[v];
+  }
+}
+
+__global__ void __launch_bounds__(TX *TY) flux_update_kernel(Args A) {
+  const Grid &g = A.g;
+  __shared__ float vf[NV][TY + 1][TX + 1], vg[NV][TY + 1][TX + 1];
+  __shared__ float xf[NV][TY][TX + 1], yg[NV][TY + 1][TX];
+  __shared__ float Fx[NV][TY][TX + 1], Gy[NV][TY + 1][TX];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const float gm1i = 1.0f / (g.gamma - 1.0f);
+
+  // time-integrated node fluxes; nodes up to index nx / ny (periodic
+  // duplicates included)
+  for (int k = tid; k < (TX + 1) * (TY + 1); k += TX * TY) {
+    const int a = k % (TX + 1), b = k / (TX + 1), i = i0 + a, j = j0 + b;
+    float F[4] = {0, 0, 0, 0}, Gf[4] = {0, 0, 0, 0};
+    if (i <= g.nx && j <= g.ny) {
+      time_flux(A, VTX, i, j, 0, gm1i, F);
+      time_flux(A, VTX, i, j, 1, gm1i, Gf);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      vf[v][b][a] = F[v];
+      vg[v][b][a] = Gf[v];
+    }
+  }
+  for (int k = tid; k < (TX + 1) * TY; k += TX * TY) {
+    const int a = k % (TX + 1), b = k / (TX + 1), i = i0 + a, j = j0 + b;
+    float F[4] = {0, 0, 0, 0};
+    if (i <= g.nx && j < g.ny) time_flux(A, XE, i, j, 0, gm1i, F);
+#pragma unroll
+    for (int v = 0; v < NV; v++) xf[v][b][a] = F[v];
+  }
+  for (int k = tid; k < TX * (TY + 1); k += TX * TY) {
+    const int a = k % TX, b = k / TX, i = i0 + a, j = j0 + b;
+    float F[4] = {0, 0, 0, 0};
+    if (i < g.nx && j <= g.ny) time_flux(A, YE, i, j, 1, gm1i, F);
+#pragma unroll
+    for (int v = 0; v < NV; v++) yg[v][b][a] = F[v];
+  }
+  __syncthreads();
+  // face fluxes, each formed once per tile
+  const float w36 = 1.0f / 36.0f;
+  for (int k = tid; k < (TX + 1) * TY; k += TX * TY) {
+    const int a = k % (TX + 1), b = k / (TX + 1);
+#pragma unroll
+    for (int v = 0; v < NV; v++) Fx[v][b][a] = (vf[v][b][a] + 4.0f * xf[v][b][a] + vf[v][b + 1][a]) * w36;
+  }
+  for (int k = tid; k < TX * (TY + 1); k += TX * TY) {
+    const int a = k % TX, b = k / TX;
+#pragma unroll
+    for (int v = 0; v < NV; v++) Gy[v][b][a] = (vg[v][b][a] + 4.0f * yg[v][b][a] + vg[v][b][a + 1]) * w36;
+  }
+  __syncthreads();
+  // finite-volume update in FP64 on the (hi, lo) pair
+  const int a = threadIdx.x, b = threadIdx.y, i = i0 + a, j = j0 + b;
+  if (i >= g.nx || j >= g.ny) return;
+  double q[4];
+  bool bad = false;
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    const long long e = at(g, v, i, j);
+    double x = (double)A.hi[e] + (double)A.lo[e];
+    x = x - A.lamx * ((double)Fx[v][b][a + 1] - (double)Fx[v][b][a]) -
+        A.lamy * ((double)Gy[v][b + 1][a] - (double)Gy[v][b][a]);
+    const float h = (float)x;
+    A.hi[e] = h;
+    A.lo[e] = (float)(x - (double)h);
+    q[v] = x;
+    bad |= !isfinite(x);
+  }
+  const double p = (double)(g.gamma - 1.0f) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
+  int st = bad ? ST_NONFINITE : ((q[0] > 0.0 && p > 0.0) ? 0 : ST_AVG_NONPOS);
+  if (__any_sync(__activemask(), st != 0) && st) atomicOr(A.status, st);
+}
+
+}  // namespace
+
+cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &n1,
+                               const NodeSet &n2, float *avg_hi, float *avg_lo, double lamx,
+                               double lamy, int *status, cudaStream_t s) {
+  Args A;
+  A.g = g;
+  for (int k = 0; k < 3; k++) {
+    A.n[0][k] = n0.k[k];
+    A.n[1][k] = n1.k[k];
+    A.n[2][k] = n2.k[k];
+  }
+  A.hi = avg_hi;
+  A.lo = avg_lo;
+  A.lamx = lamx;
+  A.lamy = lamy;
+  A.status = status;
+  dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY), blk(TX, TY);
+  flux_update_kernel<<<grd, blk, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+}  // namespace af

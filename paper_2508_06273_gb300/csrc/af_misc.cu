@@ -1,0 +1,278 @@
+// af_misc.cu -- ghost cells (Sec. 4.3), cell prep (Sec. 2), reductions and
+// layout conversion kernels.
+#include "af_common.cuh"
+#include "af_kernels.h"
+
+namespace af {
+
+namespace {
+
+// Source index of a ghost entry along one axis.  Periodic: wrap.  Outflow:
+// mirror copy of the interior.  Solid wall: the same mirror, with the normal
+// velocity negated (flip).  node: the array sits on grid lines along the axis.
+__device__ __forceinline__ int ghost_src(int i, int n, int own, int node, int per, int blo,
+                                         int bhi, bool &flip) {
+  if (i >= 0 && i < own) return i;
+  if (per) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  if (i < 0) {
+    flip = (blo == BC_REFLECTING);
+    return node ? -i : -1 - i;
+  }
+  flip = (bhi == BC_REFLECTING);
+  return node ? 2 * n - i : 2 * n - 1 - i;
+}
+
+struct GhostArgs {
+  Grid g;
+  float *a[5];  // avg_hi, avg_lo, vtx, xe, ye
+};
+
+__global__ void ghost_kernel(GhostArgs A) {
+  const Grid &g = A.g;
+  const int arr = blockIdx.y;
+  const int nodex = (arr == 2 || arr == 3), nodey = (arr == 2 || arr == 4);
+  const int ownx = nodex ? g.nxv : g.nx, owny = nodey ? g.nyv : g.ny;
+  const int hix = nodex ? g.nx + G + 1 : g.nx + G, hiy = nodey ? g.ny + G + 1 : g.ny + G;
+  const int wext = hix + G;
+  const int nb = G * wext, nt = (hiy - owny) * wext, nl = owny * G, wr = hix - ownx;
+  const int total = nb + nt + nl + owny * wr;
+  float *p = A.a[arr];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    int i, j, r = k;
+    if (r < nb) {
+      j = -G + r / wext;
+      i = -G + r % wext;
+    } else if ((r -= nb) < nt) {
+      j = owny + r / wext;
+      i = -G + r % wext;
+    } else if ((r -= nt) < nl) {
+      j = r / G;
+      i = -G + r % G;
+    } else {
+      r -= nl;
+      j = r / wr;
+      i = ownx + r % wr;
+    }
+    bool fx = false, fy = false;
+    const int si = ghost_src(i, g.nx, ownx, nodex, g.per_x, g.bc[0], g.bc[1], fx);
+    const int sj = ghost_src(j, g.ny, owny, nodey, g.per_y, g.bc[2], g.bc[3], fy);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      float x = p[at(g, v, si, sj)];
+      if ((v == 1 && fx) || (v == 2 && fy)) x = -x;
+      p[at(g, v, i, j)] = x;
+    }
+  }
+}
+
+// U_c by inverting Simpson's rule for the conservative centre value, then
+// Ubar by Simpson's rule in primitive variables (Sec. 2)
+__global__ void prep_kernel(Grid g, const float *__restrict__ avg, const float *__restrict__ V,
+                            const float *__restrict__ X, const float *__restrict__ Y, float *uc,
+                            float *ub) {
+  const int i = -G + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = -G + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+  if (i >= g.nx + G || j >= g.ny + G) return;
+  const float gm1 = g.gamma - 1.0f, gm1i = 1.0f / gm1;
+  float Qs[4] = {0, 0, 0, 0}, Us[4] = {0, 0, 0, 0};
+  const float *arr[8] = {V, V, V, V, X, X, Y, Y};
+  const int di[8] = {0, 1, 0, 1, 0, 1, 0, 0}, dj[8] = {0, 0, 1, 1, 0, 0, 0, 1};
+#pragma unroll
+  for (int n = 0; n < 8; n++) {
+    float U[4], Q[4];
+#pragma unroll
+    for (int v = 0; v < NV; v++) U[v] = __ldg(arr[n] + at(g, v, i + di[n], j + dj[n]));
+    p2c(U, gm1i, Q);
+    const float w = n < 4 ? 1.0f : 4.0f;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      Qs[v] += w * Q[v];
+      Us[v] += w * U[v];
+    }
+  }
+  float Qc[4], Uc[4];
+#pragma unroll
+  for (int v = 0; v < NV; v++) Qc[v] = (36.0f * __ldg(avg + at(g, v, i, j)) - Qs[v]) * 0.0625f;
+  c2p(Qc, gm1, Uc);
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    uc[at(g, v, i, j)] = Uc[v];
+    ub[at(g, v, i, j)] = (Us[v] + 16.0f * Uc[v]) * (1.0f / 36.0f);
+  }
+}
+
+__device__ __forceinline__ float wave_speed(const float U[4], float gam, bool &bad) {
+  if (!(U[0] > 0.0f && U[3] > 0.0f) || !isfinite(U[1]) || !isfinite(U[2])) {
+    bad = true;
+    return 0.0f;
+  }
+  return fmaxf(fabsf(U[1]), fabsf(U[2])) + sqrtf(gam * U[3] / U[0]);
+}
+
+__global__ void max_speed_kernel(Grid g, const float *__restrict__ avg, const float *__restrict__ V,
+                                 const float *__restrict__ X, const float *__restrict__ Y,
+                                 unsigned *out, int *badflag) {
+  const long long nc = (long long)g.nx * g.ny, nv = (long long)g.nxv * g.nyv;
+  const long long nxe = (long long)g.nxv * g.ny, nye = (long long)g.nx * g.nyv;
+  const long long total = nc + nv + nxe + nye;
+  float m = 0.0f;
+  bool bad = false;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    float U[4];
+    long long r = k;
+    if (r < nc) {
+      const int i = (int)(r % g.nx), j = (int)(r / g.nx);
+      float Q[4];
+#pragma unroll
+      for (int v = 0; v < NV; v++) Q[v] = __ldg(avg + at(g, v, i, j));
+      c2p(Q, g.gamma - 1.0f, U);
+    } else {
+      const float *p;
+      int ni;
+      if ((r -= nc) < nv) {
+        p = V;
+        ni = g.nxv;
+      } else if ((r -= nv) < nxe) {
+        p = X;
+        ni = g.nxv;
+      } else {
+        r -= nxe;
+        p = Y;
+        ni = g.nx;
+      }
+      const int i = (int)(r % ni), j = (int)(r / ni);
+#pragma unroll
+      for (int v = 0; v < NV; v++) U[v] = __ldg(p + at(g, v, i, j));
+    }
+    m = fmaxf(m, wave_speed(U, g.gamma, bad));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(badflag, 1);
+}
+
+// stage 1: block b sums rows b, b + nblk, ... in a fixed order
+__global__ void totals_stage1(Grid g, const float *__restrict__ hi, const float *__restrict__ lo,
+                              double *partials) {
+  __shared__ double sm[4][256];
+  double acc[4] = {0, 0, 0, 0};
+  for (int j = blockIdx.x; j < g.ny; j += gridDim.x)
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x)
+#pragma unroll
+      for (int v = 0; v < NV; v++) acc[v] += (double)hi[at(g, v, i, j)] + (double)lo[at(g, v, i, j)];
+#pragma unroll
+  for (int v = 0; v < NV; v++) sm[v][threadIdx.x] = acc[v];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int v = 0; v < NV; v++) sm[v][threadIdx.x] += sm[v][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < NV) partials[blockIdx.x * NV + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void totals_stage2(const double *partials, double *out) {
+  __shared__ double sm[4][TOTALS_BLOCKS];
+#pragma unroll
+  for (int v = 0; v < NV; v++) sm[v][threadIdx.x] = partials[threadIdx.x * NV + v];
+  __syncthreads();
+  for (int s = TOTALS_BLOCKS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int v = 0; v < NV; v++) sm[v][threadIdx.x] += sm[v][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < NV) out[threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void pack_kernel(Grid g, const float *__restrict__ src, float *dst, int ni, int nj,
+                            int to_padded) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= ni || j >= nj) return;
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    const long long e = ((long long)v * nj + j) * ni + i;
+    if (to_padded)
+      dst[at(g, v, i, j)] = src[e];
+    else
+      dst[e] = src[at(g, v, i, j)];
+  }
+}
+
+__global__ void check_dup_kernel(const float *__restrict__ a, int ni, int nj, int dup_x, int dup_y,
+                                 int *bad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  const float *p = a + (long long)v * ni * nj;
+  if (dup_x && k < nj && !(p[(long long)k * ni + ni - 1] == p[(long long)k * ni])) atomicOr(bad, 1);
+  if (dup_y && k < ni && !(p[(long long)(nj - 1) * ni + k] == p[k])) atomicOr(bad, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_ghost_fill(const Grid &g, float *avg_hi, float *avg_lo, const NodeSet &n,
+                              cudaStream_t s) {
+  GhostArgs A;
+  A.g = g;
+  A.a[0] = avg_hi;
+  A.a[1] = avg_lo;
+  A.a[2] = n.k[VTX];
+  A.a[3] = n.k[XE];
+  A.a[4] = n.k[YE];
+  const long long per = 2LL * (g.nx + g.ny + 2 * G + 2) * (2 * G + 1);
+  int blocks = (int)((per + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  ghost_kernel<<<dim3(blocks, 5), 256, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const Grid &g, const float *avg_hi, const NodeSet &n, float *uc, float *ub,
+                        cudaStream_t s) {
+  dim3 blk(32, 8), grd((g.nx + 2 * G + 31) / 32, (g.ny + 2 * G + 7) / 8);
+  prep_kernel<<<grd, blk, 0, s>>>(g, avg_hi, n.k[VTX], n.k[XE], n.k[YE], uc, ub);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_speed(const Grid &g, const float *avg_hi, const NodeSet &n,
+                             unsigned *out_bits, int *bad, cudaStream_t s) {
+  cudaMemsetAsync(out_bits, 0, sizeof(unsigned), s);
+  cudaMemsetAsync(bad, 0, sizeof(int), s);
+  long long total = 4LL * (g.nx + 1) * (g.ny + 1);
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  max_speed_kernel<<<blocks, 256, 0, s>>>(g, avg_hi, n.k[VTX], n.k[XE], n.k[YE], out_bits, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_totals(const Grid &g, const float *avg_hi, const float *avg_lo, double *partials,
+                          double *out, cudaStream_t s) {
+  totals_stage1<<<TOTALS_BLOCKS, 256, 0, s>>>(g, avg_hi, avg_lo, partials);
+  totals_stage2<<<1, TOTALS_BLOCKS, 0, s>>>(partials, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const Grid &g, const float *src, float *dst, int ni, int nj, bool to_padded,
+                        cudaStream_t s) {
+  dim3 blk(32, 8), grd((ni + 31) / 32, (nj + 7) / 8);
+  pack_kernel<<<grd, blk, 0, s>>>(g, src, dst, ni, nj, to_padded ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_dup(const float *ext, int ni, int nj, int dup_x, int dup_y, int *bad,
+                             cudaStream_t s) {
+  int n = ni > nj ? ni : nj;
+  check_dup_kernel<<<dim3((n + 255) / 256, NV), 256, 0, s>>>(ext, ni, nj, dup_x, dup_y, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(float *p, long long n, cudaStream_t s) {
+  return cudaMemsetAsync(p, 0, (size_t)n * sizeof(float), s);
+}
+
+}  // namespace af

@@ -111,6 +111,59 @@ def discretise(prob: Problem, field: Optional[Field] = None):
     return avg, vtx, xe, ye
 
 
+def discretise_torch(prob: Problem, device, field: Optional[Field] = None, dtype=None):
+    """Same as ``discretise`` but evaluated with torch in float64 on ``device``
+    (for large grids); returns float32 tensors unless ``dtype`` is given.
+    Only for fields written against numpy/torch alike (``shu_vortex``)."""
+    import torch
+
+    f = field or prob.field
+    f64 = torch.float64
+    nx, ny, dx, dy = prob.nx, prob.ny, prob.dx, prob.dy
+    xn = prob.x0 + dx * torch.arange(nx + 1, device=device, dtype=f64)
+    yn = prob.y0 + dy * torch.arange(ny + 1, device=device, dtype=f64)
+    xc = prob.x0 + dx * (torch.arange(nx, device=device, dtype=f64) + 0.5)
+    yc = prob.y0 + dy * (torch.arange(ny, device=device, dtype=f64) + 0.5)
+    out_t = dtype or torch.float32
+
+    def ev(x, y):
+        vals = f(x, y)
+        shape = torch.broadcast_shapes(x.shape, y.shape)
+        return torch.stack([torch.as_tensor(v, dtype=f64, device=device).expand(shape) for v in vals])
+
+    vtx = ev(xn[None, :], yn[:, None]).to(out_t)
+    xe = ev(xn[None, :], yc[:, None]).to(out_t)
+    ye = ev(xc[None, :], yn[:, None]).to(out_t)
+    avg = torch.zeros((4, ny, nx), dtype=f64, device=device)
+    ia = torch.arange(nx, device=device, dtype=f64)[None, :]
+    ja = torch.arange(ny, device=device, dtype=f64)[:, None]
+    for a, wa in zip(_GLX, _GLW):
+        X = prob.x0 + dx * (ia + a)
+        for b, wb in zip(_GLX, _GLW):
+            Y = prob.y0 + dy * (ja + b)
+            r, u, v, p = f(X, Y)
+            avg[0] += wa * wb * r
+            avg[1] += wa * wb * r * u
+            avg[2] += wa * wb * r * v
+            avg[3] += wa * wb * (p / (prob.gamma - 1.0) + 0.5 * r * (u * u + v * v))
+    avg = avg.to(out_t)
+    if prob.bc[0] == PERIODIC:
+        vtx[:, :, nx] = vtx[:, :, 0]
+        xe[:, :, nx] = xe[:, :, 0]
+    if prob.bc[2] == PERIODIC:
+        vtx[:, ny, :] = vtx[:, 0, :]
+        ye[:, ny, :] = ye[:, 0, :]
+    return avg, vtx, xe, ye
+
+
+def subproblem(prob: Problem, i0: int, j0: int, ni: int, nj: int, bc=(1, 1, 1, 1)):
+    """The cells [i0, i0+ni) x [j0, j0+nj) of ``prob`` as a problem of its
+    own (for checking sampled windows of a large grid)."""
+    return Problem(prob.name + "_window", ni, nj, prob.x0 + i0 * prob.dx, prob.y0 + j0 * prob.dy,
+                   ni * prob.dx, nj * prob.dy, bc, prob.field, prob.t_end, prob.cfl, prob.gamma,
+                   dict(prob.options), prob.exact)
+
+
 def to_f32(state):
     """Round a state to FP32 (the GPU's storage) and back to float64."""
     return tuple(np.asarray(a, dtype=np.float32).astype(np.float64) for a in state)
@@ -121,6 +174,15 @@ def _wrap(d, period):
 
 
 # ----------------------------------------------------------------- problems
+def _mod(x):
+    """numpy, or torch when the coordinates are torch tensors."""
+    if type(x).__module__.startswith("torch"):
+        import torch
+
+        return torch
+    return np
+
+
 def shu_vortex(n=32, eps=5.0, xc=5.0, yc=5.0, L=10.0, t_end=10.0, ny=None, cfl=0.3):
     """Isentropic vortex of strength eps on the periodic box [0,L]^2 moving
     with (1,1) through the background rho = u = v = p = 1 (minimum-image
@@ -131,10 +193,13 @@ def shu_vortex(n=32, eps=5.0, xc=5.0, yc=5.0, L=10.0, t_end=10.0, ny=None, cfl=0
         cx, cy = xc + t, yc + t
 
         def f(x, y):
-            X = _wrap(x - cx, L)
-            Y = _wrap(y - cy, L)
+            m = _mod(x)
+            X = x - cx
+            X = X - L * m.floor(X / L + 0.5)
+            Y = y - cy
+            Y = Y - L * m.floor(Y / L + 0.5)
             r2 = X * X + Y * Y
-            e = np.exp(0.5 * (1.0 - r2))
+            e = m.exp(0.5 * (1.0 - r2))
             T = 1.0 - (g - 1.0) * eps * eps / (8.0 * g * np.pi ** 2) * e * e
             rho = T ** (1.0 / (g - 1.0))
             return rho, 1.0 - eps / (2 * np.pi) * e * Y, 1.0 + eps / (2 * np.pi) * e * X, rho ** g

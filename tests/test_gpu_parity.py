@@ -1,0 +1,291 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: relative L1 <= 1e-5 after one step and <= 1e-4 at the final
+time on smooth data; the metric is per array and per variable, with
+velocities (and momenta) measured against the local speed scale
+|u| + |v| + c so that a vanishing velocity field has a defined error.
+Positivity of the point values is checked exactly.
+"""
+import numpy as np
+import pytest
+
+from helpers import make_oracle
+from paper_2508_06273_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-5
+FINAL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def env(oracle_mod):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2508_06273_gb300 import af
+
+    return torch, af, oracle_mod
+
+
+def to_dev(torch, state):
+    return [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda() for a in state]
+
+
+def solver(env, prob, opts=None, state=None):
+    torch, af, _ = env
+    o = dict(prob.options)
+    o.update(opts or {})
+    s = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=o)
+    s.set_state(*to_dev(torch, state if state is not None else W.to_f32(W.discretise(prob))))
+    return s
+
+
+def host(ts):
+    return [t.cpu().double().numpy() for t in ts]
+
+
+def rel_l1(got, want, conservative):
+    """max over variables of the relative L1 distance of one array."""
+    g = 1.4
+    if conservative:
+        r = want[0]
+        p = (g - 1) * (want[3] - 0.5 * (want[1] ** 2 + want[2] ** 2) / r)
+        scale_vel = (np.abs(want[1]) + np.abs(want[2]) + r * np.sqrt(np.abs(g * p / r))).sum()
+    else:
+        scale_vel = (np.abs(want[1]) + np.abs(want[2]) + np.sqrt(np.abs(g * want[3] / want[0]))).sum()
+    out = 0.0
+    for v in range(4):
+        den = scale_vel if v in (1, 2) else np.abs(want[v]).sum()
+        out = max(out, np.abs(got[v] - want[v]).sum() / den)
+    return out
+
+
+def state_err(got, want):
+    return max(rel_l1(a, b, k == 0) for k, (a, b) in enumerate(zip(got, want)))
+
+
+SMOOTH = {
+    "vortex32": lambda: W.shu_vortex(32),
+    "fourier_ragged": lambda: W.fourier_smooth(50, 37, seed=5, lx=1.0, ly=0.81),
+    "vortex_seeded128": lambda: W.shu_vortex_seeded(128),
+}
+MODES = {"avg": {}, "point": {"lin_mode": 1}, "alg1": {"lin_mode": 2}, "nocorr": {"correction": 0},
+         "tsw": {"tsw": 1}}
+
+
+@pytest.mark.parametrize("case", list(SMOOTH))
+@pytest.mark.parametrize("mode", list(MODES))
+def test_one_step_parity(env, case, mode):
+    torch, af, oracle = env
+    prob = SMOOTH[case]()
+    st = W.to_f32(W.discretise(prob))
+    o = make_oracle(oracle, prob, MODES[mode], state=st)
+    dt = prob.cfl * min(prob.dx, prob.dy) / o.max_speed()
+    o.step(dt)
+    s = solver(env, prob, MODES[mode], st)
+    s.step(dt)
+    assert s.status() == 0
+    assert state_err(host(s.get_state()), o.get_state()) < STEP_TOL
+    assert state_err(host(s.get_half()), o.get_half()) < STEP_TOL
+
+
+def test_final_time_vortex32(env):
+    """32x32 isentropic vortex, CFL 0.3, to t = 10 (one period)."""
+    torch, af, oracle = env
+    prob = W.shu_vortex(32)
+    st = W.to_f32(W.discretise(prob))
+    o = make_oracle(oracle, prob, state=st)
+    s = solver(env, prob, state=st)
+    t, n = 0.0, 0
+    while t < prob.t_end * (1 - 1e-12):
+        dt = min(prob.cfl * prob.dx / o.max_speed(), prob.t_end - t)
+        o.step(dt)
+        s.step(dt)
+        t += dt
+        n += 1
+    assert s.status() == 0
+    err = state_err(host(s.get_state()), o.get_state())
+    assert err < FINAL_TOL, (n, err)
+
+
+def test_conservation_periodic(env):
+    torch, af, _ = env
+    prob = W.fourier_smooth(64, 48, seed=8, lx=1.0, ly=0.75)
+    s = solver(env, prob)
+    t0 = s.totals()
+    absq = np.abs(W.discretise(prob)[0]).sum(axis=(1, 2)) * prob.dx * prob.dy
+    for _ in range(50):
+        s.step(0.3 * prob.dx / 2.0)
+    drift = np.abs(s.totals() - t0) / absq
+    assert s.status() == 0
+    assert np.all(drift < 1e-13), drift
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1), (2, 2, 2, 2), (1, 2, 0, 0)])
+def test_constant_state_is_exact(env, bc):
+    torch, af, _ = env
+    U = (0.8, 0.0 if 2 in bc else 0.3, 0.0 if 2 in bc else -0.6, 1.7)
+    prob = W.Problem("const", 33, 20, 0.0, 0.0, 3.3, 2.0, bc, lambda x, y: U, 1.0)
+    st = W.to_f32(W.discretise(prob))
+    s = solver(env, prob, state=st)
+    for _ in range(3):
+        s.step(0.05)
+    for a, b in zip(host(s.get_state()), st):
+        assert np.array_equal(a, b)
+
+
+def _wall_problem(n=40):
+    rng = np.random.default_rng(4)
+    c = rng.normal(size=(4, 3, 3)) * 0.05
+
+    def f(x, y):
+        out = []
+        for k in range(4):
+            s = [1.0, 0.2, 0.0, 1.0][k] + 0.0 * x
+            for a in range(3):
+                for b in range(3):
+                    if k == 2:
+                        s = s + c[k, a, b] * np.cos(2 * np.pi * a * x) * np.sin(np.pi * (b + 1) * y)
+                    else:
+                        s = s + c[k, a, b] * np.cos(2 * np.pi * a * x) * np.cos(np.pi * b * y)
+            out.append(s)
+        return tuple(out)
+
+    return W.Problem("wall", n, n - 7, 0.0, 0.0, 1.0, 1.0, (1, 1, 2, 2), f, 0.05)
+
+
+def test_walls_and_outflow_parity(env):
+    torch, af, oracle = env
+    prob = _wall_problem()
+    st = W.to_f32(W.discretise(prob))
+    o = make_oracle(oracle, prob, state=st)
+    s = solver(env, prob, state=st)
+    for _ in range(5):
+        dt = 0.3 * prob.dy / o.max_speed()
+        o.step(dt)
+        s.step(dt)
+        assert state_err(host(s.get_state()), o.get_state()) < 5 * STEP_TOL
+    _, vtx, xe, ye = host(s.get_state())
+    assert np.max(np.abs(vtx[2, [0, -1], :])) < 1e-6
+    assert np.max(np.abs(ye[2, [0, -1], :])) < 1e-6
+
+
+@pytest.mark.parametrize("force", [1, 2])
+def test_low_order_paths_parity(env, force):
+    """Alg. 3's EG1-on-pc and Lax-Friedrichs updates, forced at every node."""
+    torch, af, oracle = env
+    prob = W.four_quadrant(24, seed=3)
+    st = W.to_f32(W.discretise(prob))
+    opts = {"force_lo": force, "tsw": 0}
+    o = make_oracle(oracle, prob, opts, state=st)
+    dt = 0.3 * prob.dx / o.max_speed()
+    o.step(dt)
+    s = solver(env, prob, opts, st)
+    s.step(dt)
+    assert state_err(host(s.get_half()), o.get_half()) < STEP_TOL
+    assert state_err(host(s.get_state())[1:], o.get_state()[1:]) < STEP_TOL
+    assert s.counters()[:2] == o.counters()[:2]
+
+
+def test_riemann_limiter_positivity(env):
+    """Four-quadrant data with Alg. 2 and Alg. 3: every point value stays
+    admissible; the distance to the oracle is reported loosely (branch
+    decisions near rho, p = 0 may differ between FP32 and FP64)."""
+    torch, af, oracle = env
+    prob = W.four_quadrant(64, seed=0)
+    st = W.to_f32(W.discretise(prob))
+    o = make_oracle(oracle, prob, state=st)
+    s = solver(env, prob, state=st)
+    for _ in range(30):
+        dt = 0.3 * prob.dx / o.max_speed()
+        o.step(dt)
+        s.step(dt)
+        for a in host(s.get_state())[1:]:
+            assert np.all(a[0] > 0) and np.all(a[3] > 0)
+    st_bits = s.status()
+    assert not (st_bits & af.ST_NONFINITE)
+    err = np.abs(host(s.get_state())[0][0] - o.get_state()[0][0]).sum() / np.abs(o.get_state()[0][0]).sum()
+    assert err < 1e-2, err
+
+
+def test_double_rarefaction_positivity(env):
+    torch, af, _ = env
+    prob = W.double_rarefaction(128)
+    s = solver(env, prob)
+    for _ in range(40):
+        s.step(0.3 * prob.dx / s.max_speed())
+        assert all(np.all(a[0] > 0) and np.all(a[3] > 0) for a in host(s.get_state())[1:])
+    assert sum(s.counters()[:2]) >= 0
+
+
+def test_status_flags_and_errors(env):
+    torch, af, _ = env
+    prob = W.shu_vortex(16)
+    s = solver(env, prob)
+    s.step(3.0 * prob.dx / s.max_speed())  # CFL 3: the cone base leaves the stencil
+    assert s.status() & af.ST_CFL
+    st = W.to_f32(W.discretise(prob))
+    with pytest.raises(af.AFError):  # host memory passed as device memory
+        af._check(s.L.af_set_state(s.h, *[np.asarray(a, dtype=np.float32).ctypes.data for a in st], None))
+    bad = [a.copy() for a in st]
+    bad[1][0, 3, -1] += 1.0  # periodic duplicate line differs from the first
+    with pytest.raises(af.AFError):
+        s.set_state(*to_dev(torch, bad))
+    fresh = af.Solver(8, 8, 0.1, 0.1)
+    with pytest.raises(af.AFError):
+        fresh.step(0.01)
+    with pytest.raises(af.AFError):
+        fresh.set_option("lin_mode", 7)
+
+
+def test_host_transfer_roundtrip(env):
+    torch, af, _ = env
+    prob = W.fourier_smooth(30, 20, seed=2)
+    st = [np.asarray(a, dtype=np.float32) for a in W.discretise(prob)]
+    s = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, bc=prob.bc)
+    s.set_state(*st)
+    for a, b in zip(s.get_state_host(), st):
+        assert np.array_equal(a, b)
+    for a, b in zip(host(s.get_state()), st):
+        assert np.array_equal(a, b)
+
+
+def test_full_size_sampled_windows(env):
+    """The 8192^2 seeded vortex in the benchmark's launch configuration: one
+    step on the GPU; windows of 16x16 cells are recomputed by the oracle
+    (outflow ghosts at the window edge) and their central cells and nodes
+    compared; conservation and status at full size."""
+    torch, af, oracle = env
+    n = 8192
+    prob = W.shu_vortex_seeded(n)
+    dev = W.discretise_torch(prob, "cuda")
+    s = af.Solver(n, n, prob.dx, prob.dy, prob.gamma, prob.bc)
+    s.set_state(*dev)
+    t0 = s.totals()
+    dt = prob.cfl * prob.dx / s.max_speed()
+    s.step(dt)
+    assert s.status() == 0
+    t1 = s.totals()
+    mass = float(dev[0][0].double().sum()) * prob.dx * prob.dy
+    assert abs(t1[0] - t0[0]) < 1e-12 * mass
+    out = s.get_state()
+    rng = np.random.default_rng(0)
+    w, m = 16, 4
+    for _ in range(4):
+        i0, j0 = (int(x) for x in rng.integers(0, n - w, size=2))
+        win = [dev[0][:, j0:j0 + w, i0:i0 + w], dev[1][:, j0:j0 + w + 1, i0:i0 + w + 1],
+               dev[2][:, j0:j0 + w, i0:i0 + w + 1], dev[3][:, j0:j0 + w + 1, i0:i0 + w]]
+        sub = W.subproblem(prob, i0, j0, w, w)
+        o = make_oracle(oracle, sub, state=[a.cpu().double().numpy() for a in win])
+        o.step(dt)
+        ref = o.get_state()
+        got = [out[0][:, j0:j0 + w, i0:i0 + w], out[1][:, j0:j0 + w + 1, i0:i0 + w + 1],
+               out[2][:, j0:j0 + w, i0:i0 + w + 1], out[3][:, j0:j0 + w + 1, i0:i0 + w]]
+        got = [a.cpu().double().numpy()[:, m:-m, m:-m] for a in got]
+        ref = [a[:, m:-m, m:-m] for a in ref]
+        assert state_err(got, ref) < STEP_TOL, (i0, j0)
+    s.close()
