@@ -305,7 +305,7 @@ def run_ours(args):
                      "frac_at_median_clock": (pv_tflops / fp32_peak_tflops(sms, clk["sm_mhz"])
                                               if clk else None),
                      "ms_per_launch": pv_ms},
-        "roofline_flux": {"bound": "hbm", "kernel": "Simpson flux + FP64 update", "achieved": flux_gbs,
+        "roofline_flux": {"bound": "hbm", "kernel": "Simpson flux + compensated (double-word FP32) update", "achieved": flux_gbs,
                           "peak": hbm, "unit": "GB/s", "frac": flux_gbs / hbm, "peak_source": hbm_src,
                           "bytes_per_cell": FLUX_BYTES_PER_CELL, "ms_per_launch": flux_ms},
         "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},

@@ -80,15 +80,18 @@ void af_destroy(af_ctx *h);
 /* Message of the last error on this host thread (static storage). */
 const char *af_last_error(void);
 
-/* Stream all later work of the handle is enqueued on (cudaStream_t; NULL =
- * the handle's own stream). */
+/* Stream all later work of the handle is enqueued on (a cudaStream_t; 0 is
+ * the legacy default stream).  A new handle uses a non-blocking stream of
+ * its own until this is called.  Work already queued is ordered before the
+ * new stream's later work. */
 int af_set_stream(af_ctx *h, void *stream);
 int af_set_option(af_ctx *h, int key, double value);
 int af_get_option(af_ctx *h, int key, double *value);
 
 /* Copy a state from caller-owned DEVICE memory (FP32, layout above) into
  * the handle; the low words of the averages are cleared.  Ordered after
- * prior work on `stream` (may be NULL) and the handle's stream.  Returns
+ * prior work on `stream` (a cudaStream_t the caller wrote the arrays on; 0
+ * is the legacy default stream) and on the handle's stream.  Returns
  * AF_ERR_ARG for host pointers or non-matching periodic duplicates. */
 int af_set_state(af_ctx *h, const float *avg, const float *vtx, const float *xe,
                  const float *ye, void *stream);
@@ -96,7 +99,8 @@ int af_set_state(af_ctx *h, const float *avg, const float *vtx, const float *xe,
 int af_set_state_host(af_ctx *h, const float *avg, const float *vtx, const float *xe,
                       const float *ye);
 /* Copy the current state into caller-owned DEVICE memory (any pointer may
- * be NULL to skip that array).  Ordered before later work on `stream`. */
+ * be NULL to skip that array).  Ordered before later work on `stream` (0 is
+ * the legacy default stream). */
 int af_get_state(af_ctx *h, float *avg, float *vtx, float *xe, float *ye, void *stream);
 /* Same into HOST memory; synchronous. */
 int af_get_state_host(af_ctx *h, float *avg, float *vtx, float *xe, float *ye);

@@ -78,14 +78,16 @@ bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// make the handle's stream wait for `user`, or the reverse
+// make the handle's stream wait for `user`, or the reverse.  A null handle
+// is a real stream here: the legacy default stream, which does not order
+// itself with the handle's own (non-blocking) stream.
 void order_after(af_ctx *h, cudaStream_t user) {
-  if (!user || user == h->stream) return;
+  if (user == h->stream) return;
   cudaEventRecord(h->ev_in, user);
   cudaStreamWaitEvent(h->stream, h->ev_in, 0);
 }
 void order_before(af_ctx *h, cudaStream_t user) {
-  if (!user || user == h->stream) return;
+  if (user == h->stream) return;
   cudaEventRecord(h->ev_out, h->stream);
   cudaStreamWaitEvent(user, h->ev_out, 0);
 }
@@ -254,7 +256,7 @@ void af_destroy(af_ctx *h) {
 
 int af_set_stream(af_ctx *h, void *stream) {
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
-  cudaStream_t s = stream ? (cudaStream_t)stream : h->own_stream;
+  cudaStream_t s = (cudaStream_t)stream;
   if (s != h->stream) {
     DeviceGuard dg(h->device);
     order_after(h, s);  // new stream starts after everything queued so far

@@ -4,10 +4,18 @@
 // A block owns a TX x TY tile of cells.  It first integrates f (and g) in
 // time at every node of the tile's faces with Simpson weights (1, 4, 1) over
 // t^n, t^{n+1/2}, t^{n+1}, then forms each face flux once with the weights
-// (1, 4, 1) along the face and 1/36, and finally updates every cell in FP64
-// on its FP32 (hi, lo) pair.  A face on a tile boundary is computed by both
+// (1, 4, 1) along the face and 1/36, and finally updates every cell on its
+// (hi, lo) pair of FP32 words.  A face on a tile boundary is computed by both
 // tiles with the same instructions from the same inputs, so the two cells
 // sharing it see bit-identical fluxes and the update conserves to round-off.
+//
+// The compensated update uses double-word FP32 arithmetic built from the
+// error-free transformations TwoSum (Knuth) and TwoProduct via FMA: the flux
+// differences are formed exactly, multiplied by dt/dx held as a double-word
+// constant, and added to (hi, lo) with a renormalisation.  Its accuracy is
+// that of a ~48-bit significand, like an FP64 update rounded back to hi/lo,
+// without the FP64 pipe, whose throughput on this GPU is a small fraction of
+// FP32.
 #include "af_common.cuh"
 #include "af_kernels.h"
 
@@ -21,9 +29,44 @@ struct Args {
   Grid g;
   const float *__restrict__ n[3][3];  // [level][kind]
   float *hi, *lo;
-  double lamx, lamy;
+  float lxh, lxl, lyh, lyl;  // dt/dx and dt/dy as double-word FP32 (hi + lo)
   int *status;
 };
+
+// error-free transformations (exact: a + b = s + e, a * b = p + e)
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+__device__ __forceinline__ float fast_two_sum(float a, float b, float &e) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+  return s;
+}
+__device__ __forceinline__ float two_prod(float a, float b, float &e) {
+  const float p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+  return p;
+}
+// (h, l) = lam * (fr - fl) in double-word arithmetic, lam = (lh, ll)
+__device__ __forceinline__ void scaled_diff(float fr, float fl, float lh, float ll, float &h, float &l) {
+  float de;
+  const float d = two_sum(fr, -fl, de);
+  float pe;
+  const float p = two_prod(lh, d, pe);
+  pe = __fmaf_rn(lh, de, pe);
+  pe = __fmaf_rn(ll, d, pe);
+  h = fast_two_sum(p, pe, l);
+}
+// (ah, al) + (bh, bl), renormalised (TwoSum again: s may cancel below e)
+__device__ __forceinline__ void dw_add(float ah, float al, float bh, float bl, float &h, float &l) {
+  float e;
+  const float s = two_sum(ah, bh, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  h = two_sum(s, e, l);
+}
 
 // f (dir 0) or g (dir 1) of the conservative form at primitive U
 __device__ __forceinline__ void phys_flux(const float U[4], float gm1i, int dir, float F[4]) {
@@ -104,26 +147,27 @@ __global__ void __launch_bounds__(TX *TY) flux_update_kernel(Args A) {
     for (int v = 0; v < NV; v++) Gy[v][b][a] = (vg[v][b][a] + 4.0f * yg[v][b][a] + vg[v][b][a + 1]) * w36;
   }
   __syncthreads();
-  // finite-volume update in FP64 on the (hi, lo) pair
+  // finite-volume update on the (hi, lo) pair in double-word arithmetic
   const int a = threadIdx.x, b = threadIdx.y, i = i0 + a, j = j0 + b;
   if (i >= g.nx || j >= g.ny) return;
-  double q[4];
+  float qh[4];
   bool bad = false;
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     const long long e = at(g, v, i, j);
-    double x = (double)A.hi[e] + (double)A.lo[e];
-    x = x - A.lamx * ((double)Fx[v][b][a + 1] - (double)Fx[v][b][a]) -
-        A.lamy * ((double)Gy[v][b + 1][a] - (double)Gy[v][b][a]);
-    const float h = (float)x;
-    A.hi[e] = h;
-    A.lo[e] = (float)(x - (double)h);
-    q[v] = x;
-    bad |= !isfinite(x);
+    float xh, xl, yh, yl, dh, dl, nh, nl;
+    scaled_diff(Fx[v][b][a + 1], Fx[v][b][a], A.lxh, A.lxl, xh, xl);
+    scaled_diff(Gy[v][b + 1][a], Gy[v][b][a], A.lyh, A.lyl, yh, yl);
+    dw_add(xh, xl, yh, yl, dh, dl);
+    dw_add(A.hi[e], A.lo[e], -dh, -dl, nh, nl);
+    A.hi[e] = nh;
+    A.lo[e] = nl;
+    qh[v] = nh + nl;
+    bad |= !isfinite(nh);
   }
-  const double p = (double)(g.gamma - 1.0f) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / q[0]);
-  int st = bad ? ST_NONFINITE : ((q[0] > 0.0 && p > 0.0) ? 0 : ST_AVG_NONPOS);
-  if (__any_sync(__activemask(), st != 0) && st) atomicOr(A.status, st);
+  const float p = (g.gamma - 1.0f) * (qh[3] - 0.5f * (qh[1] * qh[1] + qh[2] * qh[2]) / qh[0]);
+  int st = bad ? ST_NONFINITE : ((qh[0] > 0.0f && p > 0.0f) ? 0 : ST_AVG_NONPOS);
+  if (st) atomicOr(A.status, st);
 }
 
 }  // namespace
@@ -140,8 +184,10 @@ cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &
   }
   A.hi = avg_hi;
   A.lo = avg_lo;
-  A.lamx = lamx;
-  A.lamy = lamy;
+  A.lxh = (float)lamx;
+  A.lxl = (float)(lamx - (double)A.lxh);
+  A.lyh = (float)lamy;
+  A.lyl = (float)(lamy - (double)A.lyh);
   A.status = status;
   dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY), blk(TX, TY);
   flux_update_kernel<<<grd, blk, 0, s>>>(A);

@@ -291,12 +291,17 @@ def _piecewise(states, xs, ys):
     return f
 
 
-def four_quadrant(n=64, seed=0, t_end=0.25, cfl=0.3):
+def four_quadrant(n=64, seed=0, t_end=0.25, cfl=0.3, states=None):
     """Four-quadrant Riemann data on [0,1]^2 split at (0.5,0.5), outflow
-    boundaries; rho in [0.1,1.5], p in [0.01,1.5], u, v in [-1.2,1.2]."""
-    rng = np.random.default_rng(seed)
-    st = np.stack([rng.uniform(0.1, 1.5, 4), rng.uniform(-1.2, 1.2, 4),
-                   rng.uniform(-1.2, 1.2, 4), rng.uniform(0.01, 1.5, 4)], axis=1)
+    boundaries; rho in [0.1,1.5], p in [0.01,1.5], u, v in [-1.2,1.2] drawn
+    from ``seed``, unless ``states`` (lower-left, lower-right, upper-left,
+    upper-right; each rho, u, v, p) is given."""
+    if states is None:
+        rng = np.random.default_rng(seed)
+        st = np.stack([rng.uniform(0.1, 1.5, 4), rng.uniform(-1.2, 1.2, 4),
+                       rng.uniform(-1.2, 1.2, 4), rng.uniform(0.01, 1.5, 4)], axis=1)
+    else:
+        st = np.asarray(states, dtype=np.float64)
     p = Problem(f"four_quadrant_seed{seed}", n, n, 0.0, 0.0, 1.0, 1.0, (1, 1, 1, 1),
                 _piecewise(st, 0.5, 0.5), t_end, cfl=cfl, options={"tsw": 1, "limiter": 1})
     p.states = st
