@@ -38,6 +38,27 @@ PV_FLOP_PER_CELL = 12900
 # algorithmic HBM bytes of the flux/update kernel per cell: 3 levels x 3 node
 # arrays read (144 B), averages hi/lo read and written (64 B)
 FLUX_BYTES_PER_CELL = 208
+# DRAM bytes (read + write) per cell update of the point-value stage from one
+# ncu capture (1024^2 case, scaled per cell), valid only for the kernel source
+# it was taken on (sha256 of the files below); otherwise reported as null
+PV_TRAFFIC = {"bytes_per_cell": 289.0, "profile": "profiles/pointvalue_flux_vortex1024.md",
+              "sha256": {"paper_2508_06273_gb300/csrc/af_pointvalue.cu":
+                         "40d6631865af040856b87f498f3451abd8b566f580e7a3997a4044a64fa4d14d",
+                         "paper_2508_06273_gb300/csrc/af_common.cuh":
+                         "9597639230bd1ff69574e367548646b422fab464a46deb4ee743ddf117208755"}}
+
+
+def measured_traffic(spec, cells):
+    """Per-launch DRAM bytes from a capture, or None if the source changed since."""
+    import hashlib
+
+    for rel, digest in spec["sha256"].items():
+        try:
+            if hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest() != digest:
+                return None
+        except OSError:
+            return None
+    return spec["bytes_per_cell"] * cells
 
 
 # ------------------------------------------------------------ distributed
@@ -205,7 +226,7 @@ def run_ours(args):
     from paper_2508_06273_gb300 import af
     from paper_2508_06273_gb300 import workloads as W
 
-    n = args.n
+    n = args.grid
     prob = workload(n, rank)
     cells = n * n
     dev = W.discretise_torch(prob, "cuda")
@@ -300,13 +321,15 @@ def run_ours(args):
         "status": status,
         "roofline": {"bound": "alu", "kernel": "point-value stage (3 launches: vertices, x-edges, y-edges)",
                      "achieved": pv_tflops, "peak": peak, "unit": "TFLOP/s", "frac": pv_tflops / peak,
-                     "traffic": None, "flop_per_cell": PV_FLOP_PER_CELL,
+                     "traffic": measured_traffic(PV_TRAFFIC, cells), "traffic_unit": "B per stage",
+                     "traffic_source": PV_TRAFFIC["profile"], "flop_per_cell": PV_FLOP_PER_CELL,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (max clock)",
                      "frac_at_median_clock": (pv_tflops / fp32_peak_tflops(sms, clk["sm_mhz"])
                                               if clk else None),
                      "ms_per_launch": pv_ms},
         "roofline_flux": {"bound": "hbm", "kernel": "Simpson flux + compensated (double-word FP32) update", "achieved": flux_gbs,
                           "peak": hbm, "unit": "GB/s", "frac": flux_gbs / hbm, "peak_source": hbm_src,
+                          "traffic": None,
                           "bytes_per_cell": FLUX_BYTES_PER_CELL, "ms_per_launch": flux_ms},
         "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "gpu_launches": int(sum(launches.values())),
@@ -323,7 +346,7 @@ def run_reference(args):
     rank, world, _ = dist_setup()
     if rank != 0:
         return
-    n = args.n
+    n = args.grid
     w = OracleWindow(n)
     for _ in range(args.warmup):
         w.step()
@@ -350,7 +373,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=8192, help="cells per side (default: 8192)")
+    ap.add_argument("--grid", type=int, default=8192, help="cells per side (default: 8192)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
