@@ -127,10 +127,12 @@ def test_conservation_periodic(env):
 
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1), (2, 2, 2, 2), (1, 2, 0, 0)])
 def test_constant_state_preserved(env, bc):
-    """Constant data: every face flux is the same, so the averages stay
-    bitwise unchanged.  The FP32 centre value from inverse Simpson cannot be
+    """Constant data.  The FP32 centre value from inverse Simpson cannot be
     exactly consistent with FP32 averages, so point values settle within a
-    few ulp of the constant (a bounded offset, not a drift)."""
+    few ulp of the constant (a bounded offset, not a drift).  Without walls
+    every node sees the same arithmetic, every face flux is the same and the
+    averages stay bitwise unchanged; wall nodes are linearised about their own
+    value, so next to a wall the averages move by FP32 round-off only."""
     torch, af, _ = env
     U = (0.8, 0.0 if 2 in bc else 0.3, 0.0 if 2 in bc else -0.6, 1.7)
     prob = W.Problem("const", 33, 20, 0.0, 0.0, 3.3, 2.0, bc, lambda x, y: U, 1.0)
@@ -142,7 +144,10 @@ def test_constant_state_preserved(env, bc):
         s.step(dt)
         if k in (19, 39):
             got = host(s.get_state())
-            assert np.array_equal(got[0], st[0])
+            if 2 in bc:
+                np.testing.assert_allclose(got[0], st[0], rtol=2e-6, atol=2e-6)
+            else:
+                assert np.array_equal(got[0], st[0])
             dev.append(max(np.max(np.abs(a - b) / (np.abs(b) + 1.0)) for a, b in zip(got[1:], st[1:])))
     assert s.status() == 0
     assert dev[1] < 2e-6 and dev[1] <= 1.5 * dev[0] + 1e-7, dev
