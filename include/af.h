@@ -137,6 +137,32 @@ int af_max_speed(af_ctx *h, float *out);
  * (always counted).  Synchronises; reset != 0 clears both afterwards. */
 int af_profile(af_ctx *h, double ms[4], int64_t launches[4], int reset);
 
+/* Largest ny that af_conserved_totals_noalloc accepts. */
+#define AF_TOTALS_NOALLOC_MAX_ROWS 16384
+
+/* The conserved totals of caller-owned cell averages, computed without the
+ * library allocating any memory.  The paper has no counterpart: this is for
+ * callers that cannot allocate at the point of the call, such as a
+ * time-stepping loop that must not take the device-wide synchronisation that
+ * cudaFree implies, or an application whose device memory is owned by
+ * another allocator that forbids side allocations.
+ *   avg     device [4][ny][nx] FP32 cell averages (rho, rho u, rho v, E)
+ *   avg_lo  device [4][ny][nx] FP32 low words to add, or NULL
+ *   out     device double[4]: dx dy * sum over the cells, per variable
+ *   stream  cudaStream_t to run on (0: the legacy default stream); the call
+ *           is asynchronous on it and calls no cudaMalloc or cudaFree.
+ * Scratch: a static device array of AF_TOTALS_NOALLOC_MAX_ROWS x 4 doubles
+ * (512 KiB) that every GPU loading the library holds until exit; ny above
+ * the limit is rejected with AF_ERR_ARG before anything runs.  The first
+ * call on a device looks the array's device address up (cudaGetSymbolAddress)
+ * and should come before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU race.  Nothing in it needs to start at zero
+ * (each call writes every row partial it reads).  Fixed-order summation, so
+ * a repeated call gives the same bits; it differs from af_conserved_totals
+ * only in summation order.  Returns AF_OK, AF_ERR_ARG or AF_ERR_CUDA. */
+int af_conserved_totals_noalloc(const float *avg, const float *avg_lo, int nx, int ny, double dx,
+                                double dy, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ EXPORTS = [
     "af_get_option", "af_set_state", "af_set_state_host", "af_get_state", "af_get_state_host",
     "af_get_avg_lo", "af_set_avg_lo", "af_get_half", "af_step", "af_run", "af_status",
     "af_counters", "af_conserved_totals", "af_max_speed", "af_profile",
+    "af_conserved_totals_noalloc",
 ]
 
 
@@ -65,6 +66,7 @@ def lib():
                 "af_conserved_totals": (i, [vp, C.POINTER(C.c_double)]),
                 "af_max_speed": (i, [vp, C.POINTER(C.c_float)]),
                 "af_profile": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i]),
+                "af_conserved_totals_noalloc": (i, [fp, fp, i, i, d, d, fp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)

@@ -22,6 +22,10 @@ static int cuda_fail(cudaError_t e, const char *where) {
   std::snprintf(g_err, sizeof(g_err), "%s: %s", where, cudaGetErrorString(e));
   return AF_ERR_CUDA;
 }
+int af::set_error(int code, const char *msg) {
+  std::snprintf(g_err, sizeof(g_err), "%s", msg);
+  return code;
+}
 #define CK(call, where)                         \
   do {                                          \
     cudaError_t e_ = (call);                    \

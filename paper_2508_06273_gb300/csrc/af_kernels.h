@@ -48,4 +48,7 @@ cudaError_t launch_check_dup(const float *ext, int ni, int nj, int dup_x, int du
                              cudaStream_t s);
 cudaError_t launch_zero(float *p, long long n, cudaStream_t s);
 
+// record a message for af_last_error on this host thread; returns code
+int set_error(int code, const char *msg);
+
 }  // namespace af
