@@ -31,10 +31,12 @@ if ROOT not in sys.path:
 METRIC = "cell updates/s (FP32 plain vs MLP-surrogate+fallback) at stated L1 error vs FP64 oracle"
 UNIT = "cell updates/s"
 SEED = 2508
-# FP32 operations of the point-value stage per cell update (one vertex and two
-# edge midpoints, two time levels; subsonic linearisation: 4 arcs per vertex,
-# 2 per edge), counted from the kernel source; see the design doc.
-PV_FLOP_PER_CELL = 12900
+# FP32 operations of the point-value stage per cell update, counted from the
+# kernel source (add, sub, mul = 1, fma = 2; sqrt, div and transcendental
+# calls not counted): one vertex (4 arcs) and two edge midpoints (2 arcs each)
+# at two time levels, 449 per arc and 103 per operator evaluation, plus the
+# correction term, linearisation state and the fused cell prep; see the design doc.
+PV_FLOP_PER_CELL = 8600
 # algorithmic HBM bytes of the flux/update kernel per cell: 3 levels x 3 node
 # arrays read (144 B), averages hi/lo read and written (64 B)
 FLUX_BYTES_PER_CELL = 208
@@ -319,7 +321,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "node_updates_per_s": 3 * value,
         "status": status,
-        "roofline": {"bound": "alu", "kernel": "point-value stage (3 launches: vertices, x-edges, y-edges)",
+        "roofline": {"bound": "alu", "kernel": "point-value stage (1 launch: fused cell prep, vertices and edge midpoints)",
                      "achieved": pv_tflops, "peak": peak, "unit": "TFLOP/s", "frac": pv_tflops / peak,
                      "traffic": measured_traffic(PV_TRAFFIC, cells), "traffic_unit": "B per stage",
                      "traffic_source": PV_TRAFFIC["profile"], "flop_per_cell": PV_FLOP_PER_CELL,

@@ -131,8 +131,8 @@ int af_conserved_totals(af_ctx *h, double out[4]);
  * speed in the paper's CFL number (Sec. 2); synchronises. */
 int af_max_speed(af_ctx *h, float *out);
 
-/* Per-stage device time in ms (ghost fill + cell prep, point values, flux
- * update, reductions), accumulated with CUDA events on the handle's stream
+/* Per-stage device time in ms (ghost fill, cell prep with point values,
+ * flux update, reductions), accumulated with CUDA events on the handle's stream
  * while AF_OPT_PROFILE is 1, and the number of kernels each stage launched
  * (always counted).  Synchronises; reset != 0 clears both afterwards. */
 int af_profile(af_ctx *h, double ms[4], int64_t launches[4], int reset);

@@ -39,7 +39,7 @@ struct af_ctx {
   int device;
   cudaStream_t own_stream, stream;
   float *base;  // all planes in one allocation
-  float *hi, *lo, *uc, *ub;
+  float *hi, *lo;
   NodeSet lev[3];  // 0: t^n, 1: t^{n+1/2}, 2: t^{n+1}
   // small device buffers
   void *small;
@@ -196,8 +196,8 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   h->dx = dx;
   h->dy = dy;
   cudaGetDevice(&h->device);
-  // hi, lo, U_c, Ubar and 3 levels x 3 node kinds: 13 arrays of 4 planes
-  const size_t state_bytes = 13 * (size_t)NV * (size_t)g.plane * sizeof(float);
+  // hi, lo and 3 levels x 3 node kinds: 11 arrays of 4 planes
+  const size_t state_bytes = 11 * (size_t)NV * (size_t)g.plane * sizeof(float);
   cudaError_t e = cudaMalloc(&h->base, state_bytes);
   if (e != cudaSuccess) {
     cuda_fail(e, "af_create: cudaMalloc(state)");
@@ -212,8 +212,6 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   };
   h->hi = take();
   h->lo = take();
-  h->uc = take();
-  h->ub = take();
   for (int l = 0; l < 3; l++)
     for (int k = 0; k < 3; k++) h->lev[l].k[k] = take();
   const size_t small = 64 + 64 + 64 + 64 + sizeof(double) * (TOTALS_BLOCKS * NV + NV);
@@ -443,14 +441,13 @@ static int enqueue_step(af_ctx *h, double dt) {
     cudaEventRecord(h->ev_stage[0], s);
   }
   CK(launch_ghost_fill(h->g, h->hi, h->lo, h->lev[0], s), "ghost fill");
-  CK(launch_prep(h->g, h->hi, h->lev[0], h->uc, h->ub, s), "prep");
-  h->launches[AF_STAGE_PREP] += 2;
+  h->launches[AF_STAGE_PREP] += 1;
   CK(cudaMemsetAsync(h->d_counters, 0, 4 * sizeof(unsigned long long), s), "memset counters");
   if (prof) cudaEventRecord(h->ev_stage[1], s);
-  CK(launch_pointvalue(h->g, h->lev[0], h->uc, h->ub, h->lev[1], h->lev[2], (float)dt, h->opt,
-                       h->d_status, h->d_counters, s),
+  CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->lev[1], h->lev[2], (float)dt, h->opt, h->d_status,
+                       h->d_counters, s),
      "point values");
-  h->launches[AF_STAGE_POINTVALUE] += 3;
+  h->launches[AF_STAGE_POINTVALUE] += 1;
   if (prof) {
     cudaEventRecord(h->ev_stage[2], s);
     cudaEventRecord(h->ev_stage[3], s);

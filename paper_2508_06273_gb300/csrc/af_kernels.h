@@ -22,11 +22,8 @@ struct Options {
 // ghost layers of the t^n state (cell averages hi/lo and the three node arrays)
 cudaError_t launch_ghost_fill(const Grid &g, float *avg_hi, float *avg_lo, const NodeSet &n,
                               cudaStream_t s);
-// U_c and Ubar of every cell of the ghosted range
-cudaError_t launch_prep(const Grid &g, const float *avg_hi, const NodeSet &n, float *uc, float *ub,
-                        cudaStream_t s);
-// point values at t^{n+1/2} (n1) and t^{n+1} (n2)
-cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *uc, const float *ub,
+// cell prep and point values at t^{n+1/2} (n1) and t^{n+1} (n2)
+cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
                               int *status, unsigned long long *counters, cudaStream_t s);
 // Simpson fluxes and the finite-volume update of the averages (FP64 on hi/lo)

@@ -1,5 +1,5 @@
-// af_misc.cu -- ghost cells (Sec. 4.3), cell prep (Sec. 2), reductions and
-// layout conversion kernels.
+// af_misc.cu -- ghost cells (Sec. 4.3), reductions and layout conversion
+// kernels.
 #include "af_common.cuh"
 #include "af_kernels.h"
 
@@ -65,42 +65,6 @@ __global__ void ghost_kernel(GhostArgs A) {
       if ((v == 1 && fx) || (v == 2 && fy)) x = -x;
       p[at(g, v, i, j)] = x;
     }
-  }
-}
-
-// U_c by inverting Simpson's rule for the conservative centre value, then
-// Ubar by Simpson's rule in primitive variables (Sec. 2)
-__global__ void prep_kernel(Grid g, const float *__restrict__ avg, const float *__restrict__ V,
-                            const float *__restrict__ X, const float *__restrict__ Y, float *uc,
-                            float *ub) {
-  const int i = -G + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int j = -G + (int)(blockIdx.y * blockDim.y + threadIdx.y);
-  if (i >= g.nx + G || j >= g.ny + G) return;
-  const float gm1 = g.gamma - 1.0f, gm1i = 1.0f / gm1;
-  float Qs[4] = {0, 0, 0, 0}, Us[4] = {0, 0, 0, 0};
-  const float *arr[8] = {V, V, V, V, X, X, Y, Y};
-  const int di[8] = {0, 1, 0, 1, 0, 1, 0, 0}, dj[8] = {0, 0, 1, 1, 0, 0, 0, 1};
-#pragma unroll
-  for (int n = 0; n < 8; n++) {
-    float U[4], Q[4];
-#pragma unroll
-    for (int v = 0; v < NV; v++) U[v] = __ldg(arr[n] + at(g, v, i + di[n], j + dj[n]));
-    p2c(U, gm1i, Q);
-    const float w = n < 4 ? 1.0f : 4.0f;
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-      Qs[v] += w * Q[v];
-      Us[v] += w * U[v];
-    }
-  }
-  float Qc[4], Uc[4];
-#pragma unroll
-  for (int v = 0; v < NV; v++) Qc[v] = (36.0f * __ldg(avg + at(g, v, i, j)) - Qs[v]) * 0.0625f;
-  c2p(Qc, gm1, Uc);
-#pragma unroll
-  for (int v = 0; v < NV; v++) {
-    uc[at(g, v, i, j)] = Uc[v];
-    ub[at(g, v, i, j)] = (Us[v] + 16.0f * Uc[v]) * (1.0f / 36.0f);
   }
 }
 
@@ -229,13 +193,6 @@ cudaError_t launch_ghost_fill(const Grid &g, float *avg_hi, float *avg_lo, const
   int blocks = (int)((per + 255) / 256);
   if (blocks < 1) blocks = 1;
   ghost_kernel<<<dim3(blocks, 5), 256, 0, s>>>(A);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_prep(const Grid &g, const float *avg_hi, const NodeSet &n, float *uc, float *ub,
-                        cudaStream_t s) {
-  dim3 blk(32, 8), grd((g.nx + 2 * G + 31) / 32, (g.ny + 2 * G + 7) / 8);
-  prep_kernel<<<grd, blk, 0, s>>>(g, avg_hi, n.k[VTX], n.k[XE], n.k[YE], uc, ub);
   return cudaGetLastError();
 }
 

@@ -1,14 +1,25 @@
 // af_pointvalue.cu -- point values at t^{n+1/2} and t^{n+1} (Alg. 1 steps 1
-// and 2, with eq. (Un+1/2), eq. (1stStep), Alg. 2 and Alg. 3).
+// and 2, with eq. (Un+1/2), eq. (1stStep), Alg. 2 and Alg. 3), with the cell
+// prep of Sec. 2 fused in.
 //
-// One thread per owned node.  For each time level the node's EG2 operator
-// (eq. (EG2)) is evaluated on the continuous piecewise-quadratic
-// reconstruction of the cells around the node.  The Mach-cone base is a
-// circle of radius c' tau around P' = node - u' tau; it crosses the grid
-// lines through the node at cos(theta) = u'/c' and sin(theta) = v'/c', which
-// splits it into at most four arcs, each inside one cell.  On an arc the
-// integrand is a trigonometric polynomial of degree <= 6, so every arc
-// integral is taken exactly from its end points with the recurrences
+// A block owns a TX x TY tile of cells; its threads (one per cell) each
+// update the three nodes the cell owns: the vertex (i-1/2, j-1/2), the x-edge
+// midpoint (i-1/2, j) and the y-edge midpoint (i, j-1/2).
+//
+// Prologue: for every cell of the tile and a one-cell halo the block forms
+// the cell prep (Q_c by inverting Simpson's rule, U_c = C2P(Q_c), Ubar by
+// Simpson's rule) and stores, per variable, the cell's biquadratic
+// reconstruction as monomial coefficients about the cell centre in shared
+// memory, plus Ubar.
+//
+// Node update: for each time level the node's EG2 operator (eq. (EG2)) is
+// evaluated on that reconstruction.  The Mach-cone base is a circle of radius
+// c' tau around P' = node - u' tau; it crosses the grid lines through the
+// node at cos(theta) = u'/c' and sin(theta) = v'/c', which splits it into at
+// most four arcs, each inside one cell.  On an arc a cell's biquadratic is a
+// polynomial in cos and sin of degree <= 2 in each (a Taylor shift of the
+// monomials), the EG2 weights raise that to degree <= 6, and every arc
+// integral is taken exactly from the arc's end points with the recurrences
 //   (m+n) J_mn = [cos^(m-1) sin^(n+1)] + (m-1) J_(m-2)n
 //   (m+n) J_mn = -[cos^(m+1) sin^(n-1)] + (n-1) J_m(n-2)
 // for J_mn = int cos^m sin^n dtheta.  All data are taken relative to the
@@ -25,11 +36,17 @@ constexpr float PI_F = 3.14159265358979f;
 constexpr float INV_PI = 0.318309886183791f;
 constexpr float INV_2PI = 0.159154943091895f;
 
+constexpr int TX = 32, TY = 8;               // cells per tile
+constexpr int HX = TX + 2, HY = TY + 2;      // with a one-cell halo on each side
+constexpr int CELL_F = 52;                   // floats per cell in shared memory
+// per cell: 4 variables x (9 monomial coefficients + 3 pad) = 48 floats, then Ubar (4)
+constexpr int UBAR_OFF = 48;
+constexpr int SMEM_FLOATS = HX * HY * CELL_F;
+
 struct Args {
   Grid g;
   const float *__restrict__ n0[3];
-  const float *__restrict__ uc;
-  const float *__restrict__ ub;
+  const float *__restrict__ hi;
   float *n1[3];
   float *n2[3];
   float dt;
@@ -46,49 +63,74 @@ __device__ __forceinline__ void ld4(const Args &A, const float *p, int i, int j,
   for (int v = 0; v < NV; v++) U[v] = ld(A, p, v, i, j);
 }
 
-// nodal values of variable v of cell (ci,cj): f[k][l] at local (k/2, l/2)
-__device__ __forceinline__ void cell9(const Args &A, int v, int ci, int cj, float f[3][3]) {
+// shared-memory cell record of tile-local cell (a, b), a in [0, HX), b in [0, HY)
+__device__ __forceinline__ const float *cell_rec(const float *sm, int a, int b) {
+  return sm + (b * HX + a) * CELL_F;
+}
+
+// ----------------------------------------------------------------- prologue
+// nodal values f[k][l] at local (k/2, l/2) -> coefficients m[a][b] of
+// x^a y^b with x, y in [-1/2, 1/2] about the cell centre
+__device__ __forceinline__ void to_monomial(const float f[3][3], float m[3][3]) {
+  float r[3][3];  // r[a][l]: along x for each row l
+#pragma unroll
+  for (int l = 0; l < 3; l++) {
+    r[0][l] = f[1][l];
+    r[1][l] = f[2][l] - f[0][l];
+    r[2][l] = 2.0f * (f[0][l] + f[2][l]) - 4.0f * f[1][l];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    m[a][0] = r[a][1];
+    m[a][1] = r[a][2] - r[a][0];
+    m[a][2] = 2.0f * (r[a][0] + r[a][2]) - 4.0f * r[a][1];
+  }
+}
+
+// prep of cell (ci, cj) and its record in shared memory
+__device__ __forceinline__ void build_cell(const Args &A, int ci, int cj, float *rec) {
+  const Grid &g = A.g;
+  const float gm1 = g.gamma - 1.0f, gm1i = 1.0f / gm1;
   const float *V = A.n0[VTX], *X = A.n0[XE], *Y = A.n0[YE];
-  f[0][0] = ld(A, V, v, ci, cj);
-  f[1][0] = ld(A, Y, v, ci, cj);
-  f[2][0] = ld(A, V, v, ci + 1, cj);
-  f[0][1] = ld(A, X, v, ci, cj);
-  f[1][1] = ld(A, A.uc, v, ci, cj);
-  f[2][1] = ld(A, X, v, ci + 1, cj);
-  f[0][2] = ld(A, V, v, ci, cj + 1);
-  f[1][2] = ld(A, Y, v, ci, cj + 1);
-  f[2][2] = ld(A, V, v, ci + 1, cj + 1);
+  float N[8][4];  // corners (ll, lr, ul, ur), then edges (left, right, bottom, top)
+  ld4(A, V, ci, cj, N[0]);
+  ld4(A, V, ci + 1, cj, N[1]);
+  ld4(A, V, ci, cj + 1, N[2]);
+  ld4(A, V, ci + 1, cj + 1, N[3]);
+  ld4(A, X, ci, cj, N[4]);
+  ld4(A, X, ci + 1, cj, N[5]);
+  ld4(A, Y, ci, cj, N[6]);
+  ld4(A, Y, ci, cj + 1, N[7]);
+  float Qs[4] = {0, 0, 0, 0}, Us[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int n = 0; n < 8; n++) {
+    float Q[4];
+    p2c(N[n], gm1i, Q);
+    const float w = n < 4 ? 1.0f : 4.0f;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      Qs[v] += w * Q[v];
+      Us[v] += w * N[n][v];
+    }
+  }
+  float Qc[4], Uc[4];
+#pragma unroll
+  for (int v = 0; v < NV; v++) Qc[v] = (36.0f * ld(A, A.hi, v, ci, cj) - Qs[v]) * 0.0625f;
+  c2p(Qc, gm1, Uc);
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    const float f[3][3] = {{N[0][v], N[4][v], N[2][v]}, {N[6][v], Uc[v], N[7][v]}, {N[1][v], N[5][v], N[3][v]}};
+    float m[3][3];
+    to_monomial(f, m);
+    float4 *r4 = reinterpret_cast<float4 *>(rec + 12 * v);
+    r4[0] = make_float4(m[0][0], m[0][1], m[0][2], m[1][0]);
+    r4[1] = make_float4(m[1][1], m[1][2], m[2][0], m[2][1]);
+    r4[2] = make_float4(m[2][2], 0.0f, 0.0f, 0.0f);
+    rec[UBAR_OFF + v] = (Us[v] + 16.0f * Uc[v]) * (1.0f / 36.0f);
+  }
 }
 
-// Quadratic Lagrange basis on the nodes 0, 1/2, 1 along the circle:
-// L_k(x0 + r c) = l[k][0] + l[k][1] c + l[k][2] c^2.
-__device__ __forceinline__ void lag_coef(float x0, float r, float l[3][3]) {
-  float r2 = r * r;
-  l[0][0] = (1.0f - x0) * (1.0f - 2.0f * x0);
-  l[0][1] = (4.0f * x0 - 3.0f) * r;
-  l[0][2] = 2.0f * r2;
-  l[1][0] = 4.0f * x0 * (1.0f - x0);
-  l[1][1] = (4.0f - 8.0f * x0) * r;
-  l[1][2] = -4.0f * r2;
-  l[2][0] = x0 * (2.0f * x0 - 1.0f);
-  l[2][1] = (4.0f * x0 - 1.0f) * r;
-  l[2][2] = 2.0f * r2;
-}
-
-// b[a][c] = coefficient of cos^a sin^c of the cell's biquadratic on the circle
-__device__ __forceinline__ void circle_coef(const float f[3][3], const float lx[3][3],
-                                            const float ly[3][3], float b[3][3]) {
-  float gq[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; a++)
-#pragma unroll
-    for (int l = 0; l < 3; l++) gq[a][l] = lx[0][a] * f[0][l] + lx[1][a] * f[1][l] + lx[2][a] * f[2][l];
-#pragma unroll
-  for (int a = 0; a < 3; a++)
-#pragma unroll
-    for (int c = 0; c < 3; c++) b[a][c] = gq[a][0] * ly[0][c] + gq[a][1] * ly[1][c] + gq[a][2] * ly[2][c];
-}
-
+// ----------------------------------------------------------------- arcs
 // J[m][n] = int_{t0}^{t1} cos^m sin^n for m, n <= 4, m + n <= 6
 __device__ __forceinline__ void jtable(float t0, float c0, float s0, float t1, float c1, float s1,
                                        float J[5][5]) {
@@ -169,12 +211,83 @@ __device__ __forceinline__ int crossings(float am, float bm, float t[4], float c
   return n;
 }
 
-// EG2 of the cpq reconstruction at node (K, i, j), linearised about ul,
-// relative to the reference state Kr: out = EG2[data]
+// end points, cell side and length of arc k (of narcs)
 template <int K>
-__device__ __forceinline__ void eg2(const Args &A, int i, int j, const float Kr[4], const float ul[4],
-                                    float tau, float out[4], bool &cfl_bad) {
-  const Grid &g = A.g;
+__device__ __forceinline__ void arc(int k, int ncross, float am, float bm, const float t[4],
+                                    const float c[4], const float s[4], float &t0, float &c0,
+                                    float &s0, float &t1, float &c1, float &s1, int &right,
+                                    int &top) {
+  if (ncross == 0) {  // whole circle on one side of every line
+    t0 = -PI_F; c0 = -1.0f; s0 = 0.0f;
+    t1 = PI_F; c1 = -1.0f; s1 = 0.0f;
+    right = am < 0.0f;
+    top = bm < 0.0f;
+  } else {
+    t0 = pick(t, k); c0 = pick(c, k); s0 = pick(s, k);
+    const int k1 = k + 1 < ncross ? k + 1 : 0;
+    t1 = pick(t, k1); c1 = pick(c, k1); s1 = pick(s, k1);
+    if (k1 == 0) t1 += 2.0f * PI_F;
+    float sm, cm;
+    sincosf(0.5f * (t0 + t1), &sm, &cm);
+    right = cm > am;
+    top = sm > bm;
+  }
+}
+
+// Taylor shift of q(x) = a0 + a1 x + a2 x^2 to x = x0 + r c:  q = b0 + b1 c + b2 c^2
+__device__ __forceinline__ void shift(float a0, float a1, float a2, float x0, float r, float r2,
+                                      float &b0, float &b1, float &b2) {
+  const float t = fmaf(a2, x0, a1);
+  b0 = fmaf(t, x0, a0);
+  b1 = fmaf(a2, x0, t) * r;
+  b2 = a2 * r2;
+}
+
+// coefficients b[a][e] of cos^a sin^e of (cell polynomial - K) on the circle
+// x = x0 + rx cos, y = y0 + ry sin (cell-centred units)
+__device__ __forceinline__ void circle_coef(const float *rec, float K, float x0, float y0, float rx,
+                                            float rx2, float ry, float ry2, float b[3][3]) {
+  const float4 p0 = reinterpret_cast<const float4 *>(rec)[0];
+  const float4 p1 = reinterpret_cast<const float4 *>(rec)[1];
+  const float m22 = reinterpret_cast<const float4 *>(rec)[2].x;
+  // m[a][e]: x^a y^e;  p0 = (m00, m01, m02, m10), p1 = (m11, m12, m20, m21)
+  float q[3][3];  // q[a][e]: cos^a y^e
+  shift(p0.x - K, p0.w, p1.z, x0, rx, rx2, q[0][0], q[1][0], q[2][0]);
+  shift(p0.y, p1.x, p1.w, x0, rx, rx2, q[0][1], q[1][1], q[2][1]);
+  shift(p0.z, p1.y, m22, x0, rx, rx2, q[0][2], q[1][2], q[2][2]);
+#pragma unroll
+  for (int a = 0; a < 3; a++) shift(q[a][0], q[a][1], q[a][2], y0, ry, ry2, b[a][0], b[a][1], b[a][2]);
+}
+
+// value of (cell polynomial - K) at (x0, y0)
+__device__ __forceinline__ float eval_at(const float *rec, float K, float x0, float y0) {
+  const float4 p0 = reinterpret_cast<const float4 *>(rec)[0];
+  const float4 p1 = reinterpret_cast<const float4 *>(rec)[1];
+  const float m22 = reinterpret_cast<const float4 *>(rec)[2].x;
+  const float e0 = fmaf(fmaf(p1.z, x0, p0.w), x0, p0.x - K);
+  const float e1 = fmaf(fmaf(p1.w, x0, p1.x), x0, p0.y);
+  const float e2 = fmaf(fmaf(m22, x0, p1.y), x0, p0.z);
+  return fmaf(fmaf(e2, y0, e1), y0, e0);
+}
+
+// tile-local cell indices of the cells around node (K, i, j)
+template <int K>
+__device__ __forceinline__ void arc_cell(int li, int lj, int right, int top, int &a, int &b) {
+  a = (K == YE) ? li + 1 : li + right;
+  b = (K == XE) ? lj + 1 : lj + top;
+}
+// node position in the cell-centred units of that cell, before the shift by -u' tau
+template <int K>
+__device__ __forceinline__ void node_in_cell(int right, int top, float &xn, float &yn) {
+  xn = (K == YE) ? 0.0f : (right ? -0.5f : 0.5f);
+  yn = (K == XE) ? 0.0f : (top ? -0.5f : 0.5f);
+}
+
+// EG2 of the cpq reconstruction at node (K, li, lj) of the tile, linearised
+// about ul, relative to the reference state Kr
+template <int K>
+__device__ __forceinline__ void eg2(const Grid &g, const float *sm, int li, int lj, const float Kr[4],
+                                    const float ul[4], float tau, float out[4], bool &cfl_bad) {
   if (!(ul[0] > 0.0f && ul[3] > 0.0f && tau > 0.0f)) {
 #pragma unroll
     for (int v = 0; v < NV; v++) out[v] = __int_as_float(0x7fc00000);
@@ -184,11 +297,11 @@ __device__ __forceinline__ void eg2(const Args &A, int i, int j, const float Kr[
   const float R = cp * tau, icp = 1.0f / cp;
   const float am = ul[1] * icp, bm = ul[2] * icp;
   {
-    float ex = fabsf(ul[1]) * tau + R, ey = fabsf(ul[2]) * tau + R;
-    float lx = (K == YE) ? 0.5f * g.dx : g.dx, ly = (K == XE) ? 0.5f * g.dy : g.dy;
+    const float ex = fabsf(ul[1]) * tau + R, ey = fabsf(ul[2]) * tau + R;
+    const float lx = (K == YE) ? 0.5f * g.dx : g.dx, ly = (K == XE) ? 0.5f * g.dy : g.dy;
     if (ex > lx || ey > ly) cfl_bad = true;
   }
-  const float rx = R * g.idx, ry = R * g.idy;
+  const float rx = R * g.idx, ry = R * g.idy, rx2 = rx * rx, ry2 = ry * ry;
   const float sx = ul[1] * tau * g.idx, sy = ul[2] * tau * g.idy;
 
   float t[4], c[4], s[4];
@@ -200,102 +313,60 @@ __device__ __forceinline__ void eg2(const Args &A, int i, int j, const float Kr[
   for (int k = 0; k < narcs; k++) {
     float t0, c0, s0, t1, c1, s1;
     int right, top;
-    if (ncross == 0) {  // whole circle on one side of every line
-      t0 = -PI_F; c0 = -1.0f; s0 = 0.0f;
-      t1 = PI_F; c1 = -1.0f; s1 = 0.0f;
-      right = am < 0.0f;
-      top = bm < 0.0f;
-    } else {
-      t0 = pick(t, k); c0 = pick(c, k); s0 = pick(s, k);
-      int k1 = k + 1 < ncross ? k + 1 : 0;
-      t1 = pick(t, k1); c1 = pick(c, k1); s1 = pick(s, k1);
-      if (k1 == 0) t1 += 2.0f * PI_F;
-      float sm, cm;
-      sincosf(0.5f * (t0 + t1), &sm, &cm);
-      right = cm > am;
-      top = sm > bm;
-    }
-    const int ci = (K == YE) ? i : i - 1 + right;
-    const int cj = (K == XE) ? j : j - 1 + top;
-    const float xn = (K == YE) ? 0.5f : (right ? 0.0f : 1.0f);
-    const float yn = (K == XE) ? 0.5f : (top ? 0.0f : 1.0f);
-    float lx[3][3], ly[3][3], J[5][5];
-    lag_coef(xn - sx, rx, lx);
-    lag_coef(yn - sy, ry, ly);
+    arc<K>(k, ncross, am, bm, t, c, s, t0, c0, s0, t1, c1, s1, right, top);
+    int a, b;
+    arc_cell<K>(li, lj, right, top, a, b);
+    const float *rec = cell_rec(sm, a, b);
+    float xn, yn;
+    node_in_cell<K>(right, top, xn, yn);
+    const float x0 = xn - sx, y0 = yn - sy;
+    float J[5][5];
     jtable(t0, c0, s0, t1, c1, s1, J);
-    float f[3][3], b[3][3];
+    float q[3][3];
     // pressure: int p, int p cos, int p sin
-    cell9(A, 3, ci, cj, f);
+    circle_coef(rec + 36, Kr[3], x0, y0, rx, rx2, ry, ry2, q);
 #pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int l = 0; l < 3; l++) f[a][l] -= Kr[3];
-    circle_coef(f, lx, ly, b);
-#pragma unroll
-    for (int a = 0; a < 3; a++)
+    for (int i = 0; i < 3; i++)
 #pragma unroll
       for (int e = 0; e < 3; e++) {
-        p0 += b[a][e] * J[a][e];
-        pc += b[a][e] * J[a + 1][e];
-        ps += b[a][e] * J[a][e + 1];
+        p0 = fmaf(q[i][e], J[i][e], p0);
+        pc = fmaf(q[i][e], J[i + 1][e], pc);
+        ps = fmaf(q[i][e], J[i][e + 1], ps);
       }
     // x-velocity: int u cos, int u cos^2, int u, int u sin cos
-    cell9(A, 1, ci, cj, f);
+    circle_coef(rec + 12, Kr[1], x0, y0, rx, rx2, ry, ry2, q);
 #pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int l = 0; l < 3; l++) f[a][l] -= Kr[1];
-    circle_coef(f, lx, ly, b);
-#pragma unroll
-    for (int a = 0; a < 3; a++)
+    for (int i = 0; i < 3; i++)
 #pragma unroll
       for (int e = 0; e < 3; e++) {
-        uc += b[a][e] * J[a + 1][e];
-        u2 += b[a][e] * J[a + 2][e];
-        u0 += b[a][e] * J[a][e];
-        usc += b[a][e] * J[a + 1][e + 1];
+        uc = fmaf(q[i][e], J[i + 1][e], uc);
+        u2 = fmaf(q[i][e], J[i + 2][e], u2);
+        u0 = fmaf(q[i][e], J[i][e], u0);
+        usc = fmaf(q[i][e], J[i + 1][e + 1], usc);
       }
     // y-velocity: int v sin, int v sin^2, int v, int v sin cos
-    cell9(A, 2, ci, cj, f);
+    circle_coef(rec + 24, Kr[2], x0, y0, rx, rx2, ry, ry2, q);
 #pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int l = 0; l < 3; l++) f[a][l] -= Kr[2];
-    circle_coef(f, lx, ly, b);
-#pragma unroll
-    for (int a = 0; a < 3; a++)
+    for (int i = 0; i < 3; i++)
 #pragma unroll
       for (int e = 0; e < 3; e++) {
-        vs += b[a][e] * J[a][e + 1];
-        v2 += b[a][e] * J[a][e + 2];
-        v0 += b[a][e] * J[a][e];
-        vsc += b[a][e] * J[a + 1][e + 1];
+        vs = fmaf(q[i][e], J[i][e + 1], vs);
+        v2 = fmaf(q[i][e], J[i][e + 2], v2);
+        v0 = fmaf(q[i][e], J[i][e], v0);
+        vsc = fmaf(q[i][e], J[i + 1][e + 1], vsc);
       }
   }
   // rho and p at P' (any cell whose closure holds P'; the data are continuous)
   float drP, dpP;
   {
     const int right = ul[1] < 0.0f, top = ul[2] < 0.0f;
-    const int ci = (K == YE) ? i : i - 1 + right;
-    const int cj = (K == XE) ? j : j - 1 + top;
-    const float xp = ((K == YE) ? 0.5f : (right ? 0.0f : 1.0f)) - sx;
-    const float yp = ((K == XE) ? 0.5f : (top ? 0.0f : 1.0f)) - sy;
-    float lx[3][3], ly[3][3], f[3][3];
-    lag_coef(xp, 0.0f, lx);
-    lag_coef(yp, 0.0f, ly);
-    float r = 0.0f, p = 0.0f;
-    cell9(A, 0, ci, cj, f);
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int l = 0; l < 3; l++) r += lx[a][0] * ly[l][0] * (f[a][l] - Kr[0]);
-    cell9(A, 3, ci, cj, f);
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int l = 0; l < 3; l++) p += lx[a][0] * ly[l][0] * (f[a][l] - Kr[3]);
-    drP = r;
-    dpP = p;
+    int a, b;
+    arc_cell<K>(li, lj, right, top, a, b);
+    const float *rec = cell_rec(sm, a, b);
+    float xn, yn;
+    node_in_cell<K>(right, top, xn, yn);
+    drP = eval_at(rec, Kr[0], xn - sx, yn - sy);
+    dpP = eval_at(rec + 36, Kr[3], xn - sx, yn - sy);
   }
   const float rp = ul[0], rc = rp * cp, irc = 1.0f / rc, icp2 = icp * icp;
   const float div = uc + vs;
@@ -306,11 +377,20 @@ __device__ __forceinline__ void eg2(const Args &A, int i, int j, const float Kr[
 }
 
 // ---------------------------------------------------------------- Alg. 3 parts
+// Records are read as float4 only: the record stride (52 words, 13 float4) is
+// free of bank conflicts for 128-bit accesses of consecutive cells.
+__device__ __forceinline__ float4 ubar4(const float *sm, int a, int b) {
+  return reinterpret_cast<const float4 *>(cell_rec(sm, a, b) + UBAR_OFF)[0];
+}
+// U_c (the monomial m00) of variable v of tile-local cell (a, b)
+__device__ __forceinline__ float centre(const float *sm, int a, int b, int v) {
+  return reinterpret_cast<const float4 *>(cell_rec(sm, a, b) + 12 * v)[0].x;
+}
+
 // EG1 (Sec. 3.3) on piecewise-constant primitive averages, relative to Kr
 template <int K>
-__device__ __noinline__ void eg1_pc(const Args &A, int i, int j, const float *Kr, const float *ul,
-                                    float tau, float *out) {
-  const Grid &g = A.g;
+__device__ __noinline__ void eg1_pc(const Grid &g, const float *sm, int li, int lj, const float *Kr,
+                                    const float *ul, float tau, float *out) {
   if (!(ul[0] > 0.0f && ul[3] > 0.0f && tau > 0.0f)) {
     for (int v = 0; v < NV; v++) out[v] = __int_as_float(0x7fc00000);
     return;
@@ -323,28 +403,13 @@ __device__ __noinline__ void eg1_pc(const Args &A, int i, int j, const float *Kr
   float P0 = 0, P10 = 0, P01 = 0, UC = 0, VS = 0, U20 = 0, U00 = 0, U11 = 0, V11 = 0, V02 = 0, V00 = 0;
   for (int k = 0; k < narcs; k++) {
     float t0, c0, s0, t1, c1, s1;
-    int right, top;
-    if (ncross == 0) {
-      t0 = -PI_F; c0 = -1.0f; s0 = 0.0f;
-      t1 = PI_F; c1 = -1.0f; s1 = 0.0f;
-      right = am < 0.0f;
-      top = bm < 0.0f;
-    } else {
-      t0 = pick(t, k); c0 = pick(c, k); s0 = pick(s, k);
-      int k1 = k + 1 < ncross ? k + 1 : 0;
-      t1 = pick(t, k1); c1 = pick(c, k1); s1 = pick(s, k1);
-      if (k1 == 0) t1 += 2.0f * PI_F;
-      float sm, cm;
-      sincosf(0.5f * (t0 + t1), &sm, &cm);
-      right = cm > am;
-      top = sm > bm;
-    }
-    const int ci = (K == YE) ? i : i - 1 + right;
-    const int cj = (K == XE) ? j : j - 1 + top;
-    float d[4];
-    for (int v = 0; v < NV; v++) d[v] = ld(A, A.ub, v, ci, cj) - Kr[v];
-    float J00 = t1 - t0, J10 = s1 - s0, J01 = c0 - c1;
-    float J20 = 0.5f * (c1 * s1 - c0 * s0 + J00), J02 = J00 - J20, J11 = 0.5f * (s1 * s1 - s0 * s0);
+    int right, top, a, b;
+    arc<K>(k, ncross, am, bm, t, c, s, t0, c0, s0, t1, c1, s1, right, top);
+    arc_cell<K>(li, lj, right, top, a, b);
+    const float4 w = ubar4(sm, a, b);
+    const float d[4] = {w.x - Kr[0], w.y - Kr[1], w.z - Kr[2], w.w - Kr[3]};
+    const float J00 = t1 - t0, J10 = s1 - s0, J01 = c0 - c1;
+    const float J20 = 0.5f * (c1 * s1 - c0 * s0 + J00), J02 = J00 - J20, J11 = 0.5f * (s1 * s1 - s0 * s0);
     P0 += d[3] * J00;
     P10 += d[3] * J10;
     P01 += d[3] * J01;
@@ -365,9 +430,13 @@ __device__ __noinline__ void eg1_pc(const Args &A, int i, int j, const float *Kr
     int cnt = 0;
     for (int rr = xa; rr <= xb; rr++)
       for (int tt = ya; tt <= yb; tt++) {
-        const int ci = (K == YE) ? i : i - 1 + rr;
-        const int cj = (K == XE) ? j : j - 1 + tt;
-        for (int v = 0; v < NV; v++) dP[v] += ld(A, A.ub, v, ci, cj) - Kr[v];
+        int a, b;
+        arc_cell<K>(li, lj, rr, tt, a, b);
+        const float4 w = ubar4(sm, a, b);
+        dP[0] += w.x - Kr[0];
+        dP[1] += w.y - Kr[1];
+        dP[2] += w.z - Kr[2];
+        dP[3] += w.w - Kr[3];
         cnt++;
       }
     const float ic = 1.0f / (float)cnt;
@@ -420,30 +489,32 @@ __device__ __noinline__ void lf_node(const Args &A, int i, int j, float tau, flo
 
 // averaged linearisation state, eq. (Un+1/2)
 template <int K>
-__device__ __forceinline__ void lin_avg(const Args &A, int i, int j, float ul[4]) {
+__device__ __forceinline__ void lin_avg(const float *sm, int li, int lj, float ul[4]) {
+  const int a = li + 1, b = lj + 1;
+  float4 s;
   if (K == VTX) {
-#pragma unroll
-    for (int v = 0; v < NV; v++)
-      ul[v] = 0.25f * (ld(A, A.ub, v, i - 1, j - 1) + ld(A, A.ub, v, i, j - 1) +
-                       ld(A, A.ub, v, i - 1, j) + ld(A, A.ub, v, i, j));
-  } else if (K == XE) {
-#pragma unroll
-    for (int v = 0; v < NV; v++) ul[v] = 0.5f * (ld(A, A.ub, v, i - 1, j) + ld(A, A.ub, v, i, j));
+    const float4 q0 = ubar4(sm, a - 1, b - 1), q1 = ubar4(sm, a, b - 1), q2 = ubar4(sm, a - 1, b), q3 = ubar4(sm, a, b);
+    s = make_float4(0.25f * (q0.x + q1.x + q2.x + q3.x), 0.25f * (q0.y + q1.y + q2.y + q3.y),
+                    0.25f * (q0.z + q1.z + q2.z + q3.z), 0.25f * (q0.w + q1.w + q2.w + q3.w));
   } else {
-#pragma unroll
-    for (int v = 0; v < NV; v++) ul[v] = 0.5f * (ld(A, A.ub, v, i, j - 1) + ld(A, A.ub, v, i, j));
+    const float4 q0 = (K == XE) ? ubar4(sm, a - 1, b) : ubar4(sm, a, b - 1), q1 = ubar4(sm, a, b);
+    s = make_float4(0.5f * (q0.x + q1.x), 0.5f * (q0.y + q1.y), 0.5f * (q0.z + q1.z), 0.5f * (q0.w + q1.w));
   }
+  ul[0] = s.x;
+  ul[1] = s.y;
+  ul[2] = s.z;
+  ul[3] = s.w;
 }
 
-// Alg. 3 for one time level: ho if admissible, else EG1 on pc data with the
-// averaged linearisation, else Lax-Friedrichs, else the node's t^n value
+// Alg. 3 for one time level: EG1 on pc data with the averaged linearisation,
+// else Lax-Friedrichs, else the node's t^n value (the high-order value failed)
 template <int K>
-__device__ __noinline__ void limit(const Args &A, int i, int j, float tau, const float *Kr,
-                                   float *res, unsigned *cnt) {
+__device__ __noinline__ void limit(const Args &A, const float *sm, int i, int j, int li, int lj,
+                                   float tau, const float *Kr, float *res, unsigned *cnt) {
   if (A.force_lo != 2) {
     float ul[4], lo[4];
-    lin_avg<K>(A, i, j, ul);
-    eg1_pc<K>(A, i, j, Kr, ul, tau, lo);
+    lin_avg<K>(sm, li, lj, ul);
+    eg1_pc<K>(A.g, sm, li, lj, Kr, ul, tau, lo);
     cnt[CNT_EG1]++;
     if (admissible(lo)) {
       for (int v = 0; v < NV; v++) res[v] = lo[v];
@@ -461,16 +532,17 @@ __device__ __noinline__ void limit(const Args &A, int i, int j, float tau, const
   cnt[CNT_KEPT]++;
 }
 
-// Alg. 2 indicator of vertex (i,j) from the primitive averages of its four cells
-__device__ __forceinline__ bool tsw_vertex(const Args &A, int i, int j) {
+// Alg. 2 indicator of the vertex at tile-local cell corner (a, b): the
+// primitive averages of cells (a-1, b-1), (a, b-1), (a-1, b), (a, b)
+__device__ __forceinline__ bool tsw_vertex(const float *sm, float gam, int a, int b) {
   float u[4], v[4], c[4];
-  const int ci[4] = {i - 1, i, i - 1, i}, cj[4] = {j - 1, j - 1, j, j};  // LL, RL, LU, RU
+  const int ca[4] = {a - 1, a, a - 1, a}, cb[4] = {b - 1, b - 1, b, b};  // LL, RL, LU, RU
 #pragma unroll
   for (int q = 0; q < 4; q++) {
-    float r = ld(A, A.ub, 0, ci[q], cj[q]), p = ld(A, A.ub, 3, ci[q], cj[q]);
-    u[q] = ld(A, A.ub, 1, ci[q], cj[q]);
-    v[q] = ld(A, A.ub, 2, ci[q], cj[q]);
-    c[q] = sqrtf(A.g.gamma * p / r);
+    const float4 w = ubar4(sm, ca[q], cb[q]);
+    u[q] = w.y;
+    v[q] = w.z;
+    c[q] = sqrtf(gam * w.w / w.x);
   }
   bool f = false;
 #pragma unroll
@@ -484,23 +556,25 @@ __device__ __forceinline__ bool tsw_vertex(const Args &A, int i, int j) {
 }
 
 // Corollary 1: T such that C = tau^2/2 T, from centred differences of
-// neighbouring point values or cell-centre values
+// neighbouring point values or cell-centre values (U_c = monomial m00)
 template <int K>
-__device__ __forceinline__ void correction(const Args &A, int i, int j, const float U[4], float T[4]) {
+__device__ __forceinline__ void correction(const Args &A, const float *sm, int i, int j, int li, int lj,
+                                           const float U[4], float T[4]) {
   const Grid &g = A.g;
   float Ux[4], Uy[4];
   const float *V = A.n0[VTX], *X = A.n0[XE], *Y = A.n0[YE];
+  const int a = li + 1, b = lj + 1;
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     if (K == VTX) {
       Ux[v] = (ld(A, Y, v, i, j) - ld(A, Y, v, i - 1, j)) * g.idx;
       Uy[v] = (ld(A, X, v, i, j) - ld(A, X, v, i, j - 1)) * g.idy;
     } else if (K == XE) {
-      Ux[v] = (ld(A, A.uc, v, i, j) - ld(A, A.uc, v, i - 1, j)) * g.idx;
+      Ux[v] = (centre(sm, a, b, v) - centre(sm, a - 1, b, v)) * g.idx;
       Uy[v] = (ld(A, V, v, i, j + 1) - ld(A, V, v, i, j)) * g.idy;
     } else {
       Ux[v] = (ld(A, V, v, i + 1, j) - ld(A, V, v, i, j)) * g.idx;
-      Uy[v] = (ld(A, A.uc, v, i, j) - ld(A, A.uc, v, i, j - 1)) * g.idy;
+      Uy[v] = (centre(sm, a, b, v) - centre(sm, a, b - 1, v)) * g.idy;
     }
   }
   const float r = U[0], u = U[1], v = U[2], p = U[3], gm = g.gamma, ir = 1.0f / r;
@@ -521,27 +595,24 @@ __device__ __forceinline__ void st4(float *p, const Grid &g, int i, int j, const
   for (int v = 0; v < NV; v++) p[at(g, v, i, j)] = U[v];
 }
 
+// both time levels of node (K, i, j), tile-local (li, lj)
 template <int K>
-__global__ void __launch_bounds__(128) pointvalue_kernel(Args A) {
+__device__ __forceinline__ void node_update(const Args &A, const float *sm, int i, int j, int li,
+                                            int lj, unsigned cnt[4], bool &cfl_bad, bool &nonfinite) {
   const Grid &g = A.g;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int ni = (K == YE) ? g.nx : g.nxv, nj = (K == XE) ? g.ny : g.nyv;
   if (i >= ni || j >= nj) return;
-
   float U0[4], T[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   ld4(A, A.n0[K], i, j, U0);
-  if (A.correction) correction<K>(A, i, j, U0, T);
-  unsigned cnt[4] = {0, 0, 0, 0};
-  bool cfl_bad = false, nonfinite = false;
+  if (A.correction) correction<K>(A, sm, i, j, li, lj, U0, T);
 
   float ul[4], res[4];
-  // ---- linearisation state of the half step
+  // linearisation state of the half step
   if (A.lin_mode == 1) {
 #pragma unroll
     for (int v = 0; v < NV; v++) ul[v] = U0[v];
   } else if (A.lin_mode == 2) {
-    eg2<K>(A, i, j, U0, U0, 0.25f * A.dt, ul, cfl_bad);
+    eg2<K>(g, sm, li, lj, U0, U0, 0.25f * A.dt, ul, cfl_bad);
   } else {
     const bool wx = (K != YE) && ((i == 0 && g.bc[0] == BC_REFLECTING) || (i == g.nx && g.bc[1] == BC_REFLECTING));
     const bool wy = (K != XE) && ((j == 0 && g.bc[2] == BC_REFLECTING) || (j == g.ny && g.bc[3] == BC_REFLECTING));
@@ -551,35 +622,36 @@ __global__ void __launch_bounds__(128) pointvalue_kernel(Args A) {
       if (wx) ul[1] = 0.0f;
       if (wy) ul[2] = 0.0f;
     } else {
-      lin_avg<K>(A, i, j, ul);
+      lin_avg<K>(sm, li, lj, ul);
     }
   }
-  if (A.tsw && K == VTX && tsw_vertex(A, i, j)) cnt[CNT_TSW]++;
+  bool sw = false;
+  if (A.tsw) {
+    const int a = li + 1, b = lj + 1;
+    if (K == VTX) sw = tsw_vertex(sm, g.gamma, a, b);
+    else if (K == XE) sw = tsw_vertex(sm, g.gamma, a, b) || tsw_vertex(sm, g.gamma, a, b + 1);
+    else sw = tsw_vertex(sm, g.gamma, a, b) || tsw_vertex(sm, g.gamma, a + 1, b);
+    if (K == VTX && sw) cnt[CNT_TSW]++;
+  }
 
 #pragma unroll 1
   for (int lev = 1; lev <= 2; lev++) {
     const float tau = lev == 1 ? 0.5f * A.dt : A.dt;
     if (lev == 2) {
-      bool sw = false;
-      if (A.tsw) {
-        if (K == VTX) sw = tsw_vertex(A, i, j);
-        else if (K == XE) sw = tsw_vertex(A, i, j) || tsw_vertex(A, i, j + 1);
-        else sw = tsw_vertex(A, i, j) || tsw_vertex(A, i + 1, j);
-      }
       if (sw) {
-        lin_avg<K>(A, i, j, ul);
+        lin_avg<K>(sm, li, lj, ul);
       } else {
 #pragma unroll
         for (int v = 0; v < NV; v++) ul[v] = res[v];
       }
     }
     float ho[4];
-    eg2<K>(A, i, j, U0, ul, tau, ho, cfl_bad);
+    eg2<K>(g, sm, li, lj, U0, ul, tau, ho, cfl_bad);
     const float ht = 0.5f * tau * tau;
 #pragma unroll
-    for (int v = 0; v < NV; v++) ho[v] += ht * T[v];
+    for (int v = 0; v < NV; v++) ho[v] = fmaf(ht, T[v], ho[v]);
     if (A.force_lo || (A.limiter && !admissible(ho))) {
-      limit<K>(A, i, j, tau, U0, res, cnt);
+      limit<K>(A, sm, i, j, li, lj, tau, U0, res, cnt);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; v++) res[v] = ho[v];
@@ -594,17 +666,44 @@ __global__ void __launch_bounds__(128) pointvalue_kernel(Args A) {
     if (dy_) st4(dst, g, i, g.ny, res);
     if (dx_ && dy_) st4(dst, g, g.nx, g.ny, res);
   }
+}
 
-  int st = (cfl_bad ? ST_CFL : 0) | (nonfinite ? ST_NONFINITE : 0) | (cnt[CNT_KEPT] ? ST_KEPT : 0);
+// prologue: the block builds the records of its (TX+2) x (TY+2) cells; only
+// cells -1..nx, -1..ny can be referenced by owned nodes, the others are skipped
+__device__ __forceinline__ void tile_prologue(const Args &A, float *sm, int i0, int j0, int tid) {
+  for (int k = tid; k < HX * HY; k += TX * TY) {
+    const int a = k % HX, b = k / HX, ci = i0 - 1 + a, cj = j0 - 1 + b;
+    if (ci <= A.g.nx && cj <= A.g.ny) build_cell(A, ci, cj, sm + k * CELL_F);
+  }
+}
+
+// node updates of the cell (i0 + tx, j0 + ty)
+__device__ __forceinline__ void tile_nodes(const Args &A, const float *sm, int i0, int j0, int tx, int ty) {
+  unsigned cnt[4] = {0, 0, 0, 0};
+  bool cfl_bad = false, nonfinite = false;
+  const int i = i0 + tx, j = j0 + ty;
+  node_update<VTX>(A, sm, i, j, tx, ty, cnt, cfl_bad, nonfinite);
+  node_update<XE>(A, sm, i, j, tx, ty, cnt, cfl_bad, nonfinite);
+  node_update<YE>(A, sm, i, j, tx, ty, cnt, cfl_bad, nonfinite);
+  const int st = (cfl_bad ? ST_CFL : 0) | (nonfinite ? ST_NONFINITE : 0) | (cnt[CNT_KEPT] ? ST_KEPT : 0);
   if (st) atomicOr(A.status, st);
 #pragma unroll
   for (int k = 0; k < 4; k++)
     if (cnt[k]) atomicAdd(&A.counters[k], (unsigned long long)cnt[k]);
 }
 
+__global__ void __launch_bounds__(TX *TY) pointvalue_kernel(Args A) {
+  extern __shared__ float4 smem4[];
+  float *sm = reinterpret_cast<float *>(smem4);
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  tile_prologue(A, sm, i0, j0, threadIdx.y * TX + threadIdx.x);
+  __syncthreads();
+  tile_nodes(A, sm, i0, j0, threadIdx.x, threadIdx.y);
+}
+
 }  // namespace
 
-cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *uc, const float *ub,
+cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
                               int *status, unsigned long long *counters, cudaStream_t s) {
   Args A;
@@ -614,8 +713,7 @@ cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *uc,
     A.n1[k] = n1.k[k];
     A.n2[k] = n2.k[k];
   }
-  A.uc = uc;
-  A.ub = ub;
+  A.hi = avg_hi;
   A.dt = dt;
   A.lin_mode = o.lin_mode;
   A.tsw = o.tsw;
@@ -624,12 +722,13 @@ cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *uc,
   A.force_lo = o.force_lo;
   A.status = status;
   A.counters = counters;
-  dim3 blk(32, 4);
-  dim3 gv((g.nxv + 31) / 32, (g.nyv + 3) / 4), gx((g.nxv + 31) / 32, (g.ny + 3) / 4),
-      gy((g.nx + 31) / 32, (g.nyv + 3) / 4);
-  pointvalue_kernel<VTX><<<gv, blk, 0, s>>>(A);
-  pointvalue_kernel<XE><<<gx, blk, 0, s>>>(A);
-  pointvalue_kernel<YE><<<gy, blk, 0, s>>>(A);
+  const int bytes = SMEM_FLOATS * (int)sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(pointvalue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  // tiles cover the owned nodes: up to nxv x nyv (vertex lines n + 1 on a
+  // non-periodic axis)
+  dim3 grd((g.nxv + TX - 1) / TX, (g.nyv + TY - 1) / TY), blk(TX, TY);
+  pointvalue_kernel<<<grd, blk, bytes, s>>>(A);
   return cudaGetLastError();
 }
 
