@@ -54,8 +54,10 @@ enum {
   AF_ST_CFL = 1,        /* a Mach-cone base left the node's cell block: dt too large */
   AF_ST_AVG_NONPOS = 2, /* a cell average with rho <= 0 or p <= 0 after the update */
   AF_ST_NONFINITE = 4,  /* a non-finite point value or cell average */
-  AF_ST_KEPT = 8        /* Alg. 3's Lax-Friedrichs value was not admissible in FP32;
+  AF_ST_KEPT = 8,       /* Alg. 3's Lax-Friedrichs value was not admissible in FP32;
                            the node kept its old value */
+  AF_ST_TIMEOUT = 16    /* a block's wait for its staged tile timed out; the tile was
+                           not updated (the step's result is invalid) */
 };
 
 /* option keys for af_set_option */

@@ -41,6 +41,11 @@ struct af_ctx {
   float *base;  // all planes in one allocation
   float *hi, *lo;
   NodeSet lev[3];  // 0: t^n, 1: t^{n+1/2}, 2: t^{n+1}
+  // TMA descriptors for t^n held in either of the two buffers that swap
+  // roles each step; tmap_cur selects the one now holding t^n
+  TileMaps tmaps[2];
+  NodeSet tbuf[2];
+  int tmap_cur;
   // small device buffers
   void *small;
   int *d_status, *d_bad;
@@ -214,6 +219,18 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   h->lo = take();
   for (int l = 0; l < 3; l++)
     for (int k = 0; k < 3; k++) h->lev[l].k[k] = take();
+  h->tbuf[0] = h->lev[0];
+  h->tbuf[1] = h->lev[2];
+  h->tmap_cur = 0;
+  for (int b = 0; b < 2; b++) {
+    cudaError_t te = make_tile_maps(g, h->tbuf[b].k[VTX], h->tbuf[b].k[XE], h->tbuf[b].k[YE], h->hi, &h->tmaps[b]);
+    if (te != cudaSuccess) {
+      cuda_fail(te, "af_create: TMA descriptors");
+      cudaFree(h->base);
+      delete h;
+      return nullptr;
+    }
+  }
   const size_t small = 64 + 64 + 64 + 64 + sizeof(double) * (TOTALS_BLOCKS * NV + NV);
   e = cudaMalloc(&h->small, small);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
@@ -444,8 +461,8 @@ static int enqueue_step(af_ctx *h, double dt) {
   h->launches[AF_STAGE_PREP] += 1;
   CK(cudaMemsetAsync(h->d_counters, 0, 4 * sizeof(unsigned long long), s), "memset counters");
   if (prof) cudaEventRecord(h->ev_stage[1], s);
-  CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->lev[1], h->lev[2], (float)dt, h->opt, h->d_status,
-                       h->d_counters, s),
+  CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
+                       h->opt, h->d_status, h->d_counters, s),
      "point values");
   h->launches[AF_STAGE_POINTVALUE] += 1;
   if (prof) {
@@ -463,6 +480,7 @@ static int enqueue_step(af_ctx *h, double dt) {
   NodeSet t = h->lev[0];
   h->lev[0] = h->lev[2];
   h->lev[2] = t;
+  h->tmap_cur ^= 1;
   return AF_OK;
 }
 

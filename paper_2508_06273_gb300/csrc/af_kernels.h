@@ -1,5 +1,7 @@
 // af_kernels.h -- host-side launchers of the library's CUDA kernels.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "af_common.cuh"
@@ -22,8 +24,14 @@ struct Options {
 // ghost layers of the t^n state (cell averages hi/lo and the three node arrays)
 cudaError_t launch_ghost_fill(const Grid &g, float *avg_hi, float *avg_lo, const NodeSet &n,
                               cudaStream_t s);
+// TMA descriptors of the t^n node arrays and the cell averages (one set per
+// physical buffer that can hold t^n)
+struct TileMaps {
+  CUtensorMap vtx, xe, ye, avg;
+};
+cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, float *avg, TileMaps *out);
 // cell prep and point values at t^{n+1/2} (n1) and t^{n+1} (n2)
-cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi,
+cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
                               int *status, unsigned long long *counters, cudaStream_t s);
 // Simpson fluxes and the finite-volume update of the averages (FP64 on hi/lo)

@@ -41,7 +41,19 @@ constexpr int HX = TX + 2, HY = TY + 2;      // with a one-cell halo on each sid
 constexpr int CELL_F = 52;                   // floats per cell in shared memory
 // per cell: 4 variables x (9 monomial coefficients + 3 pad) = 48 floats, then Ubar (4)
 constexpr int UBAR_OFF = 48;
-constexpr int SMEM_FLOATS = HX * HY * CELL_F;
+constexpr int REC_FLOATS = HX * HY * CELL_F;
+// Raw t^n data of a tile, staged by TMA: for each of the node arrays (vertex,
+// x-edge, y-edge) and the cell averages a box of RAW_W x RAW_H points x 4
+// variables.  The box starts 4 points left of the first halo point so that
+// its x coordinate is a multiple of 4 floats (16 bytes), and 1 row below.
+constexpr int RAW_W = TX + 8, RAW_H = TY + 3;
+constexpr int RAW_ARR = RAW_W * RAW_H * NV;  // floats per array
+constexpr int RAW_FLOATS = 4 * RAW_ARR;
+constexpr unsigned RAW_BYTES = RAW_FLOATS * 4u;
+constexpr int SMEM_BYTES = (RAW_FLOATS + REC_FLOATS) * 4 + 128;  // + alignment slack
+enum { RAW_VTX = 0, RAW_XE = 1, RAW_YE = 2, RAW_AVG = 3 };
+// bound on the mbarrier wait (try_wait suspends in hardware between polls)
+constexpr unsigned WAIT_LIMIT = 1u << 22;
 
 struct Args {
   Grid g;
@@ -54,6 +66,16 @@ struct Args {
   int *status;
   unsigned long long *counters;
 };
+
+// staged t^n value of array arr, variable v, at grid index (i, j), for the
+// tile with origin (i0, j0)
+__device__ __forceinline__ float raw_at(const float *raw, int arr, int v, int i, int j, int i0, int j0) {
+  return raw[((arr * NV + v) * RAW_H + (j - j0 + 1)) * RAW_W + (i - i0 + 4)];
+}
+__device__ __forceinline__ void raw4(const float *raw, int arr, int i, int j, int i0, int j0, float U[4]) {
+#pragma unroll
+  for (int v = 0; v < NV; v++) U[v] = raw_at(raw, arr, v, i, j, i0, j0);
+}
 
 __device__ __forceinline__ float ld(const Args &A, const float *p, int v, int i, int j) {
   return __ldg(p + at(A.g, v, i, j));
@@ -87,20 +109,19 @@ __device__ __forceinline__ void to_monomial(const float f[3][3], float m[3][3]) 
   }
 }
 
-// prep of cell (ci, cj) and its record in shared memory
-__device__ __forceinline__ void build_cell(const Args &A, int ci, int cj, float *rec) {
-  const Grid &g = A.g;
+// prep of cell (ci, cj) and its record in shared memory, from the staged tile
+__device__ __forceinline__ void build_cell(const Grid &g, const float *raw, int i0, int j0, int ci, int cj,
+                                           float *rec) {
   const float gm1 = g.gamma - 1.0f, gm1i = 1.0f / gm1;
-  const float *V = A.n0[VTX], *X = A.n0[XE], *Y = A.n0[YE];
   float N[8][4];  // corners (ll, lr, ul, ur), then edges (left, right, bottom, top)
-  ld4(A, V, ci, cj, N[0]);
-  ld4(A, V, ci + 1, cj, N[1]);
-  ld4(A, V, ci, cj + 1, N[2]);
-  ld4(A, V, ci + 1, cj + 1, N[3]);
-  ld4(A, X, ci, cj, N[4]);
-  ld4(A, X, ci + 1, cj, N[5]);
-  ld4(A, Y, ci, cj, N[6]);
-  ld4(A, Y, ci, cj + 1, N[7]);
+  raw4(raw, RAW_VTX, ci, cj, i0, j0, N[0]);
+  raw4(raw, RAW_VTX, ci + 1, cj, i0, j0, N[1]);
+  raw4(raw, RAW_VTX, ci, cj + 1, i0, j0, N[2]);
+  raw4(raw, RAW_VTX, ci + 1, cj + 1, i0, j0, N[3]);
+  raw4(raw, RAW_XE, ci, cj, i0, j0, N[4]);
+  raw4(raw, RAW_XE, ci + 1, cj, i0, j0, N[5]);
+  raw4(raw, RAW_YE, ci, cj, i0, j0, N[6]);
+  raw4(raw, RAW_YE, ci, cj + 1, i0, j0, N[7]);
   float Qs[4] = {0, 0, 0, 0}, Us[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int n = 0; n < 8; n++) {
@@ -115,7 +136,7 @@ __device__ __forceinline__ void build_cell(const Args &A, int ci, int cj, float 
   }
   float Qc[4], Uc[4];
 #pragma unroll
-  for (int v = 0; v < NV; v++) Qc[v] = (36.0f * ld(A, A.hi, v, ci, cj) - Qs[v]) * 0.0625f;
+  for (int v = 0; v < NV; v++) Qc[v] = (36.0f * raw_at(raw, RAW_AVG, v, ci, cj, i0, j0) - Qs[v]) * 0.0625f;
   c2p(Qc, gm1, Uc);
 #pragma unroll
   for (int v = 0; v < NV; v++) {
@@ -130,7 +151,6 @@ __device__ __forceinline__ void build_cell(const Args &A, int ci, int cj, float 
   }
 }
 
-// ----------------------------------------------------------------- arcs
 // J[m][n] = int_{t0}^{t1} cos^m sin^n for m, n <= 4, m + n <= 6
 __device__ __forceinline__ void jtable(float t0, float c0, float s0, float t1, float c1, float s1,
                                        float J[5][5]) {
@@ -179,10 +199,15 @@ __device__ __forceinline__ void cswap(float t[4], float c[4], float s[4], int a,
 }
 
 // Crossings of the circle with the grid lines through the node, sorted by
-// angle in (-pi, pi]; am = u'/c' (vertical line), bm = v'/c' (horizontal line).
+// angle in (-pi, pi]; am = u'/c' (vertical line), bm = v'/c' (horizontal
+// line).  Also returns al = acos(am) (0 when the vertical line is not
+// crossed) and be = asin(bm) (when the horizontal line is crossed).
 template <int K>
-__device__ __forceinline__ int crossings(float am, float bm, float t[4], float c[4], float s[4]) {
+__device__ __forceinline__ int crossings(float am, float bm, float t[4], float c[4], float s[4],
+                                         float &al, float &be) {
   int n = 0;
+  al = 0.0f;
+  be = 0.0f;
 #pragma unroll
   for (int k = 0; k < 4; k++) {
     t[k] = 1e30f;
@@ -190,13 +215,15 @@ __device__ __forceinline__ int crossings(float am, float bm, float t[4], float c
     s[k] = 0.0f;
   }
   if (K != YE && fabsf(am) < 1.0f) {
-    float al = acosf(am), sq = sqrtf(fmaxf(0.0f, 1.0f - am * am));
+    al = acosf(am);
+    const float sq = sqrtf(fmaxf(0.0f, 1.0f - am * am));
     t[0] = al; c[0] = am; s[0] = sq;
     t[1] = -al; c[1] = am; s[1] = -sq;
     n = 2;
   }
   if (K != XE && fabsf(bm) < 1.0f) {
-    float be = asinf(bm), sq = sqrtf(fmaxf(0.0f, 1.0f - bm * bm));
+    be = asinf(bm);
+    const float sq = sqrtf(fmaxf(0.0f, 1.0f - bm * bm));
     float t2 = PI_F - be;
     if (t2 > PI_F) t2 -= 2.0f * PI_F;
     t[2] = be; c[2] = sq; s[2] = bm;
@@ -211,27 +238,37 @@ __device__ __forceinline__ int crossings(float am, float bm, float t[4], float c
   return n;
 }
 
-// end points, cell side and length of arc k (of narcs)
+// angle d - 2 pi floor(d / 2 pi), in [0, 2 pi)
+__device__ __forceinline__ float wrap_2pi(float d) {
+  return fmaf(-2.0f * PI_F, floorf(d * (0.5f / PI_F)), d);
+}
+
+// End points of arc k (of narcs) and the side of each line it lies on.  The
+// circle point at angle theta is right of the vertical line iff theta is in
+// (-al, al) and above the horizontal line iff theta is in (be, pi - be), mod
+// 2 pi; the test is made at the arc's mid angle, which lies strictly inside
+// one cell for every arc of positive length.
 template <int K>
-__device__ __forceinline__ void arc(int k, int ncross, float am, float bm, const float t[4],
-                                    const float c[4], const float s[4], float &t0, float &c0,
-                                    float &s0, float &t1, float &c1, float &s1, int &right,
+__device__ __forceinline__ void arc(int k, int ncross, float am, float bm, float al, float be,
+                                    const float t[4], const float c[4], const float s[4], float &t0,
+                                    float &c0, float &s0, float &t1, float &c1, float &s1, int &right,
                                     int &top) {
   if (ncross == 0) {  // whole circle on one side of every line
     t0 = -PI_F; c0 = -1.0f; s0 = 0.0f;
     t1 = PI_F; c1 = -1.0f; s1 = 0.0f;
     right = am < 0.0f;
     top = bm < 0.0f;
-  } else {
-    t0 = pick(t, k); c0 = pick(c, k); s0 = pick(s, k);
-    const int k1 = k + 1 < ncross ? k + 1 : 0;
-    t1 = pick(t, k1); c1 = pick(c, k1); s1 = pick(s, k1);
-    if (k1 == 0) t1 += 2.0f * PI_F;
-    float sm, cm;
-    sincosf(0.5f * (t0 + t1), &sm, &cm);
-    right = cm > am;
-    top = sm > bm;
+    return;
   }
+  t0 = pick(t, k); c0 = pick(c, k); s0 = pick(s, k);
+  const int k1 = k + 1 < ncross ? k + 1 : 0;
+  t1 = pick(t, k1); c1 = pick(c, k1); s1 = pick(s, k1);
+  if (k1 == 0) t1 += 2.0f * PI_F;
+  const float mid = 0.5f * (t0 + t1);
+  if (K != YE) right = fabsf(am) < 1.0f ? (wrap_2pi(mid + al) < 2.0f * al) : (am < 0.0f);
+  else right = 0;
+  if (K != XE) top = fabsf(bm) < 1.0f ? (wrap_2pi(mid - be) < PI_F - 2.0f * be) : (bm < 0.0f);
+  else top = 0;
 }
 
 // Taylor shift of q(x) = a0 + a1 x + a2 x^2 to x = x0 + r c:  q = b0 + b1 c + b2 c^2
@@ -304,8 +341,8 @@ __device__ __forceinline__ void eg2(const Grid &g, const float *sm, int li, int 
   const float rx = R * g.idx, ry = R * g.idy, rx2 = rx * rx, ry2 = ry * ry;
   const float sx = ul[1] * tau * g.idx, sy = ul[2] * tau * g.idy;
 
-  float t[4], c[4], s[4];
-  const int ncross = crossings<K>(am, bm, t, c, s);
+  float t[4], c[4], s[4], al, be;
+  const int ncross = crossings<K>(am, bm, t, c, s, al, be);
   const int narcs = ncross > 0 ? ncross : 1;
 
   float p0 = 0, pc = 0, ps = 0, uc = 0, u2 = 0, u0 = 0, usc = 0, vs = 0, v2 = 0, v0 = 0, vsc = 0;
@@ -313,7 +350,7 @@ __device__ __forceinline__ void eg2(const Grid &g, const float *sm, int li, int 
   for (int k = 0; k < narcs; k++) {
     float t0, c0, s0, t1, c1, s1;
     int right, top;
-    arc<K>(k, ncross, am, bm, t, c, s, t0, c0, s0, t1, c1, s1, right, top);
+    arc<K>(k, ncross, am, bm, al, be, t, c, s, t0, c0, s0, t1, c1, s1, right, top);
     int a, b;
     arc_cell<K>(li, lj, right, top, a, b);
     const float *rec = cell_rec(sm, a, b);
@@ -397,14 +434,14 @@ __device__ __noinline__ void eg1_pc(const Grid &g, const float *sm, int li, int 
   }
   const float cp = sqrtf(g.gamma * ul[3] / ul[0]), icp = 1.0f / cp;
   const float am = ul[1] * icp, bm = ul[2] * icp;
-  float t[4], c[4], s[4];
-  const int ncross = crossings<K>(am, bm, t, c, s);
+  float t[4], c[4], s[4], al, be;
+  const int ncross = crossings<K>(am, bm, t, c, s, al, be);
   const int narcs = ncross > 0 ? ncross : 1;
   float P0 = 0, P10 = 0, P01 = 0, UC = 0, VS = 0, U20 = 0, U00 = 0, U11 = 0, V11 = 0, V02 = 0, V00 = 0;
   for (int k = 0; k < narcs; k++) {
     float t0, c0, s0, t1, c1, s1;
     int right, top, a, b;
-    arc<K>(k, ncross, am, bm, t, c, s, t0, c0, s0, t1, c1, s1, right, top);
+    arc<K>(k, ncross, am, bm, al, be, t, c, s, t0, c0, s0, t1, c1, s1, right, top);
     arc_cell<K>(li, lj, right, top, a, b);
     const float4 w = ubar4(sm, a, b);
     const float d[4] = {w.x - Kr[0], w.y - Kr[1], w.z - Kr[2], w.w - Kr[3]};
@@ -558,22 +595,20 @@ __device__ __forceinline__ bool tsw_vertex(const float *sm, float gam, int a, in
 // Corollary 1: T such that C = tau^2/2 T, from centred differences of
 // neighbouring point values or cell-centre values (U_c = monomial m00)
 template <int K>
-__device__ __forceinline__ void correction(const Args &A, const float *sm, int i, int j, int li, int lj,
-                                           const float U[4], float T[4]) {
-  const Grid &g = A.g;
+__device__ __forceinline__ void correction(const Grid &g, const float *sm, const float *raw, int i, int j,
+                                           int i0, int j0, const float U[4], float T[4]) {
   float Ux[4], Uy[4];
-  const float *V = A.n0[VTX], *X = A.n0[XE], *Y = A.n0[YE];
-  const int a = li + 1, b = lj + 1;
+  const int a = i - i0 + 1, b = j - j0 + 1;
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     if (K == VTX) {
-      Ux[v] = (ld(A, Y, v, i, j) - ld(A, Y, v, i - 1, j)) * g.idx;
-      Uy[v] = (ld(A, X, v, i, j) - ld(A, X, v, i, j - 1)) * g.idy;
+      Ux[v] = (raw_at(raw, RAW_YE, v, i, j, i0, j0) - raw_at(raw, RAW_YE, v, i - 1, j, i0, j0)) * g.idx;
+      Uy[v] = (raw_at(raw, RAW_XE, v, i, j, i0, j0) - raw_at(raw, RAW_XE, v, i, j - 1, i0, j0)) * g.idy;
     } else if (K == XE) {
       Ux[v] = (centre(sm, a, b, v) - centre(sm, a - 1, b, v)) * g.idx;
-      Uy[v] = (ld(A, V, v, i, j + 1) - ld(A, V, v, i, j)) * g.idy;
+      Uy[v] = (raw_at(raw, RAW_VTX, v, i, j + 1, i0, j0) - raw_at(raw, RAW_VTX, v, i, j, i0, j0)) * g.idy;
     } else {
-      Ux[v] = (ld(A, V, v, i + 1, j) - ld(A, V, v, i, j)) * g.idx;
+      Ux[v] = (raw_at(raw, RAW_VTX, v, i + 1, j, i0, j0) - raw_at(raw, RAW_VTX, v, i, j, i0, j0)) * g.idx;
       Uy[v] = (centre(sm, a, b, v) - centre(sm, a, b - 1, v)) * g.idy;
     }
   }
@@ -597,14 +632,15 @@ __device__ __forceinline__ void st4(float *p, const Grid &g, int i, int j, const
 
 // both time levels of node (K, i, j), tile-local (li, lj)
 template <int K>
-__device__ __forceinline__ void node_update(const Args &A, const float *sm, int i, int j, int li,
-                                            int lj, unsigned cnt[4], bool &cfl_bad, bool &nonfinite) {
+__device__ __forceinline__ void node_update(const Args &A, const float *sm, const float *raw, int i0, int j0,
+                                            int i, int j, int li, int lj, unsigned cnt[4], bool &cfl_bad,
+                                            bool &nonfinite) {
   const Grid &g = A.g;
   const int ni = (K == YE) ? g.nx : g.nxv, nj = (K == XE) ? g.ny : g.nyv;
   if (i >= ni || j >= nj) return;
   float U0[4], T[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  ld4(A, A.n0[K], i, j, U0);
-  if (A.correction) correction<K>(A, sm, i, j, li, lj, U0, T);
+  raw4(raw, K == VTX ? RAW_VTX : (K == XE ? RAW_XE : RAW_YE), i, j, i0, j0, U0);
+  if (A.correction) correction<K>(g, sm, raw, i, j, i0, j0, U0, T);
 
   float ul[4], res[4];
   // linearisation state of the half step
@@ -670,21 +706,23 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, int 
 
 // prologue: the block builds the records of its (TX+2) x (TY+2) cells; only
 // cells -1..nx, -1..ny can be referenced by owned nodes, the others are skipped
-__device__ __forceinline__ void tile_prologue(const Args &A, float *sm, int i0, int j0, int tid) {
+__device__ __forceinline__ void tile_prologue(const Args &A, const float *raw, float *sm, int i0, int j0,
+                                              int tid) {
   for (int k = tid; k < HX * HY; k += TX * TY) {
     const int a = k % HX, b = k / HX, ci = i0 - 1 + a, cj = j0 - 1 + b;
-    if (ci <= A.g.nx && cj <= A.g.ny) build_cell(A, ci, cj, sm + k * CELL_F);
+    if (ci <= A.g.nx && cj <= A.g.ny) build_cell(A.g, raw, i0, j0, ci, cj, sm + k * CELL_F);
   }
 }
 
 // node updates of the cell (i0 + tx, j0 + ty)
-__device__ __forceinline__ void tile_nodes(const Args &A, const float *sm, int i0, int j0, int tx, int ty) {
+__device__ __forceinline__ void tile_nodes(const Args &A, const float *sm, const float *raw, int i0, int j0,
+                                           int tx, int ty) {
   unsigned cnt[4] = {0, 0, 0, 0};
   bool cfl_bad = false, nonfinite = false;
   const int i = i0 + tx, j = j0 + ty;
-  node_update<VTX>(A, sm, i, j, tx, ty, cnt, cfl_bad, nonfinite);
-  node_update<XE>(A, sm, i, j, tx, ty, cnt, cfl_bad, nonfinite);
-  node_update<YE>(A, sm, i, j, tx, ty, cnt, cfl_bad, nonfinite);
+  node_update<VTX>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
+  node_update<XE>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
+  node_update<YE>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
   const int st = (cfl_bad ? ST_CFL : 0) | (nonfinite ? ST_NONFINITE : 0) | (cnt[CNT_KEPT] ? ST_KEPT : 0);
   if (st) atomicOr(A.status, st);
 #pragma unroll
@@ -692,18 +730,102 @@ __device__ __forceinline__ void tile_nodes(const Args &A, const float *sm, int i
     if (cnt[k]) atomicAdd(&A.counters[k], (unsigned long long)cnt[k]);
 }
 
-__global__ void __launch_bounds__(TX *TY) pointvalue_kernel(Args A) {
+// ---------------------------------------------------------------- TMA staging
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// one thread: arm the barrier with the byte count and issue the four box loads
+__device__ __forceinline__ void tile_fetch(const TileMaps &T, float *raw, unsigned long long *bar, int i0,
+                                           int j0) {
+  const unsigned b = smem_addr(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(RAW_BYTES) : "memory");
+  // box origin: column i0 (grid index i0 - 4), row j0 + 1 (grid index j0 - 1), variable 0
+  const int x = i0, y = j0 + OY - 1;
+  const CUtensorMap *maps[4] = {&T.vtx, &T.xe, &T.ye, &T.avg};
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(raw + a * RAW_ARR)),
+        "l"(reinterpret_cast<unsigned long long>(maps[a])), "r"(x), "r"(y), "r"(0), "r"(b)
+        : "memory");
+  }
+}
+
+// bounded wait for phase 0 of the barrier; false on time-out
+__device__ __forceinline__ bool tile_wait(unsigned long long *bar) {
+  const unsigned b = smem_addr(bar);
+  for (unsigned it = 0; it < WAIT_LIMIT; it++) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(b)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(TX *TY) pointvalue_kernel(Args A, const __grid_constant__ TileMaps T) {
   extern __shared__ float4 smem4[];
-  float *sm = reinterpret_cast<float *>(smem4);
+  __shared__ alignas(8) unsigned long long bar;
+  // TMA destinations must start on 128-byte boundaries
+  float *raw = reinterpret_cast<float *>((reinterpret_cast<size_t>(smem4) + 127) & ~size_t(127));
+  float *sm = raw + RAW_FLOATS;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  tile_prologue(A, sm, i0, j0, threadIdx.y * TX + threadIdx.x);
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  if (tid == 0) tile_fetch(T, raw, &bar, i0, j0);
   __syncthreads();
-  tile_nodes(A, sm, i0, j0, threadIdx.x, threadIdx.y);
+  if (!tile_wait(&bar)) {
+    // the copy did not land in time: report it, give it one more bounded
+    // wait so that nothing is still writing this block's shared memory, and
+    // leave the tile alone
+    if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
+    tile_wait(&bar);
+    return;
+  }
+  tile_prologue(A, raw, sm, i0, j0, tid);
+  __syncthreads();
+  tile_nodes(A, sm, raw, i0, j0, threadIdx.x, threadIdx.y);
 }
 
 }  // namespace
 
-cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi,
+cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, float *avg, TileMaps *out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorSymbolNotFound;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  // planes of P x H floats, 4 variables: 3-D tensors (x, row, variable)
+  const cuuint64_t dims[3] = {(cuuint64_t)g.P, (cuuint64_t)g.H, (cuuint64_t)NV};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.P * 4u, (cuuint64_t)g.plane * 4u};
+  const cuuint32_t box[3] = {(cuuint32_t)RAW_W, (cuuint32_t)RAW_H, (cuuint32_t)NV};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  float *base[4] = {vtx, xe, ye, avg};
+  CUtensorMap *dst[4] = {&out->vtx, &out->xe, &out->ye, &out->avg};
+  for (int k = 0; k < 4; k++) {
+    if ((reinterpret_cast<size_t>(base[k]) & 15) != 0 || (strides[0] & 15) != 0 || (strides[1] & 15) != 0 ||
+        (RAW_W * 4) % 16 != 0)
+      return cudaErrorInvalidValue;
+    CUresult r = encode(dst[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base[k], dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
                               int *status, unsigned long long *counters, cudaStream_t s) {
   Args A;
@@ -722,13 +844,12 @@ cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg
   A.force_lo = o.force_lo;
   A.status = status;
   A.counters = counters;
-  const int bytes = SMEM_FLOATS * (int)sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(pointvalue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaFuncSetAttribute(pointvalue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;
   // tiles cover the owned nodes: up to nxv x nyv (vertex lines n + 1 on a
-  // non-periodic axis)
+  // non-periodic axis); every box x coordinate is a multiple of TX floats
   dim3 grd((g.nxv + TX - 1) / TX, (g.nyv + TY - 1) / TY), blk(TX, TY);
-  pointvalue_kernel<<<grd, blk, bytes, s>>>(A);
+  pointvalue_kernel<<<grd, blk, SMEM_BYTES, s>>>(A, maps);
   return cudaGetLastError();
 }
 
