@@ -117,7 +117,9 @@ int af_get_half(af_ctx *h, float *vtx, float *xe, float *ye, void *stream);
  * correction term with Alg. 3 limiting, Simpson fluxes and the
  * finite-volume update (eq. (2dfvm)).  Asynchronous. */
 int af_step(af_ctx *h, double dt);
-/* nsteps steps of fixed size dt, enqueued back to back.  Asynchronous. */
+/* nsteps steps of fixed size dt.  From 4 steps on, two consecutive steps are
+ * captured once as a CUDA graph (per dt and options) and replayed.
+ * Asynchronous. */
 int af_run(af_ctx *h, int nsteps, double dt);
 
 /* Synchronise the handle's stream; return the accumulated AF_ST_* bits

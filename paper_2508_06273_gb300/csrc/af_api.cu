@@ -48,13 +48,19 @@ struct af_ctx {
   int tmap_cur;
   // small device buffers
   void *small;
-  int *d_status, *d_bad;
+  int *d_status, *d_bad, *d_speed_bad;
   unsigned *d_speed;
   unsigned long long *d_counters;
   double *d_partials, *d_totals;
   float *staging;  // host-transfer staging (lazily allocated)
   size_t staging_floats;
   bool has_state;
+  // af_run: two captured steps per parity of the t^n buffer, with the dt and
+  // options they were captured with
+  cudaGraphExec_t run_exec[2];
+  double run_dt[2];
+  Options run_opt[2];
+  bool speed_valid;  // d_speed holds the max wave speed of the current state
   cudaEvent_t ev_in, ev_out;
   // profiling: events around each stage of the last step, accumulated times
   int profile;
@@ -124,6 +130,7 @@ int ensure_staging(af_ctx *h) {
 
 // device external arrays -> padded planes (after the periodic-duplicate check)
 int load_state(af_ctx *h, const float *const src[4]) {
+  h->speed_valid = false;
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(h->d_bad, 0, sizeof(int), s), "memset");
   for (int w = 1; w < 4; w++) {
@@ -222,6 +229,15 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   h->tbuf[0] = h->lev[0];
   h->tbuf[1] = h->lev[2];
   h->tmap_cur = 0;
+  {
+    cudaError_t pe = prepare_pointvalue();
+    if (pe != cudaSuccess) {
+      cuda_fail(pe, "af_create: kernel attributes");
+      cudaFree(h->base);
+      delete h;
+      return nullptr;
+    }
+  }
   for (int b = 0; b < 2; b++) {
     cudaError_t te = make_tile_maps(g, h->tbuf[b].k[VTX], h->tbuf[b].k[XE], h->tbuf[b].k[YE], h->hi, &h->tmaps[b]);
     if (te != cudaSuccess) {
@@ -248,6 +264,7 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   h->d_status = (int *)sp;
   h->d_bad = (int *)(sp + 64);
   h->d_speed = (unsigned *)(sp + 128);
+  h->d_speed_bad = (int *)(sp + 160);
   h->d_counters = (unsigned long long *)(sp + 192);
   h->d_totals = (double *)(sp + 256);
   h->d_partials = h->d_totals + NV;
@@ -264,6 +281,8 @@ void af_destroy(af_ctx *h) {
   DeviceGuard dg(h->device);
   cudaStreamSynchronize(h->stream);
   if (h->staging) cudaFree(h->staging);
+  for (int p = 0; p < 2; p++)
+    if (h->run_exec[p]) cudaGraphExecDestroy(h->run_exec[p]);
   cudaFree(h->small);
   cudaFree(h->base);
   cudaEventDestroy(h->ev_in);
@@ -334,6 +353,7 @@ int af_set_state(af_ctx *h, const float *avg, const float *vtx, const float *xe,
 
 int af_set_state_host(af_ctx *h, const float *avg, const float *vtx, const float *xe,
                       const float *ye) {
+  h->speed_valid = false;
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
   if (!avg || !vtx || !xe || !ye) return fail(AF_ERR_ARG, "af_set_state_host: null array%s");
   DeviceGuard dg(h->device);
@@ -428,6 +448,7 @@ int af_get_avg_lo(af_ctx *h, float *avg_lo, void *stream) {
 }
 
 int af_set_avg_lo(af_ctx *h, const float *avg_lo, void *stream) {
+  h->speed_valid = false;
   if (!h || !is_device_ptr(avg_lo)) return fail(AF_ERR_ARG, "af_set_avg_lo: need a device array%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
   DeviceGuard dg(h->device);
@@ -470,8 +491,9 @@ static int enqueue_step(af_ctx *h, double dt) {
     cudaEventRecord(h->ev_stage[3], s);
   }
   CK(launch_flux_update(h->g, h->lev[0], h->lev[1], h->lev[2], h->hi, h->lo, dt / h->dx, dt / h->dy,
-                        h->d_status, s),
+                        h->d_status, h->d_speed, h->d_speed_bad, s),
      "flux update");
+  h->speed_valid = true;
   h->launches[AF_STAGE_FLUX] += 1;
   if (prof) {
     cudaEventRecord(h->ev_stage[4], s);
@@ -492,15 +514,68 @@ int af_step(af_ctx *h, double dt) {
   return enqueue_step(h, dt);
 }
 
+static bool same_options(const Options &a, const Options &b) {
+  return a.lin_mode == b.lin_mode && a.tsw == b.tsw && a.limiter == b.limiter &&
+         a.correction == b.correction && a.force_lo == b.force_lo;
+}
+
+// Capture two steps on the handle's own stream (the t^n and t^{n+1} buffers
+// swap every step, so after two steps every pointer is back where it was).
+static int capture_pair(af_ctx *h, double dt) {
+  const int p = h->tmap_cur;
+  if (h->run_exec[p]) {
+    cudaGraphExecDestroy(h->run_exec[p]);
+    h->run_exec[p] = nullptr;
+  }
+  cudaStream_t keep = h->stream;
+  const int keep_prof = h->profile;
+  h->stream = h->own_stream;
+  h->profile = 0;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->own_stream, cudaStreamCaptureModeThreadLocal);
+  int rc = AF_OK;
+  if (e == cudaSuccess) {
+    rc = enqueue_step(h, dt);
+    if (rc == AF_OK) rc = enqueue_step(h, dt);
+    e = cudaStreamEndCapture(h->own_stream, &graph);
+  }
+  h->stream = keep;
+  h->profile = keep_prof;
+  if (rc != AF_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "af_run: capture");
+  e = cudaGraphInstantiate(&h->run_exec[p], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "af_run: instantiate");
+  h->run_dt[p] = dt;
+  h->run_opt[p] = h->opt;
+  return AF_OK;
+}
+
 int af_run(af_ctx *h, int nsteps, double dt) {
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
   if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(AF_ERR_ARG, "af_run: bad arguments%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
   DeviceGuard dg(h->device);
-  for (int k = 0; k < nsteps; k++) {
-    int rc = enqueue_step(h, dt);
+  if (h->profile || nsteps < 4) {  // profiled runs time every stage: plain launches
+    for (int k = 0; k < nsteps; k++) {
+      int rc = enqueue_step(h, dt);
+      if (rc) return rc;
+    }
+    return AF_OK;
+  }
+  const int p = h->tmap_cur;
+  if (!h->run_exec[p] || h->run_dt[p] != dt || !same_options(h->run_opt[p], h->opt)) {
+    int rc = capture_pair(h, dt);
     if (rc) return rc;
   }
+  for (int k = 0; k + 1 < nsteps; k += 2) {
+    CK(cudaGraphLaunch(h->run_exec[p], h->stream), "af_run: graph launch");
+    h->launches[AF_STAGE_PREP] += 2;
+    h->launches[AF_STAGE_POINTVALUE] += 2;
+    h->launches[AF_STAGE_FLUX] += 2;
+  }
+  h->speed_valid = true;
+  if (nsteps & 1) return enqueue_step(h, dt);
   return AF_OK;
 }
 
@@ -541,6 +616,17 @@ int af_max_speed(af_ctx *h, float *out) {
   if (!h || !out) return fail(AF_ERR_ARG, "null argument%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
   DeviceGuard dg(h->device);
+  if (h->speed_valid) {  // computed by the last step's flux kernel
+    unsigned bits = 0;
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bits, h->d_speed, sizeof(bits), cudaMemcpyDeviceToHost, h->stream), "speed");
+    CK(cudaMemcpyAsync(&bad, h->d_speed_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "speed");
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    float m;
+    std::memcpy(&m, &bits, sizeof(m));
+    *out = bad ? NAN : m;
+    return AF_OK;
+  }
   cudaEvent_t e0 = h->ev_in, e1 = h->ev_out;
   if (h->profile) {
     collect_stages(h);
@@ -548,13 +634,13 @@ int af_max_speed(af_ctx *h, float *out) {
     CK(cudaEventCreate(&e1), "event");
     cudaEventRecord(e0, h->stream);
   }
-  CK(launch_max_speed(h->g, h->hi, h->lev[0], h->d_speed, h->d_bad, h->stream), "max speed");
+  CK(launch_max_speed(h->g, h->hi, h->lev[0], h->d_speed, h->d_speed_bad, h->stream), "max speed");
   h->launches[AF_STAGE_REDUCE] += 1;
   if (h->profile) cudaEventRecord(e1, h->stream);
   unsigned bits = 0;
   int bad = 0;
   CK(cudaMemcpyAsync(&bits, h->d_speed, sizeof(bits), cudaMemcpyDeviceToHost, h->stream), "speed");
-  CK(cudaMemcpyAsync(&bad, h->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "speed");
+  CK(cudaMemcpyAsync(&bad, h->d_speed_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "speed");
   CK(cudaStreamSynchronize(h->stream), "sync");
   if (h->profile) {
     float ms = 0.0f;
@@ -565,6 +651,7 @@ int af_max_speed(af_ctx *h, float *out) {
   float m;
   std::memcpy(&m, &bits, sizeof(m));
   *out = bad ? NAN : m;
+  h->speed_valid = true;
   return AF_OK;
 }
 

@@ -53,4 +53,18 @@ __device__ __forceinline__ void c2p(const float Q[4], float gm1, float U[4]) {
 }
 __device__ __forceinline__ bool admissible(const float U[4]) { return U[0] > 0.0f && U[3] > 0.0f; }
 
+// max(|u|, |v|) + c of a primitive state, c^2 = gamma p / rho; sets bad if
+// the state is not admissible.  It feeds the CFL time step only, so the
+// hardware approximations of 1/x and 1/sqrt(x) (a few ulp) are accurate
+// enough, and they keep the kernels that fold it in free of the IEEE divide
+// and square-root subroutines.
+__device__ __forceinline__ float wave_speed(const float U[4], float gam, bool &bad) {
+  if (!(U[0] > 0.0f && U[3] > 0.0f) || !isfinite(U[1]) || !isfinite(U[2])) {
+    bad = true;
+    return 0.0f;
+  }
+  const float c2 = gam * __fdividef(U[3], U[0]);
+  return fmaxf(fabsf(U[1]), fabsf(U[2])) + c2 * rsqrtf(c2);
+}
+
 }  // namespace af

@@ -31,6 +31,8 @@ struct Args {
   float *hi, *lo;
   float lxh, lxl, lyh, lyl;  // dt/dx and dt/dy as double-word FP32 (hi + lo)
   int *status;
+  unsigned *speed;  // max of max(|u|,|v|) + c over the new state, as float bits
+  int *speed_bad;   // set if a new value is not admissible
 };
 
 // error-free transformations (exact: a + b = s + e, a * b = p + e)
@@ -79,9 +81,11 @@ __device__ __forceinline__ void phys_flux(const float U[4], float gm1i, int dir,
   F[3] = un * (E + p);
 }
 
-// Simpson in time at one node: f(U^n) + 4 f(U^{n+1/2}) + f(U^{n+1})
-__device__ __forceinline__ void time_flux(const Args &A, int kind, int i, int j, int dir, float gm1i,
-                                          float F[4]) {
+// Simpson in time at one node: f(U^n) + 4 f(U^{n+1/2}) + f(U^{n+1}); with
+// fold set, also folds the node's new value into the running wave-speed
+// maximum (set on one visit of each node only)
+__device__ __forceinline__ void time_flux(const Args &A, int kind, int i, int j, int dir, bool fold,
+                                          float gm1i, float F[4], float &smax, bool &bad) {
   F[0] = F[1] = F[2] = F[3] = 0.0f;
 #pragma unroll
   for (int l = 0; l < 3; l++) {
@@ -92,10 +96,13 @@ __device__ __forceinline__ void time_flux(const Args &A, int kind, int i, int j,
     const float w = l == 1 ? 4.0f : 1.0f;
 #pragma unroll
     for (int v = 0; v < NV; v++) F[v] += w * f[v];
+    if (l == 2 && fold) smax = fmaxf(smax, wave_speed(U, A.g.gamma, bad));
   }
 }
 
-__global__ void __launch_bounds__(TX *TY) flux_update_kernel(Args A) {
+// 6 resident blocks per SM (40 registers a thread): the kernel streams
+// ~200 B a cell, and the extra warps keep more loads in flight
+__global__ void __launch_bounds__(TX *TY, 6) flux_update_kernel(Args A) {
   const Grid &g = A.g;
   __shared__ float vf[NV][TY + 1][TX + 1], vg[NV][TY + 1][TX + 1];
   __shared__ float xf[NV][TY][TX + 1], yg[NV][TY + 1][TX];
@@ -103,6 +110,8 @@ __global__ void __launch_bounds__(TX *TY) flux_update_kernel(Args A) {
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const float gm1i = 1.0f / (g.gamma - 1.0f);
+  float smax = 0.0f;
+  bool sbad = false;
 
   // time-integrated node fluxes; nodes up to index nx / ny (periodic
   // duplicates included)
@@ -110,8 +119,8 @@ __global__ void __launch_bounds__(TX *TY) flux_update_kernel(Args A) {
     const int a = k % (TX + 1), b = k / (TX + 1), i = i0 + a, j = j0 + b;
     float F[4] = {0, 0, 0, 0}, Gf[4] = {0, 0, 0, 0};
     if (i <= g.nx && j <= g.ny) {
-      time_flux(A, VTX, i, j, 0, gm1i, F);
-      time_flux(A, VTX, i, j, 1, gm1i, Gf);
+      time_flux(A, VTX, i, j, 0, true, gm1i, F, smax, sbad);
+      time_flux(A, VTX, i, j, 1, false, gm1i, Gf, smax, sbad);
     }
 #pragma unroll
     for (int v = 0; v < NV; v++) {
@@ -122,14 +131,14 @@ __global__ void __launch_bounds__(TX *TY) flux_update_kernel(Args A) {
   for (int k = tid; k < (TX + 1) * TY; k += TX * TY) {
     const int a = k % (TX + 1), b = k / (TX + 1), i = i0 + a, j = j0 + b;
     float F[4] = {0, 0, 0, 0};
-    if (i <= g.nx && j < g.ny) time_flux(A, XE, i, j, 0, gm1i, F);
+    if (i <= g.nx && j < g.ny) time_flux(A, XE, i, j, 0, true, gm1i, F, smax, sbad);
 #pragma unroll
     for (int v = 0; v < NV; v++) xf[v][b][a] = F[v];
   }
   for (int k = tid; k < TX * (TY + 1); k += TX * TY) {
     const int a = k % TX, b = k / TX, i = i0 + a, j = j0 + b;
     float F[4] = {0, 0, 0, 0};
-    if (i < g.nx && j <= g.ny) time_flux(A, YE, i, j, 1, gm1i, F);
+    if (i < g.nx && j <= g.ny) time_flux(A, YE, i, j, 1, true, gm1i, F, smax, sbad);
 #pragma unroll
     for (int v = 0; v < NV; v++) yg[v][b][a] = F[v];
   }
@@ -149,9 +158,10 @@ __global__ void __launch_bounds__(TX *TY) flux_update_kernel(Args A) {
   __syncthreads();
   // finite-volume update on the (hi, lo) pair in double-word arithmetic
   const int a = threadIdx.x, b = threadIdx.y, i = i0 + a, j = j0 + b;
-  if (i >= g.nx || j >= g.ny) return;
-  float qh[4];
+  const bool inside = i < g.nx && j < g.ny;
+  float qh[4] = {1.0f, 0.0f, 0.0f, 1.0f};
   bool bad = false;
+  if (inside) {
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     const long long e = at(g, v, i, j);
@@ -165,16 +175,41 @@ __global__ void __launch_bounds__(TX *TY) flux_update_kernel(Args A) {
     qh[v] = nh + nl;
     bad |= !isfinite(nh);
   }
-  const float p = (g.gamma - 1.0f) * (qh[3] - 0.5f * (qh[1] * qh[1] + qh[2] * qh[2]) / qh[0]);
-  int st = bad ? ST_NONFINITE : ((qh[0] > 0.0f && p > 0.0f) ? 0 : ST_AVG_NONPOS);
+  }
+  float U[4];
+  c2p(qh, g.gamma - 1.0f, U);
+  int st = bad ? ST_NONFINITE : ((U[0] > 0.0f && U[3] > 0.0f) ? 0 : ST_AVG_NONPOS);
   if (st) atomicOr(A.status, st);
+  if (inside) smax = fmaxf(smax, wave_speed(U, g.gamma, sbad));
+  // block maximum of the new state's wave speed, then one atomic per block
+  // (positive floats order like their bit patterns)
+  __shared__ float wmax[TX * TY / 32];
+  __shared__ int wbad[TX * TY / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  const bool anybad = __any_sync(0xffffffffu, sbad);
+  if ((tid & 31) == 0) {
+    wmax[tid >> 5] = smax;
+    wbad[tid >> 5] = anybad;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float m = 0.0f;
+    int b = 0;
+    for (int w = 0; w < TX * TY / 32; w++) {
+      m = fmaxf(m, wmax[w]);
+      b |= wbad[w];
+    }
+    atomicMax(A.speed, __float_as_uint(m));
+    if (b) atomicOr(A.speed_bad, 1);
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &n1,
                                const NodeSet &n2, float *avg_hi, float *avg_lo, double lamx,
-                               double lamy, int *status, cudaStream_t s) {
+                               double lamy, int *status, unsigned *speed, int *speed_bad, cudaStream_t s) {
   Args A;
   A.g = g;
   for (int k = 0; k < 3; k++) {
@@ -189,6 +224,10 @@ cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &
   A.lyh = (float)lamy;
   A.lyl = (float)(lamy - (double)A.lyh);
   A.status = status;
+  A.speed = speed;
+  A.speed_bad = speed_bad;
+  cudaMemsetAsync(speed, 0, sizeof(unsigned), s);
+  cudaMemsetAsync(speed_bad, 0, sizeof(int), s);
   dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY), blk(TX, TY);
   flux_update_kernel<<<grd, blk, 0, s>>>(A);
   return cudaGetLastError();

@@ -30,14 +30,17 @@ struct TileMaps {
   CUtensorMap vtx, xe, ye, avg;
 };
 cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, float *avg, TileMaps *out);
+// one-time kernel attributes (shared-memory size) on the current device
+cudaError_t prepare_pointvalue();
 // cell prep and point values at t^{n+1/2} (n1) and t^{n+1} (n2)
 cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
                               int *status, unsigned long long *counters, cudaStream_t s);
-// Simpson fluxes and the finite-volume update of the averages (FP64 on hi/lo)
+// Simpson fluxes and the finite-volume update of the averages (compensated
+// hi/lo); also the max wave speed of the new state into *speed (float bits)
 cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &n1,
                                const NodeSet &n2, float *avg_hi, float *avg_lo, double lamx,
-                               double lamy, int *status, cudaStream_t s);
+                               double lamy, int *status, unsigned *speed, int *speed_bad, cudaStream_t s);
 // max over averages and owned point values of max(|u|,|v|) + c (as float bits)
 cudaError_t launch_max_speed(const Grid &g, const float *avg_hi, const NodeSet &n,
                              unsigned *out_bits, int *bad, cudaStream_t s);

@@ -68,14 +68,6 @@ __global__ void ghost_kernel(GhostArgs A) {
   }
 }
 
-__device__ __forceinline__ float wave_speed(const float U[4], float gam, bool &bad) {
-  if (!(U[0] > 0.0f && U[3] > 0.0f) || !isfinite(U[1]) || !isfinite(U[2])) {
-    bad = true;
-    return 0.0f;
-  }
-  return fmaxf(fabsf(U[1]), fabsf(U[2])) + sqrtf(gam * U[3] / U[0]);
-}
-
 __global__ void max_speed_kernel(Grid g, const float *__restrict__ avg, const float *__restrict__ V,
                                  const float *__restrict__ X, const float *__restrict__ Y,
                                  unsigned *out, int *badflag) {

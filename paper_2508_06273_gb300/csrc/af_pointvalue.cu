@@ -825,6 +825,10 @@ cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, floa
   return cudaSuccess;
 }
 
+cudaError_t prepare_pointvalue() {
+  return cudaFuncSetAttribute(pointvalue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+}
+
 cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
                               int *status, unsigned long long *counters, cudaStream_t s) {
@@ -844,8 +848,6 @@ cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg
   A.force_lo = o.force_lo;
   A.status = status;
   A.counters = counters;
-  cudaError_t e = cudaFuncSetAttribute(pointvalue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  if (e != cudaSuccess) return e;
   // tiles cover the owned nodes: up to nxv x nyv (vertex lines n + 1 on a
   // non-periodic axis); every box x coordinate is a multiple of TX floats
   dim3 grd((g.nxv + TX - 1) / TX, (g.nyv + TY - 1) / TY), blk(TX, TY);

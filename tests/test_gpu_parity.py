@@ -340,3 +340,37 @@ def test_full_size_sampled_windows(env):
         ref = [a[:, m:-m, m:-m] for a in ref]
         assert state_err(got, ref) < STEP_TOL, (i0, j0)
     s.close()
+
+
+@pytest.mark.parametrize("nsteps", [7, 10])
+def test_graph_replay_is_bitwise_equal_to_steps(env, nsteps):
+    """af_run replays two captured steps as a CUDA graph; the kernels are
+    deterministic, so the result equals nsteps calls of af_step bit for bit."""
+    torch, af, _ = env
+    prob = W.fourier_smooth(40, 33, seed=21)
+    st = W.to_f32(W.discretise(prob))
+    a, b = solver(env, prob, state=st), solver(env, prob, state=st)
+    dt = 0.3 * prob.dx / a.max_speed()
+    for _ in range(nsteps):
+        a.step(dt)
+    b.run(nsteps, dt)
+    b.run(nsteps, dt)  # second call replays the cached graph
+    for _ in range(nsteps):
+        a.step(dt)
+    assert a.status() == 0 and b.status() == 0
+    for x, y in zip(host(a.get_state()), host(b.get_state())):
+        assert np.array_equal(x, y)
+    assert np.array_equal(host([a.get_avg_lo()])[0], host([b.get_avg_lo()])[0])
+
+
+def test_fused_max_speed_matches_reduction(env):
+    """The flux kernel's wave-speed maximum of the new state equals the
+    standalone reduction over the same state."""
+    torch, af, _ = env
+    prob = W.shu_vortex_seeded(96)
+    s = solver(env, prob)
+    s.step(0.3 * prob.dx / s.max_speed())
+    fused = s.max_speed()
+    s.set_state(*s.get_state())  # invalidates the cached value: reduction kernel
+    again = s.max_speed()
+    assert abs(fused - again) <= 1e-6 * again
