@@ -338,10 +338,53 @@ def run_ours(args):
         "clocks": clk,
         "e2e": e2e,
     }
+    if world == 1 and args.batch_steps > 0:
+        line["batch"] = run_batch_leg(args, torch, af, W)
     if world == 1 and not args.no_cpu:
         v, threads, desc, _ = cpu_sample(n, min_seconds=args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
     print(json.dumps(line), flush=True)
+
+
+def run_batch_leg(args, torch, af, W):
+    """Seeded ensemble of 256 grids of 64^2 to 512^2 cells (half isentropic
+    vortices, half four-quadrant Riemann problems) advanced by one graph
+    launch of ``--batch-steps`` batched steps, tile height autotuned; cell
+    updates counted per instance from the steps each one actually took."""
+    probs = W.ensemble(256, seed=4096)
+    b = af.Batch([(p.nx, p.ny) for p in probs], [(p.dx, p.dy) for p in probs], bcs=[p.bc for p in probs])
+    for k, p in enumerate(probs):
+        for key, v in p.options.items():
+            b.set_option(key, v, k)
+        b.set_state(k, *W.discretise_torch(p, "cuda"))
+    cells = [p.nx * p.ny for p in probs]
+    tile_h, tune_ms = b.autotune()
+    b.run(args.warmup)
+    _, steps0, _, _ = b.query()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    b.run(args.batch_steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    _, steps1, active, status = b.query()
+    updates = int(sum(c * (a - z) for c, a, z in zip(cells, steps1, steps0)))
+    b.close()
+    kinds = ["vortex" if k % 2 == 0 else "riemann" for k in range(len(probs))]
+    stopped = [k for k in range(len(probs)) if status[k] & af.ST_STOPPED or not active[k]]
+    return {
+        "workload": "ensemble of 256 grids, N x N with N = round(64 * 8^U), U ~ U[0,1) from seed 4096; "
+                    "even: isentropic vortex (centre, strength in [3,6]), odd: four-quadrant Riemann "
+                    "(transmissive, tsw + limiter)",
+        "instances": len(probs), "cells": int(sum(cells)), "steps": args.batch_steps,
+        "value": updates / (ms / 1e3), "unit": UNIT, "ms": ms, "cell_updates": updates,
+        "graph_launches": (args.batch_steps + 255) // 256, "tile_h": tile_h,
+        "autotune_ms_per_launch": tune_ms,
+        "stopped": {"vortex": sum(kinds[k] == "vortex" for k in stopped),
+                    "riemann": sum(kinds[k] == "riemann" for k in stopped)},
+    }
 
 
 def run_reference(args):
@@ -379,6 +422,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=200,
+                    help="steps of the batched-ensemble leg (0: skip it)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

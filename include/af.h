@@ -56,8 +56,10 @@ enum {
   AF_ST_NONFINITE = 4,  /* a non-finite point value or cell average */
   AF_ST_KEPT = 8,       /* Alg. 3's Lax-Friedrichs value was not admissible in FP32;
                            the node kept its old value */
-  AF_ST_TIMEOUT = 16    /* a block's wait for its staged tile timed out; the tile was
+  AF_ST_TIMEOUT = 16,   /* a block's wait for its staged tile timed out; the tile was
                            not updated (the step's result is invalid) */
+  AF_ST_STOPPED = 32    /* batch only: the instance's state had no finite positive wave
+                           speed, so it was stopped before its end time */
 };
 
 /* option keys for af_set_option */
@@ -166,6 +168,66 @@ int af_profile(af_ctx *h, double ms[4], int64_t launches[4], int reset);
  * only in summation order.  Returns AF_OK, AF_ERR_ARG or AF_ERR_CUDA. */
 int af_conserved_totals_noalloc(const float *avg, const float *avg_lo, int nx, int ny, double dx,
                                 double dy, double *out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batches: n independent grids of uneven sizes (an ensemble) advanced
+ * together.  Every step runs the same four batched kernels over all
+ * instances (dt, ghost layers, point values, flux and update), each launch
+ * covering the tiles of every instance; af_batch_run captures its whole run
+ * of steps in one CUDA graph and launches it once.  Each instance takes its
+ * own time step on the device, dt = cfl * min(dx, dy) / s with s the
+ * maximum of max(|u|,|v|) + c over its cell averages and point values
+ * (Sec. 2), the last step clipped to end at its t_end; an instance at its
+ * end time (or stopped, AF_ST_STOPPED) is skipped by every kernel.  Options
+ * (the AF_OPT_* keys but AF_OPT_PROFILE) are per instance.  Layouts and pointer rules of the state arrays are those of
+ * af_set_state / af_get_state.  A batch must not be used by two host
+ * threads at once.
+ */
+typedef struct af_batch af_batch;
+
+/* Create n instances; instance k has nx[k] x ny[k] cells of dx[k] x dy[k]
+ * and boundary word bc[k] (as af_create).  Host arrays of length n.  All
+ * instances start with t = 0, t_end = +inf, cfl = 0.3.  NULL on error. */
+af_batch *af_batch_create(int n, const int *nx, const int *ny, const double *dx, const double *dy,
+                          double gamma, const uint32_t *bc);
+/* Free everything the batch owns.  NULL-safe. */
+void af_batch_destroy(af_batch *b);
+/* Option `key` of instance k, or of every instance if k = -1. */
+int af_batch_set_option(af_batch *b, int k, int key, double value);
+/* Device arrays of instance k (copied; layouts as af_set_state).  Resets
+ * the instance's time to 0, its status and counters, and re-activates it. */
+int af_batch_set_state(af_batch *b, int k, const float *avg, const float *vtx, const float *xe,
+                       const float *ye, void *stream);
+/* Instance k's state at its current time into caller-owned device arrays. */
+int af_batch_get_state(af_batch *b, int k, float *avg, float *vtx, float *xe, float *ye,
+                       void *stream);
+/* End times (host array of n; +inf: no end) and the CFL number of every
+ * instance; keeps each instance's current time and re-activates the
+ * instances that have not reached their new end. */
+int af_batch_set_end(af_batch *b, const double *t_end, double cfl);
+/* Advance every active instance by up to nsteps steps (asynchronous, one
+ * graph launch on the batch's stream).  If hist is given, the dt of each
+ * instance's s-th step since af_batch_set_state is also written to
+ * hist[s * n + k] for s < hist_steps (a device array of doubles the caller
+ * owns and keeps alive until the run is done). */
+int af_batch_run(af_batch *b, int nsteps, double *hist, int hist_steps);
+/* Synchronise; per instance (host arrays of n, any may be NULL): current
+ * time, steps taken, active flag, and AF_ST_* status (cleared when read). */
+int af_batch_query(af_batch *b, double *t, int *steps, int *active, int *status);
+/* Synchronise; per-instance Alg. 3 counters (host array [n][4], as af_counters,
+ * accumulated since af_batch_set_state). */
+int af_batch_counters(af_batch *b, int64_t *out);
+/* Point-value tile height (4, 8 or 16 rows of 32 cells) of the batched
+ * kernel.  af_batch_autotune times each height on the batch's current state
+ * (point-value launches only; the state and time are unchanged), keeps the
+ * fastest and returns it in *tile_h (and the mean milliseconds of each
+ * candidate in ms[3] if given).  Needs every instance's state. */
+int af_batch_set_tile(af_batch *b, int tile_h);
+int af_batch_autotune(af_batch *b, int *tile_h, double *ms);
+/* Total cells of the instances still active (after a sync). */
+long long af_batch_active_cells(af_batch *b);
+/* The batch's stream (0 = the legacy default stream); as af_set_stream. */
+int af_batch_set_stream(af_batch *b, void *stream);
 
 #ifdef __cplusplus
 }

@@ -21,13 +21,16 @@ _LIB = None
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING = 0, 1, 2
 OPT = {"lin_mode": 0, "tsw": 1, "limiter": 2, "correction": 3, "force_lo": 4, "profile": 5}
 STAGES = ("prep", "pointvalue", "flux", "reduce")
-ST_CFL, ST_AVG_NONPOS, ST_NONFINITE, ST_KEPT = 1, 2, 4, 8
+ST_CFL, ST_AVG_NONPOS, ST_NONFINITE, ST_KEPT, ST_TIMEOUT, ST_STOPPED = 1, 2, 4, 8, 16, 32
 EXPORTS = [
     "af_create", "af_destroy", "af_last_error", "af_set_stream", "af_set_option",
     "af_get_option", "af_set_state", "af_set_state_host", "af_get_state", "af_get_state_host",
     "af_get_avg_lo", "af_set_avg_lo", "af_get_half", "af_step", "af_run", "af_status",
     "af_counters", "af_conserved_totals", "af_max_speed", "af_profile",
     "af_conserved_totals_noalloc",
+    "af_batch_create", "af_batch_destroy", "af_batch_set_option", "af_batch_set_state",
+    "af_batch_get_state", "af_batch_set_end", "af_batch_run", "af_batch_query", "af_batch_counters",
+    "af_batch_set_tile", "af_batch_autotune", "af_batch_active_cells", "af_batch_set_stream",
 ]
 
 
@@ -67,6 +70,19 @@ def lib():
                 "af_max_speed": (i, [vp, C.POINTER(C.c_float)]),
                 "af_profile": (i, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), i]),
                 "af_conserved_totals_noalloc": (i, [fp, fp, i, i, d, d, fp, vp]),
+                "af_batch_create": (vp, [i, fp, fp, fp, fp, d, fp]),
+                "af_batch_destroy": (None, [vp]),
+                "af_batch_set_option": (i, [vp, i, i, d]),
+                "af_batch_set_state": (i, [vp, i, fp, fp, fp, fp, vp]),
+                "af_batch_get_state": (i, [vp, i, fp, fp, fp, fp, vp]),
+                "af_batch_set_end": (i, [vp, fp, d]),
+                "af_batch_run": (i, [vp, i, fp, i]),
+                "af_batch_query": (i, [vp, fp, fp, fp, fp]),
+                "af_batch_counters": (i, [vp, fp]),
+                "af_batch_set_tile": (i, [vp, i]),
+                "af_batch_autotune": (i, [vp, C.POINTER(C.c_int), fp]),
+                "af_batch_active_cells": (C.c_longlong, [vp]),
+                "af_batch_set_stream": (i, [vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -200,3 +216,100 @@ class Solver:
         out = C.c_float()
         _check(self.L.af_max_speed(self.h, C.byref(out)))
         return out.value
+
+
+def _shapes(nx, ny):
+    return (4, ny, nx), (4, ny + 1, nx + 1), (4, ny, nx + 1), (4, ny + 1, nx)
+
+
+class Batch:
+    """An ensemble of independent grids (an af_batch) advanced together by
+    batched kernels, each instance with its own device-side time step."""
+
+    def __init__(self, sizes, spacings, gamma=1.4, bcs=None, stream=None, options=None):
+        import torch
+
+        self.torch = torch
+        self.L = lib()
+        self.n = len(sizes)
+        self.sizes = [(int(a), int(b)) for a, b in sizes]
+        self.spacings = [(float(a), float(b)) for a, b in spacings]
+        bcs = bcs or [(0, 0, 0, 0)] * self.n
+        nx = np.array([s[0] for s in self.sizes], dtype=np.int32)
+        ny = np.array([s[1] for s in self.sizes], dtype=np.int32)
+        dx = np.array([s[0] for s in self.spacings], dtype=np.float64)
+        dy = np.array([s[1] for s in self.spacings], dtype=np.float64)
+        bc = np.array([bc_code(b) for b in bcs], dtype=np.uint32)
+        self._keep = (nx, ny, dx, dy, bc)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.h = self.L.af_batch_create(self.n, *[C.c_void_p(a.ctypes.data) for a in (nx, ny, dx, dy)],
+                                        float(gamma), C.c_void_p(bc.ctypes.data))
+        if not self.h:
+            raise AFError(self.L.af_last_error().decode())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        _check(self.L.af_batch_set_stream(self.h, C.c_void_p(self.stream.cuda_stream)))
+        for k, v in (options or {}).items():
+            self.set_option(k, v)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.af_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def _s(self):
+        return C.c_void_p(self.stream.cuda_stream)
+
+    def set_option(self, key, value, k=-1):
+        """Option of instance k (all instances if k = -1)."""
+        _check(self.L.af_batch_set_option(self.h, int(k), OPT[key] if isinstance(key, str) else key,
+                                          float(value)))
+
+    def set_state(self, k, avg, vtx, xe, ye):
+        ts = []
+        for a, s in zip((avg, vtx, xe, ye), _shapes(*self.sizes[k])):
+            if tuple(a.shape) != s or a.dtype != self.torch.float32 or not a.is_cuda:
+                raise ValueError(f"need CUDA float32 tensors of shape {s}")
+            ts.append(a.contiguous())
+        _check(self.L.af_batch_set_state(self.h, k, *[_ptr(t) for t in ts], self._s()))
+
+    def get_state(self, k):
+        out = [self.torch.empty(s, dtype=self.torch.float32, device=self.device)
+               for s in _shapes(*self.sizes[k])]
+        _check(self.L.af_batch_get_state(self.h, k, *[_ptr(t) for t in out], self._s()))
+        return tuple(out)
+
+    def set_end(self, t_end, cfl=0.3):
+        te = np.ascontiguousarray(np.broadcast_to(np.asarray(t_end, dtype=np.float64), (self.n,)))
+        _check(self.L.af_batch_set_end(self.h, C.c_void_p(te.ctypes.data), float(cfl)))
+
+    def run(self, nsteps, hist=None):
+        """Advance up to nsteps steps; hist: optional CUDA float64 tensor
+        [steps, n] that receives each instance's dt per step."""
+        hp, hs = (None, 0) if hist is None else (_ptr(hist), int(hist.shape[0]))
+        _check(self.L.af_batch_run(self.h, int(nsteps), hp, hs))
+
+    def query(self):
+        """(t, steps, active, status) per instance; clears the status words."""
+        t = np.zeros(self.n, dtype=np.float64)
+        st, ac, ss = (np.zeros(self.n, dtype=np.int32) for _ in range(3))
+        _check(self.L.af_batch_query(self.h, *[C.c_void_p(a.ctypes.data) for a in (t, st, ac, ss)]))
+        return t, st, ac, ss
+
+    def counters(self):
+        out = np.zeros((self.n, 4), dtype=np.int64)
+        _check(self.L.af_batch_counters(self.h, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def set_tile(self, tile_h):
+        _check(self.L.af_batch_set_tile(self.h, int(tile_h)))
+
+    def autotune(self):
+        """Pick the fastest point-value tile height; returns (height, {height: ms})."""
+        th, ms = C.c_int(), np.zeros(3, dtype=np.float64)
+        _check(self.L.af_batch_autotune(self.h, C.byref(th), C.c_void_p(ms.ctypes.data)))
+        return th.value, dict(zip((4, 8, 16), ms.tolist()))
+
+    def active_cells(self):
+        return _check(self.L.af_batch_active_cells(self.h))

@@ -8,6 +8,7 @@
 
 #include "../../include/af.h"
 #include "af_common.cuh"
+#include "af_ctx.h"
 #include "af_kernels.h"
 
 using namespace af;
@@ -31,44 +32,6 @@ int af::set_error(int code, const char *msg) {
     cudaError_t e_ = (call);                    \
     if (e_ != cudaSuccess) return cuda_fail(e_, where); \
   } while (0)
-
-struct af_ctx {
-  Grid g;
-  double dx, dy;
-  Options opt;
-  int device;
-  cudaStream_t own_stream, stream;
-  float *base;  // all planes in one allocation
-  float *hi, *lo;
-  NodeSet lev[3];  // 0: t^n, 1: t^{n+1/2}, 2: t^{n+1}
-  // TMA descriptors for t^n held in either of the two buffers that swap
-  // roles each step; tmap_cur selects the one now holding t^n
-  TileMaps tmaps[2];
-  NodeSet tbuf[2];
-  int tmap_cur;
-  // small device buffers
-  void *small;
-  int *d_status, *d_bad, *d_speed_bad;
-  unsigned *d_speed;
-  unsigned long long *d_counters;
-  double *d_partials, *d_totals;
-  float *staging;  // host-transfer staging (lazily allocated)
-  size_t staging_floats;
-  bool has_state;
-  // af_run: two captured steps per parity of the t^n buffer, with the dt and
-  // options they were captured with
-  cudaGraphExec_t run_exec[2];
-  double run_dt[2];
-  Options run_opt[2];
-  bool speed_valid;  // d_speed holds the max wave speed of the current state
-  cudaEvent_t ev_in, ev_out;
-  // profiling: events around each stage of the last step, accumulated times
-  int profile;
-  cudaEvent_t ev_stage[5];
-  bool stage_pending;
-  double stage_ms[4];
-  long long launches[4];
-};
 
 namespace {
 
@@ -239,7 +202,8 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
     }
   }
   for (int b = 0; b < 2; b++) {
-    cudaError_t te = make_tile_maps(g, h->tbuf[b].k[VTX], h->tbuf[b].k[XE], h->tbuf[b].k[YE], h->hi, &h->tmaps[b]);
+    cudaError_t te = make_tile_maps(g, h->tbuf[b].k[VTX], h->tbuf[b].k[XE], h->tbuf[b].k[YE], h->hi, 8,
+                                   &h->tmaps[b]);
     if (te != cudaSuccess) {
       cuda_fail(te, "af_create: TMA descriptors");
       cudaFree(h->base);

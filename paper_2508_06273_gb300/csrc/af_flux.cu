@@ -25,15 +25,7 @@ namespace {
 
 constexpr int TX = 32, TY = 8;
 
-struct Args {
-  Grid g;
-  const float *__restrict__ n[3][3];  // [level][kind]
-  float *hi, *lo;
-  float lxh, lxl, lyh, lyl;  // dt/dx and dt/dy as double-word FP32 (hi + lo)
-  int *status;
-  unsigned *speed;  // max of max(|u|,|v|) + c over the new state, as float bits
-  int *speed_bad;   // set if a new value is not admissible
-};
+using Args = FluxArgs;
 
 // error-free transformations (exact: a + b = s + e, a * b = p + e)
 __device__ __forceinline__ float two_sum(float a, float b, float &e) {
@@ -100,14 +92,23 @@ __device__ __forceinline__ void time_flux(const Args &A, int kind, int i, int j,
   }
 }
 
-// 6 resident blocks per SM (40 registers a thread): the kernel streams
-// ~200 B a cell, and the extra warps keep more loads in flight
-__global__ void __launch_bounds__(TX *TY, 6) flux_update_kernel(Args A) {
+struct FluxSmem {
+  float vf[NV][TY + 1][TX + 1], vg[NV][TY + 1][TX + 1];
+  float xf[NV][TY][TX + 1], yg[NV][TY + 1][TX];
+  float Fx[NV][TY][TX + 1], Gy[NV][TY + 1][TX];
+  float wmax[TX * TY / 32];
+  int wbad[TX * TY / 32];
+};
+
+// the tile of cells with origin (i0, j0)
+__device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, int i0, int j0) {
   const Grid &g = A.g;
-  __shared__ float vf[NV][TY + 1][TX + 1], vg[NV][TY + 1][TX + 1];
-  __shared__ float xf[NV][TY][TX + 1], yg[NV][TY + 1][TX];
-  __shared__ float Fx[NV][TY][TX + 1], Gy[NV][TY + 1][TX];
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  auto &vf = S.vf;
+  auto &vg = S.vg;
+  auto &xf = S.xf;
+  auto &yg = S.yg;
+  auto &Fx = S.Fx;
+  auto &Gy = S.Gy;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const float gm1i = 1.0f / (g.gamma - 1.0f);
   float smax = 0.0f;
@@ -183,8 +184,8 @@ __global__ void __launch_bounds__(TX *TY, 6) flux_update_kernel(Args A) {
   if (inside) smax = fmaxf(smax, wave_speed(U, g.gamma, sbad));
   // block maximum of the new state's wave speed, then one atomic per block
   // (positive floats order like their bit patterns)
-  __shared__ float wmax[TX * TY / 32];
-  __shared__ int wbad[TX * TY / 32];
+  auto &wmax = S.wmax;
+  auto &wbad = S.wbad;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
   const bool anybad = __any_sync(0xffffffffu, sbad);
@@ -205,11 +206,36 @@ __global__ void __launch_bounds__(TX *TY, 6) flux_update_kernel(Args A) {
   }
 }
 
+// 6 resident blocks per SM (40 registers a thread): the kernel streams
+// ~200 B a cell, and the extra warps keep more loads in flight
+__global__ void __launch_bounds__(TX *TY, 6) flux_update_kernel(Args A) {
+  __shared__ FluxSmem S;
+  flux_tile(A, S, blockIdx.x * TX, blockIdx.y * TY);
+}
+
+// batched form: tile B.tiles[b] = (instance, i0, j0); the instance's dt
+// ratios come from its control block
+__global__ void __launch_bounds__(TX *TY, 6) flux_batch_kernel(FluxBatch B) {
+  __shared__ FluxSmem S;
+  __shared__ Args A;
+  const int4 t = B.tiles[blockIdx.x];
+  const BatchCtl &c = B.ctl[t.x];
+  if (!c.active) return;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    A = B.args[2 * t.x + c.cur];
+    A.lxh = c.lxh;
+    A.lxl = c.lxl;
+    A.lyh = c.lyh;
+    A.lyl = c.lyl;
+  }
+  __syncthreads();
+  flux_tile(A, S, t.y, t.z);
+}
+
 }  // namespace
 
-cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &n1,
-                               const NodeSet &n2, float *avg_hi, float *avg_lo, double lamx,
-                               double lamy, int *status, unsigned *speed, int *speed_bad, cudaStream_t s) {
+FluxArgs flux_args(const Grid &g, const NodeSet &n0, const NodeSet &n1, const NodeSet &n2, float *avg_hi,
+                   float *avg_lo, int *status, unsigned *speed, int *speed_bad) {
   Args A;
   A.g = g;
   for (int k = 0; k < 3; k++) {
@@ -219,17 +245,30 @@ cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &
   }
   A.hi = avg_hi;
   A.lo = avg_lo;
-  A.lxh = (float)lamx;
-  A.lxl = (float)(lamx - (double)A.lxh);
-  A.lyh = (float)lamy;
-  A.lyl = (float)(lamy - (double)A.lyh);
+  A.lxh = A.lxl = A.lyh = A.lyl = 0.0f;
   A.status = status;
   A.speed = speed;
   A.speed_bad = speed_bad;
+  return A;
+}
+
+cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &n1,
+                               const NodeSet &n2, float *avg_hi, float *avg_lo, double lamx,
+                               double lamy, int *status, unsigned *speed, int *speed_bad, cudaStream_t s) {
+  Args A = flux_args(g, n0, n1, n2, avg_hi, avg_lo, status, speed, speed_bad);
+  split_double(lamx, A.lxh, A.lxl);
+  split_double(lamy, A.lyh, A.lyl);
   cudaMemsetAsync(speed, 0, sizeof(unsigned), s);
   cudaMemsetAsync(speed_bad, 0, sizeof(int), s);
   dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY), blk(TX, TY);
   flux_update_kernel<<<grd, blk, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flux_batch(const FluxBatch &B, int ntiles, cudaStream_t s) {
+  static_assert(TX == FLUX_TX && TY == FLUX_TY, "tile list shape");
+  if (ntiles <= 0) return cudaSuccess;
+  flux_batch_kernel<<<ntiles, dim3(TX, TY), 0, s>>>(B);
   return cudaGetLastError();
 }
 

@@ -21,17 +21,120 @@ struct Options {
   int force_lo = 0;    // test hook
 };
 
-// ghost layers of the t^n state (cell averages hi/lo and the three node arrays)
-cudaError_t launch_ghost_fill(const Grid &g, float *avg_hi, float *avg_lo, const NodeSet &n,
-                              cudaStream_t s);
 // TMA descriptors of the t^n node arrays and the cell averages (one set per
 // physical buffer that can hold t^n)
 struct TileMaps {
   CUtensorMap vtx, xe, ye, avg;
 };
-cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, float *avg, TileMaps *out);
+
+// arguments of the point-value kernel for one grid (dt set per step)
+struct PointValueArgs {
+  Grid g;
+  const float *__restrict__ n0[3];
+  const float *__restrict__ hi;
+  float *n1[3];
+  float *n2[3];
+  float dt;
+  int lin_mode, tsw, limiter, correction, force_lo;
+  int *status;
+  unsigned long long *counters;
+};
+inline PointValueArgs pointvalue_args(const Grid &g, const NodeSet &n0, const float *avg_hi, const NodeSet &n1,
+                                      const NodeSet &n2, const Options &o, int *status,
+                                      unsigned long long *counters) {
+  PointValueArgs A;
+  A.g = g;
+  for (int k = 0; k < 3; k++) {
+    A.n0[k] = n0.k[k];
+    A.n1[k] = n1.k[k];
+    A.n2[k] = n2.k[k];
+  }
+  A.hi = avg_hi;
+  A.dt = 0.0f;
+  A.lin_mode = o.lin_mode;
+  A.tsw = o.tsw;
+  A.limiter = o.limiter;
+  A.correction = o.correction;
+  A.force_lo = o.force_lo;
+  A.status = status;
+  A.counters = counters;
+  return A;
+}
+
+// arguments of the flux / update kernel for one grid (time-step ratios set per step)
+struct FluxArgs {
+  Grid g;
+  const float *__restrict__ n[3][3];  // [level][kind]
+  float *hi, *lo;
+  float lxh, lxl, lyh, lyl;  // dt/dx and dt/dy as double-word FP32 (hi + lo)
+  int *status;
+  unsigned *speed;  // max of max(|u|,|v|) + c over the new state, as float bits
+  int *speed_bad;   // set if a new value is not admissible
+};
+FluxArgs flux_args(const Grid &g, const NodeSet &n0, const NodeSet &n1, const NodeSet &n2, float *avg_hi,
+                   float *avg_lo, int *status, unsigned *speed, int *speed_bad);
+// (h, l) with h + l = x to about 48 bits
+inline void split_double(double x, float &h, float &l) {
+  h = (float)x;
+  l = (float)(x - (double)h);
+}
+
+// Per-instance control block of a batch, on the device.  The dt kernel
+// writes dt and the ratios each step from the wave speed that the previous
+// step's flux kernel left in `speed`.
+struct BatchCtl {
+  double t, t_end, cfl, h, dx, dy;
+  float dt;
+  float lxh, lxl, lyh, lyl;
+  int active;   // 0 once t reaches t_end or the state stopped being admissible
+  int cur;      // which of the two t^n / t^{n+1} buffers holds t^n
+  int stepped;  // the step just enqueued advances this instance (cur flips after it)
+  int status;   // StatusBits, accumulated until read
+  unsigned speed;
+  int speed_bad;
+  int steps;
+  unsigned long long counters[4];
+};
+enum BatchDtMode { DT_STEP = 0, DT_SETTLE = 1, DT_PROBE = 2 };
+
+// batched launches: one block per tile (instance, i0, j0, -)
+struct PointValueBatch {
+  const int4 *tiles;
+  const BatchCtl *ctl;
+  const PointValueArgs *args;  // [instance][buffer]
+  const TileMaps *maps;        // [instance][buffer]
+};
+struct FluxBatch {
+  const int4 *tiles;
+  BatchCtl *ctl;
+  const FluxArgs *args;  // [instance][buffer]
+};
+struct GhostBatch {
+  const BatchCtl *ctl;
+  const Grid *grids;       // [instance]
+  float *const *arrays;    // [instance][buffer][5]: avg hi, avg lo, vtx, xe, ye of t^n
+};
+
+// ghost layers of the t^n state (cell averages hi/lo and the three node arrays)
+cudaError_t launch_ghost_fill(const Grid &g, float *avg_hi, float *avg_lo, const NodeSet &n,
+                              cudaStream_t s);
+// tile_h: the point-value tile height the maps are for (4, 8 or 16)
+cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, float *avg, int tile_h,
+                           TileMaps *out);
 // one-time kernel attributes (shared-memory size) on the current device
 cudaError_t prepare_pointvalue();
+// batched point values over a tile list of tile height tile_h (4, 8 or 16)
+cudaError_t launch_pointvalue_batch(const PointValueBatch &B, int ntiles, int tile_h, cudaStream_t s);
+// batched flux / update over a tile list of 32 x 8 cells
+cudaError_t launch_flux_batch(const FluxBatch &B, int ntiles, cudaStream_t s);
+constexpr int FLUX_TX = 32, FLUX_TY = 8;
+// batched ghost fill; max_per: the largest per-instance ghost count
+cudaError_t launch_ghost_batch(const GhostBatch &B, int n, long long max_per, cudaStream_t s);
+long long ghost_count(const Grid &g);
+// per-instance dt for the coming step (mode DT_STEP; records it into
+// hist[step * n + k] if hist), only the buffer flip of the last step
+// (DT_SETTLE), or dt without advancing anything (DT_PROBE)
+cudaError_t launch_batch_dt(BatchCtl *ctl, int n, double *hist, int hist_cap, int mode, cudaStream_t s);
 // cell prep and point values at t^{n+1/2} (n1) and t^{n+1} (n2)
 cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,

@@ -30,41 +30,118 @@ struct GhostArgs {
   float *a[5];  // avg_hi, avg_lo, vtx, xe, ye
 };
 
-__global__ void ghost_kernel(GhostArgs A) {
-  const Grid &g = A.g;
-  const int arr = blockIdx.y;
-  const int nodex = (arr == 2 || arr == 3), nodey = (arr == 2 || arr == 4);
-  const int ownx = nodex ? g.nxv : g.nx, owny = nodey ? g.nyv : g.ny;
-  const int hix = nodex ? g.nx + G + 1 : g.nx + G, hiy = nodey ? g.ny + G + 1 : g.ny + G;
-  const int wext = hix + G;
-  const int nb = G * wext, nt = (hiy - owny) * wext, nl = owny * G, wr = hix - ownx;
-  const int total = nb + nt + nl + owny * wr;
-  float *p = A.a[arr];
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
-    int i, j, r = k;
-    if (r < nb) {
-      j = -G + r / wext;
-      i = -G + r % wext;
-    } else if ((r -= nb) < nt) {
-      j = owny + r / wext;
-      i = -G + r % wext;
-    } else if ((r -= nt) < nl) {
-      j = r / G;
-      i = -G + r % G;
-    } else {
-      r -= nl;
-      j = r / wr;
-      i = ownx + r % wr;
-    }
-    bool fx = false, fy = false;
-    const int si = ghost_src(i, g.nx, ownx, nodex, g.per_x, g.bc[0], g.bc[1], fx);
-    const int sj = ghost_src(j, g.ny, owny, nodey, g.per_y, g.bc[2], g.bc[3], fy);
+// entries of array arr (0..4) in ghost order; total is their number
+struct GhostRange {
+  int nodex, nodey, ownx, owny, hix, hiy, wext, nb, nt, nl, wr, total;
+  __host__ __device__ GhostRange(const Grid &g, int arr) {
+    nodex = (arr == 2 || arr == 3);
+    nodey = (arr == 2 || arr == 4);
+    ownx = nodex ? g.nxv : g.nx;
+    owny = nodey ? g.nyv : g.ny;
+    hix = nodex ? g.nx + G + 1 : g.nx + G;
+    hiy = nodey ? g.ny + G + 1 : g.ny + G;
+    wext = hix + G;
+    nb = G * wext;
+    nt = (hiy - owny) * wext;
+    nl = owny * G;
+    wr = hix - ownx;
+    total = nb + nt + nl + owny * wr;
+  }
+};
+
+// ghost entry k of an array: copy from its source (flipping the normal velocity at walls)
+__device__ __forceinline__ void ghost_entry(const Grid &g, const GhostRange &R, float *p, int k) {
+  int i, j, r = k;
+  if (r < R.nb) {
+    j = -G + r / R.wext;
+    i = -G + r % R.wext;
+  } else if ((r -= R.nb) < R.nt) {
+    j = R.owny + r / R.wext;
+    i = -G + r % R.wext;
+  } else if ((r -= R.nt) < R.nl) {
+    j = r / G;
+    i = -G + r % G;
+  } else {
+    r -= R.nl;
+    j = r / R.wr;
+    i = R.ownx + r % R.wr;
+  }
+  bool fx = false, fy = false;
+  const int si = ghost_src(i, g.nx, R.ownx, R.nodex, g.per_x, g.bc[0], g.bc[1], fx);
+  const int sj = ghost_src(j, g.ny, R.owny, R.nodey, g.per_y, g.bc[2], g.bc[3], fy);
 #pragma unroll
-    for (int v = 0; v < NV; v++) {
-      float x = p[at(g, v, si, sj)];
-      if ((v == 1 && fx) || (v == 2 && fy)) x = -x;
-      p[at(g, v, i, j)] = x;
+  for (int v = 0; v < NV; v++) {
+    float x = p[at(g, v, si, sj)];
+    if ((v == 1 && fx) || (v == 2 && fy)) x = -x;
+    p[at(g, v, i, j)] = x;
+  }
+}
+
+__global__ void ghost_kernel(GhostArgs A) {
+  const int arr = blockIdx.y;
+  const GhostRange R(A.g, arr);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < R.total; k += gridDim.x * blockDim.x)
+    ghost_entry(A.g, R, A.a[arr], k);
+}
+
+// batched: blockIdx.z is the instance
+__global__ void ghost_batch_kernel(GhostBatch B) {
+  const int inst = blockIdx.z, arr = blockIdx.y;
+  if (!B.ctl[inst].active) return;
+  const Grid g = B.grids[inst];
+  const GhostRange R(g, arr);
+  float *p = B.arrays[(2 * inst + B.ctl[inst].cur) * 5 + arr];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < R.total; k += gridDim.x * blockDim.x)
+    ghost_entry(g, R, p, k);
+}
+
+// Per-instance dt for the coming step from the wave speed of the current
+// state (CFL condition, Sec. 2): dt = cfl * min(dx, dy) / speed, clipped so
+// that the step ends at t_end.  An instance stops at t_end, or when its
+// state has no finite positive wave speed (flagged ST_STOPPED).  The flip of
+// the t^n buffer of the previous step is applied first; the speed is zeroed
+// for the coming step's flux kernel, which refills it.
+__global__ void batch_dt_kernel(BatchCtl *ctl, int n, double *hist, int hist_cap, int mode) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  BatchCtl &c = ctl[k];
+  if (mode != DT_PROBE && c.stepped) {
+    c.cur ^= 1;
+    c.stepped = 0;
+  }
+  if (mode == DT_SETTLE) return;
+  double dt = 0.0;
+  int go = 0;
+  if (c.active) {
+    const float sp = __uint_as_float(c.speed);
+    const double left = c.t_end - c.t;
+    if (c.speed_bad || !(sp > 0.0f) || !isfinite(sp)) {
+      if (mode == DT_STEP) {
+        c.active = 0;
+        c.status |= ST_STOPPED;
+      }
+    } else if (isfinite(c.t_end) && !(left > 1e-12 * fabs(c.t_end))) {
+      if (mode == DT_STEP) c.active = 0;
+    } else {
+      dt = c.cfl * c.h / (double)sp;
+      if (dt >= left) dt = left;
+      go = 1;
     }
+  }
+  c.dt = (float)dt;
+  const double lx = dt / c.dx, ly = dt / c.dy;
+  c.lxh = (float)lx;
+  c.lxl = (float)(lx - (double)c.lxh);
+  c.lyh = (float)ly;
+  c.lyl = (float)(ly - (double)c.lyh);
+  if (mode == DT_PROBE) return;
+  if (go) {
+    if (hist && c.steps < hist_cap) hist[(long long)c.steps * n + k] = dt;
+    c.t += dt;
+    c.steps += 1;
+    c.stepped = 1;
+    c.speed = 0u;
+    c.speed_bad = 0;
   }
 }
 
@@ -185,6 +262,29 @@ cudaError_t launch_ghost_fill(const Grid &g, float *avg_hi, float *avg_lo, const
   int blocks = (int)((per + 255) / 256);
   if (blocks < 1) blocks = 1;
   ghost_kernel<<<dim3(blocks, 5), 256, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+long long ghost_count(const Grid &g) {
+  long long m = 0;
+  for (int arr = 0; arr < 5; arr++) {
+    const GhostRange R(g, arr);
+    if (R.total > m) m = R.total;
+  }
+  return m;
+}
+
+cudaError_t launch_ghost_batch(const GhostBatch &B, int n, long long max_per, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (int)((max_per + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  ghost_batch_kernel<<<dim3(blocks, 5, n), 256, 0, s>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_dt(BatchCtl *ctl, int n, double *hist, int hist_cap, int mode, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  batch_dt_kernel<<<(n + 127) / 128, 128, 0, s>>>(ctl, n, hist, hist_cap, mode);
   return cudaGetLastError();
 }
 

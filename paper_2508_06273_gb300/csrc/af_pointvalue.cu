@@ -36,45 +36,44 @@ constexpr float PI_F = 3.14159265358979f;
 constexpr float INV_PI = 0.318309886183791f;
 constexpr float INV_2PI = 0.159154943091895f;
 
-constexpr int TX = 32, TY = 8;               // cells per tile
-constexpr int HX = TX + 2, HY = TY + 2;      // with a one-cell halo on each side
+// A tile is TX x TY cells: TX = 32 (one warp along x) and TY rows, TY one
+// of the heights in tile_heights (the batched path picks one by timing).
+constexpr int TX = 32;
+constexpr int HX = TX + 2;                   // with a one-cell halo on each side
 constexpr int CELL_F = 52;                   // floats per cell in shared memory
 // per cell: 4 variables x (9 monomial coefficients + 3 pad) = 48 floats, then Ubar (4)
 constexpr int UBAR_OFF = 48;
-constexpr int REC_FLOATS = HX * HY * CELL_F;
 // Raw t^n data of a tile, staged by TMA: for each of the node arrays (vertex,
-// x-edge, y-edge) and the cell averages a box of RAW_W x RAW_H points x 4
+// x-edge, y-edge) and the cell averages a box of RAW_W x (TY + 3) points x 4
 // variables.  The box starts 4 points left of the first halo point so that
 // its x coordinate is a multiple of 4 floats (16 bytes), and 1 row below.
-constexpr int RAW_W = TX + 8, RAW_H = TY + 3;
-constexpr int RAW_ARR = RAW_W * RAW_H * NV;  // floats per array
-constexpr int RAW_FLOATS = 4 * RAW_ARR;
-constexpr unsigned RAW_BYTES = RAW_FLOATS * 4u;
-constexpr int SMEM_BYTES = (RAW_FLOATS + REC_FLOATS) * 4 + 128;  // + alignment slack
+constexpr int RAW_W = TX + 8;
+template <int TY>
+struct Tile {
+  static constexpr int HY = TY + 2;
+  static constexpr int REC_FLOATS = HX * HY * CELL_F;
+  static constexpr int RAW_H = TY + 3;
+  static constexpr int RAW_ARR = RAW_W * RAW_H * NV;  // floats per array
+  static constexpr int RAW_FLOATS = 4 * RAW_ARR;
+  static constexpr unsigned RAW_BYTES = RAW_FLOATS * 4u;
+  static constexpr int SMEM_BYTES = (RAW_FLOATS + REC_FLOATS) * 4 + 128;  // + alignment slack
+};
 enum { RAW_VTX = 0, RAW_XE = 1, RAW_YE = 2, RAW_AVG = 3 };
 // bound on the mbarrier wait (try_wait suspends in hardware between polls)
 constexpr unsigned WAIT_LIMIT = 1u << 22;
 
-struct Args {
-  Grid g;
-  const float *__restrict__ n0[3];
-  const float *__restrict__ hi;
-  float *n1[3];
-  float *n2[3];
-  float dt;
-  int lin_mode, tsw, limiter, correction, force_lo;
-  int *status;
-  unsigned long long *counters;
-};
+using Args = PointValueArgs;
 
 // staged t^n value of array arr, variable v, at grid index (i, j), for the
 // tile with origin (i0, j0)
+template <int TY>
 __device__ __forceinline__ float raw_at(const float *raw, int arr, int v, int i, int j, int i0, int j0) {
-  return raw[((arr * NV + v) * RAW_H + (j - j0 + 1)) * RAW_W + (i - i0 + 4)];
+  return raw[((arr * NV + v) * Tile<TY>::RAW_H + (j - j0 + 1)) * RAW_W + (i - i0 + 4)];
 }
+template <int TY>
 __device__ __forceinline__ void raw4(const float *raw, int arr, int i, int j, int i0, int j0, float U[4]) {
 #pragma unroll
-  for (int v = 0; v < NV; v++) U[v] = raw_at(raw, arr, v, i, j, i0, j0);
+  for (int v = 0; v < NV; v++) U[v] = raw_at<TY>(raw, arr, v, i, j, i0, j0);
 }
 
 __device__ __forceinline__ float ld(const Args &A, const float *p, int v, int i, int j) {
@@ -110,18 +109,19 @@ __device__ __forceinline__ void to_monomial(const float f[3][3], float m[3][3]) 
 }
 
 // prep of cell (ci, cj) and its record in shared memory, from the staged tile
+template <int TY>
 __device__ __forceinline__ void build_cell(const Grid &g, const float *raw, int i0, int j0, int ci, int cj,
                                            float *rec) {
   const float gm1 = g.gamma - 1.0f, gm1i = 1.0f / gm1;
   float N[8][4];  // corners (ll, lr, ul, ur), then edges (left, right, bottom, top)
-  raw4(raw, RAW_VTX, ci, cj, i0, j0, N[0]);
-  raw4(raw, RAW_VTX, ci + 1, cj, i0, j0, N[1]);
-  raw4(raw, RAW_VTX, ci, cj + 1, i0, j0, N[2]);
-  raw4(raw, RAW_VTX, ci + 1, cj + 1, i0, j0, N[3]);
-  raw4(raw, RAW_XE, ci, cj, i0, j0, N[4]);
-  raw4(raw, RAW_XE, ci + 1, cj, i0, j0, N[5]);
-  raw4(raw, RAW_YE, ci, cj, i0, j0, N[6]);
-  raw4(raw, RAW_YE, ci, cj + 1, i0, j0, N[7]);
+  raw4<TY>(raw, RAW_VTX, ci, cj, i0, j0, N[0]);
+  raw4<TY>(raw, RAW_VTX, ci + 1, cj, i0, j0, N[1]);
+  raw4<TY>(raw, RAW_VTX, ci, cj + 1, i0, j0, N[2]);
+  raw4<TY>(raw, RAW_VTX, ci + 1, cj + 1, i0, j0, N[3]);
+  raw4<TY>(raw, RAW_XE, ci, cj, i0, j0, N[4]);
+  raw4<TY>(raw, RAW_XE, ci + 1, cj, i0, j0, N[5]);
+  raw4<TY>(raw, RAW_YE, ci, cj, i0, j0, N[6]);
+  raw4<TY>(raw, RAW_YE, ci, cj + 1, i0, j0, N[7]);
   float Qs[4] = {0, 0, 0, 0}, Us[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int n = 0; n < 8; n++) {
@@ -136,7 +136,7 @@ __device__ __forceinline__ void build_cell(const Grid &g, const float *raw, int 
   }
   float Qc[4], Uc[4];
 #pragma unroll
-  for (int v = 0; v < NV; v++) Qc[v] = (36.0f * raw_at(raw, RAW_AVG, v, ci, cj, i0, j0) - Qs[v]) * 0.0625f;
+  for (int v = 0; v < NV; v++) Qc[v] = (36.0f * raw_at<TY>(raw, RAW_AVG, v, ci, cj, i0, j0) - Qs[v]) * 0.0625f;
   c2p(Qc, gm1, Uc);
 #pragma unroll
   for (int v = 0; v < NV; v++) {
@@ -594,7 +594,7 @@ __device__ __forceinline__ bool tsw_vertex(const float *sm, float gam, int a, in
 
 // Corollary 1: T such that C = tau^2/2 T, from centred differences of
 // neighbouring point values or cell-centre values (U_c = monomial m00)
-template <int K>
+template <int K, int TY>
 __device__ __forceinline__ void correction(const Grid &g, const float *sm, const float *raw, int i, int j,
                                            int i0, int j0, const float U[4], float T[4]) {
   float Ux[4], Uy[4];
@@ -602,13 +602,13 @@ __device__ __forceinline__ void correction(const Grid &g, const float *sm, const
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     if (K == VTX) {
-      Ux[v] = (raw_at(raw, RAW_YE, v, i, j, i0, j0) - raw_at(raw, RAW_YE, v, i - 1, j, i0, j0)) * g.idx;
-      Uy[v] = (raw_at(raw, RAW_XE, v, i, j, i0, j0) - raw_at(raw, RAW_XE, v, i, j - 1, i0, j0)) * g.idy;
+      Ux[v] = (raw_at<TY>(raw, RAW_YE, v, i, j, i0, j0) - raw_at<TY>(raw, RAW_YE, v, i - 1, j, i0, j0)) * g.idx;
+      Uy[v] = (raw_at<TY>(raw, RAW_XE, v, i, j, i0, j0) - raw_at<TY>(raw, RAW_XE, v, i, j - 1, i0, j0)) * g.idy;
     } else if (K == XE) {
       Ux[v] = (centre(sm, a, b, v) - centre(sm, a - 1, b, v)) * g.idx;
-      Uy[v] = (raw_at(raw, RAW_VTX, v, i, j + 1, i0, j0) - raw_at(raw, RAW_VTX, v, i, j, i0, j0)) * g.idy;
+      Uy[v] = (raw_at<TY>(raw, RAW_VTX, v, i, j + 1, i0, j0) - raw_at<TY>(raw, RAW_VTX, v, i, j, i0, j0)) * g.idy;
     } else {
-      Ux[v] = (raw_at(raw, RAW_VTX, v, i + 1, j, i0, j0) - raw_at(raw, RAW_VTX, v, i, j, i0, j0)) * g.idx;
+      Ux[v] = (raw_at<TY>(raw, RAW_VTX, v, i + 1, j, i0, j0) - raw_at<TY>(raw, RAW_VTX, v, i, j, i0, j0)) * g.idx;
       Uy[v] = (centre(sm, a, b, v) - centre(sm, a, b - 1, v)) * g.idy;
     }
   }
@@ -631,7 +631,7 @@ __device__ __forceinline__ void st4(float *p, const Grid &g, int i, int j, const
 }
 
 // both time levels of node (K, i, j), tile-local (li, lj)
-template <int K>
+template <int K, int TY>
 __device__ __forceinline__ void node_update(const Args &A, const float *sm, const float *raw, int i0, int j0,
                                             int i, int j, int li, int lj, unsigned cnt[4], bool &cfl_bad,
                                             bool &nonfinite) {
@@ -639,8 +639,8 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
   const int ni = (K == YE) ? g.nx : g.nxv, nj = (K == XE) ? g.ny : g.nyv;
   if (i >= ni || j >= nj) return;
   float U0[4], T[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  raw4(raw, K == VTX ? RAW_VTX : (K == XE ? RAW_XE : RAW_YE), i, j, i0, j0, U0);
-  if (A.correction) correction<K>(g, sm, raw, i, j, i0, j0, U0, T);
+  raw4<TY>(raw, K == VTX ? RAW_VTX : (K == XE ? RAW_XE : RAW_YE), i, j, i0, j0, U0);
+  if (A.correction) correction<K, TY>(g, sm, raw, i, j, i0, j0, U0, T);
 
   float ul[4], res[4];
   // linearisation state of the half step
@@ -706,23 +706,25 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
 
 // prologue: the block builds the records of its (TX+2) x (TY+2) cells; only
 // cells -1..nx, -1..ny can be referenced by owned nodes, the others are skipped
+template <int TY>
 __device__ __forceinline__ void tile_prologue(const Args &A, const float *raw, float *sm, int i0, int j0,
                                               int tid) {
-  for (int k = tid; k < HX * HY; k += TX * TY) {
+  for (int k = tid; k < HX * Tile<TY>::HY; k += TX * TY) {
     const int a = k % HX, b = k / HX, ci = i0 - 1 + a, cj = j0 - 1 + b;
-    if (ci <= A.g.nx && cj <= A.g.ny) build_cell(A.g, raw, i0, j0, ci, cj, sm + k * CELL_F);
+    if (ci <= A.g.nx && cj <= A.g.ny) build_cell<TY>(A.g, raw, i0, j0, ci, cj, sm + k * CELL_F);
   }
 }
 
 // node updates of the cell (i0 + tx, j0 + ty)
+template <int TY>
 __device__ __forceinline__ void tile_nodes(const Args &A, const float *sm, const float *raw, int i0, int j0,
                                            int tx, int ty) {
   unsigned cnt[4] = {0, 0, 0, 0};
   bool cfl_bad = false, nonfinite = false;
   const int i = i0 + tx, j = j0 + ty;
-  node_update<VTX>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
-  node_update<XE>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
-  node_update<YE>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
+  node_update<VTX, TY>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
+  node_update<XE, TY>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
+  node_update<YE, TY>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
   const int st = (cfl_bad ? ST_CFL : 0) | (nonfinite ? ST_NONFINITE : 0) | (cnt[CNT_KEPT] ? ST_KEPT : 0);
   if (st) atomicOr(A.status, st);
 #pragma unroll
@@ -736,13 +738,14 @@ __device__ __forceinline__ unsigned smem_addr(const void *p) {
 }
 
 // one thread: arm the barrier with the byte count and issue the four box loads
+template <int TY>
 __device__ __forceinline__ void tile_fetch(const TileMaps &T, float *raw, unsigned long long *bar, int i0,
                                            int j0) {
   const unsigned b = smem_addr(bar);
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(RAW_BYTES) : "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(Tile<TY>::RAW_BYTES) : "memory");
   // box origin: column i0 (grid index i0 - 4), row j0 + 1 (grid index j0 - 1), variable 0
   const int x = i0, y = j0 + OY - 1;
   const CUtensorMap *maps[4] = {&T.vtx, &T.xe, &T.ye, &T.avg};
@@ -750,7 +753,7 @@ __device__ __forceinline__ void tile_fetch(const TileMaps &T, float *raw, unsign
   for (int a = 0; a < 4; a++) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(raw + a * RAW_ARR)),
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(raw + a * Tile<TY>::RAW_ARR)),
         "l"(reinterpret_cast<unsigned long long>(maps[a])), "r"(x), "r"(y), "r"(0), "r"(b)
         : "memory");
   }
@@ -771,32 +774,62 @@ __device__ __forceinline__ bool tile_wait(unsigned long long *bar) {
   return false;
 }
 
-__global__ void __launch_bounds__(TX *TY) pointvalue_kernel(Args A, const __grid_constant__ TileMaps T) {
-  extern __shared__ float4 smem4[];
-  __shared__ alignas(8) unsigned long long bar;
-  // TMA destinations must start on 128-byte boundaries
-  float *raw = reinterpret_cast<float *>((reinterpret_cast<size_t>(smem4) + 127) & ~size_t(127));
-  float *sm = raw + RAW_FLOATS;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+// one tile: stage the t^n box, build the cell records, update the nodes
+template <int TY>
+__device__ __forceinline__ void tile_body(const Args &A, const TileMaps &T, float *raw, unsigned long long *bar,
+                                          int i0, int j0) {
+  float *sm = raw + Tile<TY>::RAW_FLOATS;
   const int tid = threadIdx.y * TX + threadIdx.x;
-  if (tid == 0) tile_fetch(T, raw, &bar, i0, j0);
+  if (tid == 0) tile_fetch<TY>(T, raw, bar, i0, j0);
   __syncthreads();
-  if (!tile_wait(&bar)) {
+  if (!tile_wait(bar)) {
     // the copy did not land in time: report it, give it one more bounded
     // wait so that nothing is still writing this block's shared memory, and
     // leave the tile alone
     if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
-    tile_wait(&bar);
+    tile_wait(bar);
     return;
   }
-  tile_prologue(A, raw, sm, i0, j0, tid);
+  tile_prologue<TY>(A, raw, sm, i0, j0, tid);
   __syncthreads();
-  tile_nodes(A, sm, raw, i0, j0, threadIdx.x, threadIdx.y);
+  tile_nodes<TY>(A, sm, raw, i0, j0, threadIdx.x, threadIdx.y);
+}
+
+// TMA destinations must start on 128-byte boundaries
+__device__ __forceinline__ float *tile_smem(float4 *smem4) {
+  return reinterpret_cast<float *>((reinterpret_cast<size_t>(smem4) + 127) & ~size_t(127));
+}
+
+template <int TY>
+__global__ void __launch_bounds__(TX *TY) pointvalue_kernel(Args A, const __grid_constant__ TileMaps T) {
+  extern __shared__ float4 smem4[];
+  __shared__ alignas(8) unsigned long long bar;
+  tile_body<TY>(A, T, tile_smem(smem4), &bar, blockIdx.x * TX, blockIdx.y * TY);
+}
+
+// Batched form: block b takes tile B.tiles[b] = (instance, i0, j0) and the
+// instance's arguments and descriptors for the buffer now holding its t^n;
+// instances that have stopped are skipped.
+template <int TY>
+__global__ void __launch_bounds__(TX *TY) pointvalue_batch_kernel(PointValueBatch B) {
+  extern __shared__ float4 smem4[];
+  __shared__ alignas(8) unsigned long long bar;
+  __shared__ Args A;
+  const int4 t = B.tiles[blockIdx.x];
+  const BatchCtl &c = B.ctl[t.x];
+  if (!c.active) return;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    A = B.args[2 * t.x + c.cur];
+    A.dt = c.dt;
+  }
+  __syncthreads();
+  tile_body<TY>(A, B.maps[2 * t.x + c.cur], tile_smem(smem4), &bar, t.y, t.z);
 }
 
 }  // namespace
 
-cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, float *avg, TileMaps *out) {
+cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, float *avg, int tile_h,
+                           TileMaps *out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void *fn = nullptr;
@@ -806,10 +839,11 @@ cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, floa
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorSymbolNotFound;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
+  if (tile_h != 4 && tile_h != 8 && tile_h != 16) return cudaErrorInvalidValue;
   // planes of P x H floats, 4 variables: 3-D tensors (x, row, variable)
   const cuuint64_t dims[3] = {(cuuint64_t)g.P, (cuuint64_t)g.H, (cuuint64_t)NV};
   const cuuint64_t strides[2] = {(cuuint64_t)g.P * 4u, (cuuint64_t)g.plane * 4u};
-  const cuuint32_t box[3] = {(cuuint32_t)RAW_W, (cuuint32_t)RAW_H, (cuuint32_t)NV};
+  const cuuint32_t box[3] = {(cuuint32_t)RAW_W, (cuuint32_t)(tile_h + 3), (cuuint32_t)NV};
   const cuuint32_t estr[3] = {1, 1, 1};
   float *base[4] = {vtx, xe, ye, avg};
   CUtensorMap *dst[4] = {&out->vtx, &out->xe, &out->ye, &out->avg};
@@ -826,32 +860,41 @@ cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, floa
 }
 
 cudaError_t prepare_pointvalue() {
-  return cudaFuncSetAttribute(pointvalue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaError_t e = cudaFuncSetAttribute(pointvalue_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Tile<8>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pointvalue_batch_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Tile<4>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pointvalue_batch_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Tile<8>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pointvalue_batch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Tile<16>::SMEM_BYTES);
+  return e;
 }
 
 cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
                               int *status, unsigned long long *counters, cudaStream_t s) {
-  Args A;
-  A.g = g;
-  for (int k = 0; k < 3; k++) {
-    A.n0[k] = n0.k[k];
-    A.n1[k] = n1.k[k];
-    A.n2[k] = n2.k[k];
-  }
-  A.hi = avg_hi;
+  Args A = pointvalue_args(g, n0, avg_hi, n1, n2, o, status, counters);
   A.dt = dt;
-  A.lin_mode = o.lin_mode;
-  A.tsw = o.tsw;
-  A.limiter = o.limiter;
-  A.correction = o.correction;
-  A.force_lo = o.force_lo;
-  A.status = status;
-  A.counters = counters;
   // tiles cover the owned nodes: up to nxv x nyv (vertex lines n + 1 on a
   // non-periodic axis); every box x coordinate is a multiple of TX floats
+  constexpr int TY = 8;
   dim3 grd((g.nxv + TX - 1) / TX, (g.nyv + TY - 1) / TY), blk(TX, TY);
-  pointvalue_kernel<<<grd, blk, SMEM_BYTES, s>>>(A, maps);
+  pointvalue_kernel<TY><<<grd, blk, Tile<TY>::SMEM_BYTES, s>>>(A, maps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pointvalue_batch(const PointValueBatch &B, int ntiles, int tile_h, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  switch (tile_h) {
+    case 4: pointvalue_batch_kernel<4><<<ntiles, dim3(TX, 4), Tile<4>::SMEM_BYTES, s>>>(B); break;
+    case 8: pointvalue_batch_kernel<8><<<ntiles, dim3(TX, 8), Tile<8>::SMEM_BYTES, s>>>(B); break;
+    case 16: pointvalue_batch_kernel<16><<<ntiles, dim3(TX, 16), Tile<16>::SMEM_BYTES, s>>>(B); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -114,7 +114,8 @@ def discretise(prob: Problem, field: Optional[Field] = None):
 def discretise_torch(prob: Problem, device, field: Optional[Field] = None, dtype=None):
     """Same as ``discretise`` but evaluated with torch in float64 on ``device``
     (for large grids); returns float32 tensors unless ``dtype`` is given.
-    Only for fields written against numpy/torch alike (``shu_vortex``)."""
+    Only for fields written against numpy/torch alike (``shu_vortex``,
+    the four-quadrant data)."""
     import torch
 
     f = field or prob.field
@@ -282,11 +283,16 @@ def _piecewise(states, xs, ys):
     S = np.asarray(states, dtype=np.float64)  # (4 quadrants, 4 vars)
 
     def f(x, y):
-        x, y = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
-        wx_r = np.where(x > xs, 1.0, np.where(x == xs, 0.5, 0.0))
-        wy_u = np.where(y > ys, 1.0, np.where(y == ys, 0.5, 0.0))
+        m = _mod(x)
+        if m is np:
+            x, y = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
+        else:
+            x, y = m.broadcast_tensors(x, y)
+        one = (lambda c: c.astype(np.float64)) if m is np else (lambda c: c.to(x.dtype))
+        wx_r = one(x > xs) + 0.5 * one(x == xs)
+        wy_u = one(y > ys) + 0.5 * one(y == ys)
         w = [(1 - wx_r) * (1 - wy_u), wx_r * (1 - wy_u), (1 - wx_r) * wy_u, wx_r * wy_u]
-        return tuple(sum(w[q] * S[q, k] for q in range(4)) for k in range(4))
+        return tuple(sum(w[q] * float(S[q, k]) for q in range(4)) for k in range(4))
 
     return f
 
@@ -330,6 +336,25 @@ def kelvin_helmholtz(n=64, t_end=1.0, cfl=0.3):
 
     return Problem("kelvin_helmholtz", n, n, -0.5, -0.5, 1.0, 1.0, (0, 0, 0, 0), f, t_end,
                    cfl=cfl, options={"limiter": 1})
+
+
+def ensemble(n=256, seed=4096, lo=64, ratio=8.0, steps=200):
+    """Ensemble of ``n`` independent problems of uneven sizes: N x N cells
+    with N = round(lo * ratio**U), U ~ U[0,1) drawn from ``seed`` (64^2 to
+    512^2 by default, log-uniform); even instances are seeded isentropic
+    vortices (centre and strength in [3,6] on periodic [0,10]^2), odd ones
+    seeded four-quadrant Riemann problems on [0,1]^2 with outflow boundaries.
+    Every instance runs ``steps`` steps (end time +inf)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.rint(lo * ratio ** rng.uniform(0.0, 1.0, size=n)).astype(int)
+    probs = []
+    for k, N in enumerate(sizes):
+        if k % 2 == 0:
+            p = shu_vortex_seeded(int(N), seed=seed + k, t_end=np.inf)
+        else:
+            p = four_quadrant(int(N), seed=seed + k, t_end=np.inf)
+        probs.append(p)
+    return probs
 
 
 def fourier_smooth(nx=32, ny=32, seed=1, amp=0.15, lx=1.0, ly=1.0, modes=3):
