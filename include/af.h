@@ -229,6 +229,21 @@ long long af_batch_active_cells(af_batch *b);
 /* The batch's stream (0 = the legacy default stream); as af_set_stream. */
 int af_batch_set_stream(af_batch *b, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Tensor-core GEMM used by the surrogate's training: D (+)= A B^T (+ bias)
+ * with A (M x K) and B (N x K) row-major BF16 device arrays (leading
+ * dimensions lda, ldb in elements) and D (M x N, leading dimension ldd) FP32,
+ * accumulated in FP32 on the tcgen05 tensor cores.  0 < N <= 128; K, lda and
+ * ldb multiples of 8; A and B 16-byte aligned.  splits > 1 divides K over
+ * that many CTAs per 128-row block, whose partial products are added into D
+ * with atomics (summation order then varies).  accumulate = 1 adds into D
+ * instead of overwriting it; bias (N floats, or NULL) is added once.  err:
+ * a device int that gets bit 1 if a tensor-core wait timed out (NULL: a
+ * library-owned flag).  Asynchronous on `stream`; AF_ERR_ARG for shapes
+ * outside these limits. */
+int af_gemm_bf16(const void *A, int lda, const void *B, int ldb, float *D, int ldd, int M, int N, int K,
+                 const float *bias, int splits, int accumulate, int *err, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

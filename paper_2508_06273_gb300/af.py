@@ -31,6 +31,7 @@ EXPORTS = [
     "af_batch_create", "af_batch_destroy", "af_batch_set_option", "af_batch_set_state",
     "af_batch_get_state", "af_batch_set_end", "af_batch_run", "af_batch_query", "af_batch_counters",
     "af_batch_set_tile", "af_batch_autotune", "af_batch_active_cells", "af_batch_set_stream",
+    "af_gemm_bf16",
 ]
 
 
@@ -83,6 +84,7 @@ def lib():
                 "af_batch_autotune": (i, [vp, C.POINTER(C.c_int), fp]),
                 "af_batch_active_cells": (C.c_longlong, [vp]),
                 "af_batch_set_stream": (i, [vp, vp]),
+                "af_gemm_bf16": (i, [vp, i, vp, i, fp, i, i, i, i, fp, i, i, fp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)

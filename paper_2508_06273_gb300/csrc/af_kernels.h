@@ -159,6 +159,14 @@ cudaError_t launch_check_dup(const float *ext, int ni, int nj, int dup_x, int du
                              cudaStream_t s);
 cudaError_t launch_zero(float *p, long long n, cudaStream_t s);
 
+// tcgen05 BF16 GEMM: D[M x N] (+)= A[M x K] B[N x K]^T (+ bias); N <= 128,
+// K, lda, ldb multiples of 8; split-K over `splits` CTAs per row block
+// (partial sums added with atomics); *err |= 1 if an MMA wait timed out
+cudaError_t prepare_gemm();
+cudaError_t launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, float *D, int ldd, int M, int N,
+                             int K, const float *bias, int splits, int accumulate, int *err, cudaStream_t s);
+int *gemm_default_err();
+
 // record a message for af_last_error on this host thread; returns code
 int set_error(int code, const char *msg);
 
