@@ -244,6 +244,44 @@ int af_batch_set_stream(af_batch *b, void *stream);
 int af_gemm_bf16(const void *A, int lda, const void *B, int ldb, float *D, int ldd, int M, int N, int K,
                  const float *bias, int splits, int accumulate, int *err, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Surrogate network (af_mlp): a learned stand-in for the point-value
+ * operator at one node.  64 inputs -> 128 -> 128 -> 128 -> 16 outputs (8
+ * used), GELU (tanh form) on the hidden layers, BF16 weights on the tensor
+ * cores with FP32 accumulation.  Inputs are multiplied by fixed per-input
+ * scales and outputs by per-output scales (af_mlp_fit_scales).  Parameters
+ * are exchanged as AF_MLP_NPARAM floats: W1 (128 x 64, row-major, out x in),
+ * b1 (128), W2 (128 x 128), b2, W3 (128 x 128), b3, W4 (16 x 128, rows 8..15
+ * zero), b4 (16), the 64 input scales, the 8 output scales.  Feature and
+ * target layouts: see af_set_surrogate.
+ */
+#define AF_MLP_NPARAM 43480
+typedef struct af_mlp af_mlp;
+
+/* He-normal initial weights from a counter-based generator keyed by seed.
+ * NULL on error. */
+af_mlp *af_mlp_create(uint64_t seed);
+void af_mlp_destroy(af_mlp *m);
+/* Host arrays of AF_MLP_NPARAM floats.  Setting resets Adam's moments. */
+int af_mlp_set_params(af_mlp *m, const float *host);
+int af_mlp_get_params(af_mlp *m, float *host_out);
+/* Input scales 1 / rms(X[:, k]) (0 for an input that is always 0) and output
+ * scales rms(T[:, k]) from device arrays X (n x 64) and T (n x 8). */
+int af_mlp_fit_scales(af_mlp *m, const float *X, const float *T, long long n);
+/* Y (n x 8, device) = the network at the rows of X (n x 64, device),
+ * including both scales.  Through the training path's GEMM kernels. */
+int af_mlp_forward(af_mlp *m, const float *X, float *Y, int n, void *stream);
+/* Mean squared error over the 8 outputs of the n rows (targets divided by
+ * the output scales) and its gradient with respect to the trained
+ * parameters (host array of the first 43408 floats of the layout, or NULL). */
+int af_mlp_loss_grad(af_mlp *m, const float *X, const float *T, int n, double *loss, float *grads);
+/* `steps` Adam steps (lr, beta1 0.9, beta2 0.999, eps 1e-8) on minibatches of
+ * `batch` rows (a multiple of 8) drawn with replacement from the n samples
+ * by a counter-based generator keyed by seed (!= 0); loss_hist (host,
+ * `steps` floats, or NULL) gets each minibatch's loss.  Synchronous. */
+int af_mlp_train(af_mlp *m, const float *X, const float *T, long long n, int steps, int batch, double lr,
+                 uint64_t seed, float *loss_hist);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,9 @@ rho', c' = sqrt(gamma p'/rho') (rho by rho', u and v by c', p by rho' c'^2):
 * y-edge (i, j-1/2): the x-edge stencil of the frame with x and y (and u
   and v) exchanged, so that one network serves both edge kinds;
 
-then the CFL number (max(|u'|, |v'|) + c') dt / h, zero-padded to 64.
+then the geometry of the Mach-cone base over one step in cell units,
+c' dt / h, u' dt / h and v' dt / h (square cells, h = dx = dy; u and v
+exchanged for y-edges), zero-padded to 64: 55 vertex and 63 edge inputs.
 Outputs: (U^{n+1/2} - U^n) and (U^{n+1} - U^n) at the node in the same
 scaling (8 values, rotated for y-edges).
 
@@ -165,7 +167,9 @@ def features(state, bc, kind, I, J, dt, h, gamma=GAMMA):
     for q, v in enumerate(order):
         for m, w in enumerate(vals):
             X[:, q * per + m] = (w[v] - ut[v]) / s[v]
-    X[:, 4 * per] = (np.maximum(np.abs(ut[1]), np.abs(ut[2])) + c) * dt / h
+    X[:, 4 * per] = c * dt / h
+    X[:, 4 * per + 1] = ut[order[1]] * dt / h
+    X[:, 4 * per + 2] = ut[order[2]] * dt / h
     return X, ut.T, s.T
 
 

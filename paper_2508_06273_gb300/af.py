@@ -32,7 +32,10 @@ EXPORTS = [
     "af_batch_get_state", "af_batch_set_end", "af_batch_run", "af_batch_query", "af_batch_counters",
     "af_batch_set_tile", "af_batch_autotune", "af_batch_active_cells", "af_batch_set_stream",
     "af_gemm_bf16",
+    "af_mlp_create", "af_mlp_destroy", "af_mlp_set_params", "af_mlp_get_params", "af_mlp_fit_scales",
+    "af_mlp_forward", "af_mlp_loss_grad", "af_mlp_train",
 ]
+MLP_NPARAM, MLP_NTRAIN = 43480, 43408
 
 
 class AFError(RuntimeError):
@@ -85,6 +88,14 @@ def lib():
                 "af_batch_active_cells": (C.c_longlong, [vp]),
                 "af_batch_set_stream": (i, [vp, vp]),
                 "af_gemm_bf16": (i, [vp, i, vp, i, fp, i, i, i, i, fp, i, i, fp, vp]),
+                "af_mlp_create": (vp, [C.c_uint64]),
+                "af_mlp_destroy": (None, [vp]),
+                "af_mlp_set_params": (i, [vp, fp]),
+                "af_mlp_get_params": (i, [vp, fp]),
+                "af_mlp_fit_scales": (i, [vp, fp, fp, C.c_longlong]),
+                "af_mlp_forward": (i, [vp, fp, fp, i, vp]),
+                "af_mlp_loss_grad": (i, [vp, fp, fp, i, C.POINTER(C.c_double), fp]),
+                "af_mlp_train": (i, [vp, fp, fp, C.c_longlong, i, i, d, C.c_uint64, fp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -315,3 +326,62 @@ class Batch:
 
     def active_cells(self):
         return _check(self.L.af_batch_active_cells(self.h))
+
+
+class Mlp:
+    """The surrogate network (an af_mlp) on the current CUDA device."""
+
+    def __init__(self, seed=1):
+        import torch
+
+        self.torch = torch
+        self.L = lib()
+        self.h = self.L.af_mlp_create(int(seed))
+        if not self.h:
+            raise AFError(self.L.af_last_error().decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.af_mlp_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def get_params(self):
+        out = np.zeros(MLP_NPARAM, dtype=np.float32)
+        _check(self.L.af_mlp_get_params(self.h, C.c_void_p(out.ctypes.data)))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.shape != (MLP_NPARAM,):
+            raise ValueError(f"need {MLP_NPARAM} floats")
+        _check(self.L.af_mlp_set_params(self.h, C.c_void_p(p.ctypes.data)))
+
+    def fit_scales(self, X, T):
+        _check(self.L.af_mlp_fit_scales(self.h, _ptr(X.contiguous()), _ptr(T.contiguous()), X.shape[0]))
+
+    def forward(self, X):
+        """(n, 8) outputs for CUDA float32 features X (n, 64)."""
+        X = X.contiguous()
+        Y = self.torch.empty((X.shape[0], 8), dtype=self.torch.float32, device=X.device)
+        _check(self.L.af_mlp_forward(self.h, _ptr(X), _ptr(Y), X.shape[0],
+                                     C.c_void_p(self.torch.cuda.current_stream().cuda_stream)))
+        return Y
+
+    def loss_grad(self, X, T):
+        """(loss, gradient of the trained parameters as a float32 array)."""
+        loss = C.c_double()
+        g = np.zeros(MLP_NTRAIN, dtype=np.float32)
+        self.torch.cuda.synchronize()
+        _check(self.L.af_mlp_loss_grad(self.h, _ptr(X.contiguous()), _ptr(T.contiguous()), X.shape[0],
+                                       C.byref(loss), C.c_void_p(g.ctypes.data)))
+        return loss.value, g
+
+    def train(self, X, T, steps, batch=8192, lr=1e-3, seed=1):
+        """Adam steps on minibatches of (X, T); returns the loss per step."""
+        hist = np.zeros(max(steps, 1), dtype=np.float32)
+        self.torch.cuda.synchronize()
+        _check(self.L.af_mlp_train(self.h, _ptr(X.contiguous()), _ptr(T.contiguous()), X.shape[0], int(steps),
+                                   int(batch), float(lr), int(seed), C.c_void_p(hist.ctypes.data)))
+        return hist[:steps]

@@ -75,3 +75,97 @@ def test_gemm_rejects_bad_shapes(lib):
     s = C.c_void_p(0)
     assert L.af_gemm_bf16(_p(A), 60, _p(A), 60, _p(D), 200, 128, 129, 60, None, 1, 0, None, s) == -1
     assert L.af_gemm_bf16(_p(A), 60, _p(A), 60, _p(D), 200, 128, 64, 60, None, 1, 0, None, s) == -1  # K % 8
+
+
+# ------------------------------------------------------------ the network
+from oracle import surrogate as S  # noqa: E402
+
+LAYERS = (("W1", 0, (128, 64)), ("b1", 8192, (128,)), ("W2", 8320, (128, 128)), ("b2", 24704, (128,)),
+          ("W3", 24832, (128, 128)), ("b3", 41216, (128,)), ("W4", 41344, (16, 128)), ("b4", 43392, (16,)))
+
+
+def _unpack(p, bf16_weights):
+    import torch
+
+    P = {}
+    for name, off, shape in LAYERS:
+        a = np.asarray(p[off:off + int(np.prod(shape))], dtype=np.float32).reshape(shape)
+        if bf16_weights and name.startswith("W"):
+            a = torch.from_numpy(a.copy()).to(torch.bfloat16).float().numpy()
+        P[name] = a.astype(np.float64)
+    return P, p[43408:43472].astype(np.float64), p[43472:43480].astype(np.float64)
+
+
+def _bf16(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).double().numpy()
+
+
+@pytest.fixture(scope="module")
+def net(lib):
+    torch, L = lib
+    from paper_2508_06273_gb300 import af
+
+    m = af.Mlp(seed=11)
+    p = m.get_params()
+    rng = np.random.default_rng(4)
+    p[8192:8320] = rng.normal(0, 0.1, 128)     # b1
+    p[41216:41344] = rng.normal(0, 0.1, 128)   # b3
+    p[43392:43400] = rng.normal(0, 0.1, 8)     # b4 (used rows)
+    p[43408:43472] = rng.uniform(0.5, 2.0, 64)  # input scales
+    p[43472:43480] = rng.uniform(0.5, 2.0, 8)   # output scales
+    m.set_params(p)
+    yield m, p
+    m.close()
+
+
+def _data(torch, n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, 64)).astype(np.float32)
+    T = rng.normal(size=(n, 8)).astype(np.float32)
+    return X, T, torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+
+
+def test_mlp_forward_matches_the_oracle(lib, net):
+    torch, _ = lib
+    m, p = net
+    X, _, Xd, _ = _data(torch, 333, 1)
+    P, ins, outs = _unpack(p, True)
+    want = S.forward(P, _bf16(X * ins))[0][:, :8] * outs
+    got = m.forward(Xd).double().cpu().numpy()
+    rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert rel < 1e-2, rel  # hidden activations are rounded to BF16 on the GPU
+
+
+def test_mlp_gradient_matches_the_oracle(lib, net):
+    torch, _ = lib
+    m, p = net
+    X, T, Xd, Td = _data(torch, 1000, 2)
+    P, ins, outs = _unpack(p, True)
+    lo, go = S.loss_and_grads(P, _bf16(X * ins), T / outs)
+    lg, gg = m.loss_grad(Xd, Td)
+    assert lg == pytest.approx(lo, rel=1e-2)
+    for name, off, shape in LAYERS:
+        a = gg[off:off + int(np.prod(shape))].reshape(shape).astype(np.float64)
+        b = go[name]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert rel < 3e-2, (name, rel)
+
+
+def test_mlp_training_reduces_the_loss(lib):
+    torch, _ = lib
+    from paper_2508_06273_gb300 import af
+
+    rng = np.random.default_rng(5)
+    n = 20000
+    X = rng.normal(size=(n, 64)).astype(np.float32)
+    A = rng.normal(size=(64, 8)) / 8
+    T = (X @ A + 0.3 * np.tanh(X[:, :8])).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    m = af.Mlp(seed=2)
+    m.fit_scales(Xd, Td)
+    hist = m.train(Xd, Td, steps=400, batch=1024, lr=2e-3, seed=9)
+    assert np.all(np.isfinite(hist))
+    assert hist[-20:].mean() < 0.05 * hist[:5].mean(), (hist[:5], hist[-20:])
+    m.close()

@@ -24,16 +24,17 @@ def test_ubar_matches_the_c_oracle(oracle_mod):
             assert np.allclose(ub[:, j + 1, i + 1], want, rtol=1e-13, atol=1e-13), (i, j)
 
 
-def test_constant_state_has_only_the_cfl_feature():
-    prob = W.fourier_smooth(8, 6, amp=0.0)
+def test_constant_state_has_only_the_cone_features():
+    prob = W.fourier_smooth(8, 6, amp=0.0, lx=1.0, ly=0.75)
     st = W.discretise(prob)
     r, u, v, p = st[1][:, 0, 0]
     c = np.sqrt(1.4 * p / r)
     dt, h = 0.01, prob.dx
     for kind, n in ((S.VERTEX, 52), (S.XEDGE, 60), (S.YEDGE, 60)):
         X, ut, s = S.features(st, prob.bc, kind, np.array([0, 3, 7]), np.array([0, 2, 5]), dt, h)
-        assert np.abs(X[:, :n]).max() < 1e-14 and np.all(X[:, n + 1:] == 0)
-        assert np.allclose(X[:, n], (max(abs(u), abs(v)) + c) * dt / h, rtol=1e-14)
+        assert np.abs(X[:, :n]).max() < 1e-14 and np.all(X[:, n + 3:] == 0)
+        a, b = (v, u) if kind == S.YEDGE else (u, v)
+        assert np.allclose(X[:, n:n + 3], np.array([c, a, b]) * dt / h, rtol=1e-14)
 
 
 def _transpose(state):
