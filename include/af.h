@@ -70,7 +70,12 @@ enum {
   AF_OPT_LIMITER = 2,    /* 1 (default): Algorithm 3 bound-preserving point values */
   AF_OPT_CORRECTION = 3, /* 1 (default): Corollary 1 correction term */
   AF_OPT_FORCE_LO = 4,   /* test hook, single steps only: 1 EG1 at every node, 2 LF at every node */
-  AF_OPT_PROFILE = 5     /* 1: time every stage of af_step with CUDA events (see af_profile) */
+  AF_OPT_PROFILE = 5,    /* 1: time every stage of af_step with CUDA events (see af_profile) */
+  AF_OPT_SURROGATE = 6,  /* 1: point values from the learned surrogate (af_set_surrogate), with
+                            the exact operator at every node the surrogate's check rejects */
+  AF_OPT_SURR_TOL = 7,   /* surrogate check: a new value may leave the range of the node's
+                            stencil by at most this fraction of the range's width (default 0.5) */
+  AF_OPT_SURR_ABS = 8    /* ... plus this much in the scaled units of the features (default 2e-3) */
 };
 
 /* stages reported by af_profile */
@@ -169,6 +174,34 @@ int af_profile(af_ctx *h, double ms[4], int64_t launches[4], int reset);
 int af_conserved_totals_noalloc(const float *avg, const float *avg_lo, int nx, int ny, double dx,
                                 double dy, double *out, void *stream);
 
+/* Learned surrogate of the point-value operator (see af_mlp below): with
+ * AF_OPT_SURROGATE on, every node's t^{n+1/2} and t^{n+1} values come from
+ * a network (vertex_net for vertices, edge_net for both edge kinds), fed
+ * the features of the node's stencil: relative to the node's averaged
+ * linearisation state u~ (the mean primitive Ubar of the cells sharing the
+ * node) and scaled by rho', c' = sqrt(gamma p'/rho') (rho / rho', u / c',
+ * v / c', p / (rho' c'^2)):
+ *   vertex: Ubar of the 4 cells (LL, LR, UL, UR), the 3 x 3 vertices around
+ *           the node row by row, per variable rho, u, v, p (52 values);
+ *   x-edge: Ubar of the 2 cells (left, right), the 6 vertices of the cells
+ *           (lower row left to right, then upper), the x-edges i-3/2, i-1/2,
+ *           i+1/2 of row j, the y-edges (i-1, j-1/2), (i, j-1/2),
+ *           (i-1, j+1/2), (i, j+1/2), per variable (60 values);
+ *   y-edge: the x-edge stencil of the grid with x, y and u, v exchanged;
+ * then c' dt/h, u' dt/h, v' dt/h (u, v exchanged for y-edges), zeros to 64.
+ * Outputs: (U^{n+1/2} - U^n) and (U^{n+1} - U^n) in the same scaling and
+ * frame.  A node's result is kept if rho, p > 0, it is finite and each
+ * scaled variable lies within the stencil's range widened by
+ * AF_OPT_SURR_TOL times its width plus AF_OPT_SURR_ABS; otherwise the exact operator (with its
+ * limiter) computes that node.  The networks stay owned by the caller and
+ * must outlive their use; square cells only (AF_ERR_ARG otherwise).
+ * Passing NULL, NULL removes them. */
+typedef struct af_mlp af_mlp;
+int af_set_surrogate(af_ctx *h, af_mlp *vertex_net, af_mlp *edge_net);
+/* Nodes evaluated by the network and nodes sent to the exact operator
+ * since the last reset (synchronises). */
+int af_surrogate_stats(af_ctx *h, int64_t out[2], int reset);
+
 /* ------------------------------------------------------------------------
  * Batches: n independent grids of uneven sizes (an ensemble) advanced
  * together.  Every step runs the same four batched kernels over all
@@ -224,6 +257,17 @@ int af_batch_counters(af_batch *b, int64_t *out);
  * candidate in ms[3] if given).  Needs every instance's state. */
 int af_batch_set_tile(af_batch *b, int tile_h);
 int af_batch_autotune(af_batch *b, int *tile_h, double *ms);
+/* Training-set sampler for the surrogate: during every later batch step,
+ * each node is kept with probability `rate` (a counter-based hash of seed,
+ * instance, step, node kind and index) and its features (64 floats), the
+ * exact operator's targets (8 floats; layouts at af_set_surrogate) and its
+ * id (instance, step, kind 0/1/2, i | j << 16: 4 ints, or idv / ide NULL)
+ * are appended to the vertex arrays (Xv, Tv, idv; cap_v rows) or the edge
+ * arrays (Xe, Te, ide; cap_e rows).  counts (device int[2], zeroed by the
+ * caller) counts the nodes offered per class; rows beyond a capacity are
+ * dropped.  Device arrays owned by the caller.  rate = 0 stops sampling. */
+int af_batch_set_sampler(af_batch *b, float *Xv, float *Tv, int *idv, int cap_v, float *Xe, float *Te, int *ide,
+                         int cap_e, int *counts, uint64_t seed, double rate);
 /* Total cells of the instances still active (after a sync). */
 long long af_batch_active_cells(af_batch *b);
 /* The batch's stream (0 = the legacy default stream); as af_set_stream. */
@@ -256,7 +300,6 @@ int af_gemm_bf16(const void *A, int lda, const void *B, int ldb, float *D, int l
  * target layouts: see af_set_surrogate.
  */
 #define AF_MLP_NPARAM 43480
-typedef struct af_mlp af_mlp;
 
 /* He-normal initial weights from a counter-based generator keyed by seed.
  * NULL on error. */

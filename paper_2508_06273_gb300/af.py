@@ -19,7 +19,8 @@ _LOCK = threading.Lock()
 _LIB = None
 
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING = 0, 1, 2
-OPT = {"lin_mode": 0, "tsw": 1, "limiter": 2, "correction": 3, "force_lo": 4, "profile": 5}
+OPT = {"lin_mode": 0, "tsw": 1, "limiter": 2, "correction": 3, "force_lo": 4, "profile": 5, "surrogate": 6,
+       "surr_tol": 7, "surr_abs": 8}
 STAGES = ("prep", "pointvalue", "flux", "reduce")
 ST_CFL, ST_AVG_NONPOS, ST_NONFINITE, ST_KEPT, ST_TIMEOUT, ST_STOPPED = 1, 2, 4, 8, 16, 32
 EXPORTS = [
@@ -34,6 +35,7 @@ EXPORTS = [
     "af_gemm_bf16",
     "af_mlp_create", "af_mlp_destroy", "af_mlp_set_params", "af_mlp_get_params", "af_mlp_fit_scales",
     "af_mlp_forward", "af_mlp_loss_grad", "af_mlp_train",
+    "af_set_surrogate", "af_surrogate_stats", "af_batch_set_sampler",
 ]
 MLP_NPARAM, MLP_NTRAIN = 43480, 43408
 
@@ -96,6 +98,9 @@ def lib():
                 "af_mlp_forward": (i, [vp, fp, fp, i, vp]),
                 "af_mlp_loss_grad": (i, [vp, fp, fp, i, C.POINTER(C.c_double), fp]),
                 "af_mlp_train": (i, [vp, fp, fp, C.c_longlong, i, i, d, C.c_uint64, fp]),
+                "af_set_surrogate": (i, [vp, vp, vp]),
+                "af_surrogate_stats": (i, [vp, C.POINTER(C.c_int64), i]),
+                "af_batch_set_sampler": (i, [vp, fp, fp, fp, i, fp, fp, fp, i, fp, C.c_uint64, d]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -230,6 +235,22 @@ class Solver:
         _check(self.L.af_max_speed(self.h, C.byref(out)))
         return out.value
 
+    def set_surrogate(self, vertex_net, edge_net, tol=None):
+        """Attach networks (Mlp) and switch the surrogate on (None, None: off)."""
+        self._nets = (vertex_net, edge_net)  # keep them alive while attached
+        _check(self.L.af_set_surrogate(self.h, vertex_net.h if vertex_net else None,
+                                       edge_net.h if edge_net else None))
+        if vertex_net:
+            if tol is not None:
+                self.set_option("surr_tol", tol)
+            self.set_option("surrogate", 1)
+
+    def surrogate_stats(self, reset=False):
+        """(nodes from the network, nodes from the exact fallback)."""
+        out = (C.c_int64 * 2)()
+        _check(self.L.af_surrogate_stats(self.h, out, 1 if reset else 0))
+        return out[0], out[1]
+
 
 def _shapes(nx, ny):
     return (4, ny, nx), (4, ny + 1, nx + 1), (4, ny, nx + 1), (4, ny + 1, nx)
@@ -326,6 +347,33 @@ class Batch:
 
     def active_cells(self):
         return _check(self.L.af_batch_active_cells(self.h))
+
+    def set_sampler(self, cap_v, cap_e, seed=1, rate=0.01):
+        """Collect surrogate training samples (features, targets, ids) into
+        device tensors held by this object; returns them as a dict."""
+        t = self.torch
+        dev = self.device
+        self._samples = {
+            "Xv": t.zeros((cap_v, 64), dtype=t.float32, device=dev), "Tv": t.zeros((cap_v, 8), dtype=t.float32, device=dev),
+            "idv": t.zeros((cap_v, 4), dtype=t.int32, device=dev),
+            "Xe": t.zeros((cap_e, 64), dtype=t.float32, device=dev), "Te": t.zeros((cap_e, 8), dtype=t.float32, device=dev),
+            "ide": t.zeros((cap_e, 4), dtype=t.int32, device=dev),
+            "counts": t.zeros(2, dtype=t.int32, device=dev)}
+        S = self._samples
+        _check(self.L.af_batch_set_sampler(self.h, _ptr(S["Xv"]), _ptr(S["Tv"]), _ptr(S["idv"]), int(cap_v),
+                                           _ptr(S["Xe"]), _ptr(S["Te"]), _ptr(S["ide"]), int(cap_e),
+                                           _ptr(S["counts"]), int(seed), float(rate)))
+        return S
+
+    def stop_sampler(self):
+        _check(self.L.af_batch_set_sampler(self.h, None, None, None, 0, None, None, None, 0, None, 0, 0.0))
+
+    def samples(self):
+        """(Xv, Tv, idv, Xe, Te, ide) trimmed to the rows filled so far."""
+        S = self._samples
+        self.torch.cuda.synchronize()
+        nv, ne = (min(int(c), cap) for c, cap in zip(S["counts"].tolist(), (S["Xv"].shape[0], S["Xe"].shape[0])))
+        return S["Xv"][:nv], S["Tv"][:nv], S["idv"][:nv], S["Xe"][:ne], S["Te"][:ne], S["ide"][:ne]
 
 
 class Mlp:

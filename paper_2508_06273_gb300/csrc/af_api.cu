@@ -10,6 +10,7 @@
 #include "af_common.cuh"
 #include "af_ctx.h"
 #include "af_kernels.h"
+#include "af_mlp.h"
 
 using namespace af;
 
@@ -249,6 +250,7 @@ void af_destroy(af_ctx *h) {
     if (h->run_exec[p]) cudaGraphExecDestroy(h->run_exec[p]);
   cudaFree(h->small);
   cudaFree(h->base);
+  if (h->surr_mask) cudaFree(h->surr_mask);
   cudaEventDestroy(h->ev_in);
   cudaEventDestroy(h->ev_out);
   for (int k = 0; k < 5; k++) cudaEventDestroy(h->ev_stage[k]);
@@ -285,6 +287,18 @@ int af_set_option(af_ctx *h, int key, double value) {
       h->opt.force_lo = iv;
       return AF_OK;
     case AF_OPT_PROFILE: h->profile = iv != 0; return AF_OK;
+    case AF_OPT_SURROGATE:
+      if (iv && (!h->surr[0] || !h->surr[1])) return fail(AF_ERR_STATE, "no surrogate networks set%s");
+      h->opt.surrogate = iv != 0;
+      return AF_OK;
+    case AF_OPT_SURR_TOL:
+      if (!(value >= 0.0) || !std::isfinite(value)) return fail(AF_ERR_ARG, "surrogate tolerance must be >= 0%s");
+      h->opt.surr_tol = (float)value;
+      return AF_OK;
+    case AF_OPT_SURR_ABS:
+      if (!(value >= 0.0) || !std::isfinite(value)) return fail(AF_ERR_ARG, "surrogate tolerance must be >= 0%s");
+      h->opt.surr_abs = (float)value;
+      return AF_OK;
     default: return fail(AF_ERR_ARG, "unknown option%s");
   }
 }
@@ -298,6 +312,9 @@ int af_get_option(af_ctx *h, int key, double *value) {
     case AF_OPT_CORRECTION: *value = h->opt.correction; return AF_OK;
     case AF_OPT_FORCE_LO: *value = h->opt.force_lo; return AF_OK;
     case AF_OPT_PROFILE: *value = h->profile; return AF_OK;
+    case AF_OPT_SURROGATE: *value = h->opt.surrogate; return AF_OK;
+    case AF_OPT_SURR_TOL: *value = h->opt.surr_tol; return AF_OK;
+    case AF_OPT_SURR_ABS: *value = h->opt.surr_abs; return AF_OK;
     default: return fail(AF_ERR_ARG, "unknown option%s");
   }
 }
@@ -446,10 +463,43 @@ static int enqueue_step(af_ctx *h, double dt) {
   h->launches[AF_STAGE_PREP] += 1;
   CK(cudaMemsetAsync(h->d_counters, 0, 4 * sizeof(unsigned long long), s), "memset counters");
   if (prof) cudaEventRecord(h->ev_stage[1], s);
-  CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
-                       h->opt, h->d_status, h->d_counters, s),
-     "point values");
-  h->launches[AF_STAGE_POINTVALUE] += 1;
+  if (h->opt.surrogate) {
+    // network at every node, then the exact operator at the nodes it rejected
+    CK(cudaMemsetAsync(h->surr_tiles, 0, sizeof(int) * h->surr_ntiles, s), "memset tiles");
+    const unsigned char *mask[3];
+    for (int k = 0; k < 3; k++) {
+      SurrogateArgs A;
+      A.g = h->g;
+      for (int q = 0; q < 3; q++) {
+        A.n0[q] = h->lev[0].k[q];
+        A.n1[q] = h->lev[1].k[q];
+        A.n2[q] = h->lev[2].k[q];
+      }
+      A.hi = h->hi;
+      A.dt = (float)dt;
+      A.tol = h->opt.surr_tol;
+      A.tol_abs = h->opt.surr_abs;
+      af_mlp *net = h->surr[k == VTX ? 0 : 1];
+      A.wb = net->wb;
+      A.params = net->params;
+      A.mask = h->surr_mask + (size_t)k * h->g.plane;
+      mask[k] = A.mask;
+      A.tile_flag = h->surr_tiles;
+      A.tiles_x = h->surr_tiles_x;
+      A.stats = h->surr_stats;
+      A.status = h->d_status;
+      CK(launch_surrogate(k, A, h->sms, s), "surrogate");
+    }
+    CK(launch_pointvalue_masked(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
+                                h->opt, h->d_status, h->d_counters, mask, h->surr_tiles, s),
+       "point values (fallback)");
+    h->launches[AF_STAGE_POINTVALUE] += 4;
+  } else {
+    CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
+                         h->opt, h->d_status, h->d_counters, s),
+       "point values");
+    h->launches[AF_STAGE_POINTVALUE] += 1;
+  }
   if (prof) {
     cudaEventRecord(h->ev_stage[2], s);
     cudaEventRecord(h->ev_stage[3], s);
@@ -480,7 +530,8 @@ int af_step(af_ctx *h, double dt) {
 
 static bool same_options(const Options &a, const Options &b) {
   return a.lin_mode == b.lin_mode && a.tsw == b.tsw && a.limiter == b.limiter &&
-         a.correction == b.correction && a.force_lo == b.force_lo;
+         a.correction == b.correction && a.force_lo == b.force_lo && a.surrogate == b.surrogate &&
+         a.surr_tol == b.surr_tol && a.surr_abs == b.surr_abs;
 }
 
 // Capture two steps on the handle's own stream (the t^n and t^{n+1} buffers
@@ -535,7 +586,7 @@ int af_run(af_ctx *h, int nsteps, double dt) {
   for (int k = 0; k + 1 < nsteps; k += 2) {
     CK(cudaGraphLaunch(h->run_exec[p], h->stream), "af_run: graph launch");
     h->launches[AF_STAGE_PREP] += 2;
-    h->launches[AF_STAGE_POINTVALUE] += 2;
+    h->launches[AF_STAGE_POINTVALUE] += h->opt.surrogate ? 8 : 2;
     h->launches[AF_STAGE_FLUX] += 2;
   }
   h->speed_valid = true;
@@ -632,6 +683,55 @@ int af_profile(af_ctx *h, double ms[4], int64_t launches[4], int reset) {
       h->launches[k] = 0;
     }
   }
+  return AF_OK;
+}
+
+int af_set_surrogate(af_ctx *h, af_mlp *vertex_net, af_mlp *edge_net) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (!vertex_net != !edge_net) return fail(AF_ERR_ARG, "af_set_surrogate: give both networks or neither%s");
+  if (vertex_net && std::fabs(h->dx - h->dy) > 1e-12 * h->dx)
+    return fail(AF_ERR_ARG, "af_set_surrogate: the surrogate needs square cells (dx = dy)%s");
+  DeviceGuard dg(h->device);
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  if (vertex_net && !h->surr_mask) {
+    const int tx = (h->g.nxv + 31) / 32, ty = (h->g.nyv + 7) / 8;
+    const size_t mask_bytes = (3 * (size_t)h->g.plane + 255) & ~size_t(255);
+    const size_t bytes = mask_bytes + sizeof(int) * (size_t)tx * ty + 2 * sizeof(unsigned long long);
+    void *p = nullptr;
+    CK(cudaMalloc(&p, bytes), "af_set_surrogate: cudaMalloc");
+    cudaMemset(p, 0, bytes);
+    h->surr_mask = (unsigned char *)p;
+    h->surr_tiles = (int *)((char *)p + mask_bytes);
+    h->surr_ntiles = tx * ty;
+    h->surr_tiles_x = tx;
+    h->surr_stats = (unsigned long long *)(h->surr_tiles + (size_t)tx * ty);
+    CK(prepare_surrogate(), "af_set_surrogate: kernel attributes");
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  }
+  h->surr[0] = vertex_net;
+  h->surr[1] = edge_net;
+  if (!vertex_net) h->opt.surrogate = 0;
+  for (int p = 0; p < 2; p++)  // captured steps hold the old networks
+    if (h->run_exec[p]) {
+      cudaGraphExecDestroy(h->run_exec[p]);
+      h->run_exec[p] = nullptr;
+    }
+  return AF_OK;
+}
+
+int af_surrogate_stats(af_ctx *h, int64_t out[2], int reset) {
+  if (!h || !out) return fail(AF_ERR_ARG, "null argument%s");
+  if (!h->surr_stats) {
+    out[0] = out[1] = 0;
+    return AF_OK;
+  }
+  DeviceGuard dg(h->device);
+  unsigned long long c[2];
+  CK(cudaMemcpyAsync(c, h->surr_stats, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "stats");
+  if (reset) CK(cudaMemsetAsync(h->surr_stats, 0, sizeof(c), h->stream), "stats");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  out[0] = (int64_t)c[0];
+  out[1] = (int64_t)c[1];
   return AF_OK;
 }
 

@@ -55,6 +55,8 @@ struct af_batch {
   long long ghost_max = 0;
   bool maps_ok = false;
   std::vector<GraphEntry> graphs;
+  bool sampling = false;  // training-set sampler between point values and fluxes
+  SampleBatch sampler;
 };
 
 namespace {
@@ -193,6 +195,9 @@ int enqueue_batch_step(af_batch *b, double *hist, int hist_steps, cudaStream_t s
   G.arrays = b->d_arrays;
   BCK(launch_ghost_batch(G, b->n, b->ghost_max, s), "batch: ghost fill");
   BCK(launch_pointvalue_batch(pv_batch(b), b->n_pv_tiles, b->tile_h, s), "batch: point values");
+  if (b->sampling)
+    BCK(launch_sample_batch(b->sampler, b->d_pv_tiles, b->n_pv_tiles, b->tile_h, b->d_ctl, b->d_pv, s),
+        "batch: sampler");
   FluxBatch F;
   F.tiles = b->d_fx_tiles;
   F.ctl = b->d_ctl;
@@ -524,6 +529,36 @@ int af_batch_autotune(af_batch *b, int *tile_h, double *ms) {
   for (int k = 0; k < b->n; k++) b->speed_ok[k] = 0;  // recomputed at the next run
   if (tile_h) *tile_h = best_h;
   return put_ctl(b);
+}
+
+int af_batch_set_sampler(af_batch *b, float *Xv, float *Tv, int *idv, int cap_v, float *Xe, float *Te, int *ide,
+                         int cap_e, int *counts, uint64_t seed, double rate) {
+  if (!b) return bfail(AF_ERR_ARG, "null batch");
+  if (!(rate >= 0.0 && rate <= 1.0)) return bfail(AF_ERR_ARG, "af_batch_set_sampler: rate must be in [0, 1]");
+  Dev d(b->device);
+  BCK(cudaStreamSynchronize(b->stream), "batch: sync");
+  drop_graphs(b);
+  if (rate == 0.0) {
+    b->sampling = false;
+    return AF_OK;
+  }
+  if (!Xv || !Tv || !Xe || !Te || !counts || cap_v < 0 || cap_e < 0)
+    return bfail(AF_ERR_ARG, "af_batch_set_sampler: need the sample arrays and the counts");
+  SampleBatch &S = b->sampler;
+  S.X[0] = Xv;
+  S.T[0] = Tv;
+  S.id[0] = reinterpret_cast<int4 *>(idv);
+  S.cap[0] = cap_v;
+  S.X[1] = Xe;
+  S.T[1] = Te;
+  S.id[1] = reinterpret_cast<int4 *>(ide);
+  S.cap[1] = cap_e;
+  S.counts = counts;
+  S.seed = seed;
+  const double th = rate * 4294967296.0;
+  S.threshold = th >= 4294967295.0 ? 0xFFFFFFFFu : (unsigned)th;
+  b->sampling = true;
+  return AF_OK;
 }
 
 long long af_batch_active_cells(af_batch *b) {

@@ -47,5 +47,13 @@ struct af_ctx {
   bool stage_pending;
   double stage_ms[4];
   long long launches[4];
+  // learned surrogate: networks (vertex, edge; owned by the caller), fallback
+  // bytes per node kind, flags per point-value tile, node counts
+  struct af_mlp *surr[2];
+  unsigned char *surr_mask;
+  int *surr_tiles;
+  int surr_ntiles, surr_tiles_x;
+  unsigned long long *surr_stats;
+  int sms;
 };
 

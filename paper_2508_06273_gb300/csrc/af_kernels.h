@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "af_common.cuh"
@@ -19,6 +20,9 @@ struct Options {
   int limiter = 1;     // Algorithm 3
   int correction = 1;  // Corollary 1
   int force_lo = 0;    // test hook
+  int surrogate = 0;   // learned point-value operator with exact fallback
+  float surr_tol = 0.5f;
+  float surr_abs = 2e-3f;
 };
 
 // TMA descriptors of the t^n node arrays and the cell averages (one set per
@@ -38,6 +42,10 @@ struct PointValueArgs {
   int lin_mode, tsw, limiter, correction, force_lo;
   int *status;
   unsigned long long *counters;
+  // exact operator as the surrogate's fallback: only nodes with a nonzero
+  // mask byte (index (j + OY) * P + i + OX), only tiles with a nonzero flag
+  const unsigned char *mask[3];
+  const int *tile_flag;
 };
 inline PointValueArgs pointvalue_args(const Grid &g, const NodeSet &n0, const float *avg_hi, const NodeSet &n1,
                                       const NodeSet &n2, const Options &o, int *status,
@@ -58,6 +66,8 @@ inline PointValueArgs pointvalue_args(const Grid &g, const NodeSet &n0, const fl
   A.force_lo = o.force_lo;
   A.status = status;
   A.counters = counters;
+  A.mask[0] = A.mask[1] = A.mask[2] = nullptr;
+  A.tile_flag = nullptr;
   return A;
 }
 
@@ -166,6 +176,43 @@ cudaError_t prepare_gemm();
 cudaError_t launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, float *D, int ldd, int M, int N,
                              int K, const float *bias, int splits, int accumulate, int *err, cudaStream_t s);
 int *gemm_default_err();
+
+// ---- learned surrogate (af_surrogate.cu)
+// training-set sampler of batched runs: a node is kept when a counter-based
+// hash of (seed, instance, step, kind, i, j) falls below threshold / 2^32
+struct SampleBatch {
+  float *X[2], *T[2];  // [vertex, edge]: features (cap x 64), targets (cap x 8)
+  int4 *id[2];         // (instance, step, kind, i | j << 16) or NULL
+  int cap[2];
+  int *counts;  // device int[2], samples offered (may exceed cap)
+  uint64_t seed;
+  unsigned threshold;
+};
+cudaError_t launch_sample_batch(const SampleBatch &B, const int4 *tiles, int ntiles, int tile_h, const BatchCtl *ctl,
+                                const PointValueArgs *args, cudaStream_t s);
+// fused inference of one node kind: network on the tensor cores, decode,
+// a-posteriori check; failing nodes get mask = 1 and their tile flagged
+struct SurrogateArgs {
+  Grid g;
+  const float *n0[3];
+  const float *hi;
+  float *n1[3], *n2[3];
+  float dt, tol, tol_abs;
+  const __nv_bfloat16 *wb;  // network weights (row-major, packed)
+  const float *params;      // FP32 parameters (biases, scales)
+  unsigned char *mask;      // this kind's fallback bytes
+  int *tile_flag;           // per point-value tile (32 x 8)
+  int tiles_x;
+  unsigned long long *stats;  // [0] nodes from the network, [1] nodes sent to the exact operator
+  int *status;
+};
+cudaError_t prepare_surrogate();
+cudaError_t launch_surrogate(int kind, const SurrogateArgs &A, int sms, cudaStream_t s);
+// point values of the single-grid kernel restricted to flagged nodes
+cudaError_t launch_pointvalue_masked(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
+                                     const NodeSet &n1, const NodeSet &n2, float dt, const Options &o, int *status,
+                                     unsigned long long *counters, const unsigned char *const mask[3],
+                                     const int *tile_flag, cudaStream_t s);
 
 // record a message for af_last_error on this host thread; returns code
 int set_error(int code, const char *msg);

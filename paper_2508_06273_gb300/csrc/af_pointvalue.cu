@@ -638,6 +638,7 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
   const Grid &g = A.g;
   const int ni = (K == YE) ? g.nx : g.nxv, nj = (K == XE) ? g.ny : g.nyv;
   if (i >= ni || j >= nj) return;
+  if (A.mask[K] && !A.mask[K][(long long)(j + OY) * g.P + (i + OX)]) return;
   float U0[4], T[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   raw4<TY>(raw, K == VTX ? RAW_VTX : (K == XE ? RAW_XE : RAW_YE), i, j, i0, j0, U0);
   if (A.correction) correction<K, TY>(g, sm, raw, i, j, i0, j0, U0, T);
@@ -804,6 +805,7 @@ template <int TY>
 __global__ void __launch_bounds__(TX *TY) pointvalue_kernel(Args A, const __grid_constant__ TileMaps T) {
   extern __shared__ float4 smem4[];
   __shared__ alignas(8) unsigned long long bar;
+  if (A.tile_flag && !A.tile_flag[blockIdx.y * gridDim.x + blockIdx.x]) return;
   tile_body<TY>(A, T, tile_smem(smem4), &bar, blockIdx.x * TX, blockIdx.y * TY);
 }
 
@@ -881,6 +883,20 @@ cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg
   A.dt = dt;
   // tiles cover the owned nodes: up to nxv x nyv (vertex lines n + 1 on a
   // non-periodic axis); every box x coordinate is a multiple of TX floats
+  constexpr int TY = 8;
+  dim3 grd((g.nxv + TX - 1) / TX, (g.nyv + TY - 1) / TY), blk(TX, TY);
+  pointvalue_kernel<TY><<<grd, blk, Tile<TY>::SMEM_BYTES, s>>>(A, maps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pointvalue_masked(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
+                                     const NodeSet &n1, const NodeSet &n2, float dt, const Options &o, int *status,
+                                     unsigned long long *counters, const unsigned char *const mask[3],
+                                     const int *tile_flag, cudaStream_t s) {
+  Args A = pointvalue_args(g, n0, avg_hi, n1, n2, o, status, counters);
+  A.dt = dt;
+  for (int k = 0; k < 3; k++) A.mask[k] = mask[k];
+  A.tile_flag = tile_flag;
   constexpr int TY = 8;
   dim3 grd((g.nxv + TX - 1) / TX, (g.nyv + TY - 1) / TY), blk(TX, TY);
   pointvalue_kernel<TY><<<grd, blk, Tile<TY>::SMEM_BYTES, s>>>(A, maps);

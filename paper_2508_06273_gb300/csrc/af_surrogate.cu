@@ -1,0 +1,450 @@
+// af_surrogate.cu -- the learned point-value surrogate on the GPU: its input
+// features (from the t^n data around a node), the training-set sampler of
+// batched runs, and the fused inference kernel that evaluates the network
+// on the tcgen05 tensor cores and falls back to the exact operator per node.
+//
+// Features (per node, relative to the node's linearisation state u~, the
+// mean of the primitive cell averages Ubar of the cells sharing the node,
+// eq. (Un+1/2); rho scaled by rho', u and v by c' = sqrt(gamma p'/rho'),
+// p by rho' c'^2):
+//   vertex: Ubar of its 4 cells (LL, LR, UL, UR), the 3 x 3 vertices around
+//           it row by row; 13 values per variable
+//   x-edge: Ubar of its 2 cells, the 6 vertices of the cells (lower row,
+//           then upper), x-edges left, self, right, y-edges (i-1, j-1/2),
+//           (i, j-1/2), (i-1, j+1/2), (i, j+1/2); 15 values per variable
+//   y-edge: the x-edge stencil with x and y (and u and v) exchanged
+// then c' dt/h, u' dt/h, v' dt/h (u, v exchanged for y-edges); 55 or 63
+// inputs of 64.  Targets: (U^{n+1/2} - U^n) / scale, (U^{n+1} - U^n) / scale.
+#include <cstdio>
+
+#include "../../include/af.h"
+#include "af_kernels.h"
+#include "af_mlp.h"
+#include "af_tc.cuh"
+
+namespace af {
+
+using namespace mlp;
+
+namespace {
+
+__device__ __forceinline__ void ld4g(const Grid &g, const float *p, int i, int j, float U[4]) {
+#pragma unroll
+  for (int v = 0; v < NV; v++) U[v] = __ldg(p + at(g, v, i, j));
+}
+
+// primitive cell average Ubar of cell (ci, cj) (Sec. 2 cell prep)
+__device__ __forceinline__ void cell_ubar(const Grid &g, const float *avg, const float *vtx, const float *xe,
+                                          const float *ye, int ci, int cj, float Ub[4]) {
+  const float gm1 = g.gamma - 1.0f, gm1i = 1.0f / gm1;
+  float N[8][4];
+  ld4g(g, vtx, ci, cj, N[0]);
+  ld4g(g, vtx, ci + 1, cj, N[1]);
+  ld4g(g, vtx, ci, cj + 1, N[2]);
+  ld4g(g, vtx, ci + 1, cj + 1, N[3]);
+  ld4g(g, xe, ci, cj, N[4]);
+  ld4g(g, xe, ci + 1, cj, N[5]);
+  ld4g(g, ye, ci, cj, N[6]);
+  ld4g(g, ye, ci, cj + 1, N[7]);
+  float Qs[4] = {0, 0, 0, 0}, Us[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int n = 0; n < 8; n++) {
+    float Q[4];
+    p2c(N[n], gm1i, Q);
+    const float w = n < 4 ? 1.0f : 4.0f;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      Qs[v] += w * Q[v];
+      Us[v] += w * N[n][v];
+    }
+  }
+  float A[4], Qc[4], Uc[4];
+  ld4g(g, avg, ci, cj, A);
+#pragma unroll
+  for (int v = 0; v < NV; v++) Qc[v] = (36.0f * A[v] - Qs[v]) * 0.0625f;
+  c2p(Qc, gm1, Uc);
+#pragma unroll
+  for (int v = 0; v < NV; v++) Ub[v] = (Us[v] + 16.0f * Uc[v]) * (1.0f / 36.0f);
+}
+
+// values of the node's stencil (cells first, then points) in template order
+template <int K>
+struct Stencil {
+  static constexpr int NC = K == VTX ? 4 : 2;
+  static constexpr int NP = K == VTX ? 9 : 13;
+  static constexpr int N = NC + NP;
+  static constexpr int SELF = K == VTX ? NC + 4 : NC + 7;  // index of the node's own value
+};
+
+template <int K>
+__device__ __forceinline__ void stencil(const Grid &g, const float *avg, const float *vtx, const float *xe,
+                                        const float *ye, int i, int j, float W[][4]) {
+  if (K == VTX) {
+    cell_ubar(g, avg, vtx, xe, ye, i - 1, j - 1, W[0]);
+    cell_ubar(g, avg, vtx, xe, ye, i, j - 1, W[1]);
+    cell_ubar(g, avg, vtx, xe, ye, i - 1, j, W[2]);
+    cell_ubar(g, avg, vtx, xe, ye, i, j, W[3]);
+#pragma unroll
+    for (int b = -1; b <= 1; b++)
+#pragma unroll
+      for (int a = -1; a <= 1; a++) ld4g(g, vtx, i + a, j + b, W[4 + 3 * (b + 1) + (a + 1)]);
+  } else if (K == XE) {
+    cell_ubar(g, avg, vtx, xe, ye, i - 1, j, W[0]);
+    cell_ubar(g, avg, vtx, xe, ye, i, j, W[1]);
+#pragma unroll
+    for (int a = -1; a <= 1; a++) {
+      ld4g(g, vtx, i + a, j, W[2 + a + 1]);
+      ld4g(g, vtx, i + a, j + 1, W[5 + a + 1]);
+      ld4g(g, xe, i + a, j, W[8 + a + 1]);
+    }
+    ld4g(g, ye, i - 1, j, W[11]);
+    ld4g(g, ye, i, j, W[12]);
+    ld4g(g, ye, i - 1, j + 1, W[13]);
+    ld4g(g, ye, i, j + 1, W[14]);
+  } else {
+    cell_ubar(g, avg, vtx, xe, ye, i, j - 1, W[0]);
+    cell_ubar(g, avg, vtx, xe, ye, i, j, W[1]);
+#pragma unroll
+    for (int a = -1; a <= 1; a++) {
+      ld4g(g, vtx, i, j + a, W[2 + a + 1]);
+      ld4g(g, vtx, i + 1, j + a, W[5 + a + 1]);
+      ld4g(g, ye, i, j + a, W[8 + a + 1]);
+    }
+    ld4g(g, xe, i, j - 1, W[11]);
+    ld4g(g, xe, i, j, W[12]);
+    ld4g(g, xe, i + 1, j - 1, W[13]);
+    ld4g(g, xe, i + 1, j, W[14]);
+  }
+}
+
+// frame slot q of variable v: u and v exchanged for y-edges
+template <int K>
+__device__ __forceinline__ int var_of_slot(int q) {
+  return K == YE ? (q == 1 ? 2 : (q == 2 ? 1 : q)) : q;
+}
+
+// Node features f[64], its linearisation state and scales; per frame slot the
+// range (min, max) of the scaled stencil and the scaled own value.
+template <int K>
+__device__ __forceinline__ void node_features(const Grid &g, const float *avg, const float *vtx, const float *xe,
+                                              const float *ye, int i, int j, float dt, float f[64], float ut[4],
+                                              float s[4], float fmin[4], float fmax[4], float fself[4]) {
+  using S = Stencil<K>;
+  float W[S::N][4];
+  stencil<K>(g, avg, vtx, xe, ye, i, j, W);
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    float a = 0.0f;
+#pragma unroll
+    for (int c = 0; c < S::NC; c++) a += W[c][v];
+    ut[v] = a * (1.0f / S::NC);
+  }
+  const float c = sqrtf(g.gamma * ut[3] / ut[0]);
+  s[0] = ut[0];
+  s[1] = s[2] = c;
+  s[3] = ut[0] * c * c;
+#pragma unroll
+  for (int q = 0; q < NV; q++) {
+    const int v = var_of_slot<K>(q);
+    const float is = 1.0f / s[v];
+    float lo = 3.0e38f, hi = -3.0e38f;
+#pragma unroll
+    for (int m = 0; m < S::N; m++) {
+      const float x = (W[m][v] - ut[v]) * is;
+      f[q * S::N + m] = x;
+      lo = fminf(lo, x);
+      hi = fmaxf(hi, x);
+    }
+    fmin[q] = lo;
+    fmax[q] = hi;
+    fself[q] = f[q * S::N + S::SELF];
+  }
+  const float r = dt * g.idx;
+  f[4 * S::N] = c * r;
+  f[4 * S::N + 1] = ut[var_of_slot<K>(1)] * r;
+  f[4 * S::N + 2] = ut[var_of_slot<K>(2)] * r;
+#pragma unroll
+  for (int k = 4 * S::N + 3; k < 64; k++) f[k] = 0.0f;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {  // splitmix64 finaliser
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// ------------------------------------------------------------------ sampler
+template <int K>
+__device__ __forceinline__ void sample_node(const SampleBatch &B, const PointValueArgs &A, int inst, int step, int i,
+                                            int j) {
+  const uint64_t key = ((((uint64_t)inst * 0x100000ull + (uint64_t)step) * 4ull + K) << 40) ^
+                       ((uint64_t)j << 20) ^ (uint64_t)i;
+  if ((unsigned)(mix64(B.seed ^ mix64(key)) >> 32) >= B.threshold) return;
+  const int cls = K == VTX ? 0 : 1;
+  const int slot = atomicAdd(B.counts + cls, 1);
+  if (slot >= B.cap[cls]) return;
+  float f[64], ut[4], s[4], lo[4], hi[4], self[4];
+  node_features<K>(A.g, A.hi, A.n0[VTX], A.n0[XE], A.n0[YE], i, j, A.dt, f, ut, s, lo, hi, self);
+  float U0[4], U1[4], U2[4];
+  ld4g(A.g, A.n0[K], i, j, U0);
+  ld4g(A.g, A.n1[K], i, j, U1);
+  ld4g(A.g, A.n2[K], i, j, U2);
+  float *x = B.X[cls] + (long long)slot * NIN;
+#pragma unroll
+  for (int k = 0; k < 64; k++) x[k] = f[k];
+  float *t = B.T[cls] + (long long)slot * NOUT;
+#pragma unroll
+  for (int q = 0; q < NV; q++) {
+    const int v = var_of_slot<K>(q);
+    t[q] = (U1[v] - U0[v]) / s[v];
+    t[4 + q] = (U2[v] - U0[v]) / s[v];
+  }
+  if (B.id[cls]) B.id[cls][slot] = make_int4(inst, step, K, (j << 16) | i);
+}
+
+// one thread per cell of a point-value tile, its three owned nodes
+__global__ void sample_batch_kernel(SampleBatch B, const int4 *tiles, const BatchCtl *ctl,
+                                    const PointValueArgs *args) {
+  const int4 t = tiles[blockIdx.x];
+  const BatchCtl &c = ctl[t.x];
+  if (!c.active || !c.stepped) return;
+  const PointValueArgs &A = args[2 * t.x + c.cur];
+  const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+  const Grid &g = A.g;
+  PointValueArgs a = A;
+  a.dt = c.dt;
+  if (i < g.nxv && j < g.nyv) sample_node<VTX>(B, a, t.x, c.steps, i, j);
+  if (i < g.nxv && j < g.ny) sample_node<XE>(B, a, t.x, c.steps, i, j);
+  if (i < g.nx && j < g.nyv) sample_node<YE>(B, a, t.x, c.steps, i, j);
+}
+
+// ---------------------------------------------------------------- inference
+constexpr int TM = 128;  // nodes per tile (MMA M)
+constexpr unsigned SZ_W1 = NH * NIN * 2, SZ_W2 = NH * NH * 2, SZ_W4 = NOUT_PAD * NH * 2;
+constexpr unsigned SZ_X = TM * NIN * 2, SZ_H = TM * NH * 2;
+constexpr unsigned O_W1 = 0, O_W2 = O_W1 + SZ_W1, O_W3 = O_W2 + SZ_W2, O_W4 = O_W3 + SZ_W2;
+constexpr unsigned O_X = O_W4 + SZ_W4, O_H = O_X + SZ_X, O_B = O_H + SZ_H;
+constexpr int NBIAS = 3 * NH + NOUT_PAD + NIN + NOUT;
+constexpr unsigned SURR_SMEM = O_B + NBIAS * 4 + 128;
+constexpr unsigned SURR_WAIT = 1u << 20;
+
+// weights of one layer (R x Kd, row-major BF16) into the K-major core layout
+__device__ __forceinline__ void load_layer(unsigned char *dst, const __nv_bfloat16 *src, int R, int Kd) {
+  const int nvec = R * Kd / 8;
+  for (int idx = threadIdx.x; idx < nvec; idx += blockDim.x) {
+    const int r = idx / (Kd / 8), kv = idx % (Kd / 8);
+    *reinterpret_cast<uint4 *>(dst + tc::chunk_offset(R, r, 8 * kv)) =
+        *reinterpret_cast<const uint4 *>(src + (long long)r * Kd + 8 * kv);
+  }
+}
+
+// row `row` of an activation tile (K-major core layout, R = 128) from 32
+// FP32 values at columns cb .. cb + 31
+__device__ __forceinline__ void put_row32(unsigned char *tile, int row, int cb, const float v[32]) {
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    uint4 w;
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(v[8 * q + 0], v[8 * q + 1]);
+    __nv_bfloat162 p1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
+    __nv_bfloat162 p3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
+    w.x = *reinterpret_cast<unsigned *>(&p0);
+    w.y = *reinterpret_cast<unsigned *>(&p1);
+    w.z = *reinterpret_cast<unsigned *>(&p2);
+    w.w = *reinterpret_cast<unsigned *>(&p3);
+    *reinterpret_cast<uint4 *>(tile + tc::chunk_offset(TM, row, cb + 8 * q)) = w;
+  }
+}
+
+// D = A (TM x Kd, tile at a_s) * W^T (N x Kd, at w_s): one elected thread
+__device__ __forceinline__ void issue_layer(unsigned tmem, unsigned a_s, unsigned w_s, int Kd, int N,
+                                            unsigned long long *bar) {
+  const uint32_t idesc = tc::make_idesc(TM, N);
+  const unsigned lboA = TM * 16, lboW = (unsigned)N * 16;
+  for (int s = 0; s < Kd / 16; s++) {
+    const uint64_t da = tc::make_desc(a_s + 2 * s * lboA, lboA, 128);
+    const uint64_t dw = tc::make_desc(w_s + 2 * s * lboW, lboW, 128);
+    tc::mma_bf16(tmem, da, dw, idesc, s > 0 ? 1 : 0);
+  }
+  tc::mma_commit(bar);
+}
+
+__device__ __forceinline__ void st4g(const Grid &g, float *p, int i, int j, const float U[4]) {
+#pragma unroll
+  for (int v = 0; v < NV; v++) p[at(g, v, i, j)] = U[v];
+}
+
+template <int K>
+__global__ void __launch_bounds__(TM, 1) surrogate_kernel(SurrogateArgs A) {
+  extern __shared__ __align__(128) unsigned char ssm[];
+  __shared__ alignas(8) unsigned long long bar;
+  __shared__ unsigned tslot;
+  const Grid &g = A.g;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char *W1s = ssm + O_W1, *W2s = ssm + O_W2, *W3s = ssm + O_W3, *W4s = ssm + O_W4;
+  unsigned char *Xs = ssm + O_X, *Hs = ssm + O_H;
+  float *bias = reinterpret_cast<float *>(ssm + O_B);
+
+  load_layer(W1s, A.wb + WB_W1, NH, NIN);
+  load_layer(W2s, A.wb + WB_W2, NH, NH);
+  load_layer(W3s, A.wb + WB_W3, NH, NH);
+  load_layer(W4s, A.wb + WB_W4, NOUT_PAD, NH);
+  for (int k = tid; k < NBIAS; k += TM) {
+    int src;
+    if (k < 3 * NH) src = (k < NH ? OFF_B1 : (k < 2 * NH ? OFF_B2 - NH : OFF_B3 - 2 * NH)) + k;
+    else if (k < 3 * NH + NOUT_PAD) src = OFF_B4 + (k - 3 * NH);
+    else src = OFF_INS + (k - 3 * NH - NOUT_PAD);  // input scales, then output scales
+    bias[k] = A.params[src];
+  }
+  if (warp == 0) tc::tmem_alloc(&tslot, 128);
+  if (tid == 0) tc::bar_init(&bar, 1);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const unsigned tmem = tslot + ((unsigned)(32 * warp) << 16);
+  const float *b1 = bias, *b2 = bias + NH, *b3 = bias + 2 * NH, *b4 = bias + 3 * NH;
+  const float *ins = bias + 3 * NH + NOUT_PAD, *outs = ins + NIN;
+
+  const int ni = (K == YE) ? g.nx : g.nxv, nj = (K == XE) ? g.ny : g.nyv;
+  const long long total = (long long)ni * nj;
+  const long long ntiles = (total + TM - 1) / TM;
+  unsigned phase = 0;
+  unsigned long long n_fall = 0, n_net = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long lin = tile * TM + tid;
+    const bool valid = lin < total;
+    const int i = valid ? (int)(lin % ni) : 0, j = valid ? (int)(lin / ni) : 0;
+    float ut[4] = {1, 0, 0, 1}, s[4] = {1, 1, 1, 1}, lo[4], hi[4], self[4];
+    {
+      float f[64];
+      if (valid) {
+        node_features<K>(g, A.hi, A.n0[VTX], A.n0[XE], A.n0[YE], i, j, A.dt, f, ut, s, lo, hi, self);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 64; k++) f[k] = 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < 64; k++) f[k] *= ins[k];
+      put_row32(Xs, tid, 0, f);
+      put_row32(Xs, tid, 32, f + 32);
+    }
+    // layers 1..3: H = gelu(in W^T + b); layer 4: y = H W4^T + b4
+    const unsigned char *in_s = Xs;
+    int Kd = NIN;
+    unsigned char *Ws[3] = {W1s, W2s, W3s};
+    const float *bs[3] = {b1, b2, b3};
+    bool ok = true;
+    for (int l = 0; l < 4 && ok; l++) {
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+        issue_layer(tslot, tc::smem_u32(in_s), tc::smem_u32(l < 3 ? Ws[l] : W4s), Kd, l < 3 ? NH : NOUT_PAD, &bar);
+      }
+      ok = __syncthreads_and(tc::bar_wait(&bar, phase, SURR_WAIT)) != 0;
+      phase ^= 1;
+      if (!ok) break;
+      tc::fence_after_sync();
+      if (l < 3) {
+#pragma unroll 1
+        for (int cb = 0; cb < NH; cb += 32) {
+          float v[32];
+          tc::tmem_ld32(tmem + cb, v);
+#pragma unroll
+          for (int k = 0; k < 32; k++) v[k] = gelu(v[k] + bs[l][cb + k]);
+          put_row32(Hs, tid, cb, v);
+        }
+        in_s = Hs;
+        Kd = NH;
+      }
+    }
+    if (!ok) {
+      // the tensor cores did not finish in time: flag the step as invalid,
+      // give them one more bounded wait, and stop
+      if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
+      tc::bar_wait(&bar, phase ^ 1, SURR_WAIT);
+      break;
+    }
+    float y[32];
+    tc::tmem_ld32(tmem, y);
+    if (valid) {
+      // decode, check (admissible, inside the stencil's range widened by tol
+      // times its width plus tol_abs, finite), store or flag for the exact
+      // operator
+      bool good = true;
+      float Un[2][4];
+      float U0[4];
+      ld4g(g, A.n0[K], i, j, U0);
+#pragma unroll
+      for (int lev = 0; lev < 2; lev++) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+          const int v = var_of_slot<K>(q);
+          const float d = (y[4 * lev + q] + b4[4 * lev + q]) * outs[4 * lev + q];
+          const float x = self[q] + d, w = A.tol * (hi[q] - lo[q]) + A.tol_abs;
+          good = good && (x >= lo[q] - w) && (x <= hi[q] + w);
+          Un[lev][v] = U0[v] + s[v] * d;
+        }
+        good = good && Un[lev][0] > 0.0f && Un[lev][3] > 0.0f && isfinite(Un[lev][1]) && isfinite(Un[lev][2]);
+      }
+      const long long mi = (long long)(j + OY) * g.P + (i + OX);
+      A.mask[mi] = good ? 0 : 1;
+      if (good) {
+        n_net++;
+#pragma unroll
+        for (int lev = 0; lev < 2; lev++) {
+          float *dst = lev == 0 ? A.n1[K] : A.n2[K];
+          st4g(g, dst, i, j, Un[lev]);
+          const bool dx_ = (K != YE) && g.per_x && i == 0, dy_ = (K != XE) && g.per_y && j == 0;
+          if (dx_) st4g(g, dst, g.nx, j, Un[lev]);
+          if (dy_) st4g(g, dst, i, g.ny, Un[lev]);
+          if (dx_ && dy_) st4g(g, dst, g.nx, g.ny, Un[lev]);
+        }
+      } else {
+        n_fall++;
+        A.tile_flag[(j / 8) * A.tiles_x + i / 32] = 1;
+      }
+    }
+  }
+  if (n_net) atomicAdd(A.stats, n_net);
+  if (n_fall) atomicAdd(A.stats + 1, n_fall);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tslot, 128);
+}
+
+}  // namespace
+
+cudaError_t prepare_surrogate() {
+  cudaError_t e = cudaFuncSetAttribute(surrogate_kernel<VTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, SURR_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(surrogate_kernel<XE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SURR_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(surrogate_kernel<YE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SURR_SMEM);
+  return e;
+}
+
+cudaError_t launch_surrogate(int kind, const SurrogateArgs &A, int sms, cudaStream_t s) {
+  const int ni = (kind == YE) ? A.g.nx : A.g.nxv, nj = (kind == XE) ? A.g.ny : A.g.nyv;
+  const long long ntiles = ((long long)ni * nj + TM - 1) / TM;
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  if (grid <= 0) return cudaSuccess;
+  switch (kind) {
+    case VTX: surrogate_kernel<VTX><<<grid, TM, SURR_SMEM, s>>>(A); break;
+    case XE: surrogate_kernel<XE><<<grid, TM, SURR_SMEM, s>>>(A); break;
+    default: surrogate_kernel<YE><<<grid, TM, SURR_SMEM, s>>>(A); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_batch(const SampleBatch &B, const int4 *tiles, int ntiles, int tile_h, const BatchCtl *ctl,
+                                const PointValueArgs *args, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  sample_batch_kernel<<<ntiles, dim3(32, tile_h), 0, s>>>(B, tiles, ctl, args);
+  return cudaGetLastError();
+}
+
+}  // namespace af
