@@ -340,6 +340,8 @@ def run_ours(args):
     }
     if world == 1 and args.batch_steps > 0:
         line["batch"] = run_batch_leg(args, torch, af, W)
+    if world == 1 and args.surr_steps > 0:
+        line["surrogate"] = run_surrogate_leg(args, torch, af, W)
     if world == 1 and not args.no_cpu:
         v, threads, desc, _ = cpu_sample(n, min_seconds=args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
@@ -389,6 +391,83 @@ def run_batch_leg(args, torch, af, W):
     }
 
 
+def run_surrogate_leg(args, torch, af, W):
+    """Learned surrogate + exact fallback against the plain path on one grid
+    (default: 4096^2 isentropic vortex, centre and strength from seed 5).
+    The networks are trained here, on the GPU, from (features, exact
+    targets) pairs sampled from a batched ensemble of small seeded vortices;
+    both paths then start from the same state and take the same dt."""
+    import numpy as np
+
+    t0 = time.perf_counter()
+    rng = np.random.default_rng(17)
+    probs = [W.shu_vortex_seeded(int(rng.integers(64, 129)), seed=200 + k, t_end=np.inf) for k in range(16)]
+    b = af.Batch([(p.nx, p.ny) for p in probs], [(p.dx, p.dy) for p in probs], bcs=[p.bc for p in probs])
+    for k, p in enumerate(probs):
+        b.set_state(k, *W.discretise_torch(p, "cuda"))
+    b.set_sampler(600000, 1200000, seed=23, rate=0.08)
+    b.run(12)
+    Xv, Tv, _, Xe, Te, _ = (t.clone() for t in b.samples())
+    b.close()
+    nets = []
+    for X, T in ((Xv, Tv), (Xe, Te)):
+        m = af.Mlp(seed=5)
+        m.fit_scales(X, T)
+        hist = m.train(X, T, steps=args.surr_train_steps, batch=4096, lr=2e-3, seed=3)
+        nets.append((m, float(hist[:10].mean()), float(hist[-10:].mean())))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    n = args.surr_grid
+    prob = W.shu_vortex_seeded(n, seed=5)
+    dev = W.discretise_torch(prob, "cuda")
+    plain = af.Solver(n, n, prob.dx, prob.dy, prob.gamma, prob.bc)
+    surr = af.Solver(n, n, prob.dx, prob.dy, prob.gamma, prob.bc)
+    plain.set_state(*dev)
+    surr.set_state(*dev)
+    del dev
+    surr.set_surrogate(nets[0][0], nets[1][0])
+    dt = prob.cfl * prob.dx / plain.max_speed()
+    stream = torch.cuda.current_stream()
+    times = {}
+    for name, s in (("plain", plain), ("surrogate", surr)):
+        s.run(args.warmup, dt)
+        s.surrogate_stats(reset=True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s.run(args.surr_steps, dt)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        times[name] = ev0.elapsed_time(ev1) / args.surr_steps
+    n_net, n_fall = surr.surrogate_stats()
+    a, c = surr.get_state(), plain.get_state()
+    rel = 0.0
+    for x, y in zip(a, c):
+        for v in (0, 3):  # density and energy / pressure: no vanishing components
+            rel = max(rel, float((x[v].double() - y[v].double()).abs().sum() / y[v].double().abs().sum()))
+    status = surr.status()
+    for s in (plain, surr):
+        s.close()
+    for m, _, _ in nets:
+        m.close()
+    cells = n * n
+    return {
+        "workload": f"isentropic vortex, periodic [0,10]^2, {n}x{n} cells, centre and strength from seed 5, "
+                    f"CFL 0.3, {args.warmup + args.surr_steps} steps of fixed dt",
+        "value": cells / (times["surrogate"] / 1e3), "plain_value": cells / (times["plain"] / 1e3),
+        "unit": UNIT, "ms_per_step": times["surrogate"], "plain_ms_per_step": times["plain"],
+        "speedup_vs_plain": times["plain"] / times["surrogate"],
+        "rel_l1_vs_plain": rel, "fallback_fraction": n_fall / max(1, n_net + n_fall), "status": status,
+        "network": "64-128-128-128-16 GELU, BF16 weights, tcgen05 MMA with FP32 accumulation",
+        "training": {"samples_vertex": int(Xv.shape[0]), "samples_edge": int(Xe.shape[0]),
+                     "steps": args.surr_train_steps, "batch": 4096, "seconds_incl_sampling": train_s,
+                     "loss_first_last_vertex": [nets[0][1], nets[0][2]],
+                     "loss_first_last_edge": [nets[1][1], nets[1][2]],
+                     "data": "16 seeded vortices of 64^2 to 128^2, 12 batched steps, 8% of nodes sampled"},
+    }
+
+
 def run_reference(args):
     rank, world, _ = dist_setup()
     if rank != 0:
@@ -426,6 +505,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=200,
                     help="steps of the batched-ensemble leg (0: skip it)")
+    ap.add_argument("--surr-steps", type=int, default=10, help="timed steps of the surrogate leg (0: skip it)")
+    ap.add_argument("--surr-grid", type=int, default=4096, help="cells per side of the surrogate leg")
+    ap.add_argument("--surr-train-steps", type=int, default=2000, help="Adam steps per surrogate network")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

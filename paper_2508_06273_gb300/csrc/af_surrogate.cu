@@ -220,14 +220,24 @@ __global__ void sample_batch_kernel(SampleBatch B, const int4 *tiles, const Batc
 }
 
 // ---------------------------------------------------------------- inference
+// One CTA per SM runs NG independent pipelines ("groups") of 4 warps.  A
+// group owns a tile of TM = 128 nodes at a time: its threads build the
+// nodes' features into the group's activation buffer, one thread issues
+// the layer's MMAs into the group's 128 tensor-memory columns, and the
+// group's threads apply bias and GELU to their row and write the next
+// layer's input back into the same buffer.  The four groups interleave on
+// the tensor core and hide one another's epilogue latency; the weights are
+// shared in shared memory.
 constexpr int TM = 128;  // nodes per tile (MMA M)
+constexpr int NG = 4;    // groups per CTA
 constexpr unsigned SZ_W1 = NH * NIN * 2, SZ_W2 = NH * NH * 2, SZ_W4 = NOUT_PAD * NH * 2;
-constexpr unsigned SZ_X = TM * NIN * 2, SZ_H = TM * NH * 2;
+constexpr unsigned SZ_BUF = TM * NH * 2;  // features (K = 64) or a hidden layer (K = 128)
 constexpr unsigned O_W1 = 0, O_W2 = O_W1 + SZ_W1, O_W3 = O_W2 + SZ_W2, O_W4 = O_W3 + SZ_W2;
-constexpr unsigned O_X = O_W4 + SZ_W4, O_H = O_X + SZ_X, O_B = O_H + SZ_H;
+constexpr unsigned O_BUF = O_W4 + SZ_W4, O_B = O_BUF + NG * SZ_BUF;
 constexpr int NBIAS = 3 * NH + NOUT_PAD + NIN + NOUT;
 constexpr unsigned SURR_SMEM = O_B + NBIAS * 4 + 128;
 constexpr unsigned SURR_WAIT = 1u << 20;
+static_assert(SURR_SMEM <= 227 * 1024, "shared memory");
 
 // weights of one layer (R x Kd, row-major BF16) into the K-major core layout
 __device__ __forceinline__ void load_layer(unsigned char *dst, const __nv_bfloat16 *src, int R, int Kd) {
@@ -239,25 +249,82 @@ __device__ __forceinline__ void load_layer(unsigned char *dst, const __nv_bfloat
   }
 }
 
-// row `row` of an activation tile (K-major core layout, R = 128) from 32
-// FP32 values at columns cb .. cb + 31
-__device__ __forceinline__ void put_row32(unsigned char *tile, int row, int cb, const float v[32]) {
+// GELU of 32 accumulator values plus bias, written as BF16 at columns
+// cb .. cb + 31 of row `row`: the polynomial inside the tanh in packed FP32
+// pairs, the tanh and the final product on the packed BF16 pipe (the result
+// is stored in BF16 anyway)
+__device__ __forceinline__ void gelu_row32(unsigned char *tile, int row, int cb, const float v[32], const float *b) {
+  const float2 kc = make_float2(GELU_K * GELU_C, GELU_K * GELU_C), kk = make_float2(GELU_K, GELU_K);
+  const float2 half = make_float2(0.5f, 0.5f);
+  unsigned o[16];
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
-    uint4 w;
-    __nv_bfloat162 p0 = __floats2bfloat162_rn(v[8 * q + 0], v[8 * q + 1]);
-    __nv_bfloat162 p1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
-    __nv_bfloat162 p2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
-    __nv_bfloat162 p3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
-    w.x = *reinterpret_cast<unsigned *>(&p0);
-    w.y = *reinterpret_cast<unsigned *>(&p1);
-    w.z = *reinterpret_cast<unsigned *>(&p2);
-    w.w = *reinterpret_cast<unsigned *>(&p3);
-    *reinterpret_cast<uint4 *>(tile + tc::chunk_offset(TM, row, cb + 8 * q)) = w;
+  for (int p = 0; p < 16; p++) {
+    const float2 z = __fadd2_rn(make_float2(v[2 * p], v[2 * p + 1]), make_float2(b[2 * p], b[2 * p + 1]));
+    const float2 a = __fmul2_rn(z, __ffma2_rn(kc, __fmul2_rn(z, z), kk));
+    const __nv_bfloat162 hz = __float22bfloat162_rn(__fmul2_rn(half, z));
+    const __nv_bfloat162 t = h2tanh_approx(__float22bfloat162_rn(a));
+    const __nv_bfloat162 h = __hfma2(hz, t, hz);
+    o[p] = *reinterpret_cast<const unsigned *>(&h);
   }
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+    *reinterpret_cast<uint4 *>(tile + tc::chunk_offset(TM, row, cb + 8 * q)) =
+        make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
 }
 
-// D = A (TM x Kd, tile at a_s) * W^T (N x Kd, at w_s): one elected thread
+__device__ __forceinline__ void put_bf16(unsigned char *tile, int row, int k, float x) {
+  *reinterpret_cast<__nv_bfloat16 *>(tile + tc::chunk_offset(TM, row, k)) = __float2bfloat16_rn(x);
+}
+
+// the features of node (K, i, j) times the input scales, as row `row` of the
+// group's buffer (K = 64); u~ and the scales, and per frame slot the range of
+// the scaled stencil and the scaled own value, for the check
+template <int K>
+__device__ __forceinline__ void features_to_row(const Grid &g, const float *avg, const float *vtx, const float *xe,
+                                                const float *ye, int i, int j, float dt, const float *ins,
+                                                unsigned char *buf, int row, float s[4], float lo[4], float hi[4],
+                                                float self[4]) {
+  using St = Stencil<K>;
+  float W[St::N][4];
+  stencil<K>(g, avg, vtx, xe, ye, i, j, W);
+  float ut[4];
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    float a = 0.0f;
+#pragma unroll
+    for (int c = 0; c < St::NC; c++) a += W[c][v];
+    ut[v] = a * (1.0f / St::NC);
+  }
+  const float c = sqrtf(g.gamma * ut[3] / ut[0]);
+  s[0] = ut[0];
+  s[1] = s[2] = c;
+  s[3] = ut[0] * c * c;
+#pragma unroll
+  for (int q = 0; q < NV; q++) {
+    const int v = var_of_slot<K>(q);
+    const float is = 1.0f / s[v];
+    float mn = 3.0e38f, mx = -3.0e38f;
+#pragma unroll
+    for (int m = 0; m < St::N; m++) {
+      const float x = (W[m][v] - ut[v]) * is;
+      put_bf16(buf, row, q * St::N + m, x * ins[q * St::N + m]);
+      mn = fminf(mn, x);
+      mx = fmaxf(mx, x);
+      if (m == St::SELF) self[q] = x;
+    }
+    lo[q] = mn;
+    hi[q] = mx;
+  }
+  const float r = dt * g.idx;
+  const int k0 = 4 * St::N;
+  put_bf16(buf, row, k0, c * r * ins[k0]);
+  put_bf16(buf, row, k0 + 1, ut[var_of_slot<K>(1)] * r * ins[k0 + 1]);
+  put_bf16(buf, row, k0 + 2, ut[var_of_slot<K>(2)] * r * ins[k0 + 2]);
+#pragma unroll
+  for (int k = k0 + 3; k < 64; k++) put_bf16(buf, row, k, 0.0f);
+}
+
+// D = A (TM x Kd, at a_s) * W^T (N x Kd, at w_s): one elected thread
 __device__ __forceinline__ void issue_layer(unsigned tmem, unsigned a_s, unsigned w_s, int Kd, int N,
                                             unsigned long long *bar) {
   const uint32_t idesc = tc::make_idesc(TM, N);
@@ -275,101 +342,104 @@ __device__ __forceinline__ void st4g(const Grid &g, float *p, int i, int j, cons
   for (int v = 0; v < NV; v++) p[at(g, v, i, j)] = U[v];
 }
 
+// barrier of the 128 threads of group grp (ids 1..NG; 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int grp) {
+  asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(TM) : "memory");
+}
+
 template <int K>
-__global__ void __launch_bounds__(TM, 1) surrogate_kernel(SurrogateArgs A) {
+__global__ void __launch_bounds__(NG *TM, 1) surrogate_kernel(SurrogateArgs A) {
   extern __shared__ __align__(128) unsigned char ssm[];
-  __shared__ alignas(8) unsigned long long bar;
+  __shared__ alignas(8) unsigned long long bars[NG];
   __shared__ unsigned tslot;
+  __shared__ int gfail[NG];
   const Grid &g = A.g;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, grp = warp >> 2, row = tid & (TM - 1);
   unsigned char *W1s = ssm + O_W1, *W2s = ssm + O_W2, *W3s = ssm + O_W3, *W4s = ssm + O_W4;
-  unsigned char *Xs = ssm + O_X, *Hs = ssm + O_H;
+  unsigned char *buf = ssm + O_BUF + grp * SZ_BUF;
   float *bias = reinterpret_cast<float *>(ssm + O_B);
 
   load_layer(W1s, A.wb + WB_W1, NH, NIN);
   load_layer(W2s, A.wb + WB_W2, NH, NH);
   load_layer(W3s, A.wb + WB_W3, NH, NH);
   load_layer(W4s, A.wb + WB_W4, NOUT_PAD, NH);
-  for (int k = tid; k < NBIAS; k += TM) {
+  for (int k = tid; k < NBIAS; k += blockDim.x) {
     int src;
     if (k < 3 * NH) src = (k < NH ? OFF_B1 : (k < 2 * NH ? OFF_B2 - NH : OFF_B3 - 2 * NH)) + k;
     else if (k < 3 * NH + NOUT_PAD) src = OFF_B4 + (k - 3 * NH);
     else src = OFF_INS + (k - 3 * NH - NOUT_PAD);  // input scales, then output scales
     bias[k] = A.params[src];
   }
-  if (warp == 0) tc::tmem_alloc(&tslot, 128);
-  if (tid == 0) tc::bar_init(&bar, 1);
+  if (warp == 0) tc::tmem_alloc(&tslot, NG * 128);
+  if (tid < NG) {
+    tc::bar_init(&bars[tid], 1);
+    gfail[tid] = 0;
+  }
   tc::fence_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const unsigned tmem = tslot + ((unsigned)(32 * warp) << 16);
+  const unsigned tcol = tslot + (unsigned)(128 * grp);                  // the group's accumulator
+  const unsigned tld = tcol + ((unsigned)(32 * (warp & 3)) << 16);       // this warp's lanes
   const float *b1 = bias, *b2 = bias + NH, *b3 = bias + 2 * NH, *b4 = bias + 3 * NH;
   const float *ins = bias + 3 * NH + NOUT_PAD, *outs = ins + NIN;
+  unsigned long long *bar = &bars[grp];
 
   const int ni = (K == YE) ? g.nx : g.nxv, nj = (K == XE) ? g.ny : g.nyv;
   const long long total = (long long)ni * nj;
   const long long ntiles = (total + TM - 1) / TM;
   unsigned phase = 0;
   unsigned long long n_fall = 0, n_net = 0;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long lin = tile * TM + tid;
+  for (long long tile = (long long)blockIdx.x * NG + grp; tile < ntiles; tile += (long long)gridDim.x * NG) {
+    const long long lin = tile * TM + row;
     const bool valid = lin < total;
     const int i = valid ? (int)(lin % ni) : 0, j = valid ? (int)(lin / ni) : 0;
-    float ut[4] = {1, 0, 0, 1}, s[4] = {1, 1, 1, 1}, lo[4], hi[4], self[4];
-    {
-      float f[64];
-      if (valid) {
-        node_features<K>(g, A.hi, A.n0[VTX], A.n0[XE], A.n0[YE], i, j, A.dt, f, ut, s, lo, hi, self);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 64; k++) f[k] = 0.0f;
-      }
-#pragma unroll
-      for (int k = 0; k < 64; k++) f[k] *= ins[k];
-      put_row32(Xs, tid, 0, f);
-      put_row32(Xs, tid, 32, f + 32);
+    float s[4] = {1, 1, 1, 1}, lo[4], hi[4], self[4];
+    if (valid) {
+      features_to_row<K>(g, A.hi, A.n0[VTX], A.n0[XE], A.n0[YE], i, j, A.dt, ins, buf, row, s, lo, hi, self);
+    } else {
+      for (int k = 0; k < 64; k += 8) *reinterpret_cast<uint4 *>(buf + tc::chunk_offset(TM, row, k)) = make_uint4(0, 0, 0, 0);
     }
-    // layers 1..3: H = gelu(in W^T + b); layer 4: y = H W4^T + b4
-    const unsigned char *in_s = Xs;
+    // layers 1..3: H = gelu(in W^T + b) back into the buffer; layer 4: y = H W4^T + b4
     int Kd = NIN;
-    unsigned char *Ws[3] = {W1s, W2s, W3s};
-    const float *bs[3] = {b1, b2, b3};
     bool ok = true;
-    for (int l = 0; l < 4 && ok; l++) {
+    for (int l = 0; l < 4; l++) {
       tc::fence_async_smem();
       tc::fence_before_sync();
-      __syncthreads();
-      if (tid == 0) {
+      group_sync(grp);
+      if (row == 0) {
         tc::fence_after_sync();
-        issue_layer(tslot, tc::smem_u32(in_s), tc::smem_u32(l < 3 ? Ws[l] : W4s), Kd, l < 3 ? NH : NOUT_PAD, &bar);
+        const unsigned char *w = l == 0 ? W1s : (l == 1 ? W2s : (l == 2 ? W3s : W4s));
+        issue_layer(tcol, tc::smem_u32(buf), tc::smem_u32(w), Kd, l < 3 ? NH : NOUT_PAD, bar);
       }
-      ok = __syncthreads_and(tc::bar_wait(&bar, phase, SURR_WAIT)) != 0;
+      if (!tc::bar_wait(bar, phase, SURR_WAIT)) gfail[grp] = 1;
       phase ^= 1;
-      if (!ok) break;
+      group_sync(grp);
+      if (gfail[grp]) {
+        ok = false;
+        break;
+      }
       tc::fence_after_sync();
       if (l < 3) {
+        const float *bl = l == 0 ? b1 : (l == 1 ? b2 : b3);
 #pragma unroll 1
         for (int cb = 0; cb < NH; cb += 32) {
           float v[32];
-          tc::tmem_ld32(tmem + cb, v);
-#pragma unroll
-          for (int k = 0; k < 32; k++) v[k] = gelu(v[k] + bs[l][cb + k]);
-          put_row32(Hs, tid, cb, v);
+          tc::tmem_ld32(tld + cb, v);
+          gelu_row32(buf, row, cb, v, bl + cb);
         }
-        in_s = Hs;
         Kd = NH;
       }
     }
     if (!ok) {
       // the tensor cores did not finish in time: flag the step as invalid,
-      // give them one more bounded wait, and stop
-      if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
-      tc::bar_wait(&bar, phase ^ 1, SURR_WAIT);
+      // give them one more bounded wait, and stop this group
+      if (row == 0) atomicOr(A.status, ST_TIMEOUT);
+      tc::bar_wait(bar, phase ^ 1, SURR_WAIT);
       break;
     }
     float y[32];
-    tc::tmem_ld32(tmem, y);
+    tc::tmem_ld32(tld, y);
     if (valid) {
       // decode, check (admissible, inside the stencil's range widened by tol
       // times its width plus tol_abs, finite), store or flag for the exact
@@ -413,7 +483,7 @@ __global__ void __launch_bounds__(TM, 1) surrogate_kernel(SurrogateArgs A) {
   if (n_fall) atomicAdd(A.stats + 1, n_fall);
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tslot, 128);
+  if (warp == 0) tc::tmem_dealloc(tslot, NG * 128);
 }
 
 }  // namespace
@@ -430,12 +500,13 @@ cudaError_t prepare_surrogate() {
 cudaError_t launch_surrogate(int kind, const SurrogateArgs &A, int sms, cudaStream_t s) {
   const int ni = (kind == YE) ? A.g.nx : A.g.nxv, nj = (kind == XE) ? A.g.ny : A.g.nyv;
   const long long ntiles = ((long long)ni * nj + TM - 1) / TM;
-  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  const long long want = (ntiles + NG - 1) / NG;
+  const int grid = (int)(want < sms ? want : sms);
   if (grid <= 0) return cudaSuccess;
   switch (kind) {
-    case VTX: surrogate_kernel<VTX><<<grid, TM, SURR_SMEM, s>>>(A); break;
-    case XE: surrogate_kernel<XE><<<grid, TM, SURR_SMEM, s>>>(A); break;
-    default: surrogate_kernel<YE><<<grid, TM, SURR_SMEM, s>>>(A); break;
+    case VTX: surrogate_kernel<VTX><<<grid, NG * TM, SURR_SMEM, s>>>(A); break;
+    case XE: surrogate_kernel<XE><<<grid, NG * TM, SURR_SMEM, s>>>(A); break;
+    default: surrogate_kernel<YE><<<grid, NG * TM, SURR_SMEM, s>>>(A); break;
   }
   return cudaGetLastError();
 }
