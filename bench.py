@@ -40,14 +40,19 @@ PV_FLOP_PER_CELL = 8600
 # algorithmic HBM bytes of the flux/update kernel per cell: 3 levels x 3 node
 # arrays read (144 B), averages hi/lo read and written (64 B)
 FLUX_BYTES_PER_CELL = 208
-# DRAM bytes (read + write) per cell update of the point-value stage from one
-# ncu capture (1024^2 case, scaled per cell), valid only for the kernel source
-# it was taken on (sha256 of the files below); otherwise reported as null
-PV_TRAFFIC = {"bytes_per_cell": 289.0, "profile": "profiles/pointvalue_flux_vortex1024.md",
-              "sha256": {"paper_2508_06273_gb300/csrc/af_pointvalue.cu":
-                         "40d6631865af040856b87f498f3451abd8b566f580e7a3997a4044a64fa4d14d",
-                         "paper_2508_06273_gb300/csrc/af_common.cuh":
-                         "9597639230bd1ff69574e367548646b422fab464a46deb4ee743ddf117208755"}}
+# DRAM bytes (read + write) per cell update of the point-value and flux
+# kernels from one ncu capture (2048^2 case, scaled per cell: every array is
+# read or written once per launch), valid only for the kernel sources they
+# were taken on (sha256 of the files below); otherwise reported as null
+_KSRC = "paper_2508_06273_gb300/csrc/"
+_SHARED = {_KSRC + "af_common.cuh": "5059ee04b75fba3bd1a95539ffde842967bfd257e0dace76c7a7ef5b559e2220",
+           _KSRC + "af_kernels.h": "4833c7d116531e19a7306e979e03cbfffaea3eb03ce4e0809bc3841c126fa21a"}
+PV_TRAFFIC = {"bytes_per_cell": 150.7, "profile": "profiles/pointvalue_flux_vortex2048.md",
+              "sha256": dict(_SHARED, **{_KSRC + "af_pointvalue.cu":
+                                         "8cc2b4e36ed36898a0e79dbecb0b95c6b35dcc618d3cbc294a5d2eb6f2c927dd"})}
+FLUX_TRAFFIC = {"bytes_per_cell": 207.5, "profile": "profiles/pointvalue_flux_vortex2048.md",
+                "sha256": dict(_SHARED, **{_KSRC + "af_flux.cu":
+                                           "8b988aa84b4c800ae7b59e87c1e8613c87dd395a826033000470f925732532fb"})}
 
 
 def measured_traffic(spec, cells):
@@ -323,7 +328,7 @@ def run_ours(args):
         "status": status,
         "roofline": {"bound": "alu", "kernel": "point-value stage (1 launch: fused cell prep, vertices and edge midpoints)",
                      "achieved": pv_tflops, "peak": peak, "unit": "TFLOP/s", "frac": pv_tflops / peak,
-                     "traffic": measured_traffic(PV_TRAFFIC, cells), "traffic_unit": "B per stage",
+                     "traffic": measured_traffic(PV_TRAFFIC, cells), "traffic_unit": "B per launch",
                      "traffic_source": PV_TRAFFIC["profile"], "flop_per_cell": PV_FLOP_PER_CELL,
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (max clock)",
                      "frac_at_median_clock": (pv_tflops / fp32_peak_tflops(sms, clk["sm_mhz"])
@@ -331,7 +336,8 @@ def run_ours(args):
                      "ms_per_launch": pv_ms},
         "roofline_flux": {"bound": "hbm", "kernel": "Simpson flux + compensated (double-word FP32) update", "achieved": flux_gbs,
                           "peak": hbm, "unit": "GB/s", "frac": flux_gbs / hbm, "peak_source": hbm_src,
-                          "traffic": None,
+                          "traffic": measured_traffic(FLUX_TRAFFIC, cells), "traffic_unit": "B per launch",
+                          "traffic_source": FLUX_TRAFFIC["profile"],
                           "bytes_per_cell": FLUX_BYTES_PER_CELL, "ms_per_launch": flux_ms},
         "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "gpu_launches": int(sum(launches.values())),
