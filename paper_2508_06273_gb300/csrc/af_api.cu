@@ -250,7 +250,7 @@ void af_destroy(af_ctx *h) {
     if (h->run_exec[p]) cudaGraphExecDestroy(h->run_exec[p]);
   cudaFree(h->small);
   cudaFree(h->base);
-  if (h->surr_mask) cudaFree(h->surr_mask);
+  if (h->surr_ubar) cudaFree(h->surr_ubar);
   cudaEventDestroy(h->ev_in);
   cudaEventDestroy(h->ev_out);
   for (int k = 0; k < 5; k++) cudaEventDestroy(h->ev_stage[k]);
@@ -466,6 +466,7 @@ static int enqueue_step(af_ctx *h, double dt) {
   if (h->opt.surrogate) {
     // network at every node, then the exact operator at the nodes it rejected
     CK(cudaMemsetAsync(h->surr_tiles, 0, sizeof(int) * h->surr_ntiles, s), "memset tiles");
+    CK(launch_ubar(h->g, h->hi, h->lev[0], h->surr_ubar, s), "surrogate cell prep");
     const unsigned char *mask[3];
     for (int k = 0; k < 3; k++) {
       SurrogateArgs A;
@@ -476,6 +477,7 @@ static int enqueue_step(af_ctx *h, double dt) {
         A.n2[q] = h->lev[2].k[q];
       }
       A.hi = h->hi;
+      A.ubar = h->surr_ubar;
       A.dt = (float)dt;
       A.tol = h->opt.surr_tol;
       A.tol_abs = h->opt.surr_abs;
@@ -493,7 +495,7 @@ static int enqueue_step(af_ctx *h, double dt) {
     CK(launch_pointvalue_masked(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
                                 h->opt, h->d_status, h->d_counters, mask, h->surr_tiles, s),
        "point values (fallback)");
-    h->launches[AF_STAGE_POINTVALUE] += 4;
+    h->launches[AF_STAGE_POINTVALUE] += 5;
   } else {
     CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
                          h->opt, h->d_status, h->d_counters, s),
@@ -586,7 +588,7 @@ int af_run(af_ctx *h, int nsteps, double dt) {
   for (int k = 0; k + 1 < nsteps; k += 2) {
     CK(cudaGraphLaunch(h->run_exec[p], h->stream), "af_run: graph launch");
     h->launches[AF_STAGE_PREP] += 2;
-    h->launches[AF_STAGE_POINTVALUE] += h->opt.surrogate ? 8 : 2;
+    h->launches[AF_STAGE_POINTVALUE] += h->opt.surrogate ? 10 : 2;
     h->launches[AF_STAGE_FLUX] += 2;
   }
   h->speed_valid = true;
@@ -696,12 +698,14 @@ int af_set_surrogate(af_ctx *h, af_mlp *vertex_net, af_mlp *edge_net) {
   if (vertex_net && !h->surr_mask) {
     const int tx = (h->g.nxv + 31) / 32, ty = (h->g.nyv + 7) / 8;
     const size_t mask_bytes = (3 * (size_t)h->g.plane + 255) & ~size_t(255);
-    const size_t bytes = mask_bytes + sizeof(int) * (size_t)tx * ty + 2 * sizeof(unsigned long long);
+    const size_t ub_bytes = sizeof(float) * NV * (size_t)h->g.plane;
+    const size_t bytes = ub_bytes + mask_bytes + sizeof(int) * (size_t)tx * ty + 2 * sizeof(unsigned long long);
     void *p = nullptr;
     CK(cudaMalloc(&p, bytes), "af_set_surrogate: cudaMalloc");
     cudaMemset(p, 0, bytes);
-    h->surr_mask = (unsigned char *)p;
-    h->surr_tiles = (int *)((char *)p + mask_bytes);
+    h->surr_ubar = (float *)p;
+    h->surr_mask = (unsigned char *)p + ub_bytes;
+    h->surr_tiles = (int *)((char *)h->surr_mask + mask_bytes);
     h->surr_ntiles = tx * ty;
     h->surr_tiles_x = tx;
     h->surr_stats = (unsigned long long *)(h->surr_tiles + (size_t)tx * ty);

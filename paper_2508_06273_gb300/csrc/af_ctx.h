@@ -51,6 +51,7 @@ struct af_ctx {
   // bytes per node kind, flags per point-value tile, node counts
   struct af_mlp *surr[2];
   unsigned char *surr_mask;
+  float *surr_ubar;
   int *surr_tiles;
   int surr_ntiles, surr_tiles_x;
   unsigned long long *surr_stats;

@@ -196,6 +196,7 @@ struct SurrogateArgs {
   Grid g;
   const float *n0[3];
   const float *hi;
+  const float *ubar;  // primitive cell averages Ubar of cells -1 .. n (launch_ubar)
   float *n1[3], *n2[3];
   float dt, tol, tol_abs;
   const __nv_bfloat16 *wb;  // network weights (row-major, packed)
@@ -207,6 +208,8 @@ struct SurrogateArgs {
   int *status;
 };
 cudaError_t prepare_surrogate();
+// Ubar of the cells -1 .. nx, -1 .. ny of the t^n state into ub (4 planes)
+cudaError_t launch_ubar(const Grid &g, const float *avg_hi, const NodeSet &n0, float *ub, cudaStream_t s);
 cudaError_t launch_surrogate(int kind, const SurrogateArgs &A, int sms, cudaStream_t s);
 // point values of the single-grid kernel restricted to flagged nodes
 cudaError_t launch_pointvalue_masked(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,

@@ -117,6 +117,59 @@ __device__ __forceinline__ void stencil(const Grid &g, const float *avg, const f
   }
 }
 
+// the same stencil with the cells' Ubar read from a precomputed array
+template <int K>
+__device__ __forceinline__ void stencil_ub(const Grid &g, const float *ub, const float *vtx, const float *xe,
+                                           const float *ye, int i, int j, float W[][4]) {
+  if (K == VTX) {
+    ld4g(g, ub, i - 1, j - 1, W[0]);
+    ld4g(g, ub, i, j - 1, W[1]);
+    ld4g(g, ub, i - 1, j, W[2]);
+    ld4g(g, ub, i, j, W[3]);
+#pragma unroll
+    for (int b = -1; b <= 1; b++)
+#pragma unroll
+      for (int a = -1; a <= 1; a++) ld4g(g, vtx, i + a, j + b, W[4 + 3 * (b + 1) + (a + 1)]);
+  } else if (K == XE) {
+    ld4g(g, ub, i - 1, j, W[0]);
+    ld4g(g, ub, i, j, W[1]);
+#pragma unroll
+    for (int a = -1; a <= 1; a++) {
+      ld4g(g, vtx, i + a, j, W[2 + a + 1]);
+      ld4g(g, vtx, i + a, j + 1, W[5 + a + 1]);
+      ld4g(g, xe, i + a, j, W[8 + a + 1]);
+    }
+    ld4g(g, ye, i - 1, j, W[11]);
+    ld4g(g, ye, i, j, W[12]);
+    ld4g(g, ye, i - 1, j + 1, W[13]);
+    ld4g(g, ye, i, j + 1, W[14]);
+  } else {
+    ld4g(g, ub, i, j - 1, W[0]);
+    ld4g(g, ub, i, j, W[1]);
+#pragma unroll
+    for (int a = -1; a <= 1; a++) {
+      ld4g(g, vtx, i, j + a, W[2 + a + 1]);
+      ld4g(g, vtx, i + 1, j + a, W[5 + a + 1]);
+      ld4g(g, ye, i, j + a, W[8 + a + 1]);
+    }
+    ld4g(g, xe, i, j - 1, W[11]);
+    ld4g(g, xe, i, j, W[12]);
+    ld4g(g, xe, i + 1, j - 1, W[13]);
+    ld4g(g, xe, i + 1, j, W[14]);
+  }
+}
+
+// Ubar of cells -1 .. nx, -1 .. ny into the padded array ub
+__global__ void ubar_kernel(Grid g, const float *avg, const float *vtx, const float *xe, const float *ye,
+                            float *ub) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x - 1, j = blockIdx.y * blockDim.y + threadIdx.y - 1;
+  if (i > g.nx || j > g.ny) return;
+  float U[4];
+  cell_ubar(g, avg, vtx, xe, ye, i, j, U);
+#pragma unroll
+  for (int v = 0; v < NV; v++) ub[at(g, v, i, j)] = U[v];
+}
+
 // frame slot q of variable v: u and v exchanged for y-edges
 template <int K>
 __device__ __forceinline__ int var_of_slot(int q) {
@@ -272,21 +325,29 @@ __device__ __forceinline__ void gelu_row32(unsigned char *tile, int row, int cb,
         make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
 }
 
-__device__ __forceinline__ void put_bf16(unsigned char *tile, int row, int k, float x) {
-  *reinterpret_cast<__nv_bfloat16 *>(tile + tc::chunk_offset(TM, row, k)) = __float2bfloat16_rn(x);
+// element k of a row in BF16 into the pack w (8 elements); at the 8th the
+// pack goes to the tile as one 16-byte store (k is a compile-time index in
+// the unrolled callers)
+__device__ __forceinline__ void pack_put(unsigned char *tile, int row, int k, float x, unsigned w[4]) {
+  const unsigned b = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+  const int e = k & 7;
+  if (e & 1) w[e >> 1] |= b << 16;
+  else w[e >> 1] = b;
+  if (e == 7)
+    *reinterpret_cast<uint4 *>(tile + tc::chunk_offset(TM, row, k - 7)) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // the features of node (K, i, j) times the input scales, as row `row` of the
 // group's buffer (K = 64); u~ and the scales, and per frame slot the range of
 // the scaled stencil and the scaled own value, for the check
 template <int K>
-__device__ __forceinline__ void features_to_row(const Grid &g, const float *avg, const float *vtx, const float *xe,
+__device__ __forceinline__ void features_to_row(const Grid &g, const float *ub, const float *vtx, const float *xe,
                                                 const float *ye, int i, int j, float dt, const float *ins,
                                                 unsigned char *buf, int row, float s[4], float lo[4], float hi[4],
                                                 float self[4]) {
   using St = Stencil<K>;
   float W[St::N][4];
-  stencil<K>(g, avg, vtx, xe, ye, i, j, W);
+  stencil_ub<K>(g, ub, vtx, xe, ye, i, j, W);
   float ut[4];
 #pragma unroll
   for (int v = 0; v < NV; v++) {
@@ -299,6 +360,7 @@ __device__ __forceinline__ void features_to_row(const Grid &g, const float *avg,
   s[0] = ut[0];
   s[1] = s[2] = c;
   s[3] = ut[0] * c * c;
+  unsigned w[4];
 #pragma unroll
   for (int q = 0; q < NV; q++) {
     const int v = var_of_slot<K>(q);
@@ -307,7 +369,7 @@ __device__ __forceinline__ void features_to_row(const Grid &g, const float *avg,
 #pragma unroll
     for (int m = 0; m < St::N; m++) {
       const float x = (W[m][v] - ut[v]) * is;
-      put_bf16(buf, row, q * St::N + m, x * ins[q * St::N + m]);
+      pack_put(buf, row, q * St::N + m, x * ins[q * St::N + m], w);
       mn = fminf(mn, x);
       mx = fmaxf(mx, x);
       if (m == St::SELF) self[q] = x;
@@ -316,12 +378,12 @@ __device__ __forceinline__ void features_to_row(const Grid &g, const float *avg,
     hi[q] = mx;
   }
   const float r = dt * g.idx;
-  const int k0 = 4 * St::N;
-  put_bf16(buf, row, k0, c * r * ins[k0]);
-  put_bf16(buf, row, k0 + 1, ut[var_of_slot<K>(1)] * r * ins[k0 + 1]);
-  put_bf16(buf, row, k0 + 2, ut[var_of_slot<K>(2)] * r * ins[k0 + 2]);
+  constexpr int k0 = 4 * St::N;
+  pack_put(buf, row, k0, c * r * ins[k0], w);
+  pack_put(buf, row, k0 + 1, ut[var_of_slot<K>(1)] * r * ins[k0 + 1], w);
+  pack_put(buf, row, k0 + 2, ut[var_of_slot<K>(2)] * r * ins[k0 + 2], w);
 #pragma unroll
-  for (int k = k0 + 3; k < 64; k++) put_bf16(buf, row, k, 0.0f);
+  for (int k = k0 + 3; k < 64; k++) pack_put(buf, row, k, 0.0f, w);
 }
 
 // D = A (TM x Kd, at a_s) * W^T (N x Kd, at w_s): one elected thread
@@ -396,7 +458,7 @@ __global__ void __launch_bounds__(NG *TM, 1) surrogate_kernel(SurrogateArgs A) {
     const int i = valid ? (int)(lin % ni) : 0, j = valid ? (int)(lin / ni) : 0;
     float s[4] = {1, 1, 1, 1}, lo[4], hi[4], self[4];
     if (valid) {
-      features_to_row<K>(g, A.hi, A.n0[VTX], A.n0[XE], A.n0[YE], i, j, A.dt, ins, buf, row, s, lo, hi, self);
+      features_to_row<K>(g, A.ubar, A.n0[VTX], A.n0[XE], A.n0[YE], i, j, A.dt, ins, buf, row, s, lo, hi, self);
     } else {
       for (int k = 0; k < 64; k += 8) *reinterpret_cast<uint4 *>(buf + tc::chunk_offset(TM, row, k)) = make_uint4(0, 0, 0, 0);
     }
@@ -508,6 +570,12 @@ cudaError_t launch_surrogate(int kind, const SurrogateArgs &A, int sms, cudaStre
     case XE: surrogate_kernel<XE><<<grid, NG * TM, SURR_SMEM, s>>>(A); break;
     default: surrogate_kernel<YE><<<grid, NG * TM, SURR_SMEM, s>>>(A); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ubar(const Grid &g, const float *avg_hi, const NodeSet &n0, float *ub, cudaStream_t s) {
+  dim3 blk(32, 8), grd((g.nx + 2 + 31) / 32, (g.ny + 2 + 7) / 8);
+  ubar_kernel<<<grd, blk, 0, s>>>(g, avg_hi, n0.k[VTX], n0.k[XE], n0.k[YE], ub);
   return cudaGetLastError();
 }
 
