@@ -23,6 +23,9 @@ from .afo import (  # noqa: F401
     OPT_CORRECTION,
     OPT_FORCE_LO,
     OPT_THREADS,
+    OPT_FLUX_LIMITER,
+    OPT_SHOCK_BLEND,
+    ST_FLUX_LIMITED,
     ST_CFL,
     ST_AVG_NONPOS,
     ST_NONFINITE,

@@ -46,12 +46,13 @@ struct afo_ctx {
   int nx, ny, W, H;
   double dx, dy, gam;
   int bc[4];
-  int lin_mode, tsw, limiter, correction, force_lo, threads;
+  int lin_mode, tsw, limiter, correction, force_lo, threads, flux_limiter, shock_blend;
   double *avg;        /* conservative averages, [4][H][W] */
   double *nd[3][3];   /* point values [level][kind] -> [4][H][W]; level 0 t^n, 1 t^{n+1/2}, 2 t^{n+1} */
   double *uc, *ub;    /* cell-centre value U_c and primitive average Ubar, [4][H][W] */
   unsigned char *ind; /* Alg. 2 indicator per vertex, [H][W] */
   double *fx, *gy;    /* Simpson face fluxes, [4][H][W] */
+  double *ax, *ay;    /* x- and y-wave speeds of the averages (flux limiter), [H][W] */
   int status;
   int64_t cnt[4];
 };
@@ -158,14 +159,19 @@ static void fill_cells(afo_ctx *c, double *a) {
 }
 
 /* ------------------------------------------------ cell prep (Sec. 2) */
-/* Q_c from inverting Simpson's rule in conservative variables, U_c = C2P(Q_c),
- * then Ubar by Simpson's rule in primitive variables. */
+/* Q_c from inverting Simpson's rule in conservative variables, U_c = C2P(Q_c)
+ * (the reconstruction's centre value).  Ubar, the primitive cell average that
+ * the linearisation, Alg. 2, Alg. 3's piecewise-constant data and Sec. 3.4's
+ * indicator use, is the primitive state of the conservative cell average,
+ * C2P(Qbar): Sec. 3.5 speaks of density and pressure computed from the cell
+ * averages of the conserved quantities as the values the linearisation is
+ * built from. */
 static void prep_cells(afo_ctx *c) {
   const double *V = c->nd[0][0], *X = c->nd[0][1], *Y = c->nd[0][2];
 #pragma omp parallel for schedule(static)
   for (int j = -G; j < c->ny + G; j++) {
     for (int i = -G; i < c->nx + G; i++) {
-      double Qs[4] = {0, 0, 0, 0}, Us[4] = {0, 0, 0, 0};
+      double Qs[4] = {0, 0, 0, 0};
       const struct { const double *a; int i, j; double w; } nodes[8] = {
           {V, i, j, 1.0},     {V, i + 1, j, 1.0}, {V, i, j + 1, 1.0}, {V, i + 1, j + 1, 1.0},
           {X, i, j, 4.0},     {X, i + 1, j, 4.0}, {Y, i, j, 4.0},     {Y, i, j + 1, 4.0}};
@@ -173,15 +179,13 @@ static void prep_cells(afo_ctx *c) {
         double U[4], Q[4];
         get4(c, nodes[n].a, nodes[n].i, nodes[n].j, U);
         p2c(U, c->gam, Q);
-        for (int v = 0; v < NV; v++) {
-          Qs[v] += nodes[n].w * Q[v];
-          Us[v] += nodes[n].w * U[v];
-        }
+        for (int v = 0; v < NV; v++) Qs[v] += nodes[n].w * Q[v];
       }
-      double Qc[4], Uc[4], Ub[4];
+      double Qc[4], Uc[4], Ub[4], Qa[4];
       for (int v = 0; v < NV; v++) Qc[v] = (36.0 * AT(c, c->avg, v, i, j) - Qs[v]) / 16.0;
       c2p(Qc, c->gam, Uc);
-      for (int v = 0; v < NV; v++) Ub[v] = (Us[v] + 16.0 * Uc[v]) / 36.0;
+      get4(c, c->avg, i, j, Qa);
+      c2p(Qa, c->gam, Ub);
       put4(c, c->uc, i, j, Uc);
       put4(c, c->ub, i, j, Ub);
     }
@@ -577,13 +581,13 @@ static void eg_node(afo_ctx *c, int kind, int i, int j, int op, const double ul[
  * with the averaged linearisation, else Lax-Friedrichs; if even that fails in
  * floating point, keep the node's t^n value */
 static void limit_node(afo_ctx *c, int kind, int i, int j, double tau, const double ho[4],
-                       double out[4], nstat *st) {
-  int go_lo = c->force_lo == 1 || (c->limiter && !admissible(ho));
-  if (c->force_lo != 2 && !go_lo) {
+                       double out[4], nstat *st, int force_lo) {
+  int go_lo = force_lo == 1 || (c->limiter && !admissible(ho));
+  if (force_lo != 2 && !go_lo) {
     for (int v = 0; v < NV; v++) out[v] = ho[v];
     return;
   }
-  if (c->force_lo != 2) {
+  if (force_lo != 2) {
     double ul[4], lo[4];
     lin_avg(c, kind, i, j, ul);
     eg_node(c, kind, i, j, 1, ul, tau, lo);
@@ -603,6 +607,42 @@ static void limit_node(afo_ctx *c, int kind, int i, int j, double tau, const dou
   get4(c, c->nd[0][kind], i, j, out);
   st->kept++;
 }
+
+/* Sec. 3.4: theta = exp(-phi1 phi2) of an edge midpoint, phi1 the larger
+ * normalised second difference of the averaged pressure on either side of the
+ * edge, phi2 = 2^(max |u_n| + c over its two cells); "bar" quantities read as
+ * the primitive cell averages Ubar (as in Alg. 2).  A vertex takes the
+ * smallest theta of its four edges. */
+static double pbar(const afo_ctx *c, int i, int j) { return AT(c, c->ub, 3, i, j); }
+static double ncspeed(const afo_ctx *c, int i, int j, int dir) {
+  double U[4];
+  get4(c, c->ub, i, j, U);
+  return fabs(U[1 + dir]) + sqrt(c->gam * U[3] / U[0]);
+}
+static double d2ratio(double a, double b, double cc) { return fabs((a - 2.0 * b + cc) / (a + 2.0 * b + cc)); }
+static double shock_theta_edge(const afo_ctx *c, int kind, int i, int j) {
+  double r1, r2, s;
+  if (kind == AFO_XE) { /* (i-1/2, j): cells i-2 .. i+1 of row j */
+    r1 = d2ratio(pbar(c, i + 1, j), pbar(c, i, j), pbar(c, i - 1, j));
+    r2 = d2ratio(pbar(c, i, j), pbar(c, i - 1, j), pbar(c, i - 2, j));
+    s = fmax(ncspeed(c, i, j, 0), ncspeed(c, i - 1, j, 0));
+  } else { /* (i, j-1/2): cells j-2 .. j+1 of column i */
+    r1 = d2ratio(pbar(c, i, j + 1), pbar(c, i, j), pbar(c, i, j - 1));
+    r2 = d2ratio(pbar(c, i, j), pbar(c, i, j - 1), pbar(c, i, j - 2));
+    s = fmax(ncspeed(c, i, j, 1), ncspeed(c, i, j - 1, 1));
+  }
+  return exp(-fmax(r1, r2) * pow(2.0, s));
+}
+static double shock_theta(const afo_ctx *c, int kind, int i, int j) {
+  if (kind != AFO_VTX) return shock_theta_edge(c, kind, i, j);
+  double t = shock_theta_edge(c, AFO_XE, i, j);
+  t = fmin(t, shock_theta_edge(c, AFO_XE, i, j - 1));
+  t = fmin(t, shock_theta_edge(c, AFO_YE, i, j));
+  return fmin(t, shock_theta_edge(c, AFO_YE, i - 1, j));
+}
+/* blends with 1 - theta below this are skipped (below FP32 resolution of the
+ * stored values' change) */
+#define SB_EPS 1e-6
 
 static void node_range(const afo_ctx *c, int kind, int *ni, int *nj) {
   int px = c->bc[0] == AFO_BC_PERIODIC, py = c->bc[2] == AFO_BC_PERIODIC;
@@ -665,7 +705,9 @@ afo_ctx *afo_create(int nx, int ny, double dx, double dy, double gamma, uint32_t
   c->fx = (double *)calloc(n, sizeof(double));
   c->gy = (double *)calloc(n, sizeof(double));
   c->ind = (unsigned char *)calloc(ps(c), 1);
-  int ok = c->avg && c->uc && c->ub && c->fx && c->gy && c->ind;
+  c->ax = (double *)calloc(ps(c), sizeof(double));
+  c->ay = (double *)calloc(ps(c), sizeof(double));
+  int ok = c->avg && c->uc && c->ub && c->fx && c->gy && c->ind && c->ax && c->ay;
   for (int l = 0; l < 3; l++)
     for (int k = 0; k < 3; k++) {
       c->nd[l][k] = (double *)calloc(n, sizeof(double));
@@ -686,6 +728,8 @@ void afo_destroy(afo_ctx *c) {
   free(c->fx);
   free(c->gy);
   free(c->ind);
+  free(c->ax);
+  free(c->ay);
   for (int l = 0; l < 3; l++)
     for (int k = 0; k < 3; k++) free(c->nd[l][k]);
   free(c);
@@ -707,6 +751,8 @@ int afo_set_option(afo_ctx *c, int key, double val) {
     c->force_lo = iv;
     return 0;
   case AFO_OPT_THREADS: c->threads = iv; return 0;
+  case AFO_OPT_FLUX_LIMITER: c->flux_limiter = iv != 0; return 0;
+  case AFO_OPT_SHOCK_BLEND: c->shock_blend = iv != 0; return 0;
   default: return -1;
   }
 }
@@ -856,7 +902,17 @@ static void point_values(afo_ctx *c, int level, double dt) {
         if (!in_block(c, kind, ul, tau, c->gam)) st.cfl++;
         eg_node(c, kind, i, j, 0, ul, tau, ho);
         for (int v = 0; v < NV; v++) ho[v] += 0.5 * tau * tau * T[v];
-        limit_node(c, kind, i, j, tau, ho, out, &st);
+        limit_node(c, kind, i, j, tau, ho, out, &st, c->force_lo);
+        if (c->shock_blend) {
+          const double th = shock_theta(c, kind, i, j);
+          if (1.0 - th >= SB_EPS) {
+            /* the low-order value: Alg. 3's chain (EG1 on pc data, else
+               Lax-Friedrichs, else the t^n value), admissible like out */
+            double lo[4];
+            limit_node(c, kind, i, j, tau, ho, lo, &st, c->force_lo == 2 ? 2 : 1);
+            for (int v = 0; v < NV; v++) out[v] = th * out[v] + (1.0 - th) * lo[v];
+          }
+        }
         put4(c, c->nd[level][kind], i, j, out);
         eg1 += st.eg1;
         lf += st.lf;
@@ -874,6 +930,109 @@ static void point_values(afo_ctx *c, int level, double dt) {
   c->cnt[2] += tot.kept;
   if (tot.kept) c->status |= AFO_ST_KEPT;
   if (tot.cfl) c->status |= AFO_ST_CFL;
+}
+
+/* ------------------------- cell-average flux limiter (Sec. 3.5; own construction)
+ * The paper states that a flux limiter keeps the averages admissible but does
+ * not print it.  This one follows the convex-decomposition idea of Hu, Adams
+ * and Shu (J. Comput. Phys. 242, 2013).  With lambda_x = dt/dx, lambda_y =
+ * dt/dy, face speeds alpha_f = max over the face's two cells of |u_n| + c
+ * (from the t^n averages), r_f = lambda_f alpha_f and S = sum of r_f over the
+ * cell's 4 faces, the update of a cell is
+ *   Q^{n+1} = sum_f (r_f / S) P_f,   P_f = Q - (S / alpha_f) sigma_f (F_f - f_n(Q))
+ * (sigma_f = +1 on the east / north face, -1 on the west / south face, f_n the
+ * physical flux normal to the face at the cell's average).  With the Rusanov
+ * flux F^lo of the two averages every P_f is admissible when S <= 1 (Q +- f/alpha
+ * is admissible for alpha >= |u_n| + c).  Each face flux becomes
+ * F = theta F^ho + (1 - theta) F^lo, theta the largest value in [0, 1] for which
+ * P_f keeps rho >= ETA rho(P_f^lo) and p >= ETA p(P_f^lo) in both cells of the
+ * face (a convex set in theta, found by bisection); the update is then a
+ * convex combination of admissible states.  theta = 1 leaves F^ho untouched. */
+#define FL_ETA 0.1
+static double dir_speed(const double Q[4], double g, int dir) {
+  double U[4];
+  c2p(Q, g, U);
+  if (!(U[0] > 0.0) || !(U[3] > 0.0)) return 0.0;
+  return fabs(U[1 + dir]) + sqrt(g * U[3] / U[0]);
+}
+static void cons_flux(const double Q[4], double g, int dir, double F[4]) {
+  double U[4];
+  c2p(Q, g, U);
+  flux(U, g, dir, F);
+}
+static int fl_ok(const double A[4], const double B[4], double th, double rmin, double pmin, double g) {
+  double P[4], U[4];
+  for (int v = 0; v < NV; v++) P[v] = A[v] + th * B[v];
+  if (!(P[0] >= rmin) || !(P[0] > 0.0)) return 0;
+  c2p(P, g, U);
+  return U[3] >= pmin;
+}
+/* largest admissible theta of face state P_f of a cell with average Q */
+static double fl_theta(const double Q[4], int dir, double k, const double Fho[4], const double Flo[4], double g) {
+  double fn[4], A[4], B[4], UA[4];
+  cons_flux(Q, g, dir, fn);
+  for (int v = 0; v < NV; v++) {
+    A[v] = Q[v] - k * (Flo[v] - fn[v]);
+    B[v] = -k * (Fho[v] - Flo[v]);
+  }
+  c2p(A, g, UA);
+  if (!(UA[0] > 0.0) || !(UA[3] > 0.0)) return 0.0;
+  const double rmin = FL_ETA * UA[0], pmin = FL_ETA * UA[3];
+  if (fl_ok(A, B, 1.0, rmin, pmin, g)) return 1.0;
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 60; it++) {
+    double mid = 0.5 * (lo + hi);
+    if (fl_ok(A, B, mid, rmin, pmin, g)) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+static void flux_limit(afo_ctx *c, double dt) {
+  const double g = c->gam, lx = dt / c->dx, ly = dt / c->dy;
+  int nx = c->nx, ny = c->ny, limited = 0;
+  /* x- and y-speeds of the averages of cells -2 .. n+1 */
+  double *ax = c->ax, *ay = c->ay;
+  for (int j = -G; j < ny + G; j++)
+    for (int i = -G; i < nx + G; i++) {
+      double Q[4];
+      get4(c, c->avg, i, j, Q);
+      AT(c, ax, 0, i, j) = dir_speed(Q, g, 0);
+      AT(c, ay, 0, i, j) = dir_speed(Q, g, 1);
+    }
+#define ALX(i, j) fmax(AT(c, ax, 0, (i) - 1, j), AT(c, ax, 0, i, j)) /* x-face (i-1/2, j) */
+#define ALY(i, j) fmax(AT(c, ay, 0, i, (j) - 1), AT(c, ay, 0, i, j)) /* y-face (i, j-1/2) */
+#define SUM(i, j) (lx * (ALX(i, j) + ALX((i) + 1, j)) + ly * (ALY(i, j) + ALY(i, (j) + 1)))
+#pragma omp parallel for schedule(static) reduction(+ : limited)
+  for (int j = 0; j <= ny; j++)
+    for (int i = 0; i <= nx; i++) {
+      for (int dir = 0; dir < 2; dir++) {
+        if ((dir == 0 && j >= ny) || (dir == 1 && i >= nx)) continue;
+        const int li = dir == 0 ? i - 1 : i, lj = dir == 0 ? j : j - 1; /* west / south cell */
+        double QL[4], QR[4], fL[4], fR[4], Flo[4], Fho[4];
+        get4(c, c->avg, li, lj, QL);
+        get4(c, c->avg, i, j, QR);
+        const double al = dir == 0 ? ALX(i, j) : ALY(i, j);
+        cons_flux(QL, g, dir, fL);
+        cons_flux(QR, g, dir, fR);
+        double *fa = dir == 0 ? c->fx : c->gy;
+        get4(c, fa, i, j, Fho);
+        for (int v = 0; v < NV; v++) Flo[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * al * (QR[v] - QL[v]);
+        if (!(al > 0.0)) continue;
+        /* the face is the east/north face of the west/south cell (sigma = +1)
+           and the west/south face of the other (sigma = -1) */
+        double tl = fl_theta(QL, dir, SUM(li, lj) / al, Fho, Flo, g);
+        double tr = fl_theta(QR, dir, -SUM(i, j) / al, Fho, Flo, g);
+        double th = tl < tr ? tl : tr;
+        if (th < 1.0) {
+          limited++;
+          for (int v = 0; v < NV; v++) AT(c, fa, v, i, j) = th * Fho[v] + (1.0 - th) * Flo[v];
+        }
+      }
+    }
+#undef ALX
+#undef ALY
+#undef SUM
+  if (limited) c->status |= AFO_ST_FLUX_LIMITED;
 }
 
 int afo_step(afo_ctx *c, double dt) {
@@ -932,6 +1091,7 @@ int afo_step(afo_ctx *c, double dt) {
       }
     }
   }
+  if (c->flux_limiter) flux_limit(c, dt);
   /* finite-volume update, eq. (2dfvm) */
   int nonpos = 0, nonfin = 0;
 #pragma omp parallel for schedule(static) reduction(+ : nonpos, nonfin)
@@ -1014,6 +1174,11 @@ double afo_max_speed(const afo_ctx *c) {
 }
 
 int afo_status(const afo_ctx *c) { return c ? c->status : -1; }
+
+double afo_shock_theta(const afo_ctx *c, int kind, int i, int j) {
+  if (!c || kind < 0 || kind > 2 || i < -1 || j < -1 || i > c->nx || j > c->ny) return -1.0;
+  return shock_theta(c, kind, i, j);
+}
 
 int afo_counters(const afo_ctx *c, int64_t out[4]) {
   if (!c) return -1;

@@ -38,6 +38,8 @@ enum {
   AFO_OPT_LIMITER = 2,    /* Algorithm 3 bound-preserving point values (0/1) */
   AFO_OPT_CORRECTION = 3, /* Corollary 1 correction term (0/1) */
   AFO_OPT_FORCE_LO = 4,   /* test hook: 0 none, 1 EG1 at every node, 2 Lax-Friedrichs at every node */
+  AFO_OPT_FLUX_LIMITER = 9, /* cell-average flux limiter (0/1): Sec. 3.5 names one; own construction */
+  AFO_OPT_SHOCK_BLEND = 10,  /* Sec. 3.4 shock-indicator blend of point values with EG1 (0/1) */
   AFO_OPT_THREADS = 16    /* OpenMP threads (oracle only; 0 = runtime default) */
 };
 enum { AFO_LIN_AVG = 0, AFO_LIN_POINT = 1, AFO_LIN_ALG1 = 2 };
@@ -47,7 +49,8 @@ enum {
   AFO_ST_CFL = 1,       /* a Mach-cone base left the node's own cell block */
   AFO_ST_AVG_NONPOS = 2,/* a cell average has rho <= 0 or p <= 0 after the update */
   AFO_ST_NONFINITE = 4, /* a non-finite value was produced */
-  AFO_ST_KEPT = 8       /* Lax-Friedrichs was not admissible either; old value kept */
+  AFO_ST_KEPT = 8,      /* Lax-Friedrichs was not admissible either; old value kept */
+  AFO_ST_FLUX_LIMITED = 64 /* the flux limiter blended at least one face flux towards Rusanov */
 };
 
 /* node kinds for the unit-level entry points */
@@ -65,6 +68,9 @@ int afo_step(afo_ctx *c, double dt);
 int afo_conserved_totals(const afo_ctx *c, double out[4]);
 double afo_max_speed(const afo_ctx *c);
 int afo_status(const afo_ctx *c);
+/* Sec. 3.4 blend weight theta of node (kind, i, j) from the current Ubar
+ * (call afo_prepare first); -1 on bad arguments */
+double afo_shock_theta(const afo_ctx *c, int kind, int i, int j);
 /* counters of the last step: [EG1 fallbacks, LF fallbacks, kept values, tsw vertices] */
 int afo_counters(const afo_ctx *c, int64_t out[4]);
 

@@ -24,6 +24,8 @@ _LIB = None
 VTX, XE, YE = 0, 1, 2
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING = 0, 1, 2
 OPT_LIN_MODE, OPT_TSW, OPT_LIMITER, OPT_CORRECTION, OPT_FORCE_LO, OPT_THREADS = 0, 1, 2, 3, 4, 16
+OPT_FLUX_LIMITER, OPT_SHOCK_BLEND = 9, 10
+ST_FLUX_LIMITED = 64
 ST_CFL, ST_AVG_NONPOS, ST_NONFINITE, ST_KEPT = 1, 2, 4, 8
 
 
@@ -71,6 +73,7 @@ def _lib():
                 "afo_correction_T": (None, [_dp, _dp, _dp, d, _dp]),
                 "afo_eg_field": (i, [FIELD_FN, vp, i, d, d, _dp, d, d, _dp]),
                 "afo_set_quadrature": (None, [i, d]),
+                "afo_shock_theta": (d, [vp, i, i, i]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -151,6 +154,10 @@ class Oracle:
 
     def status(self):
         return self.lib.afo_status(self.h)
+
+    def shock_theta(self, kind, i, j):
+        """Sec. 3.4 blend weight of a node from the current Ubar (after prepare())."""
+        return self.lib.afo_shock_theta(self.h, kind, i, j)
 
     def counters(self):
         out = (C.c_int64 * 4)()

@@ -62,7 +62,8 @@ def node_xy(prob, kind, i, j):
 
 # ------------------------------------------------------------ reconstruction
 def test_recon_reproduces_biquadratic(oracle_mod):
-    """cpq is exact for biquadratic data and its cell mean is the exact mean."""
+    """cpq is exact for biquadratic data, its centre value inverts Simpson's
+    rule on the cell average, and Ubar is the primitive state of the average."""
     rng = np.random.default_rng(3)
     prob = box()
     coef = random_poly(rng)
@@ -75,16 +76,25 @@ def test_recon_reproduces_biquadratic(oracle_mod):
         got = o.recon(int(i), int(j), xi, eta)
         want = np.array(f(prob.dx * (i + xi), prob.dy * (j + eta)))
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
-    # primitive cell average = exact mean of the polynomial (3-point Gauss is
-    # exact for degree 2 per variable)
-    gx, gw = np.polynomial.legendre.leggauss(3)
+    # the centre value inverts Simpson's rule in conservative variables: the
+    # Simpson mean of the 9 conserved nodal values is the cell average; Ubar
+    # is the primitive state of the cell average
+    avg, vtx, xe, ye = o.get_state()
+    g = prob.gamma
+
+    def p2c(U):
+        r, u, v, p = U
+        return np.array([r, r * u, r * v, p / (g - 1) + 0.5 * r * (u * u + v * v)])
+
     for (i, j) in [(0, 0), (2, 3), (5, 5)]:
-        _, ub = o.cell_prim(i, j)
-        m = np.zeros(4)
-        for a, wa in zip(gx, gw):
-            for b, wb in zip(gx, gw):
-                m += 0.25 * wa * wb * np.array(f(prob.dx * (i + 0.5 + 0.5 * a), prob.dy * (j + 0.5 + 0.5 * b)))
-        np.testing.assert_allclose(ub, m, atol=1e-13)
+        uc, ub = o.cell_prim(i, j)
+        Q = (p2c(vtx[:, j, i]) + p2c(vtx[:, j, i + 1]) + p2c(vtx[:, j + 1, i]) + p2c(vtx[:, j + 1, i + 1])
+             + 4 * (p2c(xe[:, j, i]) + p2c(xe[:, j, i + 1]) + p2c(ye[:, j, i]) + p2c(ye[:, j + 1, i]))
+             + 16 * p2c(uc)) / 36
+        np.testing.assert_allclose(Q, avg[:, j, i], rtol=1e-13, atol=1e-13)
+        Qa = avg[:, j, i]
+        want = [Qa[0], Qa[1] / Qa[0], Qa[2] / Qa[0], (g - 1) * (Qa[3] - 0.5 * (Qa[1] ** 2 + Qa[2] ** 2) / Qa[0])]
+        np.testing.assert_allclose(ub, want, rtol=1e-13)
 
 
 def test_recon_continuous_across_faces(oracle_mod):
@@ -477,18 +487,39 @@ def test_reflecting_wall_zero_normal_velocity(oracle_mod):
 
 
 # ---------------------------------------------------- limiter and Alg. 2
-def test_limiter_keeps_point_values_admissible(oracle_mod):
-    """Near-vacuum double rarefaction: with Alg. 3 every point value stays
-    admissible, and the EG1 / Lax-Friedrichs fallbacks are exercised."""
-    prob = W.double_rarefaction(24)
-    o = make_oracle(oracle_mod, prob)
-    used = 0
-    for _ in range(20):
+def _admissible_state(state, g=1.4):
+    avg = state[0]
+    p = (g - 1) * (avg[3] - 0.5 * (avg[1] ** 2 + avg[2] ** 2) / avg[0])
+    ok = np.all(avg[0] > 0) and np.all(p > 0)
+    return ok and all(np.all(a[0] > 0) and np.all(a[3] > 0) for a in state[1:])
+
+
+def test_limiters_keep_every_value_admissible(oracle_mod):
+    """Near-vacuum double rarefaction (u = -+2, p = 0.1): with Alg. 3 and the
+    cell-average flux limiter every point value and average stays
+    admissible while both limiters act; without the flux limiter the
+    averages do not."""
+    prob = W.double_rarefaction(24, p=0.1)
+    o = make_oracle(oracle_mod, prob, opts={"flux_limiter": 1})
+    used, st = 0, 0
+    for _ in range(30):
         o.step(0.3 * prob.dx / o.max_speed())
         used += sum(o.counters()[:2])
-        for a in o.get_state()[1:]:
-            assert np.all(a[0] > 0) and np.all(a[3] > 0)
-    assert used > 0
+        st |= o.status()
+        assert _admissible_state(o.get_state())
+    assert used > 0 and st & oracle_mod.ST_FLUX_LIMITED and not st & 6
+    bare = make_oracle(oracle_mod, prob)
+    failed = False
+    for _ in range(30):
+        s = bare.max_speed()
+        if not np.isfinite(s):
+            failed = True
+            break
+        bare.step(0.3 * prob.dx / s)
+        if bare.status() & 6 or not _admissible_state(bare.get_state()):
+            failed = True
+            break
+    assert failed
 
 
 @pytest.mark.parametrize("force", [1, 2])
@@ -589,3 +620,83 @@ def test_ex2_pressure_is_pressure_balance():
         rho = Fraction(1, 2) + Fraction(1, 2) * (1 - rr * rr) ** 6
         v = 1024 * (1 - rr) ** 6 * rr ** 6
         assert dp == rho * v * v / rr
+
+
+# ------------------------------------------ Sec. 3.4 blend, Sec. 3.5 limiter
+def test_shock_theta_formula(oracle_mod):
+    """theta = exp(-phi1 phi2) of Sec. 3.4 on averages that vary in x only:
+    1 where the pressure is linear, the hand-computed value next to a jump,
+    and a vertex takes the smallest theta of its four edges."""
+    g = 1.4
+    n = 8
+    pbar = np.array([1.0, 1.0, 1.0, 1.0, 2.0, 2.0, 2.5, 3.0])  # cells 0..7 (periodic in y)
+    ubar = np.linspace(-0.3, 0.4, n)
+    prob = W.Problem("x_profile", n, 4, 0.0, 0.0, 1.0, 0.5, (1, 1, 0, 0), lambda x, y: (1.0, 0.0, 0.0, 1.0), 1.0)
+    avg = np.zeros((4, 4, n))
+    avg[0] = 1.0
+    avg[1] = ubar[None, :]
+    avg[3] = pbar[None, :] / (g - 1) + 0.5 * ubar[None, :] ** 2
+    vtx, xe, ye = np.ones((4, 5, n + 1)), np.ones((4, 4, n + 1)), np.ones((4, 5, n))
+    o = make_oracle(oracle_mod, prob, state=(avg, vtx, xe, ye))
+    o.prepare()
+    c = np.sqrt(g * pbar)
+
+    def ratio(a, b, cc):
+        return abs((a - 2 * b + cc) / (a + 2 * b + cc))
+
+    for i in (2, 4, 5):
+        phi1 = max(ratio(pbar[i + 1], pbar[i], pbar[i - 1]), ratio(pbar[i], pbar[i - 1], pbar[i - 2]))
+        phi2 = 2.0 ** max(abs(ubar[i]) + c[i], abs(ubar[i - 1]) + c[i - 1])
+        assert o.shock_theta(oracle_mod.XE, i, 1) == pytest.approx(np.exp(-phi1 * phi2), rel=1e-13)
+    assert o.shock_theta(oracle_mod.XE, 2, 1) == 1.0  # p linear (constant) over cells 0..3
+    for i in (3, 5):
+        edges = [o.shock_theta(oracle_mod.XE, i, 1), o.shock_theta(oracle_mod.XE, i, 0),
+                 o.shock_theta(oracle_mod.YE, i, 1), o.shock_theta(oracle_mod.YE, i - 1, 1)]
+        assert o.shock_theta(oracle_mod.VTX, i, 1) == min(edges)
+    assert o.shock_theta(oracle_mod.YE, 4, 2) == 1.0  # no variation in y
+
+
+def test_limiters_leave_smooth_data_alone(oracle_mod):
+    """On the smooth periodic vortex the flux limiter never acts: every step
+    with it on equals the plain step bit for bit."""
+    prob = W.shu_vortex(24)
+    a = make_oracle(oracle_mod, prob)
+    b = make_oracle(oracle_mod, prob, opts={"flux_limiter": 1})
+    for _ in range(3):
+        dt = 0.3 * prob.dx / a.max_speed()
+        a.step(dt)
+        b.step(dt)
+        assert not b.status() & oracle_mod.ST_FLUX_LIMITED
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+
+
+def test_flux_limiter_conserves(oracle_mod):
+    """Periodic near-vacuum data with the flux limiter acting: the totals
+    are conserved to round-off (each face keeps one flux)."""
+    prob = W.double_rarefaction(24, p=0.1)
+    prob.bc = (0, 0, 0, 0)
+    o = make_oracle(oracle_mod, prob, opts={"flux_limiter": 1})
+    t0 = o.totals()
+    acted = 0
+    for _ in range(10):
+        o.step(0.3 * prob.dx / o.max_speed())
+        acted |= o.status() & oracle_mod.ST_FLUX_LIMITED
+    assert acted
+    assert np.all(np.abs(o.totals() - t0) <= 1e-13 * np.maximum(1.0, np.abs(t0)))
+
+
+def test_seeded_riemann_problems_stay_admissible_with_both_limiters(oracle_mod):
+    """Seeded four-quadrant problems at 24^2 with Alg. 2, Alg. 3, the Sec. 3.4
+    blend and the flux limiter: every average and point value stays
+    admissible up to t = 0.25."""
+    for seed in range(4):
+        prob = W.four_quadrant(24, seed=seed)
+        o = make_oracle(oracle_mod, prob, opts={"flux_limiter": 1, "shock_blend": 1})
+        t = 0.0
+        while t < 0.25 - 1e-12:
+            dt = min(0.3 * prob.dx / o.max_speed(), 0.25 - t)
+            o.step(dt)
+            t += dt
+            assert not o.status() & 6, seed
+        assert _admissible_state(o.get_state()), seed
