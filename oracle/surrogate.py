@@ -99,29 +99,13 @@ def p2c(U, gamma=GAMMA):
 
 
 def ubar(ext, gamma=GAMMA):
-    """Primitive cell averages Ubar of the cells -1 .. n (Sec. 2): Q_c from
-    inverting Simpson's rule on the cell average, U_c = C2P(Q_c), Ubar the
-    Simpson mean of the 9 primitive values.  Returned at [v, j + 1, i + 1]."""
-    avg, vtx, xe, ye = ext
+    """Primitive cell averages Ubar of the cells -1 .. n: the primitive state of
+    the conservative cell average (the reading the C oracle uses, after
+    Sec. 3.5).  Returned at [v, j + 1, i + 1]."""
+    avg = ext[0]
     ny, nx = avg.shape[1] - 2 * G, avg.shape[2] - 2 * G
-    nj, ni = ny + 2, nx + 2
-    o = G - 1  # extended index of cell / node -1
-    A = avg[:, o:o + nj, o:o + ni]
-
-    def V(dj, di):
-        return vtx[:, o + dj:o + dj + nj, o + di:o + di + ni]
-
-    def X(dj, di):
-        return xe[:, o + dj:o + dj + nj, o + di:o + di + ni]
-
-    def Y(dj, di):
-        return ye[:, o + dj:o + dj + nj, o + di:o + di + ni]
-
-    corners = [V(0, 0), V(0, 1), V(1, 0), V(1, 1)]
-    edges = [X(0, 0), X(0, 1), Y(0, 0), Y(1, 0)]
-    Qs = sum(p2c(c, gamma) for c in corners) + 4 * sum(p2c(e, gamma) for e in edges)
-    Uc = c2p((36.0 * A - Qs) / 16.0, gamma)
-    return (sum(corners) + 4 * sum(edges) + 16.0 * Uc) / 36.0
+    o = G - 1  # extended index of cell -1
+    return c2p(avg[:, o:o + ny + 2, o:o + nx + 2], gamma)
 
 
 # --------------------------------------------------------------- features
