@@ -58,8 +58,9 @@ enum {
                            the node kept its old value */
   AF_ST_TIMEOUT = 16,   /* a block's wait for its staged tile timed out; the tile was
                            not updated (the step's result is invalid) */
-  AF_ST_STOPPED = 32    /* batch only: the instance's state had no finite positive wave
+  AF_ST_STOPPED = 32,   /* batch only: the instance's state had no finite positive wave
                            speed, so it was stopped before its end time */
+  AF_ST_FLUX_LIMITED = 64 /* the flux limiter blended at least one face flux (informational) */
 };
 
 /* option keys for af_set_option */
@@ -75,7 +76,13 @@ enum {
                             the exact operator at every node the surrogate's check rejects */
   AF_OPT_SURR_TOL = 7,   /* surrogate check: a new value may leave the range of the node's
                             stencil by at most this fraction of the range's width (default 0.5) */
-  AF_OPT_SURR_ABS = 8    /* ... plus this much in the scaled units of the features (default 2e-3) */
+  AF_OPT_SURR_ABS = 8,   /* ... plus this much in the scaled units of the features (default 2e-3) */
+  AF_OPT_FLUX_LIMITER = 9, /* 1: cell-average flux limiter (Sec. 3.5 names one without printing it): each
+                              face flux blended with the Rusanov flux of the two averages by the largest
+                              weight that keeps the convex-decomposition face states of both cells
+                              admissible (Hu, Adams & Shu 2013); AF_ST_FLUX_LIMITED when it acts */
+  AF_OPT_SHOCK_BLEND = 10  /* 1: Sec. 3.4 shock-indicator blend theta U^ho + (1 - theta) U^lo of the point
+                              values, theta = exp(-phi1 phi2), U^lo from Alg. 3's low-order chain */
 };
 
 /* stages reported by af_profile */

@@ -1020,12 +1020,18 @@ static void flux_limit(afo_ctx *c, double dt) {
         if (!(al > 0.0)) continue;
         /* the face is the east/north face of the west/south cell (sigma = +1)
            and the west/south face of the other (sigma = -1) */
-        double tl = fl_theta(QL, dir, SUM(li, lj) / al, Fho, Flo, g);
-        double tr = fl_theta(QR, dir, -SUM(i, j) / al, Fho, Flo, g);
-        double th = tl < tr ? tl : tr;
+        int finite = 1;
+        for (int v = 0; v < NV; v++) finite = finite && isfinite(Fho[v]);
+        double th = 0.0;
+        if (finite) {
+          double tl = fl_theta(QL, dir, SUM(li, lj) / al, Fho, Flo, g);
+          double tr = fl_theta(QR, dir, -SUM(i, j) / al, Fho, Flo, g);
+          th = tl < tr ? tl : tr;
+        }
         if (th < 1.0) {
+          /* theta = 0 (also for a non-finite F^ho) takes F^lo exactly */
           limited++;
-          for (int v = 0; v < NV; v++) AT(c, fa, v, i, j) = th * Fho[v] + (1.0 - th) * Flo[v];
+          for (int v = 0; v < NV; v++) AT(c, fa, v, i, j) = th > 0.0 ? th * Fho[v] + (1.0 - th) * Flo[v] : Flo[v];
         }
       }
     }

@@ -20,9 +20,10 @@ _LIB = None
 
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING = 0, 1, 2
 OPT = {"lin_mode": 0, "tsw": 1, "limiter": 2, "correction": 3, "force_lo": 4, "profile": 5, "surrogate": 6,
-       "surr_tol": 7, "surr_abs": 8}
+       "surr_tol": 7, "surr_abs": 8,
+       "flux_limiter": 9, "shock_blend": 10}
 STAGES = ("prep", "pointvalue", "flux", "reduce")
-ST_CFL, ST_AVG_NONPOS, ST_NONFINITE, ST_KEPT, ST_TIMEOUT, ST_STOPPED = 1, 2, 4, 8, 16, 32
+ST_CFL, ST_AVG_NONPOS, ST_NONFINITE, ST_KEPT, ST_TIMEOUT, ST_STOPPED, ST_FLUX_LIMITED = 1, 2, 4, 8, 16, 32, 64
 EXPORTS = [
     "af_create", "af_destroy", "af_last_error", "af_set_stream", "af_set_option",
     "af_get_option", "af_set_state", "af_set_state_host", "af_get_state", "af_get_state_host",

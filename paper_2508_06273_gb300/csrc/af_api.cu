@@ -251,6 +251,7 @@ void af_destroy(af_ctx *h) {
   cudaFree(h->small);
   cudaFree(h->base);
   if (h->surr_ubar) cudaFree(h->surr_ubar);
+  if (h->shock_theta) cudaFree(h->shock_theta);
   cudaEventDestroy(h->ev_in);
   cudaEventDestroy(h->ev_out);
   for (int k = 0; k < 5; k++) cudaEventDestroy(h->ev_stage[k]);
@@ -295,6 +296,15 @@ int af_set_option(af_ctx *h, int key, double value) {
       if (!(value >= 0.0) || !std::isfinite(value)) return fail(AF_ERR_ARG, "surrogate tolerance must be >= 0%s");
       h->opt.surr_tol = (float)value;
       return AF_OK;
+    case AF_OPT_FLUX_LIMITER: h->opt.flux_limiter = iv != 0; return AF_OK;
+    case AF_OPT_SHOCK_BLEND:
+      if (iv && !h->shock_theta) {
+        DeviceGuard dg(h->device);
+        CK(cudaMalloc(&h->shock_theta, 2 * sizeof(float) * (size_t)h->g.plane), "cudaMalloc(theta)");
+        CK(cudaMemset(h->shock_theta, 0, 2 * sizeof(float) * (size_t)h->g.plane), "memset(theta)");
+      }
+      h->opt.shock_blend = iv != 0;
+      return AF_OK;
     case AF_OPT_SURR_ABS:
       if (!(value >= 0.0) || !std::isfinite(value)) return fail(AF_ERR_ARG, "surrogate tolerance must be >= 0%s");
       h->opt.surr_abs = (float)value;
@@ -315,6 +325,8 @@ int af_get_option(af_ctx *h, int key, double *value) {
     case AF_OPT_SURROGATE: *value = h->opt.surrogate; return AF_OK;
     case AF_OPT_SURR_TOL: *value = h->opt.surr_tol; return AF_OK;
     case AF_OPT_SURR_ABS: *value = h->opt.surr_abs; return AF_OK;
+    case AF_OPT_FLUX_LIMITER: *value = h->opt.flux_limiter; return AF_OK;
+    case AF_OPT_SHOCK_BLEND: *value = h->opt.shock_blend; return AF_OK;
     default: return fail(AF_ERR_ARG, "unknown option%s");
   }
 }
@@ -462,6 +474,12 @@ static int enqueue_step(af_ctx *h, double dt) {
   CK(launch_ghost_fill(h->g, h->hi, h->lo, h->lev[0], s), "ghost fill");
   h->launches[AF_STAGE_PREP] += 1;
   CK(cudaMemsetAsync(h->d_counters, 0, 4 * sizeof(unsigned long long), s), "memset counters");
+  const float *theta[2] = {nullptr, nullptr};
+  if (h->opt.shock_blend) {
+    theta[0] = h->shock_theta;
+    theta[1] = h->shock_theta + h->g.plane;
+    CK(launch_shock_theta(h->g, h->hi, h->shock_theta, h->shock_theta + h->g.plane, s), "shock indicator");
+  }
   if (prof) cudaEventRecord(h->ev_stage[1], s);
   if (h->opt.surrogate) {
     // network at every node, then the exact operator at the nodes it rejected
@@ -493,12 +511,12 @@ static int enqueue_step(af_ctx *h, double dt) {
       CK(launch_surrogate(k, A, h->sms, s), "surrogate");
     }
     CK(launch_pointvalue_masked(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
-                                h->opt, h->d_status, h->d_counters, mask, h->surr_tiles, s),
+                                h->opt, h->d_status, h->d_counters, mask, h->surr_tiles, theta, s),
        "point values (fallback)");
     h->launches[AF_STAGE_POINTVALUE] += 5;
   } else {
     CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
-                         h->opt, h->d_status, h->d_counters, s),
+                         h->opt, h->d_status, h->d_counters, theta, s),
        "point values");
     h->launches[AF_STAGE_POINTVALUE] += 1;
   }
@@ -507,7 +525,7 @@ static int enqueue_step(af_ctx *h, double dt) {
     cudaEventRecord(h->ev_stage[3], s);
   }
   CK(launch_flux_update(h->g, h->lev[0], h->lev[1], h->lev[2], h->hi, h->lo, dt / h->dx, dt / h->dy,
-                        h->d_status, h->d_speed, h->d_speed_bad, s),
+                        h->d_status, h->d_speed, h->d_speed_bad, h->opt.flux_limiter, s),
      "flux update");
   h->speed_valid = true;
   h->launches[AF_STAGE_FLUX] += 1;
@@ -533,7 +551,8 @@ int af_step(af_ctx *h, double dt) {
 static bool same_options(const Options &a, const Options &b) {
   return a.lin_mode == b.lin_mode && a.tsw == b.tsw && a.limiter == b.limiter &&
          a.correction == b.correction && a.force_lo == b.force_lo && a.surrogate == b.surrogate &&
-         a.surr_tol == b.surr_tol && a.surr_abs == b.surr_abs;
+         a.surr_tol == b.surr_tol && a.surr_abs == b.surr_abs && a.flux_limiter == b.flux_limiter &&
+         a.shock_blend == b.shock_blend;
 }
 
 // Capture two steps on the handle's own stream (the t^n and t^{n+1} buffers

@@ -55,6 +55,9 @@ struct af_batch {
   long long ghost_max = 0;
   bool maps_ok = false;
   std::vector<GraphEntry> graphs;
+  bool any_limiter = false;  // some instance has the flux limiter on
+  bool any_blend = false;    // some instance has the Sec. 3.4 blend on
+  float **d_theta = nullptr; // [n][2] blend weight planes (NULL: off)
   bool sampling = false;  // training-set sampler between point values and fluxes
   SampleBatch sampler;
 };
@@ -119,14 +122,22 @@ int upload_args(af_batch *b) {
   std::vector<PointValueArgs> pv(2 * b->n);
   std::vector<FluxArgs> fx(2 * b->n);
   std::vector<float *> arrays(10 * (size_t)b->n);
+  bool any_lim = false, any_blend = false;
+  std::vector<float *> theta(2 * (size_t)b->n);
   for (int k = 0; k < b->n; k++) {
     af_ctx *h = b->inst[k];
     BatchCtl *c = b->d_ctl + k;
     for (int q = 0; q < 2; q++) {
       pv[2 * k + q] = pointvalue_args(h->g, h->tbuf[q], h->hi, h->lev[1], h->tbuf[q ^ 1], h->opt, &c->status,
                                       c->counters);
+      if (h->opt.shock_blend) {
+        pv[2 * k + q].theta[0] = h->shock_theta;
+        pv[2 * k + q].theta[1] = h->shock_theta + h->g.plane;
+      }
       fx[2 * k + q] = flux_args(h->g, h->tbuf[q], h->lev[1], h->tbuf[q ^ 1], h->hi, h->lo, &c->status, &c->speed,
                                 &c->speed_bad);
+      fx[2 * k + q].flux_limiter = h->opt.flux_limiter;
+      if (h->opt.flux_limiter) any_lim = true;
       float **a = &arrays[(2 * k + q) * 5];
       a[0] = h->hi;
       a[1] = h->lo;
@@ -134,11 +145,19 @@ int upload_args(af_batch *b) {
       a[3] = h->tbuf[q].k[XE];
       a[4] = h->tbuf[q].k[YE];
     }
+    theta[2 * k] = h->opt.shock_blend ? h->shock_theta : nullptr;
+    theta[2 * k + 1] = h->opt.shock_blend ? h->shock_theta + h->g.plane : nullptr;
+    if (h->opt.shock_blend) any_blend = true;
   }
   BCK(cudaMemcpy(b->d_pv, pv.data(), sizeof(PointValueArgs) * pv.size(), cudaMemcpyHostToDevice), "batch: args");
   BCK(cudaMemcpy(b->d_fx, fx.data(), sizeof(FluxArgs) * fx.size(), cudaMemcpyHostToDevice), "batch: args");
   BCK(cudaMemcpy(b->d_arrays, arrays.data(), sizeof(float *) * arrays.size(), cudaMemcpyHostToDevice),
       "batch: args");
+  BCK(cudaMemcpy(b->d_theta, theta.data(), sizeof(float *) * theta.size(), cudaMemcpyHostToDevice),
+      "batch: args");
+  if (any_lim != b->any_limiter || any_blend != b->any_blend) drop_graphs(b);  // captured launches differ
+  b->any_limiter = any_lim;
+  b->any_blend = any_blend;
   return AF_OK;
 }
 
@@ -194,6 +213,8 @@ int enqueue_batch_step(af_batch *b, double *hist, int hist_steps, cudaStream_t s
   G.grids = b->d_grids;
   G.arrays = b->d_arrays;
   BCK(launch_ghost_batch(G, b->n, b->ghost_max, s), "batch: ghost fill");
+  if (b->any_blend)
+    BCK(launch_shock_theta_batch(b->d_ctl, b->d_grids, b->d_arrays, b->d_theta, b->n, s), "batch: shock indicator");
   BCK(launch_pointvalue_batch(pv_batch(b), b->n_pv_tiles, b->tile_h, s), "batch: point values");
   if (b->sampling)
     BCK(launch_sample_batch(b->sampler, b->d_pv_tiles, b->n_pv_tiles, b->tile_h, b->d_ctl, b->d_pv, s),
@@ -202,7 +223,7 @@ int enqueue_batch_step(af_batch *b, double *hist, int hist_steps, cudaStream_t s
   F.tiles = b->d_fx_tiles;
   F.ctl = b->d_ctl;
   F.args = b->d_fx;
-  BCK(launch_flux_batch(F, b->n_fx_tiles, s), "batch: flux update");
+  BCK(launch_flux_batch(F, b->n_fx_tiles, b->any_limiter, s), "batch: flux update");
   return AF_OK;
 }
 
@@ -264,6 +285,7 @@ void free_batch(af_batch *b) {
   cudaFree(b->d_maps);
   cudaFree(b->d_grids);
   cudaFree(b->d_arrays);
+  cudaFree(b->d_theta);
   cudaFree(b->d_pv_tiles);
   cudaFree(b->d_fx_tiles);
   if (b->own_stream) cudaStreamDestroy(b->own_stream);
@@ -326,6 +348,7 @@ af_batch *af_batch_create(int n, const int *nx, const int *ny, const double *dx,
   if (e == cudaSuccess) e = cudaMalloc(&b->d_maps, sizeof(TileMaps) * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_grids, sizeof(Grid) * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_arrays, sizeof(float *) * 10 * n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_theta, sizeof(float *) * 2 * n);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_grids, grids.data(), sizeof(Grid) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     bcuda(e, "af_batch_create");

@@ -19,7 +19,9 @@ constexpr int OY = 2;
 
 enum NodeKind { VTX = 0, XE = 1, YE = 2 };
 enum BcKind { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTING = 2 };
-enum StatusBits { ST_CFL = 1, ST_AVG_NONPOS = 2, ST_NONFINITE = 4, ST_KEPT = 8, ST_TIMEOUT = 16, ST_STOPPED = 32 };
+enum StatusBits {
+  ST_CFL = 1, ST_AVG_NONPOS = 2, ST_NONFINITE = 4, ST_KEPT = 8, ST_TIMEOUT = 16, ST_STOPPED = 32, ST_FLUX_LIMITED = 64
+};
 enum Counter { CNT_EG1 = 0, CNT_LF = 1, CNT_KEPT = 2, CNT_TSW = 3 };
 
 struct Grid {

@@ -100,8 +100,150 @@ struct FluxSmem {
   int wbad[TX * TY / 32];
 };
 
+// ---- cell-average flux limiter (Sec. 3.5; the convex-decomposition
+// construction of Hu, Adams and Shu, 2013).  With face speeds alpha_f (max of
+// |u_n| + c of the face's two cells' averages), r_f = lambda_f alpha_f and S
+// the sum of r_f over a cell's faces, the cell update is the convex
+// combination sum_f (r_f / S) P_f of the face states
+//   P_f = Q - (S / alpha_f) sigma_f (F_f - f_n(Q)).
+// Each face flux becomes theta F^ho + (1 - theta) F^lo (F^lo the Rusanov flux
+// of the two averages), theta the largest value in [0, 1] for which P_f
+// keeps rho >= 0.1 rho(P_f^lo) and p >= 0.1 p(P_f^lo) in both cells (a convex
+// set in theta: bisection, 20 halvings); theta = 1 keeps F^ho exactly,
+// theta = 0 (or a non-finite F^ho) takes F^lo exactly.
+constexpr int LW = TX + 4, LH = TY + 4;  // cells i0 - 2 .. i0 + TX + 1, j0 - 2 .. j0 + TY + 1
+constexpr float FL_ETA = 0.1f;
+struct LimSmem {
+  float q[NV][LH][LW];
+  float ax[LH][LW], ay[LH][LW];
+  float sum[LH - 2][LW - 2];  // S of cells i0 - 1 .. i0 + TX, j0 - 1 .. j0 + TY
+};
+
+__device__ __forceinline__ bool fl_ok(const float A[4], const float B[4], float th, float rmin, float pmin,
+                                      float gm1) {
+  float P[4];
+#pragma unroll
+  for (int v = 0; v < NV; v++) P[v] = fmaf(th, B[v], A[v]);
+  if (!(P[0] >= rmin) || !(P[0] > 0.0f)) return false;
+  const float p = gm1 * (P[3] - 0.5f * (P[1] * P[1] + P[2] * P[2]) / P[0]);
+  return p >= pmin;
+}
+
+// largest admissible theta of the face state of a cell with average Q
+__device__ __noinline__ float fl_theta(const float *Q, int dir, float k, const float *Fho, const float *Flo,
+                                       float gam) {
+  const float gm1 = gam - 1.0f;
+  float U[4], fn[4], A[4], B[4], UA[4];
+  c2p(Q, gm1, U);
+  phys_flux(U, 1.0f / gm1, dir, fn);
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    A[v] = Q[v] - k * (Flo[v] - fn[v]);
+    B[v] = -k * (Fho[v] - Flo[v]);
+  }
+  c2p(A, gm1, UA);
+  if (!(UA[0] > 0.0f) || !(UA[3] > 0.0f)) return 0.0f;
+  const float rmin = FL_ETA * UA[0], pmin = FL_ETA * UA[3];
+  if (fl_ok(A, B, 1.0f, rmin, pmin, gm1)) return 1.0f;
+  float lo = 0.0f, hi = 1.0f;
+  for (int it = 0; it < 20; it++) {
+    const float mid = 0.5f * (lo + hi);
+    if (fl_ok(A, B, mid, rmin, pmin, gm1)) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// one face: F (in place) = theta F^ho + (1 - theta) F^lo; true if limited
+__device__ __forceinline__ bool limit_face(float *const F[4], const float QL[4], const float QR[4], float al,
+                                           float sL, float sR, int dir, float gam) {
+  if (!(al > 0.0f)) return false;
+  const float gm1 = gam - 1.0f, gm1i = 1.0f / gm1;
+  float Fho[4], Flo[4], UL[4], UR[4], fL[4], fR[4];
+  c2p(QL, gm1, UL);
+  c2p(QR, gm1, UR);
+  phys_flux(UL, gm1i, dir, fL);
+  phys_flux(UR, gm1i, dir, fR);
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    Fho[v] = *F[v];
+    Flo[v] = 0.5f * (fL[v] + fR[v]) - 0.5f * al * (QR[v] - QL[v]);
+  }
+  bool finite = true;
+#pragma unroll
+  for (int v = 0; v < NV; v++) finite = finite && isfinite(Fho[v]);
+  float th = 0.0f;
+  if (finite) {
+    const float tl = fl_theta(QL, dir, sL / al, Fho, Flo, gam);
+    const float tr = fl_theta(QR, dir, -sR / al, Fho, Flo, gam);
+    th = fminf(tl, tr);
+    if (th >= 1.0f) return false;
+  }
+  // theta = 0 takes F^lo exactly (also when F^ho overflowed)
+#pragma unroll
+  for (int v = 0; v < NV; v++) *F[v] = th > 0.0f ? th * Fho[v] + (1.0f - th) * Flo[v] : Flo[v];
+  return true;
+}
+
+__device__ __noinline__ void limit_tile(const Args &A, FluxSmem &S, LimSmem &L, int i0, int j0) {
+  const Grid &g = A.g;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const float gam = g.gamma, gm1 = gam - 1.0f;
+  for (int k = tid; k < LW * LH; k += TX * TY) {
+    const int a = k % LW, b = k / LW, ci = i0 - 2 + a, cj = j0 - 2 + b;
+    float Q[4] = {1.0f, 0.0f, 0.0f, 1.0f};  // cells beyond the ghost layers feed no face of the domain
+    if (ci <= g.nx + 1 && cj <= g.ny + 1)
+#pragma unroll
+      for (int v = 0; v < NV; v++) Q[v] = A.hi[at(g, v, ci, cj)];
+    float U[4];
+    c2p(Q, gm1, U);
+    const bool ok = U[0] > 0.0f && U[3] > 0.0f;
+    const float c = ok ? sqrtf(gam * U[3] / U[0]) : 0.0f;
+#pragma unroll
+    for (int v = 0; v < NV; v++) L.q[v][b][a] = Q[v];
+    L.ax[b][a] = ok ? fabsf(U[1]) + c : 0.0f;
+    L.ay[b][a] = ok ? fabsf(U[2]) + c : 0.0f;
+  }
+  __syncthreads();
+  for (int k = tid; k < (LW - 2) * (LH - 2); k += TX * TY) {
+    const int a = k % (LW - 2) + 1, b = k / (LW - 2) + 1;
+    L.sum[b - 1][a - 1] = A.lx * (fmaxf(L.ax[b][a - 1], L.ax[b][a]) + fmaxf(L.ax[b][a], L.ax[b][a + 1])) +
+                          A.ly * (fmaxf(L.ay[b - 1][a], L.ay[b][a]) + fmaxf(L.ay[b][a], L.ay[b + 1][a]));
+  }
+  __syncthreads();
+  bool limited = false;
+  for (int k = tid; k < (TX + 1) * TY; k += TX * TY) {  // x-faces (i0 + fa - 1/2, j0 + fb)
+    const int fa = k % (TX + 1), fb = k / (TX + 1);
+    if (i0 + fa > g.nx || j0 + fb >= g.ny) continue;
+    float QL[4], QR[4];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      QL[v] = L.q[v][fb + 2][fa + 1];
+      QR[v] = L.q[v][fb + 2][fa + 2];
+    }
+    float *F[4] = {&S.Fx[0][fb][fa], &S.Fx[1][fb][fa], &S.Fx[2][fb][fa], &S.Fx[3][fb][fa]};
+    const float al = fmaxf(L.ax[fb + 2][fa + 1], L.ax[fb + 2][fa + 2]);
+    limited |= limit_face(F, QL, QR, al, L.sum[fb + 1][fa], L.sum[fb + 1][fa + 1], 0, gam);
+  }
+  for (int k = tid; k < TX * (TY + 1); k += TX * TY) {  // y-faces (i0 + fa, j0 + fb - 1/2)
+    const int fa = k % TX, fb = k / TX;
+    if (i0 + fa >= g.nx || j0 + fb > g.ny) continue;
+    float QS[4], QN[4];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      QS[v] = L.q[v][fb + 1][fa + 2];
+      QN[v] = L.q[v][fb + 2][fa + 2];
+    }
+    float *F[4] = {&S.Gy[0][fb][fa], &S.Gy[1][fb][fa], &S.Gy[2][fb][fa], &S.Gy[3][fb][fa]};
+    const float al = fmaxf(L.ay[fb + 1][fa + 2], L.ay[fb + 2][fa + 2]);
+    limited |= limit_face(F, QS, QN, al, L.sum[fb][fa + 1], L.sum[fb + 1][fa + 1], 1, gam);
+  }
+  if (limited) atomicOr(A.status, ST_FLUX_LIMITED);
+}
+
 // the tile of cells with origin (i0, j0)
-__device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, int i0, int j0) {
+template <bool LIM>
+__device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L, int i0, int j0) {
   const Grid &g = A.g;
   auto &vf = S.vf;
   auto &vg = S.vg;
@@ -157,6 +299,10 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, int i0, in
     for (int v = 0; v < NV; v++) Gy[v][b][a] = (vg[v][b][a] + 4.0f * yg[v][b][a] + vg[v][b][a + 1]) * w36;
   }
   __syncthreads();
+  if (LIM) {
+    limit_tile(A, S, *L, i0, j0);
+    __syncthreads();
+  }
   // finite-volume update on the (hi, lo) pair in double-word arithmetic
   const int a = threadIdx.x, b = threadIdx.y, i = i0 + a, j = j0 + b;
   const bool inside = i < g.nx && j < g.ny;
@@ -210,7 +356,13 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, int i0, in
 // ~200 B a cell, and the extra warps keep more loads in flight
 __global__ void __launch_bounds__(TX *TY, 6) flux_update_kernel(Args A) {
   __shared__ FluxSmem S;
-  flux_tile(A, S, blockIdx.x * TX, blockIdx.y * TY);
+  flux_tile<false>(A, S, nullptr, blockIdx.x * TX, blockIdx.y * TY);
+}
+
+__global__ void __launch_bounds__(TX *TY) flux_limited_kernel(Args A) {
+  __shared__ FluxSmem S;
+  __shared__ LimSmem L;
+  flux_tile<true>(A, S, &L, blockIdx.x * TX, blockIdx.y * TY);
 }
 
 // batched form: tile B.tiles[b] = (instance, i0, j0); the instance's dt
@@ -229,7 +381,28 @@ __global__ void __launch_bounds__(TX *TY, 6) flux_batch_kernel(FluxBatch B) {
     A.lyl = c.lyl;
   }
   __syncthreads();
-  flux_tile(A, S, t.y, t.z);
+  flux_tile<false>(A, S, nullptr, t.y, t.z);
+}
+
+__global__ void __launch_bounds__(TX *TY) flux_batch_limited_kernel(FluxBatch B) {
+  __shared__ FluxSmem S;
+  __shared__ LimSmem L;
+  __shared__ Args A;
+  const int4 t = B.tiles[blockIdx.x];
+  const BatchCtl &c = B.ctl[t.x];
+  if (!c.active) return;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    A = B.args[2 * t.x + c.cur];
+    A.lxh = c.lxh;
+    A.lxl = c.lxl;
+    A.lyh = c.lyh;
+    A.lyl = c.lyl;
+    A.lx = c.lxh;
+    A.ly = c.lyh;
+  }
+  __syncthreads();
+  if (A.flux_limiter) flux_tile<true>(A, S, &L, t.y, t.z);
+  else flux_tile<false>(A, S, nullptr, t.y, t.z);
 }
 
 }  // namespace
@@ -245,7 +418,8 @@ FluxArgs flux_args(const Grid &g, const NodeSet &n0, const NodeSet &n1, const No
   }
   A.hi = avg_hi;
   A.lo = avg_lo;
-  A.lxh = A.lxl = A.lyh = A.lyl = 0.0f;
+  A.lxh = A.lxl = A.lyh = A.lyl = A.lx = A.ly = 0.0f;
+  A.flux_limiter = 0;
   A.status = status;
   A.speed = speed;
   A.speed_bad = speed_bad;
@@ -254,21 +428,27 @@ FluxArgs flux_args(const Grid &g, const NodeSet &n0, const NodeSet &n1, const No
 
 cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &n1,
                                const NodeSet &n2, float *avg_hi, float *avg_lo, double lamx,
-                               double lamy, int *status, unsigned *speed, int *speed_bad, cudaStream_t s) {
+                               double lamy, int *status, unsigned *speed, int *speed_bad, int flux_limiter,
+                               cudaStream_t s) {
   Args A = flux_args(g, n0, n1, n2, avg_hi, avg_lo, status, speed, speed_bad);
   split_double(lamx, A.lxh, A.lxl);
   split_double(lamy, A.lyh, A.lyl);
+  A.lx = A.lxh;
+  A.ly = A.lyh;
+  A.flux_limiter = flux_limiter;
   cudaMemsetAsync(speed, 0, sizeof(unsigned), s);
   cudaMemsetAsync(speed_bad, 0, sizeof(int), s);
   dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY), blk(TX, TY);
-  flux_update_kernel<<<grd, blk, 0, s>>>(A);
+  if (flux_limiter) flux_limited_kernel<<<grd, blk, 0, s>>>(A);
+  else flux_update_kernel<<<grd, blk, 0, s>>>(A);
   return cudaGetLastError();
 }
 
-cudaError_t launch_flux_batch(const FluxBatch &B, int ntiles, cudaStream_t s) {
+cudaError_t launch_flux_batch(const FluxBatch &B, int ntiles, bool any_limiter, cudaStream_t s) {
   static_assert(TX == FLUX_TX && TY == FLUX_TY, "tile list shape");
   if (ntiles <= 0) return cudaSuccess;
-  flux_batch_kernel<<<ntiles, dim3(TX, TY), 0, s>>>(B);
+  if (any_limiter) flux_batch_limited_kernel<<<ntiles, dim3(TX, TY), 0, s>>>(B);
+  else flux_batch_kernel<<<ntiles, dim3(TX, TY), 0, s>>>(B);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,8 @@ struct Options {
   int surrogate = 0;   // learned point-value operator with exact fallback
   float surr_tol = 0.5f;
   float surr_abs = 2e-3f;
+  int flux_limiter = 0;  // cell-average flux limiter (Sec. 3.5)
+  int shock_blend = 0;   // Sec. 3.4 shock-indicator blend of point values
 };
 
 // TMA descriptors of the t^n node arrays and the cell averages (one set per
@@ -46,6 +48,8 @@ struct PointValueArgs {
   // mask byte (index (j + OY) * P + i + OX), only tiles with a nonzero flag
   const unsigned char *mask[3];
   const int *tile_flag;
+  // Sec. 3.4 blend weights of the x- and y-edge midpoints (NULL: no blend)
+  const float *theta[2];
 };
 inline PointValueArgs pointvalue_args(const Grid &g, const NodeSet &n0, const float *avg_hi, const NodeSet &n1,
                                       const NodeSet &n2, const Options &o, int *status,
@@ -68,6 +72,7 @@ inline PointValueArgs pointvalue_args(const Grid &g, const NodeSet &n0, const fl
   A.counters = counters;
   A.mask[0] = A.mask[1] = A.mask[2] = nullptr;
   A.tile_flag = nullptr;
+  A.theta[0] = A.theta[1] = nullptr;
   return A;
 }
 
@@ -77,6 +82,8 @@ struct FluxArgs {
   const float *__restrict__ n[3][3];  // [level][kind]
   float *hi, *lo;
   float lxh, lxl, lyh, lyl;  // dt/dx and dt/dy as double-word FP32 (hi + lo)
+  float lx, ly;              // the same in FP32 (flux limiter)
+  int flux_limiter;          // cell-average flux limiter on
   int *status;
   unsigned *speed;  // max of max(|u|,|v|) + c over the new state, as float bits
   int *speed_bad;   // set if a new value is not admissible
@@ -136,11 +143,16 @@ cudaError_t prepare_pointvalue();
 // batched point values over a tile list of tile height tile_h (4, 8 or 16)
 cudaError_t launch_pointvalue_batch(const PointValueBatch &B, int ntiles, int tile_h, cudaStream_t s);
 // batched flux / update over a tile list of 32 x 8 cells
-cudaError_t launch_flux_batch(const FluxBatch &B, int ntiles, cudaStream_t s);
+cudaError_t launch_flux_batch(const FluxBatch &B, int ntiles, bool any_limiter, cudaStream_t s);
 constexpr int FLUX_TX = 32, FLUX_TY = 8;
 // batched ghost fill; max_per: the largest per-instance ghost count
 cudaError_t launch_ghost_batch(const GhostBatch &B, int n, long long max_per, cudaStream_t s);
 long long ghost_count(const Grid &g);
+// Sec. 3.4 blend weights of the edge midpoints (planes of the padded layout)
+cudaError_t launch_shock_theta(const Grid &g, const float *avg_hi, float *tx, float *ty, cudaStream_t s);
+// batched: theta[2k], theta[2k+1] the planes of instance k (NULL: skipped)
+cudaError_t launch_shock_theta_batch(const BatchCtl *ctl, const Grid *grids, const float *const *arrays,
+                                     float *const *theta, int n, cudaStream_t s);
 // per-instance dt for the coming step (mode DT_STEP; records it into
 // hist[step * n + k] if hist), only the buffer flip of the last step
 // (DT_SETTLE), or dt without advancing anything (DT_PROBE)
@@ -148,12 +160,14 @@ cudaError_t launch_batch_dt(BatchCtl *ctl, int n, double *hist, int hist_cap, in
 // cell prep and point values at t^{n+1/2} (n1) and t^{n+1} (n2)
 cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
-                              int *status, unsigned long long *counters, cudaStream_t s);
+                              int *status, unsigned long long *counters, const float *const theta[2],
+                              cudaStream_t s);
 // Simpson fluxes and the finite-volume update of the averages (compensated
 // hi/lo); also the max wave speed of the new state into *speed (float bits)
 cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &n1,
                                const NodeSet &n2, float *avg_hi, float *avg_lo, double lamx,
-                               double lamy, int *status, unsigned *speed, int *speed_bad, cudaStream_t s);
+                               double lamy, int *status, unsigned *speed, int *speed_bad, int flux_limiter,
+                               cudaStream_t s);
 // max over averages and owned point values of max(|u|,|v|) + c (as float bits)
 cudaError_t launch_max_speed(const Grid &g, const float *avg_hi, const NodeSet &n,
                              unsigned *out_bits, int *bad, cudaStream_t s);
@@ -215,7 +229,7 @@ cudaError_t launch_surrogate(int kind, const SurrogateArgs &A, int sms, cudaStre
 cudaError_t launch_pointvalue_masked(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                                      const NodeSet &n1, const NodeSet &n2, float dt, const Options &o, int *status,
                                      unsigned long long *counters, const unsigned char *const mask[3],
-                                     const int *tile_flag, cudaStream_t s);
+                                     const int *tile_flag, const float *const theta[2], cudaStream_t s);
 
 // record a message for af_last_error on this host thread; returns code
 int set_error(int code, const char *msg);

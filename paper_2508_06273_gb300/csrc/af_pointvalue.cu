@@ -7,8 +7,8 @@
 // midpoint (i-1/2, j) and the y-edge midpoint (i, j-1/2).
 //
 // Prologue: for every cell of the tile and a one-cell halo the block forms
-// the cell prep (Q_c by inverting Simpson's rule, U_c = C2P(Q_c), Ubar by
-// Simpson's rule) and stores, per variable, the cell's biquadratic
+// the cell prep (Q_c by inverting Simpson's rule, U_c = C2P(Q_c), Ubar the
+// primitive state of the cell average) and stores, per variable, the cell's biquadratic
 // reconstruction as monomial coefficients about the cell centre in shared
 // memory, plus Ubar.
 //
@@ -122,22 +122,23 @@ __device__ __forceinline__ void build_cell(const Grid &g, const float *raw, int 
   raw4<TY>(raw, RAW_XE, ci + 1, cj, i0, j0, N[5]);
   raw4<TY>(raw, RAW_YE, ci, cj, i0, j0, N[6]);
   raw4<TY>(raw, RAW_YE, ci, cj + 1, i0, j0, N[7]);
-  float Qs[4] = {0, 0, 0, 0}, Us[4] = {0, 0, 0, 0};
+  float Qs[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int n = 0; n < 8; n++) {
     float Q[4];
     p2c(N[n], gm1i, Q);
     const float w = n < 4 ? 1.0f : 4.0f;
 #pragma unroll
-    for (int v = 0; v < NV; v++) {
-      Qs[v] += w * Q[v];
-      Us[v] += w * N[n][v];
-    }
+    for (int v = 0; v < NV; v++) Qs[v] += w * Q[v];
   }
-  float Qc[4], Uc[4];
+  float Qa[4], Qc[4], Uc[4], Ub[4];
 #pragma unroll
-  for (int v = 0; v < NV; v++) Qc[v] = (36.0f * raw_at<TY>(raw, RAW_AVG, v, ci, cj, i0, j0) - Qs[v]) * 0.0625f;
+  for (int v = 0; v < NV; v++) {
+    Qa[v] = raw_at<TY>(raw, RAW_AVG, v, ci, cj, i0, j0);
+    Qc[v] = (36.0f * Qa[v] - Qs[v]) * 0.0625f;
+  }
   c2p(Qc, gm1, Uc);
+  c2p(Qa, gm1, Ub);  // Ubar: the primitive state of the cell average (Sec. 3.5)
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     const float f[3][3] = {{N[0][v], N[4][v], N[2][v]}, {N[6][v], Uc[v], N[7][v]}, {N[1][v], N[5][v], N[3][v]}};
@@ -147,7 +148,7 @@ __device__ __forceinline__ void build_cell(const Grid &g, const float *raw, int 
     r4[0] = make_float4(m[0][0], m[0][1], m[0][2], m[1][0]);
     r4[1] = make_float4(m[1][1], m[1][2], m[2][0], m[2][1]);
     r4[2] = make_float4(m[2][2], 0.0f, 0.0f, 0.0f);
-    rec[UBAR_OFF + v] = (Us[v] + 16.0f * Uc[v]) * (1.0f / 36.0f);
+    rec[UBAR_OFF + v] = Ub[v];
   }
 }
 
@@ -662,6 +663,15 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
       lin_avg<K>(sm, li, lj, ul);
     }
   }
+  // Sec. 3.4 blend weight (the same for both levels; from the t^n averages)
+  float th = 1.0f;
+  if (A.theta[0]) {
+    if (K == XE) th = __ldg(A.theta[0] + at(g, 0, i, j));
+    else if (K == YE) th = __ldg(A.theta[1] + at(g, 0, i, j));
+    else
+      th = fminf(fminf(__ldg(A.theta[0] + at(g, 0, i, j)), __ldg(A.theta[0] + at(g, 0, i, j - 1))),
+                 fminf(__ldg(A.theta[1] + at(g, 0, i, j)), __ldg(A.theta[1] + at(g, 0, i - 1, j))));
+  }
   bool sw = false;
   if (A.tsw) {
     const int a = li + 1, b = lj + 1;
@@ -692,6 +702,14 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
     } else {
 #pragma unroll
       for (int v = 0; v < NV; v++) res[v] = ho[v];
+    }
+    if (1.0f - th >= 1e-6f) {
+      // blend with the low-order value of Alg. 3's chain (EG1 on pc data,
+      // else Lax-Friedrichs, else the t^n value): both ends admissible
+      float lo[4];
+      limit<K>(A, sm, i, j, li, lj, tau, U0, lo, cnt);
+#pragma unroll
+      for (int v = 0; v < NV; v++) res[v] = th * res[v] + (1.0f - th) * lo[v];
     }
 #pragma unroll
     for (int v = 0; v < NV; v++) nonfinite |= !isfinite(res[v]);
@@ -878,9 +896,12 @@ cudaError_t prepare_pointvalue() {
 
 cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
-                              int *status, unsigned long long *counters, cudaStream_t s) {
+                              int *status, unsigned long long *counters, const float *const theta[2],
+                              cudaStream_t s) {
   Args A = pointvalue_args(g, n0, avg_hi, n1, n2, o, status, counters);
   A.dt = dt;
+  A.theta[0] = theta[0];
+  A.theta[1] = theta[1];
   // tiles cover the owned nodes: up to nxv x nyv (vertex lines n + 1 on a
   // non-periodic axis); every box x coordinate is a multiple of TX floats
   constexpr int TY = 8;
@@ -892,9 +913,11 @@ cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg
 cudaError_t launch_pointvalue_masked(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                                      const NodeSet &n1, const NodeSet &n2, float dt, const Options &o, int *status,
                                      unsigned long long *counters, const unsigned char *const mask[3],
-                                     const int *tile_flag, cudaStream_t s) {
+                                     const int *tile_flag, const float *const theta[2], cudaStream_t s) {
   Args A = pointvalue_args(g, n0, avg_hi, n1, n2, o, status, counters);
   A.dt = dt;
+  A.theta[0] = theta[0];
+  A.theta[1] = theta[1];
   for (int k = 0; k < 3; k++) A.mask[k] = mask[k];
   A.tile_flag = tile_flag;
   constexpr int TY = 8;

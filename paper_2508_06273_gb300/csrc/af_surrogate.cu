@@ -33,38 +33,13 @@ __device__ __forceinline__ void ld4g(const Grid &g, const float *p, int i, int j
   for (int v = 0; v < NV; v++) U[v] = __ldg(p + at(g, v, i, j));
 }
 
-// primitive cell average Ubar of cell (ci, cj) (Sec. 2 cell prep)
-__device__ __forceinline__ void cell_ubar(const Grid &g, const float *avg, const float *vtx, const float *xe,
-                                          const float *ye, int ci, int cj, float Ub[4]) {
-  const float gm1 = g.gamma - 1.0f, gm1i = 1.0f / gm1;
-  float N[8][4];
-  ld4g(g, vtx, ci, cj, N[0]);
-  ld4g(g, vtx, ci + 1, cj, N[1]);
-  ld4g(g, vtx, ci, cj + 1, N[2]);
-  ld4g(g, vtx, ci + 1, cj + 1, N[3]);
-  ld4g(g, xe, ci, cj, N[4]);
-  ld4g(g, xe, ci + 1, cj, N[5]);
-  ld4g(g, ye, ci, cj, N[6]);
-  ld4g(g, ye, ci, cj + 1, N[7]);
-  float Qs[4] = {0, 0, 0, 0}, Us[4] = {0, 0, 0, 0};
-#pragma unroll
-  for (int n = 0; n < 8; n++) {
-    float Q[4];
-    p2c(N[n], gm1i, Q);
-    const float w = n < 4 ? 1.0f : 4.0f;
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-      Qs[v] += w * Q[v];
-      Us[v] += w * N[n][v];
-    }
-  }
-  float A[4], Qc[4], Uc[4];
+// primitive cell average Ubar of cell (ci, cj): the primitive state of the
+// conservative cell average (the reading of Sec. 3.5 the point-value kernel uses)
+__device__ __forceinline__ void cell_ubar(const Grid &g, const float *avg, const float *, const float *,
+                                          const float *, int ci, int cj, float Ub[4]) {
+  float A[4];
   ld4g(g, avg, ci, cj, A);
-#pragma unroll
-  for (int v = 0; v < NV; v++) Qc[v] = (36.0f * A[v] - Qs[v]) * 0.0625f;
-  c2p(Qc, gm1, Uc);
-#pragma unroll
-  for (int v = 0; v < NV; v++) Ub[v] = (Us[v] + 16.0f * Uc[v]) * (1.0f / 36.0f);
+  c2p(A, g.gamma - 1.0f, Ub);
 }
 
 // values of the node's stencil (cells first, then points) in template order

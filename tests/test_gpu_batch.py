@@ -137,9 +137,10 @@ def test_end_times_are_met_exactly_and_instances_stop(env):
 
 def test_a_failing_instance_stops_alone(env):
     """Four-quadrant data whose averages lose positivity at once (seed 0 at
-    64^2 without a flux limiter): that instance is flagged and stopped,
-    the others run on unchanged."""
+    64^2 with neither the flux limiter nor the Sec. 3.4 blend): that
+    instance is flagged and stopped, the others run on unchanged."""
     probs = [W.shu_vortex_seeded(40, seed=3), W.four_quadrant(64, seed=0)]
+    probs[1].options = dict(probs[1].options, flux_limiter=0, shock_blend=0)
     b = _batch(env, probs)
     hist = _run_with_hist(env, b, 12)
     t, steps, active, status = b.query()

@@ -1,0 +1,115 @@
+"""Sec. 3.4 shock-indicator blend and the cell-average flux limiter on the
+GPU, through the C ABI, against the FP64 oracle: parity where both act,
+bitwise inactivity on smooth data, conservation while limiting, and
+admissibility of every value on seeded four-quadrant problems."""
+import numpy as np
+import pytest
+
+from helpers import make_oracle
+from paper_2508_06273_gb300 import workloads as W
+from test_gpu_parity import env, host, solver, state_err  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _admissible(state, g=1.4):
+    avg = state[0]
+    p = (g - 1) * (avg[3] - 0.5 * (avg[1] ** 2 + avg[2] ** 2) / avg[0])
+    return bool(np.all(avg[0] > 0) and np.all(p > 0)
+                and all(np.all(a[0] > 0) and np.all(a[3] > 0) for a in state[1:]))
+
+
+def test_flux_limiter_matches_the_oracle_while_acting(env):
+    """Near-vacuum double rarefaction (u = -+2, p = 0.1): both sides limit
+    fluxes on the same steps; the states agree to FP32 level."""
+    torch, af, oracle = env
+    prob = W.double_rarefaction(32, p=0.1)
+    st = W.to_f32(W.discretise(prob))
+    o = make_oracle(oracle, prob, state=st)
+    s = solver(env, prob, state=st)
+    for k in range(6):
+        dt = 0.3 * prob.dx / o.max_speed()
+        o.step(dt)
+        s.step(dt)
+        so, sg = o.status(), s.status()
+        assert bool(so & oracle.ST_FLUX_LIMITED) == bool(sg & af.ST_FLUX_LIMITED), k
+        assert not sg & (af.ST_AVG_NONPOS | af.ST_NONFINITE)
+    err = state_err(host(s.get_state()), o.get_state())
+    assert err < 1e-4, err
+    assert _admissible(host(s.get_state()))
+
+
+def test_shock_blend_matches_the_oracle(env):
+    """Mild four-quadrant data (pressure jumps of about 10%): the blend acts
+    along the jump lines with theta far from its cut-off on both sides."""
+    torch, af, oracle = env
+    from test_gpu_parity import MILD
+
+    prob = W.four_quadrant(28, states=MILD)
+    st = W.to_f32(W.discretise(prob))
+    opts = {"flux_limiter": 0, "tsw": 0}
+    o = make_oracle(oracle, prob, opts, state=st)
+    plain = make_oracle(oracle, prob, {"flux_limiter": 0, "tsw": 0, "shock_blend": 0}, state=st)
+    s = solver(env, prob, opts, st)
+    for _ in range(3):
+        dt = 0.3 * prob.dx / o.max_speed()
+        o.step(dt)
+        plain.step(dt)
+        s.step(dt)
+    # the blend changes the result measurably, and the GPU follows the oracle
+    assert state_err(o.get_state(), plain.get_state()) > 1e-4
+    assert state_err(host(s.get_state()), o.get_state()) < 3e-5
+
+
+def test_limiters_leave_smooth_data_bitwise_alone(env):
+    torch, af, _ = env
+    prob = W.shu_vortex_seeded(48, seed=4)
+    a = solver(env, prob)
+    b = solver(env, prob, {"flux_limiter": 1})
+    for _ in range(4):
+        dt = 0.3 * prob.dx / a.max_speed()
+        a.step(dt)
+        b.step(dt)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert torch.equal(x, y)
+    assert not b.status() & af.ST_FLUX_LIMITED
+
+
+def test_flux_limiter_conserves(env):
+    """Periodic near-vacuum data with the flux limiter acting: totals change
+    by round-off only (one flux per face, double-word update)."""
+    torch, af, _ = env
+    prob = W.double_rarefaction(40, p=0.1)
+    prob.bc = (0, 0, 0, 0)
+    s = solver(env, prob)
+    t0 = s.totals()
+    acted = 0
+    for _ in range(10):
+        s.step(0.3 * prob.dx / s.max_speed())
+        acted |= s.status() & af.ST_FLUX_LIMITED
+    assert acted
+    t1 = s.totals()
+    assert np.all(np.abs(t1 - t0) <= 1e-9 * np.maximum(1.0, np.abs(t0))), (t0, t1)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_seeded_riemann_problems_stay_admissible(env, seed):
+    """Seeded four-quadrant data at 64^2 (rho in [0.1, 1.5], p in [0.01,
+    1.5], |u|, |v| <= 1.2) with Alg. 2, Alg. 3, the blend and the flux
+    limiter, to t = 0.25 or 300 steps: every average and point value stays
+    admissible and finite."""
+    torch, af, _ = env
+    prob = W.four_quadrant(64, seed=seed)
+    s = solver(env, prob)
+    t = 0.0
+    for _ in range(300):
+        sp = s.max_speed()
+        assert np.isfinite(sp) and sp > 0
+        dt = min(0.3 * prob.dx / sp, 0.25 - t)
+        s.step(dt)
+        t += dt
+        assert not s.status() & (af.ST_AVG_NONPOS | af.ST_NONFINITE)
+        if t >= 0.25 - 1e-12:
+            break
+    assert _admissible(host(s.get_state()))
+    s.close()

@@ -231,7 +231,7 @@ def test_low_order_paths_parity(env, force, data):
     else:
         prob = W.four_quadrant(24, states=MILD)
     st = W.to_f32(W.discretise(prob))
-    opts = {"force_lo": force, "tsw": 0}
+    opts = {"force_lo": force, "tsw": 0, "shock_blend": 0, "flux_limiter": 0}
     o = make_oracle(oracle, prob, opts, state=st)
     dt = 0.3 * min(prob.dx, prob.dy) / o.max_speed()
     o.step(dt)

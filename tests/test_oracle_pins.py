@@ -508,7 +508,7 @@ def test_limiters_keep_every_value_admissible(oracle_mod):
         st |= o.status()
         assert _admissible_state(o.get_state())
     assert used > 0 and st & oracle_mod.ST_FLUX_LIMITED and not st & 6
-    bare = make_oracle(oracle_mod, prob)
+    bare = make_oracle(oracle_mod, prob, opts={"flux_limiter": 0})
     failed = False
     for _ in range(30):
         s = bare.max_speed()
