@@ -17,6 +17,7 @@ from .afo import (  # noqa: F401
     BC_PERIODIC,
     BC_TRANSMISSIVE,
     BC_REFLECTING,
+    BC_INFLOW,
     OPT_LIN_MODE,
     OPT_TSW,
     OPT_LIMITER,

@@ -46,6 +46,7 @@ struct afo_ctx {
   int nx, ny, W, H;
   double dx, dy, gam;
   int bc[4];
+  double inflow[4][4]; /* primitive inflow state per side (Sec. 4.3) */
   int lin_mode, tsw, limiter, correction, force_lo, threads, flux_limiter, shock_blend;
   double *avg;        /* conservative averages, [4][H][W] */
   double *nd[3][3];   /* point values [level][kind] -> [4][H][W]; level 0 t^n, 1 t^{n+1/2}, 2 t^{n+1} */
@@ -105,7 +106,7 @@ static int finite4(const double U[4]) {
  * that axis.  Periodic: wrap.  Outflow: mirror copy of the interior
  * (piecewise-constant extrapolation).  Solid wall: the same mirror with the
  * normal velocity component negated (Sec. 4.3). */
-static void fill_axis(afo_ctx *c, double *a, int axis, int node) {
+static void fill_axis(afo_ctx *c, double *a, int axis, int node, int conservative) {
   int n = axis == 0 ? c->nx : c->ny;
   int other_hi = (axis == 0 ? c->ny : c->nx) + G;
   int blo = c->bc[2 * axis], bhi = c->bc[2 * axis + 1];
@@ -122,15 +123,26 @@ static void fill_axis(afo_ctx *c, double *a, int axis, int node) {
         sl = node ? k : k - 1;
         sh = n - k;
       }
+      /* inflow sides: the side's state (conservative for cell averages) */
+      double inl[4], inh[4];
+      if (conservative) {
+        p2c(c->inflow[2 * axis], c->gam, inl);
+        p2c(c->inflow[2 * axis + 1], c->gam, inh);
+      } else {
+        for (int v = 0; v < NV; v++) {
+          inl[v] = c->inflow[2 * axis][v];
+          inh[v] = c->inflow[2 * axis + 1][v];
+        }
+      }
       for (int v = 0; v < NV; v++) {
         double sgl = (blo == AFO_BC_REFLECTING && v == flip) ? -1.0 : 1.0;
         double sgh = (bhi == AFO_BC_REFLECTING && v == flip) ? -1.0 : 1.0;
         if (axis == 0) {
-          AT(c, a, v, tl, o) = sgl * AT(c, a, v, sl, o);
-          AT(c, a, v, th, o) = sgh * AT(c, a, v, sh, o);
+          AT(c, a, v, tl, o) = blo == AFO_BC_INFLOW ? inl[v] : sgl * AT(c, a, v, sl, o);
+          AT(c, a, v, th, o) = bhi == AFO_BC_INFLOW ? inh[v] : sgh * AT(c, a, v, sh, o);
         } else {
-          AT(c, a, v, o, tl) = sgl * AT(c, a, v, o, sl);
-          AT(c, a, v, o, th) = sgh * AT(c, a, v, o, sh);
+          AT(c, a, v, o, tl) = blo == AFO_BC_INFLOW ? inl[v] : sgl * AT(c, a, v, o, sl);
+          AT(c, a, v, o, th) = bhi == AFO_BC_INFLOW ? inh[v] : sgh * AT(c, a, v, o, sh);
         }
       }
     }
@@ -149,13 +161,13 @@ static void fill_axis(afo_ctx *c, double *a, int axis, int node) {
 static const int XNODE[3] = {1, 1, 0}, YNODE[3] = {1, 0, 1};
 static void fill_nodes(afo_ctx *c, int level) {
   for (int k = 0; k < 3; k++) {
-    fill_axis(c, c->nd[level][k], 0, XNODE[k]);
-    fill_axis(c, c->nd[level][k], 1, YNODE[k]);
+    fill_axis(c, c->nd[level][k], 0, XNODE[k], 0);
+    fill_axis(c, c->nd[level][k], 1, YNODE[k], 0);
   }
 }
 static void fill_cells(afo_ctx *c, double *a) {
-  fill_axis(c, a, 0, 0);
-  fill_axis(c, a, 1, 0);
+  fill_axis(c, a, 0, 0, 1);
+  fill_axis(c, a, 1, 0, 1);
 }
 
 /* ------------------------------------------------ cell prep (Sec. 2) */
@@ -681,7 +693,7 @@ afo_ctx *afo_create(int nx, int ny, double dx, double dy, double gamma, uint32_t
   int b[4];
   for (int k = 0; k < 4; k++) {
     b[k] = (int)((bc >> (8 * k)) & 0xff);
-    if (b[k] > AFO_BC_REFLECTING) return NULL;
+    if (b[k] > AFO_BC_INFLOW) return NULL;
   }
   if ((b[0] == AFO_BC_PERIODIC) != (b[1] == AFO_BC_PERIODIC)) return NULL;
   if ((b[2] == AFO_BC_PERIODIC) != (b[3] == AFO_BC_PERIODIC)) return NULL;
@@ -695,7 +707,10 @@ afo_ctx *afo_create(int nx, int ny, double dx, double dy, double gamma, uint32_t
   c->dx = dx;
   c->dy = dy;
   c->gam = gamma;
-  for (int k = 0; k < 4; k++) c->bc[k] = b[k];
+  for (int k = 0; k < 4; k++) {
+    c->bc[k] = b[k];
+    c->inflow[k][0] = c->inflow[k][3] = 1.0; /* until set: rho = p = 1 at rest */
+  }
   c->correction = 1;
   c->limiter = 1;
   size_t n = NV * ps(c);
@@ -1180,6 +1195,12 @@ double afo_max_speed(const afo_ctx *c) {
 }
 
 int afo_status(const afo_ctx *c) { return c ? c->status : -1; }
+
+int afo_set_inflow(afo_ctx *c, int side, const double U[4]) {
+  if (!c || side < 0 || side > 3 || !U || !(U[0] > 0.0) || !(U[3] > 0.0)) return -1;
+  for (int v = 0; v < NV; v++) c->inflow[side][v] = U[v];
+  return 0;
+}
 
 double afo_shock_theta(const afo_ctx *c, int kind, int i, int j) {
   if (!c || kind < 0 || kind > 2 || i < -1 || j < -1 || i > c->nx || j > c->ny) return -1.0;

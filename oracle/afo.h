@@ -29,7 +29,7 @@ extern "C" {
 typedef struct afo_ctx afo_ctx;
 
 /* boundary kinds; bc = xlo | xhi << 8 | ylo << 16 | yhi << 24 */
-enum { AFO_BC_PERIODIC = 0, AFO_BC_TRANSMISSIVE = 1, AFO_BC_REFLECTING = 2 };
+enum { AFO_BC_PERIODIC = 0, AFO_BC_TRANSMISSIVE = 1, AFO_BC_REFLECTING = 2, AFO_BC_INFLOW = 3 };
 
 /* option keys (same numbering as the library) */
 enum {
@@ -97,6 +97,10 @@ int afo_eg_field(afo_field_fn f, void *user, int op, double xbar, double ybar,
                  const double ulin[4], double tau, double gamma, double out[4]);
 /* Gauss-Legendre points per arc piece and maximum piece length (radians) */
 void afo_set_quadrature(int npts, double max_piece);
+/* Inflow state (primitive rho, u, v, p) of side 0..3 (xlo, xhi, ylo, yhi),
+ * used by sides of kind AFO_BC_INFLOW (Sec. 4.3): ghost point values take it
+ * and ghost cell averages its conservative form. */
+int afo_set_inflow(afo_ctx *c, int side, const double U[4]);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ _LOCK = threading.Lock()
 _LIB = None
 
 VTX, XE, YE = 0, 1, 2
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING, BC_INFLOW = 0, 1, 2, 3
 OPT_LIN_MODE, OPT_TSW, OPT_LIMITER, OPT_CORRECTION, OPT_FORCE_LO, OPT_THREADS = 0, 1, 2, 3, 4, 16
 OPT_FLUX_LIMITER, OPT_SHOCK_BLEND = 9, 10
 ST_FLUX_LIMITED = 64
@@ -74,6 +74,7 @@ def _lib():
                 "afo_eg_field": (i, [FIELD_FN, vp, i, d, d, _dp, d, d, _dp]),
                 "afo_set_quadrature": (None, [i, d]),
                 "afo_shock_theta": (d, [vp, i, i, i]),
+                "afo_set_inflow": (i, [vp, i, _dp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -154,6 +155,12 @@ class Oracle:
 
     def status(self):
         return self.lib.afo_status(self.h)
+
+    def set_inflow(self, side, U):
+        """Primitive inflow state of side 0..3 (xlo, xhi, ylo, yhi)."""
+        u = np.ascontiguousarray(U, dtype=np.float64)
+        if self.lib.afo_set_inflow(self.h, int(side), _p(u)) != 0:
+            raise ValueError("afo_set_inflow rejected the state")
 
     def shock_theta(self, kind, i, j):
         """Sec. 3.4 blend weight of a node from the current Ubar (after prepare())."""

@@ -54,6 +54,7 @@ class Problem:
     gamma: float = GAMMA
     options: dict = dataclasses.field(default_factory=dict)
     exact: Optional[Callable[[float], Field]] = None
+    inflow: dict = dataclasses.field(default_factory=dict)  # side (0..3) -> primitive state, for BC 3
 
     @property
     def dx(self):
@@ -338,6 +339,25 @@ def kelvin_helmholtz(n=64, t_end=1.0, cfl=0.3):
 
     return Problem("kelvin_helmholtz", n, n, -0.5, -0.5, 1.0, 1.0, (0, 0, 0, 0), f, t_end,
                    cfl=cfl, options={"limiter": 1})
+
+
+def shock_reflection(nx=120, ny=30, t_end=6.0, cfl=0.3):
+    """Shock reflection on [0,4] x [0,1] (Sec. 4.3's final example, data as
+    printed): (1, 2.9, 0, 1/1.4) everywhere except on y = 1, which carries
+    (1.69997, 2.61934, -0.50632, 1.52819); the same states flow in at the
+    left and top boundaries; solid wall at the bottom, outflow on the right.
+    The paper runs it without any limiter."""
+    A = (1.0, 2.9, 0.0, 1.0 / 1.4)
+    B = (1.69997, 2.61934, -0.50632, 1.52819)
+
+    def f(x, y):
+        m = _mod(y)
+        top = (y >= 1.0) * 1.0 if m is np else (y >= 1.0).to(y.dtype)
+        return tuple(a + (b - a) * top for a, b in zip(A, B))
+
+    p = Problem("shock_reflection", nx, ny, 0.0, 0.0, 4.0, 1.0, (3, 1, 2, 3), f, t_end, cfl=cfl,
+                options={"limiter": 0}, inflow={0: A, 3: B})
+    return p
 
 
 def ensemble(n=256, seed=4096, lo=64, ratio=8.0, steps=200):

@@ -13,6 +13,8 @@ def make_oracle(oracle, prob, opts=None, state=None):
     merged.update(opts or {})
     for k, v in merged.items():
         o.set_option(OPTS[k] if isinstance(k, str) else k, v)
+    for side, U in getattr(prob, "inflow", {}).items():
+        o.set_inflow(side, U)
     o.set_state(*(state if state is not None else W.discretise(prob)))
     return o
 

@@ -700,3 +700,68 @@ def test_seeded_riemann_problems_stay_admissible_with_both_limiters(oracle_mod):
             t += dt
             assert not o.status() & 6, seed
         assert _admissible_state(o.get_state()), seed
+
+
+# ----------------------------------------------------- Sec. 4.3 inflow, f3
+def test_inflow_boundaries_preserve_their_own_state(oracle_mod):
+    """Inflow on every side with the interior at the inflow state: the
+    state is preserved to round-off."""
+    U = (1.3, 0.7, -0.4, 0.9)
+    prob = W.Problem("inflow_const", 12, 9, 0.0, 0.0, 1.2, 0.9, (3, 3, 3, 3), lambda x, y: U, 1.0,
+                     inflow={k: U for k in range(4)})
+    o = make_oracle(oracle_mod, prob)
+    s0 = o.get_state()
+    for _ in range(5):
+        o.step(0.3 * prob.dx / o.max_speed())
+    for a, b in zip(o.get_state(), s0):
+        assert np.allclose(a, b, rtol=1e-13, atol=1e-13)
+
+
+def _regular_reflection(U, g=1.4):
+    """State behind the reflected shock of a uniform stream U = (rho, u, v,
+    p) meeting a wall y = 0 (the weak solution of the oblique-shock relations
+    that turns the flow parallel to the wall)."""
+    from scipy.optimize import brentq
+
+    r, u, v, p = U
+    q = np.hypot(u, v)
+    M = q / np.sqrt(g * p / r)
+    delta = np.arctan2(-v, u)
+
+    def f(beta):
+        return np.tan(delta) - 2 / np.tan(beta) * (M ** 2 * np.sin(beta) ** 2 - 1) / (
+            M ** 2 * (g + np.cos(2 * beta)) + 2)
+
+    betas = np.linspace(np.arcsin(1 / M) + 1e-9, np.pi / 2 - 1e-9, 2000)
+    vals = f(betas)
+    k = np.argmax(np.sign(vals[:-1]) != np.sign(vals[1:]))  # first root: the weak shock
+    beta = brentq(f, betas[k], betas[k + 1])
+    Mn = M * np.sin(beta)
+    rho3 = r * (g + 1) * Mn ** 2 / ((g - 1) * Mn ** 2 + 2)
+    p3 = p * (1 + 2 * g / (g + 1) * (Mn ** 2 - 1))
+    return rho3, p3
+
+
+@pytest.mark.slow
+def test_shock_reflection_reaches_the_regular_reflection_state(oracle_mod):
+    """Sec. 4.3's shock reflection (inflow left and top, wall at the bottom,
+    outflow right; no limiter, as in the paper) on 120 x 30 cells to t = 6:
+    the averages next to the wall behind the reflected shock take the
+    state given by the oblique-shock relations."""
+    prob = W.shock_reflection()
+    o = make_oracle(oracle_mod, prob)
+    t = 0.0
+    while t < prob.t_end - 1e-12:
+        dt = min(0.3 * prob.dx / o.max_speed(), prob.t_end - t)
+        o.step(dt)
+        t += dt
+        assert not o.status() & 6
+    avg = o.get_state()[0]
+    x = (np.arange(prob.nx) + 0.5) * prob.dx
+    y = (np.arange(prob.ny) + 0.5) * prob.dy
+    sel = (x[None, :] > 3.2) & (x[None, :] < 3.8) & (y[:, None] < 0.15)
+    rho3, p3 = _regular_reflection(prob.inflow[3])
+    rho = avg[0][sel]
+    p = 0.4 * (avg[3] - 0.5 * (avg[1] ** 2 + avg[2] ** 2) / avg[0])[sel]
+    assert abs(rho.mean() / rho3 - 1) < 5e-3, (rho.mean(), rho3)
+    assert abs(p.mean() / p3 - 1) < 5e-3, (p.mean(), p3)
