@@ -37,9 +37,11 @@ typedef struct af_ctx af_ctx;
 
 /* boundary kinds (Sec. 4.3): periodic; outflow (piecewise-constant, mirror
  * copy into ghost cells); solid wall (mirror copy with negated normal
- * velocity).  bc = xlo | xhi << 8 | ylo << 16 | yhi << 24; periodic must
+ * velocity); inflow (ghost point values hold the side's inflow state, ghost
+ * averages its conservative form; the boundary's own nodes evolve with the
+ * method, see af_set_inflow).  bc = xlo | xhi << 8 | ylo << 16 | yhi << 24; periodic must
  * be given on both sides of an axis. */
-enum { AF_BC_PERIODIC = 0, AF_BC_TRANSMISSIVE = 1, AF_BC_REFLECTING = 2 };
+enum { AF_BC_PERIODIC = 0, AF_BC_TRANSMISSIVE = 1, AF_BC_REFLECTING = 2, AF_BC_INFLOW = 3 };
 
 enum {
   AF_OK = 0,
@@ -181,6 +183,11 @@ int af_profile(af_ctx *h, double ms[4], int64_t launches[4], int reset);
 int af_conserved_totals_noalloc(const float *avg, const float *avg_lo, int nx, int ny, double dx,
                                 double dy, double *out, void *stream);
 
+/* Primitive inflow state (rho, u, v, p; rho, p > 0) of side 0..3 (xlo, xhi,
+ * ylo, yhi) for sides of kind AF_BC_INFLOW (default rho = p = 1 at rest).
+ * At a corner the y side's rule applies to the x side's value. */
+int af_set_inflow(af_ctx *h, int side, const double U[4]);
+
 /* Learned surrogate of the point-value operator (see af_mlp below): with
  * AF_OPT_SURROGATE on, every node's t^{n+1/2} and t^{n+1} values come from
  * a network (vertex_net for vertices, edge_net for both edge kinds), fed
@@ -238,6 +245,8 @@ int af_batch_set_option(af_batch *b, int k, int key, double value);
  * the instance's time to 0, its status and counters, and re-activates it. */
 int af_batch_set_state(af_batch *b, int k, const float *avg, const float *vtx, const float *xe,
                        const float *ye, void *stream);
+/* Inflow state of side `side` of instance k (as af_set_inflow). */
+int af_batch_set_inflow(af_batch *b, int k, int side, const double U[4]);
 /* Instance k's state at its current time into caller-owned device arrays. */
 int af_batch_get_state(af_batch *b, int k, float *avg, float *vtx, float *xe, float *ye,
                        void *stream);

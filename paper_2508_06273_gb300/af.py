@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libaf.so")
 _LOCK = threading.Lock()
 _LIB = None
 
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING, BC_INFLOW = 0, 1, 2, 3
 OPT = {"lin_mode": 0, "tsw": 1, "limiter": 2, "correction": 3, "force_lo": 4, "profile": 5, "surrogate": 6,
        "surr_tol": 7, "surr_abs": 8,
        "flux_limiter": 9, "shock_blend": 10}
@@ -36,7 +36,7 @@ EXPORTS = [
     "af_gemm_bf16",
     "af_mlp_create", "af_mlp_destroy", "af_mlp_set_params", "af_mlp_get_params", "af_mlp_fit_scales",
     "af_mlp_forward", "af_mlp_loss_grad", "af_mlp_train",
-    "af_set_surrogate", "af_surrogate_stats", "af_batch_set_sampler",
+    "af_set_surrogate", "af_surrogate_stats", "af_batch_set_sampler", "af_set_inflow", "af_batch_set_inflow",
 ]
 MLP_NPARAM, MLP_NTRAIN = 43480, 43408
 
@@ -102,6 +102,8 @@ def lib():
                 "af_set_surrogate": (i, [vp, vp, vp]),
                 "af_surrogate_stats": (i, [vp, C.POINTER(C.c_int64), i]),
                 "af_batch_set_sampler": (i, [vp, fp, fp, fp, i, fp, fp, fp, i, fp, C.c_uint64, d]),
+                "af_set_inflow": (i, [vp, i, C.POINTER(C.c_double)]),
+                "af_batch_set_inflow": (i, [vp, i, i, C.POINTER(C.c_double)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -132,7 +134,7 @@ class Solver:
     """One grid on one GPU (an af_ctx).  Work is enqueued on ``stream``
     (default: PyTorch's current stream at construction)."""
 
-    def __init__(self, nx, ny, dx, dy, gamma=1.4, bc=(0, 0, 0, 0), stream=None, options=None):
+    def __init__(self, nx, ny, dx, dy, gamma=1.4, bc=(0, 0, 0, 0), stream=None, options=None, inflow=None):
         import torch
 
         self.torch = torch
@@ -146,6 +148,13 @@ class Solver:
         _check(self.L.af_set_stream(self.h, C.c_void_p(self.stream.cuda_stream)))
         for k, v in (options or {}).items():
             self.set_option(k, v)
+        for side, U in (inflow or {}).items():
+            self.set_inflow(side, U)
+
+    def set_inflow(self, side, U):
+        """Primitive inflow state of side 0..3 (xlo, xhi, ylo, yhi)."""
+        u = (C.c_double * 4)(*[float(x) for x in U])
+        _check(self.L.af_set_inflow(self.h, int(side), u))
 
     def close(self):
         if getattr(self, "h", None):
@@ -300,6 +309,10 @@ class Batch:
         """Option of instance k (all instances if k = -1)."""
         _check(self.L.af_batch_set_option(self.h, int(k), OPT[key] if isinstance(key, str) else key,
                                           float(value)))
+
+    def set_inflow(self, k, side, U):
+        u = (C.c_double * 4)(*[float(x) for x in U])
+        _check(self.L.af_batch_set_inflow(self.h, int(k), int(side), u))
 
     def set_state(self, k, avg, vtx, xe, ye):
         ts = []

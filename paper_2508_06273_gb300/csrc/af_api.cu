@@ -134,7 +134,7 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   int b[4];
   for (int k = 0; k < 4; k++) {
     b[k] = (int)((bc >> (8 * k)) & 0xffu);
-    if (b[k] > AF_BC_REFLECTING) {
+    if (b[k] > AF_BC_INFLOW) {
       fail(AF_ERR_ARG, "af_create: unknown boundary kind%s");
       return nullptr;
     }
@@ -169,6 +169,10 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   g.idx = (float)(1.0 / dx);
   g.idy = (float)(1.0 / dy);
   g.gamma = (float)gamma;
+  for (int k = 0; k < 4; k++) {  // until set: rho = p = 1 at rest
+    g.inflow[k][0] = g.inflow[k][3] = 1.0f;
+    g.inflow[k][1] = g.inflow[k][2] = 0.0f;
+  }
   h->dx = dx;
   h->dy = dy;
   cudaGetDevice(&h->device);
@@ -704,6 +708,21 @@ int af_profile(af_ctx *h, double ms[4], int64_t launches[4], int reset) {
       h->launches[k] = 0;
     }
   }
+  return AF_OK;
+}
+
+int af_set_inflow(af_ctx *h, int side, const double U[4]) {
+  if (!h || side < 0 || side > 3 || !U) return fail(AF_ERR_ARG, "af_set_inflow: bad arguments%s");
+  if (!(U[0] > 0.0) || !(U[3] > 0.0) || !std::isfinite(U[1]) || !std::isfinite(U[2]))
+    return fail(AF_ERR_ARG, "af_set_inflow: the state must have rho, p > 0%s");
+  DeviceGuard dg(h->device);
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  for (int v = 0; v < NV; v++) h->g.inflow[side][v] = (float)U[v];
+  for (int p = 0; p < 2; p++)  // captured steps hold the old grid description
+    if (h->run_exec[p]) {
+      cudaGraphExecDestroy(h->run_exec[p]);
+      h->run_exec[p] = nullptr;
+    }
   return AF_OK;
 }
 

@@ -391,6 +391,16 @@ int af_batch_set_option(af_batch *b, int k, int key, double value) {
   return upload_args(b);
 }
 
+int af_batch_set_inflow(af_batch *b, int k, int side, const double U[4]) {
+  if (!b || k < 0 || k >= b->n) return bfail(AF_ERR_ARG, "af_batch_set_inflow: bad instance");
+  Dev d(b->device);
+  BCK(cudaStreamSynchronize(b->stream), "batch: sync");
+  int rc = af_set_inflow(b->inst[k], side, U);
+  if (rc) return rc;
+  BCK(cudaMemcpy(b->d_grids + k, &b->inst[k]->g, sizeof(Grid), cudaMemcpyHostToDevice), "batch: grid");
+  return upload_args(b);  // the kernel arguments hold the grid description
+}
+
 int af_batch_set_state(af_batch *b, int k, const float *avg, const float *vtx, const float *xe,
                        const float *ye, void *stream) {
   if (!b || k < 0 || k >= b->n) return bfail(AF_ERR_ARG, "af_batch_set_state: bad instance");

@@ -18,7 +18,7 @@ constexpr int OX = 4;
 constexpr int OY = 2;
 
 enum NodeKind { VTX = 0, XE = 1, YE = 2 };
-enum BcKind { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTING = 2 };
+enum BcKind { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTING = 2, BC_INFLOW = 3 };
 enum StatusBits {
   ST_CFL = 1, ST_AVG_NONPOS = 2, ST_NONFINITE = 4, ST_KEPT = 8, ST_TIMEOUT = 16, ST_STOPPED = 32, ST_FLUX_LIMITED = 64
 };
@@ -33,6 +33,7 @@ struct Grid {
   int bc[4];          // xlo, xhi, ylo, yhi
   float dx, dy, idx, idy;
   float gamma;
+  float inflow[4][4];  // primitive inflow state of each side (BC_INFLOW sides)
 };
 
 __host__ __device__ __forceinline__ long long at(const Grid &g, int v, int i, int j) {

@@ -49,8 +49,12 @@ struct GhostRange {
   }
 };
 
-// ghost entry k of an array: copy from its source (flipping the normal velocity at walls)
-__device__ __forceinline__ void ghost_entry(const Grid &g, const GhostRange &R, float *p, int k) {
+// ghost entry k of array arr (0 averages hi, 1 averages lo, 2..4 node
+// arrays): copy from its source, flipping the normal velocity at walls; on
+// an inflow side the side's state (conservative for the averages, zero low
+// word).  A corner entry takes the y side's rule applied to the x side's
+// value, as two passes (x, then y) would give.
+__device__ __forceinline__ void ghost_entry(const Grid &g, const GhostRange &R, float *p, int arr, int k) {
   int i, j, r = k;
   if (r < R.nb) {
     j = -G + r / R.wext;
@@ -69,6 +73,20 @@ __device__ __forceinline__ void ghost_entry(const Grid &g, const GhostRange &R, 
   bool fx = false, fy = false;
   const int si = ghost_src(i, g.nx, R.ownx, R.nodex, g.per_x, g.bc[0], g.bc[1], fx);
   const int sj = ghost_src(j, g.ny, R.owny, R.nodey, g.per_y, g.bc[2], g.bc[3], fy);
+  const int xside = i < 0 ? 0 : (i >= R.ownx ? 1 : -1), yside = j < 0 ? 2 : (j >= R.owny ? 3 : -1);
+  const bool xin = !g.per_x && xside >= 0 && g.bc[xside] == BC_INFLOW;
+  const bool yin = !g.per_y && yside >= 0 && g.bc[yside] == BC_INFLOW;
+  if (xin || yin) {
+    float U[4];
+#pragma unroll
+    for (int v = 0; v < NV; v++) U[v] = g.inflow[yin ? yside : xside][v];
+    if (!yin && fy) U[2] = -U[2];
+    float Q[4];
+    if (arr == 0) p2c(U, 1.0f / (g.gamma - 1.0f), Q);
+#pragma unroll
+    for (int v = 0; v < NV; v++) p[at(g, v, i, j)] = arr == 0 ? Q[v] : (arr == 1 ? 0.0f : U[v]);
+    return;
+  }
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     float x = p[at(g, v, si, sj)];
@@ -81,7 +99,7 @@ __global__ void ghost_kernel(GhostArgs A) {
   const int arr = blockIdx.y;
   const GhostRange R(A.g, arr);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < R.total; k += gridDim.x * blockDim.x)
-    ghost_entry(A.g, R, A.a[arr], k);
+    ghost_entry(A.g, R, A.a[arr], arr, k);
 }
 
 // batched: blockIdx.z is the instance
@@ -92,7 +110,7 @@ __global__ void ghost_batch_kernel(GhostBatch B) {
   const GhostRange R(g, arr);
   float *p = B.arrays[(2 * inst + B.ctl[inst].cur) * 5 + arr];
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < R.total; k += gridDim.x * blockDim.x)
-    ghost_entry(g, R, p, k);
+    ghost_entry(g, R, p, arr, k);
 }
 
 // ---- Sec. 3.4 shock indicator: theta = exp(-phi1 phi2) per edge midpoint,

@@ -39,7 +39,7 @@ def solver(env, prob, opts=None, state=None):
     torch, af, _ = env
     o = dict(prob.options)
     o.update(opts or {})
-    s = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=o)
+    s = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=o, inflow=prob.inflow)
     s.set_state(*to_dev(torch, state if state is not None else W.to_f32(W.discretise(prob))))
     return s
 
