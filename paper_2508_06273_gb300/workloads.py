@@ -172,7 +172,7 @@ def to_f32(state):
 
 
 def _wrap(d, period):
-    return d - period * np.floor(d / period + 0.5)
+    return d - period * _mod(d).floor(d / period + 0.5)
 
 
 # ----------------------------------------------------------------- problems
@@ -230,8 +230,9 @@ _EX2_P = np.array([1 / 72, -6 / 35, 15 / 17, -74 / 33, 57 / 32, 174 / 31, -269 /
 
 def ex2_pressure(r):
     """p(r) of Example 2 (coefficients of r^36 down to r^12, times 1024^2)."""
-    r = np.asarray(r, dtype=np.float64)
-    s = np.zeros_like(r)
+    if _mod(r) is np:
+        r = np.asarray(r, dtype=np.float64)
+    s = 0.0 * r
     for k, c in enumerate(_EX2_P):
         s = s * r + c
     return 1024.0 ** 2 * s * r ** 12
@@ -245,17 +246,19 @@ def compact_vortex(n=32, t_end=1.0, cfl=0.3):
 
     def at(t):
         def f(x, y):
+            m = _mod(x)
             X = _wrap(x - 0.5 - uc * t, 1.0)
             Y = _wrap(y - 0.5 - vc * t, 1.0)
-            d = np.sqrt(X * X + Y * Y)
+            d = m.sqrt(X * X + Y * Y)
             r = d / R
-            inside = r < 1.0
-            safe = np.where(d > 0, d, 1.0)
-            prof = 1024.0 * (1.0 - r) ** 6 * r ** 6
-            rho = np.where(inside, rc + 0.5 * (1.0 - r * r) ** 6, rc)
-            u = np.where(inside, uc - prof * Y / safe, uc)
-            v = np.where(inside, vc + prof * X / safe, vc)
-            p = np.where(inside, pc + ex2_pressure(np.minimum(r, 1.0)) - p1, pc)
+            inside = (r < 1.0) * 1.0
+            safe = d + (d == 0) * 1.0
+            rr = m.minimum(r, 0.0 * r + 1.0)
+            prof = 1024.0 * (1.0 - rr) ** 6 * rr ** 6
+            rho = rc + inside * 0.5 * (1.0 - rr * rr) ** 6
+            u = uc - inside * prof * Y / safe
+            v = vc + inside * prof * X / safe
+            p = pc + inside * (ex2_pressure(rr) - p1)
             return rho, u, v, p
 
         return f
@@ -269,7 +272,7 @@ def gaussian_pulse(nx=32, ny=8, t_end=0.25, cfl=0.3):
     [0,1]; ``ny`` square cells in y, periodic both ways."""
 
     def f(x, y):
-        g = 1.0 + 0.5 * np.exp(-80.0 * (x - 0.5) ** 2) + 0.0 * y
+        g = 1.0 + 0.5 * _mod(x).exp(-80.0 * (x - 0.5) ** 2) + 0.0 * y
         return g, 0.0 * g, 0.0 * g, g
 
     dx = 1.0 / nx
