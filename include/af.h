@@ -83,8 +83,10 @@ enum {
                               face flux blended with the Rusanov flux of the two averages by the largest
                               weight that keeps the convex-decomposition face states of both cells
                               admissible (Hu, Adams & Shu 2013); AF_ST_FLUX_LIMITED when it acts */
-  AF_OPT_SHOCK_BLEND = 10  /* 1: Sec. 3.4 shock-indicator blend theta U^ho + (1 - theta) U^lo of the point
+  AF_OPT_SHOCK_BLEND = 10, /* 1: Sec. 3.4 shock-indicator blend theta U^ho + (1 - theta) U^lo of the point
                               values, theta = exp(-phi1 phi2), U^lo from Alg. 3's low-order chain */
+  AF_OPT_TILE_H = 11       /* point-value tile height: 4, 8 (default) or 16 rows of 32 cells; the result
+                              does not depend on it */
 };
 
 /* stages reported by af_profile */

@@ -83,12 +83,18 @@ void extents(const af_ctx *h, int which, int &ni, int &nj) {
 }
 
 int ensure_staging(af_ctx *h) {
-  size_t need = (size_t)NV * (h->g.nx + 1) * (h->g.ny + 1);
-  if (h->staging && h->staging_floats >= need) return AF_OK;
-  if (h->staging) cudaFree(h->staging);
-  h->staging = nullptr;
-  CK(cudaMalloc(&h->staging, need * sizeof(float)), "cudaMalloc(staging)");
-  h->staging_floats = need;
+  if (h->staging) return AF_OK;
+  size_t off = 0;
+  for (int w = 0; w < 4; w++) {
+    int ni, nj;
+    extents(h, w, ni, nj);
+    h->staging_off[w] = off;
+    off += ((size_t)NV * ni * nj + 63) / 64 * 64;  // 256-byte aligned areas
+  }
+  h->staging_off[4] = off;
+  CK(cudaMalloc(&h->staging, off * sizeof(float)), "cudaMalloc(staging)");
+  for (int w = 0; w < 4; w++) CK(cudaStreamCreateWithFlags(&h->xs[w], cudaStreamNonBlocking), "copy streams");
+  for (int k = 0; k < 5; k++) CK(cudaEventCreateWithFlags(&h->xev[k], cudaEventDisableTiming), "copy events");
   return AF_OK;
 }
 
@@ -209,6 +215,7 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   for (int b = 0; b < 2; b++) {
     cudaError_t te = make_tile_maps(g, h->tbuf[b].k[VTX], h->tbuf[b].k[XE], h->tbuf[b].k[YE], h->hi, 8,
                                    &h->tmaps[b]);
+    h->tile_h = 8;
     if (te != cudaSuccess) {
       cuda_fail(te, "af_create: TMA descriptors");
       cudaFree(h->base);
@@ -249,7 +256,11 @@ void af_destroy(af_ctx *h) {
   if (!h) return;
   DeviceGuard dg(h->device);
   cudaStreamSynchronize(h->stream);
-  if (h->staging) cudaFree(h->staging);
+  if (h->staging) {
+    cudaFree(h->staging);
+    for (int w = 0; w < 4; w++) cudaStreamDestroy(h->xs[w]);
+    for (int k = 0; k < 5; k++) cudaEventDestroy(h->xev[k]);
+  }
   for (int p = 0; p < 2; p++)
     if (h->run_exec[p]) cudaGraphExecDestroy(h->run_exec[p]);
   cudaFree(h->small);
@@ -309,6 +320,22 @@ int af_set_option(af_ctx *h, int key, double value) {
       }
       h->opt.shock_blend = iv != 0;
       return AF_OK;
+    case AF_OPT_TILE_H: {
+      if (iv != 4 && iv != 8 && iv != 16) return fail(AF_ERR_ARG, "tile height must be 4, 8 or 16%s");
+      if (iv == h->tile_h) return AF_OK;
+      DeviceGuard dg(h->device);
+      CK(cudaStreamSynchronize(h->stream), "sync");
+      for (int b = 0; b < 2; b++)
+        CK(make_tile_maps(h->g, h->tbuf[b].k[VTX], h->tbuf[b].k[XE], h->tbuf[b].k[YE], h->hi, iv, &h->tmaps[b]),
+           "TMA descriptors");
+      h->tile_h = iv;
+      for (int p = 0; p < 2; p++)  // captured steps hold the old launch shape
+        if (h->run_exec[p]) {
+          cudaGraphExecDestroy(h->run_exec[p]);
+          h->run_exec[p] = nullptr;
+        }
+      return AF_OK;
+    }
     case AF_OPT_SURR_ABS:
       if (!(value >= 0.0) || !std::isfinite(value)) return fail(AF_ERR_ARG, "surrogate tolerance must be >= 0%s");
       h->opt.surr_abs = (float)value;
@@ -331,6 +358,7 @@ int af_get_option(af_ctx *h, int key, double *value) {
     case AF_OPT_SURR_ABS: *value = h->opt.surr_abs; return AF_OK;
     case AF_OPT_FLUX_LIMITER: *value = h->opt.flux_limiter; return AF_OK;
     case AF_OPT_SHOCK_BLEND: *value = h->opt.shock_blend; return AF_OK;
+    case AF_OPT_TILE_H: *value = h->tile_h; return AF_OK;
     default: return fail(AF_ERR_ARG, "unknown option%s");
   }
 }
@@ -360,14 +388,26 @@ int af_set_state_host(af_ctx *h, const float *avg, const float *vtx, const float
   const float *src[4] = {avg, vtx, xe, ye};
   float *dst[4] = {h->hi, h->lev[0].k[VTX], h->lev[0].k[XE], h->lev[0].k[YE]};
   CK(cudaMemsetAsync(h->d_bad, 0, sizeof(int), s), "memset");
+  // the four copies run on their own streams once the handle's stream has
+  // reached this point; each array is checked and packed when it has arrived
+  CK(cudaEventRecord(h->xev[4], s), "event");
   for (int w = 0; w < 4; w++) {
     int ni, nj;
     extents(h, w, ni, nj);
-    CK(cudaMemcpyAsync(h->staging, src[w], sizeof(float) * NV * ni * nj, cudaMemcpyHostToDevice, s),
+    CK(cudaStreamWaitEvent(h->xs[w], h->xev[4], 0), "event");
+    CK(cudaMemcpyAsync(h->staging + h->staging_off[w], src[w], sizeof(float) * NV * ni * nj,
+                       cudaMemcpyHostToDevice, h->xs[w]),
        "af_set_state_host: H2D");
+    CK(cudaEventRecord(h->xev[w], h->xs[w]), "event");
+  }
+  for (int w = 0; w < 4; w++) {
+    int ni, nj;
+    extents(h, w, ni, nj);
+    float *stg = h->staging + h->staging_off[w];
+    CK(cudaStreamWaitEvent(s, h->xev[w], 0), "event");
     const int dup_x = h->g.per_x && (w == 1 || w == 2), dup_y = h->g.per_y && (w == 1 || w == 3);
-    if (dup_x || dup_y) CK(launch_check_dup(h->staging, ni, nj, dup_x, dup_y, h->d_bad, s), "check_dup");
-    CK(launch_pack(h->g, h->staging, dst[w], ni, nj, true, s), "pack");
+    if (dup_x || dup_y) CK(launch_check_dup(stg, ni, nj, dup_x, dup_y, h->d_bad, s), "check_dup");
+    CK(launch_pack(h->g, stg, dst[w], ni, nj, true, s), "pack");
   }
   int bad = 0;
   CK(cudaMemcpyAsync(&bad, h->d_bad, sizeof(int), cudaMemcpyDeviceToHost, s), "memcpy");
@@ -401,12 +441,16 @@ static int get_arrays(af_ctx *h, NodeSet &ns, const float *avgsrc, float *dst[4]
     if (!host) {
       CK(launch_pack(h->g, src[w], dst[w], ni, nj, false, s), "pack");
     } else {
-      CK(launch_pack(h->g, src[w], h->staging, ni, nj, false, s), "pack");
-      CK(cudaMemcpyAsync(dst[w], h->staging, sizeof(float) * NV * ni * nj, cudaMemcpyDeviceToHost, s),
-         "D2H");
-      CK(cudaStreamSynchronize(s), "sync");
+      // pack on the handle's stream, copy out on the array's own stream
+      float *stg = h->staging + h->staging_off[w];
+      CK(launch_pack(h->g, src[w], stg, ni, nj, false, s), "pack");
+      CK(cudaEventRecord(h->xev[w], s), "event");
+      CK(cudaStreamWaitEvent(h->xs[w], h->xev[w], 0), "event");
+      CK(cudaMemcpyAsync(dst[w], stg, sizeof(float) * NV * ni * nj, cudaMemcpyDeviceToHost, h->xs[w]), "D2H");
     }
   }
+  if (host)
+    for (int w = 0; w < 4; w++) CK(cudaStreamSynchronize(h->xs[w]), "sync");
   if (!host) order_before(h, user);
   return AF_OK;
 }
@@ -487,7 +531,8 @@ static int enqueue_step(af_ctx *h, double dt) {
   if (prof) cudaEventRecord(h->ev_stage[1], s);
   if (h->opt.surrogate) {
     // network at every node, then the exact operator at the nodes it rejected
-    CK(cudaMemsetAsync(h->surr_tiles, 0, sizeof(int) * h->surr_ntiles, s), "memset tiles");
+    CK(cudaMemsetAsync(h->surr_tiles, 0, sizeof(int) * h->surr_tiles_x * ((h->g.nyv + h->tile_h - 1) / h->tile_h), s),
+       "memset tiles");
     CK(launch_ubar(h->g, h->hi, h->lev[0], h->surr_ubar, s), "surrogate cell prep");
     const unsigned char *mask[3];
     for (int k = 0; k < 3; k++) {
@@ -510,17 +555,18 @@ static int enqueue_step(af_ctx *h, double dt) {
       mask[k] = A.mask;
       A.tile_flag = h->surr_tiles;
       A.tiles_x = h->surr_tiles_x;
+      A.tile_rows = h->tile_h;
       A.stats = h->surr_stats;
       A.status = h->d_status;
       CK(launch_surrogate(k, A, h->sms, s), "surrogate");
     }
     CK(launch_pointvalue_masked(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
-                                h->opt, h->d_status, h->d_counters, mask, h->surr_tiles, theta, s),
+                                h->opt, h->d_status, h->d_counters, mask, h->surr_tiles, theta, h->tile_h, s),
        "point values (fallback)");
     h->launches[AF_STAGE_POINTVALUE] += 5;
   } else {
     CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
-                         h->opt, h->d_status, h->d_counters, theta, s),
+                         h->opt, h->d_status, h->d_counters, theta, h->tile_h, s),
        "point values");
     h->launches[AF_STAGE_POINTVALUE] += 1;
   }
@@ -734,7 +780,7 @@ int af_set_surrogate(af_ctx *h, af_mlp *vertex_net, af_mlp *edge_net) {
   DeviceGuard dg(h->device);
   CK(cudaStreamSynchronize(h->stream), "sync");
   if (vertex_net && !h->surr_mask) {
-    const int tx = (h->g.nxv + 31) / 32, ty = (h->g.nyv + 7) / 8;
+    const int tx = (h->g.nxv + 31) / 32, ty = (h->g.nyv + 3) / 4;  // enough for every tile height
     const size_t mask_bytes = (3 * (size_t)h->g.plane + 255) & ~size_t(255);
     const size_t ub_bytes = sizeof(float) * NV * (size_t)h->g.plane;
     const size_t bytes = ub_bytes + mask_bytes + sizeof(int) * (size_t)tx * ty + 2 * sizeof(unsigned long long);

@@ -25,14 +25,19 @@ struct af_ctx {
   TileMaps tmaps[2];
   NodeSet tbuf[2];
   int tmap_cur;
+  int tile_h;  // point-value tile height (4, 8, 16): rows of 32 cells
   // small device buffers
   void *small;
   int *d_status, *d_bad, *d_speed_bad;
   unsigned *d_speed;
   unsigned long long *d_counters;
   double *d_partials, *d_totals;
-  float *staging;  // host-transfer staging (lazily allocated)
-  size_t staging_floats;
+  // host transfers: one staging area and one copy stream per external array
+  // (lazily created), so that the four copies of a transfer run concurrently
+  float *staging;
+  size_t staging_off[5];
+  cudaStream_t xs[4];
+  cudaEvent_t xev[5];
   bool has_state;
   // af_run: two captured steps per parity of the t^n buffer, with the dt and
   // options they were captured with

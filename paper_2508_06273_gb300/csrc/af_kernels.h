@@ -161,7 +161,7 @@ cudaError_t launch_batch_dt(BatchCtl *ctl, int n, double *hist, int hist_cap, in
 cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
                               int *status, unsigned long long *counters, const float *const theta[2],
-                              cudaStream_t s);
+                              int tile_h, cudaStream_t s);
 // Simpson fluxes and the finite-volume update of the averages (compensated
 // hi/lo); also the max wave speed of the new state into *speed (float bits)
 cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &n1,
@@ -216,8 +216,8 @@ struct SurrogateArgs {
   const __nv_bfloat16 *wb;  // network weights (row-major, packed)
   const float *params;      // FP32 parameters (biases, scales)
   unsigned char *mask;      // this kind's fallback bytes
-  int *tile_flag;           // per point-value tile (32 x 8)
-  int tiles_x;
+  int *tile_flag;           // per point-value tile (32 x tile_rows)
+  int tiles_x, tile_rows;
   unsigned long long *stats;  // [0] nodes from the network, [1] nodes sent to the exact operator
   int *status;
 };
@@ -229,7 +229,8 @@ cudaError_t launch_surrogate(int kind, const SurrogateArgs &A, int sms, cudaStre
 cudaError_t launch_pointvalue_masked(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                                      const NodeSet &n1, const NodeSet &n2, float dt, const Options &o, int *status,
                                      unsigned long long *counters, const unsigned char *const mask[3],
-                                     const int *tile_flag, const float *const theta[2], cudaStream_t s);
+                                     const int *tile_flag, const float *const theta[2], int tile_h,
+                                     cudaStream_t s);
 
 // record a message for af_last_error on this host thread; returns code
 int set_error(int code, const char *msg);

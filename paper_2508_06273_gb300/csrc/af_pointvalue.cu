@@ -883,6 +883,11 @@ cudaError_t prepare_pointvalue() {
   cudaError_t e = cudaFuncSetAttribute(pointvalue_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Tile<8>::SMEM_BYTES);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pointvalue_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<4>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pointvalue_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Tile<16>::SMEM_BYTES);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(pointvalue_batch_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              Tile<4>::SMEM_BYTES);
   if (e == cudaSuccess)
@@ -894,36 +899,49 @@ cudaError_t prepare_pointvalue() {
   return e;
 }
 
+// tiles cover the owned nodes: up to nxv x nyv (vertex lines n + 1 on a
+// non-periodic axis); every box x coordinate is a multiple of TX floats
+static cudaError_t launch_single(const Args &A, const TileMaps &maps, int tile_h, cudaStream_t s) {
+  const Grid &g = A.g;
+  switch (tile_h) {
+    case 4:
+      pointvalue_kernel<4><<<dim3((g.nxv + TX - 1) / TX, (g.nyv + 3) / 4), dim3(TX, 4), Tile<4>::SMEM_BYTES, s>>>(
+          A, maps);
+      break;
+    case 16:
+      pointvalue_kernel<16><<<dim3((g.nxv + TX - 1) / TX, (g.nyv + 15) / 16), dim3(TX, 16), Tile<16>::SMEM_BYTES,
+                              s>>>(A, maps);
+      break;
+    default:
+      pointvalue_kernel<8><<<dim3((g.nxv + TX - 1) / TX, (g.nyv + 7) / 8), dim3(TX, 8), Tile<8>::SMEM_BYTES, s>>>(
+          A, maps);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
                               int *status, unsigned long long *counters, const float *const theta[2],
-                              cudaStream_t s) {
+                              int tile_h, cudaStream_t s) {
   Args A = pointvalue_args(g, n0, avg_hi, n1, n2, o, status, counters);
   A.dt = dt;
   A.theta[0] = theta[0];
   A.theta[1] = theta[1];
-  // tiles cover the owned nodes: up to nxv x nyv (vertex lines n + 1 on a
-  // non-periodic axis); every box x coordinate is a multiple of TX floats
-  constexpr int TY = 8;
-  dim3 grd((g.nxv + TX - 1) / TX, (g.nyv + TY - 1) / TY), blk(TX, TY);
-  pointvalue_kernel<TY><<<grd, blk, Tile<TY>::SMEM_BYTES, s>>>(A, maps);
-  return cudaGetLastError();
+  return launch_single(A, maps, tile_h, s);
 }
 
 cudaError_t launch_pointvalue_masked(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                                      const NodeSet &n1, const NodeSet &n2, float dt, const Options &o, int *status,
                                      unsigned long long *counters, const unsigned char *const mask[3],
-                                     const int *tile_flag, const float *const theta[2], cudaStream_t s) {
+                                     const int *tile_flag, const float *const theta[2], int tile_h,
+                                     cudaStream_t s) {
   Args A = pointvalue_args(g, n0, avg_hi, n1, n2, o, status, counters);
   A.dt = dt;
   A.theta[0] = theta[0];
   A.theta[1] = theta[1];
   for (int k = 0; k < 3; k++) A.mask[k] = mask[k];
   A.tile_flag = tile_flag;
-  constexpr int TY = 8;
-  dim3 grd((g.nxv + TX - 1) / TX, (g.nyv + TY - 1) / TY), blk(TX, TY);
-  pointvalue_kernel<TY><<<grd, blk, Tile<TY>::SMEM_BYTES, s>>>(A, maps);
-  return cudaGetLastError();
+  return launch_single(A, maps, tile_h, s);
 }
 
 cudaError_t launch_pointvalue_batch(const PointValueBatch &B, int ntiles, int tile_h, cudaStream_t s) {

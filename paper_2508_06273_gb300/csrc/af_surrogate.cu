@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(NG *TM, 1) surrogate_kernel(SurrogateArgs A) {
         }
       } else {
         n_fall++;
-        A.tile_flag[(j / 8) * A.tiles_x + i / 32] = 1;
+        A.tile_flag[(j / A.tile_rows) * A.tiles_x + i / 32] = 1;
       }
     }
   }

@@ -374,3 +374,16 @@ def test_fused_max_speed_matches_reduction(env):
     s.set_state(*s.get_state())  # invalidates the cached value: reduction kernel
     again = s.max_speed()
     assert abs(fused - again) <= 1e-6 * again
+
+
+@pytest.mark.parametrize("tile_h", [4, 16])
+def test_tile_height_does_not_change_the_result(env, tile_h):
+    torch, af, _ = env
+    prob = W.double_rarefaction(40, p=0.1)
+    a, b = solver(env, prob), solver(env, prob, {"tile_h": tile_h})
+    for _ in range(3):
+        dt = 0.3 * prob.dx / a.max_speed()
+        a.step(dt)
+        b.step(dt)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert torch.equal(x, y)
