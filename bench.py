@@ -202,6 +202,43 @@ class OracleWindow:
                 f"{self.threads} OpenMP threads")
 
 
+def accuracy_leg(torch, af, W, n, steps=4, window=128):
+    """Relative L1 of the GPU state of the bench workload against the FP64
+    oracle on a window around the vortex (same initial FP32 data, same fixed
+    dt), over the window's interior that the window's outflow edges cannot
+    reach in ``steps`` steps; and the L1 error of rho against the exact
+    vortex there."""
+    import numpy as np
+
+    prob = workload(n)
+    s = af.Solver(n, n, prob.dx, prob.dy, prob.gamma, prob.bc)
+    s.set_state(*W.discretise_torch(prob, "cuda"))
+    win = OracleWindow(n, window)
+    dt = prob.cfl * prob.dx / s.max_speed()
+    for _ in range(steps):
+        s.step(dt)
+        win.o.step(dt)
+    sub = win.sub
+    i0, j0 = int(round((sub.x0 - prob.x0) / prob.dx)), int(round((sub.y0 - prob.y0) / prob.dy))
+    m = 2 * steps + 2
+    gpu = [a.double().cpu().numpy() for a in s.get_state()]
+    s.close()
+    ora = win.o.get_state()
+    worst = 0.0
+    for a, b in zip(gpu, ora):
+        ga = a[:, j0 + m:j0 + window - m, i0 + m:i0 + window - m]
+        ob = b[:, m:window - m, m:window - m]
+        for v in range(4):
+            scale = np.abs(ob[v]).sum() if v in (0, 3) else (np.abs(ob[1]) + np.abs(ob[2]) + 1.0).sum()
+            worst = max(worst, float(np.abs(ga[v] - ob[v]).sum() / scale))
+    ex = W.discretise(sub, sub.exact(steps * dt))[0][0][m:window - m, m:window - m]
+    rho = gpu[0][0][j0 + m:j0 + window - m, i0 + m:i0 + window - m]
+    return {"rel_l1_vs_oracle": worst, "l1_rho_vs_exact": float(np.abs(rho - ex).mean()),
+            "l1_rho_oracle_vs_exact": float(np.abs(ora[0][0][m:window - m, m:window - m] - ex).mean()),
+            "sample": f"{steps} steps of fixed dt on the {n}^2 grid; a {window}^2-cell window around the vortex "
+                      f"in the oracle; compared on its {window - 2 * m}^2 interior; all arrays, worst variable"}
+
+
 def cpu_sample(n, min_seconds=10.0, window=128, max_steps=200):
     """(cell updates/s, threads, description, seconds) of the oracle window."""
     w = OracleWindow(n, window)
@@ -361,6 +398,8 @@ def run_ours(args):
         "clocks": clk,
         "e2e": e2e,
     }
+    if world == 1 and not args.no_cpu:
+        line["accuracy"] = accuracy_leg(torch, af, W, n)
     if world == 1 and args.batch_steps > 0:
         line["batch"] = run_batch_leg(args, torch, af, W)
     if world == 1 and args.surr_steps > 0:
