@@ -393,6 +393,14 @@ def run_ours(args):
                           "traffic": measured_traffic(FLUX_TRAFFIC, cells), "traffic_unit": "B per launch",
                           "traffic_source": FLUX_TRAFFIC["profile"],
                           "bytes_per_cell": FLUX_BYTES_PER_CELL, "ms_per_launch": flux_ms},
+        "roofline_step": {
+            "note": "whole step: point-value flops by the hand count, flux arithmetic not counted; DRAM bytes "
+                    "of both kernels from their captures (the split design; 160 B would be a fused ideal)",
+            "tflops": PV_FLOP_PER_CELL * cells / (max_s / args.steps) / 1e12,
+            "frac_fp32": PV_FLOP_PER_CELL * cells / (max_s / args.steps) / 1e12 / peak,
+            "bytes_per_cell": PV_TRAFFIC["bytes_per_cell"] + FLUX_TRAFFIC["bytes_per_cell"],
+            "gbs": (PV_TRAFFIC["bytes_per_cell"] + FLUX_TRAFFIC["bytes_per_cell"]) * cells / (max_s / args.steps) / 1e9,
+        },
         "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "gpu_launches": int(sum(launches.values())),
         "clocks": clk,
