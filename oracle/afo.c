@@ -95,7 +95,10 @@ static void flux(const double U[4], double g, int dir, double F[4]) {
   F[2] = Q[2] * un + (dir == 1 ? U[3] : 0.0);
   F[3] = un * (Q[3] + U[3]);
 }
-static int admissible(const double U[4]) { return U[0] > 0.0 && U[3] > 0.0; }
+/* Alg. 3's test: positive density and pressure, every component finite */
+static int admissible(const double U[4]) {
+  return U[0] > 0.0 && U[3] > 0.0 && isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]);
+}
 static int finite4(const double U[4]) {
   return isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]);
 }
@@ -591,10 +594,12 @@ static void eg_node(afo_ctx *c, int kind, int i, int j, int op, const double ul[
 
 /* Alg. 3: keep the high-order value if it is admissible, else EG1 on pc data
  * with the averaged linearisation, else Lax-Friedrichs; if even that fails in
- * floating point, keep the node's t^n value */
-static void limit_node(afo_ctx *c, int kind, int i, int j, double tau, const double ho[4],
+ * floating point, keep the node's t^n value.  A high-order value whose Mach
+ * cone left the node's block of cells (inb = 0) counts as not admissible: the
+ * operator assumes the CFL bound of its linearisation state. */
+static void limit_node(afo_ctx *c, int kind, int i, int j, double tau, const double ho[4], int inb,
                        double out[4], nstat *st, int force_lo) {
-  int go_lo = force_lo == 1 || (c->limiter && !admissible(ho));
+  int go_lo = force_lo == 1 || (c->limiter && !(inb && admissible(ho)));
   if (force_lo != 2 && !go_lo) {
     for (int v = 0; v < NV; v++) out[v] = ho[v];
     return;
@@ -914,17 +919,18 @@ static void point_values(afo_ctx *c, int level, double dt) {
           get4(c, c->nd[1][kind], i, j, ul);
           if (c->tsw && tsw_node(c, kind, i, j)) lin_avg(c, kind, i, j, ul);
         }
-        if (!in_block(c, kind, ul, tau, c->gam)) st.cfl++;
+        const int inb = in_block(c, kind, ul, tau, c->gam);
+        if (!inb) st.cfl++;
         eg_node(c, kind, i, j, 0, ul, tau, ho);
         for (int v = 0; v < NV; v++) ho[v] += 0.5 * tau * tau * T[v];
-        limit_node(c, kind, i, j, tau, ho, out, &st, c->force_lo);
+        limit_node(c, kind, i, j, tau, ho, inb, out, &st, c->force_lo);
         if (c->shock_blend) {
           const double th = shock_theta(c, kind, i, j);
           if (1.0 - th >= SB_EPS) {
             /* the low-order value: Alg. 3's chain (EG1 on pc data, else
                Lax-Friedrichs, else the t^n value), admissible like out */
             double lo[4];
-            limit_node(c, kind, i, j, tau, ho, lo, &st, c->force_lo == 2 ? 2 : 1);
+            limit_node(c, kind, i, j, tau, ho, inb, lo, &st, c->force_lo == 2 ? 2 : 1);
             for (int v = 0; v < NV; v++) out[v] = th * out[v] + (1.0 - th) * lo[v];
           }
         }
