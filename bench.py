@@ -33,10 +33,12 @@ UNIT = "cell updates/s"
 SEED = 2508
 # FP32 operations of the point-value stage per cell update, counted from the
 # kernel source (add, sub, mul = 1, fma = 2; sqrt, div and transcendental
-# calls not counted): one vertex (4 arcs) and two edge midpoints (2 arcs each)
-# at two time levels, 449 per arc and 103 per operator evaluation, plus the
-# correction term, linearisation state and the fused cell prep; see the design doc.
-PV_FLOP_PER_CELL = 8600
+# calls not counted), for subsonic nodes (both grid lines cross the Mach
+# circle): one vertex (4 cells' circle coefficients, two half-circle tables
+# and one arc table, sums by inclusion-exclusion: 1529) and two edge
+# midpoints (2 cells, one half-circle table: 670 each) at two time levels,
+# plus the correction term, linearisation state and the fused cell prep (809).
+PV_FLOP_PER_CELL = 6550
 # algorithmic HBM bytes of the flux/update kernel per cell: 3 levels x 3 node
 # arrays read (144 B), averages hi/lo read and written (64 B)
 FLUX_BYTES_PER_CELL = 208
@@ -336,7 +338,9 @@ def run_ours(args):
     e2e = None
     if pinned is not None:
         h2d = sum(p.numel() * 4 for p in pinned)
-        outs = [np.empty(p.shape, dtype=np.float32) for p in pinned]
+        # results land in pinned host buffers too (a pageable destination
+        # would go through the driver's bounce buffers)
+        outs = [torch.empty(p.shape, dtype=torch.float32, pin_memory=True).numpy() for p in pinned]
         host_in = [p.numpy() for p in pinned]
         s.set_state(*host_in)
         one_step()

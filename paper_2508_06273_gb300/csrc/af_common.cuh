@@ -54,7 +54,10 @@ __device__ __forceinline__ void c2p(const float Q[4], float gm1, float U[4]) {
   U[2] = Q[2] * ir;
   U[3] = gm1 * (Q[3] - 0.5f * (Q[1] * Q[1] + Q[2] * Q[2]) * ir);
 }
-__device__ __forceinline__ bool admissible(const float U[4]) { return U[0] > 0.0f && U[3] > 0.0f; }
+// Alg. 3's test: positive density and pressure, every component finite
+__device__ __forceinline__ bool admissible(const float U[4]) {
+  return U[0] > 0.0f && U[3] > 0.0f && isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]);
+}
 
 // max(|u|, |v|) + c of a primitive state, c^2 = gamma p / rho; sets bad if
 // the state is not admissible.  It feeds the CFL time step only, so the

@@ -25,6 +25,8 @@
 // for J_mn = int cos^m sin^n dtheta.  All data are taken relative to the
 // node's own t^n value, which the operators reproduce exactly, so FP32 keeps
 // its relative accuracy in the perturbations.
+#include <type_traits>
+
 #include "af_common.cuh"
 #include "af_kernels.h"
 
@@ -308,6 +310,101 @@ __device__ __forceinline__ float eval_at(const float *rec, float K, float x0, fl
   return fmaf(fmaf(e2, y0, e1), y0, e0);
 }
 
+// ---- EG2 arc sums by inclusion-exclusion
+// In the frame reflected so that u', v' >= 0 (cos -> fx cos, sin -> fy sin),
+// the grid lines through the node split the circle into the sides
+// X = {cos > a} (a = |u'|/c') and Y = {sin > b} (b = |v'|/c'): X is the arc
+// (-acos a, acos a), Y the arc (asin b, pi - asin b), and X and Y meet in the
+// single arc (asin b, acos a) when a^2 + b^2 < 1, else not at all.  With b_q
+// the circle coefficients of the cell on side q (++, +-, -+, --), the sum
+// over the cells' arcs of int b_q w is
+//   int_circle b_-- w + int_X (b_+- - b_--) w + int_Y (b_-+ - b_--) w
+//   + int_(X and Y) (b_++ - b_+- - b_-+ + b_--) w,
+// exactly (inclusion-exclusion of the four quadrants).  Over the whole circle
+// only even powers of both cos and sin integrate to non-zero values; over X
+// (symmetric about 0) only even powers of sin, over Y (symmetric about
+// pi/2) only even powers of cos.  An edge-midpoint node (one grid line) keeps
+// the first two terms (XE) or the first and third (YE).
+
+// H[m][n] = int_{-al}^{al} cos^m sin^n for n even (al = acos a, s = sin al):
+// twice the integrals from 0, by the recurrences of jtable with the start
+// point (1, 0); the entries m <= 4, n <= 4, m + n <= 6 the moments use
+__device__ __forceinline__ void half_table(float a, float s, float al, float H[5][5]) {
+  const float s2 = s * s, s3 = s2 * s, a2 = a * a, a3 = a2 * a;
+  const float as = a * s, as3 = a * s3;
+  const float I20 = 0.5f * (as + al), I02 = 0.5f * (al - as), I12 = s3 * (1.0f / 3.0f);
+  const float I22 = 0.25f * (as3 + I02), I04 = 0.25f * (3.0f * I02 - as3);
+  H[0][0] = 2.0f * al;
+  H[1][0] = 2.0f * s;
+  H[2][0] = 2.0f * I20;
+  H[3][0] = (2.0f / 3.0f) * (a2 * s + 2.0f * s);
+  H[4][0] = 0.5f * (a3 * s + 3.0f * I20);
+  H[0][2] = 2.0f * I02;
+  H[1][2] = 2.0f * I12;
+  H[2][2] = 2.0f * I22;
+  H[3][2] = 0.4f * (a2 * s3 + 2.0f * I12);
+  H[4][2] = (1.0f / 3.0f) * (a3 * s3 + 3.0f * I22);
+  H[0][4] = 2.0f * I04;
+  H[1][4] = 0.4f * (3.0f * I12 - a2 * s3);
+  H[2][4] = (1.0f / 3.0f) * (as3 * s2 + I04);
+}
+
+// int over the whole circle of cos^m sin^n for the (m, n) the moments use
+// (zero unless m and n are even)
+__host__ __device__ constexpr float jfull(int m, int n) {
+  return ((m & 1) || (n & 1)) ? 0.0f
+         : (m == 0 && n == 0) ? 2.0f * PI_F
+         : (m + n == 2) ? PI_F
+         : (m == 2 && n == 2) ? 0.25f * PI_F
+         : (m + n == 4) ? 0.75f * PI_F
+         : (m + n == 6 && m != 0 && n != 0) ? 0.125f * PI_F
+         : 0.0f;
+}
+
+// table kinds: full arc table, X-side table H (odd n vanish), Y-side table
+// (odd m vanish; stored transposed, H[n][m]), whole circle (constants)
+enum { TB_ARC = 0, TB_X = 1, TB_Y = 2, TB_CIRCLE = 3 };
+
+// acc + sum_{i,e <= 2} b[i][e] T(i + DI, e + DE), skipping the entries the
+// table's symmetry makes zero
+template <int DI, int DE, int KIND>
+__device__ __forceinline__ float contract(const float b[3][3], const float T[5][5], float acc) {
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+      const int m = i + DI, n = e + DE;
+      if (KIND == TB_X && (n & 1)) continue;
+      if (KIND == TB_Y && (m & 1)) continue;
+      if (KIND == TB_CIRCLE && ((m | n) & 1)) continue;
+      const float t = KIND == TB_CIRCLE ? jfull(m, n) : (KIND == TB_Y ? T[n][m] : T[m][n]);
+      acc = fmaf(b[i][e], t, acc);
+    }
+  return acc;
+}
+
+// the EG2 moments of one variable against one table: p (VAR 0): int p,
+// int p cos, int p sin; u (1): int u cos, int u cos^2, int u, int u sin cos;
+// v (2): int v sin, int v sin^2, int v, int v sin cos
+template <int VAR, int KIND>
+__device__ __forceinline__ void moments(const float b[3][3], const float T[5][5], float acc[4]) {
+  if (VAR == 0) {
+    acc[0] = contract<0, 0, KIND>(b, T, acc[0]);
+    acc[1] = contract<1, 0, KIND>(b, T, acc[1]);
+    acc[2] = contract<0, 1, KIND>(b, T, acc[2]);
+  } else if (VAR == 1) {
+    acc[0] = contract<1, 0, KIND>(b, T, acc[0]);
+    acc[1] = contract<2, 0, KIND>(b, T, acc[1]);
+    acc[2] = contract<0, 0, KIND>(b, T, acc[2]);
+    acc[3] = contract<1, 1, KIND>(b, T, acc[3]);
+  } else {
+    acc[0] = contract<0, 1, KIND>(b, T, acc[0]);
+    acc[1] = contract<0, 2, KIND>(b, T, acc[1]);
+    acc[2] = contract<0, 0, KIND>(b, T, acc[2]);
+    acc[3] = contract<1, 1, KIND>(b, T, acc[3]);
+  }
+}
+
 // tile-local cell indices of the cells around node (K, i, j)
 template <int K>
 __device__ __forceinline__ void arc_cell(int li, int lj, int right, int top, int &a, int &b) {
@@ -322,82 +419,129 @@ __device__ __forceinline__ void node_in_cell(int right, int top, float &xn, floa
 }
 
 // EG2 of the cpq reconstruction at node (K, li, lj) of the tile, linearised
-// about ul, relative to the reference state Kr
+// about ul, relative to the reference state Kr.  Returns false if the Mach
+// cone base leaves the node's block of cells (the CFL bound of the
+// linearisation state fails; the value is then not an EG2 value).
 template <int K>
-__device__ __forceinline__ void eg2(const Grid &g, const float *sm, int li, int lj, const float Kr[4],
-                                    const float ul[4], float tau, float out[4], bool &cfl_bad) {
+__device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int lj, const float Kr[4],
+                                    const float ul[4], float tau, float out[4]) {
   if (!(ul[0] > 0.0f && ul[3] > 0.0f && tau > 0.0f)) {
 #pragma unroll
     for (int v = 0; v < NV; v++) out[v] = __int_as_float(0x7fc00000);
-    return;
+    return true;
   }
   const float cp = sqrtf(g.gamma * ul[3] / ul[0]);
   const float R = cp * tau, icp = 1.0f / cp;
   const float am = ul[1] * icp, bm = ul[2] * icp;
+  bool inside;
   {
     const float ex = fabsf(ul[1]) * tau + R, ey = fabsf(ul[2]) * tau + R;
     const float lx = (K == YE) ? 0.5f * g.dx : g.dx, ly = (K == XE) ? 0.5f * g.dy : g.dy;
-    if (ex > lx || ey > ly) cfl_bad = true;
+    inside = !(ex > lx || ey > ly);
   }
   const float rx = R * g.idx, ry = R * g.idy, rx2 = rx * rx, ry2 = ry * ry;
   const float sx = ul[1] * tau * g.idx, sy = ul[2] * tau * g.idy;
 
-  float t[4], c[4], s[4], al, be;
-  const int ncross = crossings<K>(am, bm, t, c, s, al, be);
-  const int narcs = ncross > 0 ? ncross : 1;
+  // reflection signs (u', v' >= 0 in the reflected frame) and the sides met
+  const float fx = (K != YE && ul[1] < 0.0f) ? -1.0f : 1.0f, fy = (K != XE && ul[2] < 0.0f) ? -1.0f : 1.0f;
+  const float ax = fabsf(am), by = fabsf(bm);
+  const bool hx = K != YE && ax < 1.0f, hy = K != XE && by < 1.0f;
+  const bool hq = K == VTX && hx && hy && fmaf(ax, ax, by * by) < 1.0f;
+  float Tx[5][5], Ty[5][5], Jq[5][5];
+  float alx = 0.0f, snx = 0.0f, aly = 0.0f, sny = 0.0f;
+  if (hx) {
+    alx = acosf(ax);
+    snx = sqrtf(fmaxf(0.0f, fmaf(-ax, ax, 1.0f)));
+    half_table(ax, snx, alx, Tx);
+  }
+  if (hy) {
+    aly = acosf(by);
+    sny = sqrtf(fmaxf(0.0f, fmaf(-by, by, 1.0f)));
+    half_table(by, sny, aly, Ty);
+  }
+  // X and Y meet in (asin b, acos a): (cos, sin) = (sin aly, b) to (a, sin alx)
+  if (hq) jtable(0.5f * PI_F - aly, sny, by, alx, ax, snx, Jq);
+  const float frx = fx * rx, fry = fy * ry;
 
-  float p0 = 0, pc = 0, ps = 0, uc = 0, u2 = 0, u0 = 0, usc = 0, vs = 0, v2 = 0, v0 = 0, vsc = 0;
-#pragma unroll 1
-  for (int k = 0; k < narcs; k++) {
-    float t0, c0, s0, t1, c1, s1;
-    int right, top;
-    arc<K>(k, ncross, am, bm, al, be, t, c, s, t0, c0, s0, t1, c1, s1, right, top);
+  // circle coefficients of variable (record offset off, reference Kv) of
+  // the cell on side (px, py) (1: the + side) of the reflected frame
+  auto side = [&](int px, int py, int off, float Kv, float q[3][3]) {
+    const int right = px ? (fx > 0.0f) : (fx < 0.0f), top = py ? (fy > 0.0f) : (fy < 0.0f);
     int a, b;
     arc_cell<K>(li, lj, right, top, a, b);
-    const float *rec = cell_rec(sm, a, b);
     float xn, yn;
     node_in_cell<K>(right, top, xn, yn);
-    const float x0 = xn - sx, y0 = yn - sy;
-    float J[5][5];
-    jtable(t0, c0, s0, t1, c1, s1, J);
-    float q[3][3];
-    // pressure: int p, int p cos, int p sin
-    circle_coef(rec + 36, Kr[3], x0, y0, rx, rx2, ry, ry2, q);
+    circle_coef(cell_rec(sm, a, b) + off, Kv, xn - sx, yn - sy, frx, rx2, fry, ry2, q);
+  };
+  // all moments of one variable: b_-- over the circle, then the differences
+  // over X, Y and their intersection
+  auto var_moments = [&](auto var_tag, int off, float Kv, float acc[4]) {
+    constexpr int VAR = decltype(var_tag)::value;
+    float b0[3][3], S[3][3], d[3][3];
+    side(0, 0, off, Kv, b0);
+    moments<VAR, TB_CIRCLE>(b0, Tx, acc);
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-      for (int e = 0; e < 3; e++) {
-        p0 = fmaf(q[i][e], J[i][e], p0);
-        pc = fmaf(q[i][e], J[i + 1][e], pc);
-        ps = fmaf(q[i][e], J[i][e + 1], ps);
-      }
-    // x-velocity: int u cos, int u cos^2, int u, int u sin cos
-    circle_coef(rec + 12, Kr[1], x0, y0, rx, rx2, ry, ry2, q);
+      for (int e = 0; e < 3; e++) S[i][e] = b0[i][e];
+    if (hx) {
+      side(1, 0, off, Kv, d);
 #pragma unroll
-    for (int i = 0; i < 3; i++)
+      for (int i = 0; i < 3; i++)
 #pragma unroll
-      for (int e = 0; e < 3; e++) {
-        uc = fmaf(q[i][e], J[i + 1][e], uc);
-        u2 = fmaf(q[i][e], J[i + 2][e], u2);
-        u0 = fmaf(q[i][e], J[i][e], u0);
-        usc = fmaf(q[i][e], J[i + 1][e + 1], usc);
-      }
-    // y-velocity: int v sin, int v sin^2, int v, int v sin cos
-    circle_coef(rec + 24, Kr[2], x0, y0, rx, rx2, ry, ry2, q);
+        for (int e = 0; e < 3; e++) {
+          S[i][e] -= d[i][e];
+          d[i][e] -= b0[i][e];
+        }
+      moments<VAR, TB_X>(d, Tx, acc);
+    }
+    if (hy) {
+      side(0, 1, off, Kv, d);
 #pragma unroll
-    for (int i = 0; i < 3; i++)
+      for (int i = 0; i < 3; i++)
 #pragma unroll
-      for (int e = 0; e < 3; e++) {
-        vs = fmaf(q[i][e], J[i][e + 1], vs);
-        v2 = fmaf(q[i][e], J[i][e + 2], v2);
-        v0 = fmaf(q[i][e], J[i][e], v0);
-        vsc = fmaf(q[i][e], J[i + 1][e + 1], vsc);
-      }
-  }
-  // rho and p at P' (any cell whose closure holds P'; the data are continuous)
+        for (int e = 0; e < 3; e++) {
+          S[i][e] -= d[i][e];
+          d[i][e] -= b0[i][e];
+        }
+      moments<VAR, TB_Y>(d, Ty, acc);
+    }
+    if (hq) {
+      side(1, 1, off, Kv, d);
+#pragma unroll
+      for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int e = 0; e < 3; e++) d[i][e] += S[i][e];
+      moments<VAR, TB_ARC>(d, Jq, acc);
+    }
+  };
+  // the moments enter the result as soon as each variable is done (moments
+  // odd in cos change sign with fx, odd in sin with fy, back in the grid frame)
+  const float rp = ul[0], rc = rp * cp, irc = 1.0f / rc, icp2 = icp * icp, rpi = rp * icp;
+  float o[4], M[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  var_moments(std::integral_constant<int, 0>(), 36, Kr[3], M);  // p0, pc, ps
+  o[0] = M[0] * icp2;
+  o[1] = -fx * M[1] * irc;
+  o[2] = -fy * M[2] * irc;
+  o[3] = M[0];
+  M[0] = M[1] = M[2] = M[3] = 0.0f;
+  var_moments(std::integral_constant<int, 1>(), 12, Kr[1], M);  // uc, u2, u0, usc
+  const float uc = fx * M[0];
+  o[0] = fmaf(-rpi, uc, o[0]);
+  o[3] = fmaf(-rc, uc, o[3]);
+  o[1] += 2.0f * M[1] - 0.5f * M[2];
+  o[2] += 2.0f * fx * fy * M[3];
+  M[0] = M[1] = M[2] = M[3] = 0.0f;
+  var_moments(std::integral_constant<int, 2>(), 24, Kr[2], M);  // vs, v2, v0, vsc
+  const float vs = fy * M[0];
+  o[0] = fmaf(-rpi, vs, o[0]);
+  o[3] = fmaf(-rc, vs, o[3]);
+  o[2] += 2.0f * M[1] - 0.5f * M[2];
+  o[1] += 2.0f * fx * fy * M[3];
+  // rho and p at P' (the cell on side --: its closure holds P')
   float drP, dpP;
   {
-    const int right = ul[1] < 0.0f, top = ul[2] < 0.0f;
+    const int right = fx < 0.0f, top = fy < 0.0f;
     int a, b;
     arc_cell<K>(li, lj, right, top, a, b);
     const float *rec = cell_rec(sm, a, b);
@@ -406,12 +550,11 @@ __device__ __forceinline__ void eg2(const Grid &g, const float *sm, int li, int 
     drP = eval_at(rec, Kr[0], xn - sx, yn - sy);
     dpP = eval_at(rec + 36, Kr[3], xn - sx, yn - sy);
   }
-  const float rp = ul[0], rc = rp * cp, irc = 1.0f / rc, icp2 = icp * icp;
-  const float div = uc + vs;
-  out[0] = Kr[0] + drP - 2.0f * dpP * icp2 + INV_PI * (p0 * icp2 - rp * icp * div);
-  out[1] = Kr[1] + INV_PI * (-pc * irc + 2.0f * u2 - 0.5f * u0 + 2.0f * vsc);
-  out[2] = Kr[2] + INV_PI * (-ps * irc + 2.0f * usc + 2.0f * v2 - 0.5f * v0);
-  out[3] = Kr[3] - dpP + INV_PI * (p0 - rc * div);
+  out[0] = Kr[0] + drP - 2.0f * dpP * icp2 + INV_PI * o[0];
+  out[1] = Kr[1] + INV_PI * o[1];
+  out[2] = Kr[2] + INV_PI * o[2];
+  out[3] = Kr[3] - dpP + INV_PI * o[3];
+  return inside;
 }
 
 // ---------------------------------------------------------------- Alg. 3 parts
@@ -650,7 +793,7 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
 #pragma unroll
     for (int v = 0; v < NV; v++) ul[v] = U0[v];
   } else if (A.lin_mode == 2) {
-    eg2<K>(g, sm, li, lj, U0, U0, 0.25f * A.dt, ul, cfl_bad);
+    cfl_bad |= !eg2<K>(g, sm, li, lj, U0, U0, 0.25f * A.dt, ul);
   } else {
     const bool wx = (K != YE) && ((i == 0 && g.bc[0] == BC_REFLECTING) || (i == g.nx && g.bc[1] == BC_REFLECTING));
     const bool wy = (K != XE) && ((j == 0 && g.bc[2] == BC_REFLECTING) || (j == g.ny && g.bc[3] == BC_REFLECTING));
@@ -693,11 +836,13 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
       }
     }
     float ho[4];
-    eg2<K>(g, sm, li, lj, U0, ul, tau, ho, cfl_bad);
+    const bool inb = eg2<K>(g, sm, li, lj, U0, ul, tau, ho);
+    cfl_bad |= !inb;
     const float ht = 0.5f * tau * tau;
 #pragma unroll
     for (int v = 0; v < NV; v++) ho[v] = fmaf(ht, T[v], ho[v]);
-    if (A.force_lo || (A.limiter && !admissible(ho))) {
+    // Alg. 3 (a value from a Mach cone outside the block counts as not admissible)
+    if (A.force_lo || (A.limiter && !(inb && admissible(ho)))) {
       limit<K>(A, sm, i, j, li, lj, tau, U0, res, cnt);
     } else {
 #pragma unroll
