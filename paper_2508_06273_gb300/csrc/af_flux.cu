@@ -92,6 +92,31 @@ __device__ __forceinline__ void time_flux(const Args &A, int kind, int i, int j,
   }
 }
 
+// both directions at a vertex from one load of its three levels
+__device__ __forceinline__ void time_flux_fg(const Args &A, int i, int j, float gm1i, float F[4], float G[4],
+                                             float &smax, bool &bad) {
+  float U[3][4];
+#pragma unroll
+  for (int l = 0; l < 3; l++)
+#pragma unroll
+    for (int v = 0; v < NV; v++) U[l][v] = __ldg(A.n[l][VTX] + at(A.g, v, i, j));
+#pragma unroll
+  for (int v = 0; v < NV; v++) F[v] = G[v] = 0.0f;
+#pragma unroll
+  for (int l = 0; l < 3; l++) {
+    float f[4], gf[4];
+    phys_flux(U[l], gm1i, 0, f);
+    phys_flux(U[l], gm1i, 1, gf);
+    const float w = l == 1 ? 4.0f : 1.0f;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      F[v] += w * f[v];
+      G[v] += w * gf[v];
+    }
+  }
+  smax = fmaxf(smax, wave_speed(U[2], A.g.gamma, bad));
+}
+
 struct FluxSmem {
   float vf[NV][TY + 1][TX + 1], vg[NV][TY + 1][TX + 1];
   float xf[NV][TY][TX + 1], yg[NV][TY + 1][TX];
@@ -261,10 +286,7 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L
   for (int k = tid; k < (TX + 1) * (TY + 1); k += TX * TY) {
     const int a = k % (TX + 1), b = k / (TX + 1), i = i0 + a, j = j0 + b;
     float F[4] = {0, 0, 0, 0}, Gf[4] = {0, 0, 0, 0};
-    if (i <= g.nx && j <= g.ny) {
-      time_flux(A, VTX, i, j, 0, true, gm1i, F, smax, sbad);
-      time_flux(A, VTX, i, j, 1, false, gm1i, Gf, smax, sbad);
-    }
+    if (i <= g.nx && j <= g.ny) time_flux_fg(A, i, j, gm1i, F, Gf, smax, sbad);
 #pragma unroll
     for (int v = 0; v < NV; v++) {
       vf[v][b][a] = F[v];
