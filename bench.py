@@ -47,14 +47,14 @@ FLUX_BYTES_PER_CELL = 208
 # read or written once per launch), valid only for the kernel sources they
 # were taken on (sha256 of the files below); otherwise reported as null
 _KSRC = "paper_2508_06273_gb300/csrc/"
-_SHARED = {_KSRC + "af_common.cuh": "280303fd94f766002f95d4ea2a76fa1e6c23d9f30d21a8d593e3f2ca6d519d0d",
-           _KSRC + "af_kernels.h": "f5074d81d0632c7334625345c097112b840b42f1b6cb25c90d1458cac734e74a"}
-PV_TRAFFIC = {"bytes_per_cell": 150.8, "profile": "profiles/pointvalue_flux_vortex2048.md",
+_SHARED = {_KSRC + "af_common.cuh": "ad367efa0749a42a00411129d4ba9b0879db4f6774a017f6d6f5cb31c8be357c",
+           _KSRC + "af_kernels.h": "848aa1977171925b6b4c3491a3eb1cbcee4367df92abde99811905255654da95"}
+PV_TRAFFIC = {"bytes_per_cell": 151.4, "profile": "profiles/pointvalue_flux_vortex2048.md",
               "sha256": dict(_SHARED, **{_KSRC + "af_pointvalue.cu":
-                                         "bf018507db41af7733f930109aa12afc08f5f69a3049391b0a064ccfd158689a"})}
-FLUX_TRAFFIC = {"bytes_per_cell": 207.2, "profile": "profiles/pointvalue_flux_vortex2048.md",
+                                         "ce7697520cc8aa9540a9f6c1bcaeb4ae0288926a1a92813f263dc170f4a6393d"})}
+FLUX_TRAFFIC = {"bytes_per_cell": 207.3, "profile": "profiles/pointvalue_flux_vortex2048.md",
                 "sha256": dict(_SHARED, **{_KSRC + "af_flux.cu":
-                                           "e157834ba88cef2a9151d0f76d70487bf6e28a2dc85b5b8fa98ecda176a911c5"})}
+                                           "be6d799d6b75165173a8e3575bfbd7931ff8c89b6db7814392ea8e0a8ca7cffb"})}
 
 
 def measured_traffic(spec, cells):
