@@ -33,12 +33,15 @@ UNIT = "cell updates/s"
 SEED = 2508
 # FP32 operations of the point-value stage per cell update, counted from the
 # kernel source (add, sub, mul = 1, fma = 2; sqrt, div and transcendental
-# calls not counted), for subsonic nodes (both grid lines cross the Mach
-# circle): one vertex (4 cells' circle coefficients, two half-circle tables
-# and one arc table, sums by inclusion-exclusion: 1529) and two edge
-# midpoints (2 cells, one half-circle table: 670 each) at two time levels,
-# plus the correction term, linearisation state and the fused cell prep (809).
-PV_FLOP_PER_CELL = 6550
+# calls not counted) for this workload's background state (u = v = 1,
+# c = 1.18: both grid lines cross every Mach circle, the node lies outside
+# it, so X and Y do not meet): a vertex (3 cells' circle coefficients, two
+# half-circle tables: 1057) and two edge midpoints (2 cells, one half-circle
+# table: 670 each) at two time levels, plus the correction term, the
+# linearisation state and the fused cell prep (809).  Vortex-core vertices,
+# whose circles also need the quarter arc, do 472 more: the count is a
+# lower bound of the work done.
+PV_FLOP_PER_CELL = 5600
 # algorithmic HBM bytes of the flux/update kernel per cell: 3 levels x 3 node
 # arrays read (144 B), averages hi/lo read and written (64 B)
 FLUX_BYTES_PER_CELL = 208
