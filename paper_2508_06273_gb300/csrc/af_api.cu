@@ -267,6 +267,7 @@ void af_destroy(af_ctx *h) {
   cudaFree(h->base);
   if (h->surr_ubar) cudaFree(h->surr_ubar);
   if (h->shock_theta) cudaFree(h->shock_theta);
+  if (h->q0) cudaFree(h->q0);
   cudaEventDestroy(h->ev_in);
   cudaEventDestroy(h->ev_out);
   for (int k = 0; k < 5; k++) cudaEventDestroy(h->ev_stage[k]);
@@ -311,7 +312,13 @@ int af_set_option(af_ctx *h, int key, double value) {
       if (!(value >= 0.0) || !std::isfinite(value)) return fail(AF_ERR_ARG, "surrogate tolerance must be >= 0%s");
       h->opt.surr_tol = (float)value;
       return AF_OK;
-    case AF_OPT_FLUX_LIMITER: h->opt.flux_limiter = iv != 0; return AF_OK;
+    case AF_OPT_FLUX_LIMITER:
+      if (iv && !h->q0) {
+        DeviceGuard dg(h->device);
+        CK(cudaMalloc(&h->q0, sizeof(float) * NV * (size_t)h->g.plane), "cudaMalloc(flux limiter snapshot)");
+      }
+      h->opt.flux_limiter = iv != 0;
+      return AF_OK;
     case AF_OPT_SHOCK_BLEND:
       if (iv && !h->shock_theta) {
         DeviceGuard dg(h->device);
@@ -574,8 +581,12 @@ static int enqueue_step(af_ctx *h, double dt) {
     cudaEventRecord(h->ev_stage[2], s);
     cudaEventRecord(h->ev_stage[3], s);
   }
+  // the limiter reads t^n averages while the kernel overwrites them: snapshot
+  if (h->opt.flux_limiter)
+    CK(cudaMemcpyAsync(h->q0, h->hi, sizeof(float) * NV * (size_t)h->g.plane, cudaMemcpyDeviceToDevice, s),
+       "flux limiter snapshot");
   CK(launch_flux_update(h->g, h->lev[0], h->lev[1], h->lev[2], h->hi, h->lo, dt / h->dx, dt / h->dy,
-                        h->d_status, h->d_speed, h->d_speed_bad, h->opt.flux_limiter, s),
+                        h->d_status, h->d_speed, h->d_speed_bad, h->opt.flux_limiter, h->q0, s),
      "flux update");
   h->speed_valid = true;
   h->launches[AF_STAGE_FLUX] += 1;

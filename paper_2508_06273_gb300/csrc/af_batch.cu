@@ -137,6 +137,7 @@ int upload_args(af_batch *b) {
       fx[2 * k + q] = flux_args(h->g, h->tbuf[q], h->lev[1], h->tbuf[q ^ 1], h->hi, h->lo, &c->status, &c->speed,
                                 &c->speed_bad);
       fx[2 * k + q].flux_limiter = h->opt.flux_limiter;
+      if (h->opt.flux_limiter) fx[2 * k + q].q0 = h->q0;
       if (h->opt.flux_limiter) any_lim = true;
       float **a = &arrays[(2 * k + q) * 5];
       a[0] = h->hi;
@@ -223,6 +224,7 @@ int enqueue_batch_step(af_batch *b, double *hist, int hist_steps, cudaStream_t s
   F.tiles = b->d_fx_tiles;
   F.ctl = b->d_ctl;
   F.args = b->d_fx;
+  if (b->any_limiter) BCK(launch_snapshot_batch(F, b->n, s), "batch: flux limiter snapshot");
   BCK(launch_flux_batch(F, b->n_fx_tiles, b->any_limiter, s), "batch: flux update");
   return AF_OK;
 }

@@ -54,6 +54,7 @@ struct af_ctx {
   long long launches[4];
   // learned surrogate: networks (vertex, edge; owned by the caller), fallback
   // bytes per node kind, flags per point-value tile, node counts
+  float *q0;           // t^n averages for the flux limiter (when it is on)
   float *shock_theta;  // Sec. 3.4 weights: x-edge plane, then y-edge plane (when the blend is on)
   struct af_mlp *surr[2];
   unsigned char *surr_mask;

@@ -219,7 +219,7 @@ __device__ __noinline__ void limit_tile(const Args &A, FluxSmem &S, LimSmem &L, 
     float Q[4] = {1.0f, 0.0f, 0.0f, 1.0f};  // cells beyond the ghost layers feed no face of the domain
     if (ci <= g.nx + 1 && cj <= g.ny + 1)
 #pragma unroll
-      for (int v = 0; v < NV; v++) Q[v] = A.hi[at(g, v, ci, cj)];
+      for (int v = 0; v < NV; v++) Q[v] = A.q0[at(g, v, ci, cj)];
     float U[4];
     c2p(Q, gm1, U);
     const bool ok = U[0] > 0.0f && U[3] > 0.0f;
@@ -406,6 +406,21 @@ __global__ void __launch_bounds__(TX *TY, 6) flux_batch_kernel(FluxBatch B) {
   flux_tile<false>(A, S, nullptr, t.y, t.z);
 }
 
+// instance blockIdx.y: its t^n averages (hi, all planes) into its snapshot
+// q0, if it is active and limits fluxes
+__global__ void __launch_bounds__(256) snapshot_batch_kernel(FluxBatch B) {
+  const int k = blockIdx.y;
+  const BatchCtl &c = B.ctl[k];
+  if (!c.active) return;
+  const FluxArgs &A = B.args[2 * k + c.cur];
+  if (!A.flux_limiter) return;
+  const long long n4 = (long long)NV * A.g.plane / 4;  // planes hold a multiple of 32 floats
+  const float4 *src = reinterpret_cast<const float4 *>(A.hi);
+  float4 *dst = reinterpret_cast<float4 *>(const_cast<float *>(A.q0));
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+
 __global__ void __launch_bounds__(TX *TY) flux_batch_limited_kernel(FluxBatch B) {
   __shared__ FluxSmem S;
   __shared__ LimSmem L;
@@ -440,6 +455,7 @@ FluxArgs flux_args(const Grid &g, const NodeSet &n0, const NodeSet &n1, const No
   }
   A.hi = avg_hi;
   A.lo = avg_lo;
+  A.q0 = avg_hi;
   A.lxh = A.lxl = A.lyh = A.lyl = A.lx = A.ly = 0.0f;
   A.flux_limiter = 0;
   A.status = status;
@@ -451,18 +467,28 @@ FluxArgs flux_args(const Grid &g, const NodeSet &n0, const NodeSet &n1, const No
 cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &n1,
                                const NodeSet &n2, float *avg_hi, float *avg_lo, double lamx,
                                double lamy, int *status, unsigned *speed, int *speed_bad, int flux_limiter,
-                               cudaStream_t s) {
+                               const float *q0, cudaStream_t s) {
   Args A = flux_args(g, n0, n1, n2, avg_hi, avg_lo, status, speed, speed_bad);
   split_double(lamx, A.lxh, A.lxl);
   split_double(lamy, A.lyh, A.lyl);
   A.lx = A.lxh;
   A.ly = A.lyh;
   A.flux_limiter = flux_limiter;
+  if (flux_limiter) {
+    if (!q0 || q0 == avg_hi) return cudaErrorInvalidValue;
+    A.q0 = q0;
+  }
   cudaMemsetAsync(speed, 0, sizeof(unsigned), s);
   cudaMemsetAsync(speed_bad, 0, sizeof(int), s);
   dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY), blk(TX, TY);
   if (flux_limiter) flux_limited_kernel<<<grd, blk, 0, s>>>(A);
   else flux_update_kernel<<<grd, blk, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_snapshot_batch(const FluxBatch &B, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  snapshot_batch_kernel<<<dim3(32, n), 256, 0, s>>>(B);
   return cudaGetLastError();
 }
 

@@ -81,6 +81,10 @@ struct FluxArgs {
   Grid g;
   const float *__restrict__ n[3][3];  // [level][kind]
   float *hi, *lo;
+  // t^n averages the flux limiter reads: a snapshot taken before the launch,
+  // since other blocks overwrite hi with t^{n+1} while a block limits its
+  // faces (equal to hi when the limiter is off)
+  const float *q0;
   float lxh, lxl, lyh, lyl;  // dt/dx and dt/dy as double-word FP32 (hi + lo)
   float lx, ly;              // the same in FP32 (flux limiter)
   int flux_limiter;          // cell-average flux limiter on
@@ -143,6 +147,8 @@ cudaError_t prepare_pointvalue();
 // batched point values over a tile list of tile height tile_h (4, 8 or 16)
 cudaError_t launch_pointvalue_batch(const PointValueBatch &B, int ntiles, int tile_h, cudaStream_t s);
 // batched flux / update over a tile list of 32 x 8 cells
+// t^n snapshot (hi -> q0) of every active instance with the flux limiter on
+cudaError_t launch_snapshot_batch(const FluxBatch &B, int n, cudaStream_t s);
 cudaError_t launch_flux_batch(const FluxBatch &B, int ntiles, bool any_limiter, cudaStream_t s);
 constexpr int FLUX_TX = 32, FLUX_TY = 8;
 // batched ghost fill; max_per: the largest per-instance ghost count
@@ -167,7 +173,7 @@ cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg
 cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &n1,
                                const NodeSet &n2, float *avg_hi, float *avg_lo, double lamx,
                                double lamy, int *status, unsigned *speed, int *speed_bad, int flux_limiter,
-                               cudaStream_t s);
+                               const float *q0, cudaStream_t s);
 // max over averages and owned point values of max(|u|,|v|) + c (as float bits)
 cudaError_t launch_max_speed(const Grid &g, const float *avg_hi, const NodeSet &n,
                              unsigned *out_bits, int *bad, cudaStream_t s);
