@@ -52,6 +52,7 @@ struct af_batch {
   float **d_arrays = nullptr;      // [n][2][5]
   int4 *d_pv_tiles = nullptr, *d_fx_tiles = nullptr;
   int n_pv_tiles = 0, n_fx_tiles = 0, pv_tiles_h = 0;
+  int n_fx_plain = -1;  // flux tiles of instances without the flux limiter (listed first)
   long long ghost_max = 0;
   bool maps_ok = false;
   std::vector<GraphEntry> graphs;
@@ -156,7 +157,24 @@ int upload_args(af_batch *b) {
       "batch: args");
   BCK(cudaMemcpy(b->d_theta, theta.data(), sizeof(float *) * theta.size(), cudaMemcpyHostToDevice),
       "batch: args");
-  if (any_lim != b->any_limiter || any_blend != b->any_blend) drop_graphs(b);  // captured launches differ
+  // flux tiles: instances without the flux limiter first (plain kernel), then
+  // the limiting ones (limited kernel)
+  std::vector<int4> fxt;
+  for (int pass = 0; pass < 2; pass++)
+    for (int k = 0; k < b->n; k++) {
+      const af_ctx *h = b->inst[k];
+      if ((h->opt.flux_limiter != 0) != (pass == 1)) continue;
+      for (int j0 = 0; j0 < h->g.ny; j0 += FLUX_TY)
+        for (int i0 = 0; i0 < h->g.nx; i0 += FLUX_TX) fxt.push_back(make_int4(k, i0, j0, 0));
+    }
+  int n_plain = 0;
+  for (const int4 &t : fxt) n_plain += b->inst[t.x]->opt.flux_limiter ? 0 : 1;
+  if (!b->d_fx_tiles) BCK(cudaMalloc(&b->d_fx_tiles, sizeof(int4) * fxt.size()), "batch: cudaMalloc(tiles)");
+  BCK(cudaMemcpy(b->d_fx_tiles, fxt.data(), sizeof(int4) * fxt.size(), cudaMemcpyHostToDevice), "batch: tiles");
+  b->n_fx_tiles = (int)fxt.size();
+  // captured launches differ
+  if (any_lim != b->any_limiter || any_blend != b->any_blend || n_plain != b->n_fx_plain) drop_graphs(b);
+  b->n_fx_plain = n_plain;
   b->any_limiter = any_lim;
   b->any_blend = any_blend;
   return AF_OK;
@@ -167,7 +185,7 @@ int build_tiles(af_batch *b) {
   if (b->maps_ok && b->pv_tiles_h == b->tile_h) return AF_OK;
   drop_graphs(b);
   std::vector<TileMaps> maps(2 * b->n);
-  std::vector<int4> pv, fx;
+  std::vector<int4> pv;
   for (int k = 0; k < b->n; k++) {
     af_ctx *h = b->inst[k];
     const Grid &g = h->g;
@@ -178,18 +196,11 @@ int build_tiles(af_batch *b) {
     }
     for (int j0 = 0; j0 < g.nyv; j0 += b->tile_h)
       for (int i0 = 0; i0 < g.nxv; i0 += 32) pv.push_back(make_int4(k, i0, j0, 0));
-    for (int j0 = 0; j0 < g.ny; j0 += FLUX_TY)
-      for (int i0 = 0; i0 < g.nx; i0 += FLUX_TX) fx.push_back(make_int4(k, i0, j0, 0));
   }
   if (b->d_pv_tiles) cudaFree(b->d_pv_tiles);
   b->d_pv_tiles = nullptr;
   BCK(cudaMalloc(&b->d_pv_tiles, sizeof(int4) * pv.size()), "batch: cudaMalloc(tiles)");
   BCK(cudaMemcpy(b->d_pv_tiles, pv.data(), sizeof(int4) * pv.size(), cudaMemcpyHostToDevice), "batch: tiles");
-  if (!b->d_fx_tiles) {
-    BCK(cudaMalloc(&b->d_fx_tiles, sizeof(int4) * fx.size()), "batch: cudaMalloc(tiles)");
-    BCK(cudaMemcpy(b->d_fx_tiles, fx.data(), sizeof(int4) * fx.size(), cudaMemcpyHostToDevice), "batch: tiles");
-    b->n_fx_tiles = (int)fx.size();
-  }
   BCK(cudaMemcpy(b->d_maps, maps.data(), sizeof(TileMaps) * maps.size(), cudaMemcpyHostToDevice), "batch: maps");
   b->n_pv_tiles = (int)pv.size();
   b->pv_tiles_h = b->tile_h;
@@ -225,7 +236,7 @@ int enqueue_batch_step(af_batch *b, double *hist, int hist_steps, cudaStream_t s
   F.ctl = b->d_ctl;
   F.args = b->d_fx;
   if (b->any_limiter) BCK(launch_snapshot_batch(F, b->n, s), "batch: flux limiter snapshot");
-  BCK(launch_flux_batch(F, b->n_fx_tiles, b->any_limiter, s), "batch: flux update");
+  BCK(launch_flux_batch(F, b->n_fx_plain, b->n_fx_tiles, s), "batch: flux update");
   return AF_OK;
 }
 

@@ -492,11 +492,15 @@ cudaError_t launch_snapshot_batch(const FluxBatch &B, int n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_flux_batch(const FluxBatch &B, int ntiles, bool any_limiter, cudaStream_t s) {
+cudaError_t launch_flux_batch(const FluxBatch &B, int nplain, int ntiles, cudaStream_t s) {
   static_assert(TX == FLUX_TX && TY == FLUX_TY, "tile list shape");
-  if (ntiles <= 0) return cudaSuccess;
-  if (any_limiter) flux_batch_limited_kernel<<<ntiles, dim3(TX, TY), 0, s>>>(B);
-  else flux_batch_kernel<<<ntiles, dim3(TX, TY), 0, s>>>(B);
+  if (nplain < 0 || nplain > ntiles) return cudaErrorInvalidValue;
+  if (nplain > 0) flux_batch_kernel<<<nplain, dim3(TX, TY), 0, s>>>(B);
+  if (ntiles > nplain) {
+    FluxBatch L = B;
+    L.tiles = B.tiles + nplain;
+    flux_batch_limited_kernel<<<ntiles - nplain, dim3(TX, TY), 0, s>>>(L);
+  }
   return cudaGetLastError();
 }
 

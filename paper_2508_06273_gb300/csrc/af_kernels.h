@@ -146,10 +146,12 @@ cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, floa
 cudaError_t prepare_pointvalue();
 // batched point values over a tile list of tile height tile_h (4, 8 or 16)
 cudaError_t launch_pointvalue_batch(const PointValueBatch &B, int ntiles, int tile_h, cudaStream_t s);
-// batched flux / update over a tile list of 32 x 8 cells
 // t^n snapshot (hi -> q0) of every active instance with the flux limiter on
 cudaError_t launch_snapshot_batch(const FluxBatch &B, int n, cudaStream_t s);
-cudaError_t launch_flux_batch(const FluxBatch &B, int ntiles, bool any_limiter, cudaStream_t s);
+// batched flux / update over a tile list of 32 x 8 cells: the first nplain
+// tiles (instances without the flux limiter) with the plain kernel, the rest
+// with the limited one
+cudaError_t launch_flux_batch(const FluxBatch &B, int nplain, int ntiles, cudaStream_t s);
 constexpr int FLUX_TX = 32, FLUX_TY = 8;
 // batched ghost fill; max_per: the largest per-instance ghost count
 cudaError_t launch_ghost_batch(const GhostBatch &B, int n, long long max_per, cudaStream_t s);
