@@ -97,6 +97,12 @@ SMOOTH = {
     "supersonic_xy": lambda: _flow((1.0, -1.5, 1.6, 1.0)),
     "sonic_x": lambda: _flow((1.0, 1.4 ** 0.5, 0.0, 1.0)),
     "at_rest": lambda: _flow((1.0, 0.0, 0.0, 1.0)),
+    # c = 1.18: both lines crossed, node outside the circle, u, v < 0
+    "outside_neg": lambda: _flow((1.0, -0.95, -0.9, 1.0)),
+    # only the vertical line crossed, u, v < 0
+    "supersonic_y": lambda: _flow((1.0, -0.3, -1.7, 1.0)),
+    # node inside the circle (quarter arc present), u < 0
+    "inside_neg": lambda: _flow((1.0, -0.5, 0.4, 1.0)),
 }
 MODES = {"avg": {}, "point": {"lin_mode": 1}, "alg1": {"lin_mode": 2}, "nocorr": {"correction": 0},
          "tsw": {"tsw": 1}}
