@@ -445,19 +445,23 @@ __device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int 
   // reflection signs (u', v' >= 0 in the reflected frame) and the sides met
   const float fx = (K != YE && ul[1] < 0.0f) ? -1.0f : 1.0f, fy = (K != XE && ul[2] < 0.0f) ? -1.0f : 1.0f;
   const float ax = fabsf(am), by = fabsf(bm);
-  const bool hx = K != YE && ax < 1.0f, hy = K != XE && by < 1.0f;
-  const bool hq = K == VTX && hx && hy && fmaf(ax, ax, by * by) < 1.0f;
+  // a line the circle does not cross gives a half table of zeros (al = 0,
+  // sin al = 0), so the X and Y stages run without branches
+  constexpr bool hx = K != YE, hy = K != XE;
+  const bool hq = K == VTX && ax < 1.0f && by < 1.0f && fmaf(ax, ax, by * by) < 1.0f;
   float Tx[5][5], Ty[5][5], Jq[5][5];
   float alx = 0.0f, snx = 0.0f, aly = 0.0f, sny = 0.0f;
   if (hx) {
-    alx = acosf(ax);
-    snx = sqrtf(fmaxf(0.0f, fmaf(-ax, ax, 1.0f)));
-    half_table(ax, snx, alx, Tx);
+    const float a = fminf(ax, 1.0f);
+    alx = acosf(a);
+    snx = sqrtf(fmaxf(0.0f, fmaf(-a, a, 1.0f)));
+    half_table(a, snx, alx, Tx);
   }
   if (hy) {
-    aly = acosf(by);
-    sny = sqrtf(fmaxf(0.0f, fmaf(-by, by, 1.0f)));
-    half_table(by, sny, aly, Ty);
+    const float b = fminf(by, 1.0f);
+    aly = acosf(b);
+    sny = sqrtf(fmaxf(0.0f, fmaf(-b, b, 1.0f)));
+    half_table(b, sny, aly, Ty);
   }
   // X and Y meet in (asin b, acos a): (cos, sin) = (sin aly, b) to (a, sin alx)
   if (hq) jtable(0.5f * PI_F - aly, sny, by, alx, ax, snx, Jq);
