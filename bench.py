@@ -51,13 +51,13 @@ FLUX_BYTES_PER_CELL = 208
 # were taken on (sha256 of the files below); otherwise reported as null
 _KSRC = "paper_2508_06273_gb300/csrc/"
 _SHARED = {_KSRC + "af_common.cuh": "ad367efa0749a42a00411129d4ba9b0879db4f6774a017f6d6f5cb31c8be357c",
-           _KSRC + "af_kernels.h": "848aa1977171925b6b4c3491a3eb1cbcee4367df92abde99811905255654da95"}
-PV_TRAFFIC = {"bytes_per_cell": 151.4, "profile": "profiles/pointvalue_flux_vortex2048.md",
+           _KSRC + "af_kernels.h": "55362771c9930cc6c18b944182879d2ec6126ad00a5d42986992e368199d4b7a"}
+PV_TRAFFIC = {"bytes_per_cell": 150.7, "profile": "profiles/pointvalue_flux_vortex2048.md",
               "sha256": dict(_SHARED, **{_KSRC + "af_pointvalue.cu":
-                                         "ce7697520cc8aa9540a9f6c1bcaeb4ae0288926a1a92813f263dc170f4a6393d"})}
-FLUX_TRAFFIC = {"bytes_per_cell": 207.3, "profile": "profiles/pointvalue_flux_vortex2048.md",
+                                         "67884730b09b7464b39f434e26696d807c2ff629e779f2539ce1337c4ced3900"})}
+FLUX_TRAFFIC = {"bytes_per_cell": 207.4, "profile": "profiles/pointvalue_flux_vortex2048.md",
                 "sha256": dict(_SHARED, **{_KSRC + "af_flux.cu":
-                                           "be6d799d6b75165173a8e3575bfbd7931ff8c89b6db7814392ea8e0a8ca7cffb"})}
+                                           "0a6795c5641e75f5ddeb809da2b20eac719378e73a8c240509406ffd11c0b9b9"})}
 
 
 def measured_traffic(spec, cells):
