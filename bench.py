@@ -54,7 +54,7 @@ _SHARED = {_KSRC + "af_common.cuh": "ad367efa0749a42a00411129d4ba9b0879db4f6774a
            _KSRC + "af_kernels.h": "55362771c9930cc6c18b944182879d2ec6126ad00a5d42986992e368199d4b7a"}
 PV_TRAFFIC = {"bytes_per_cell": 150.7, "profile": "profiles/pointvalue_flux_vortex2048.md",
               "sha256": dict(_SHARED, **{_KSRC + "af_pointvalue.cu":
-                                         "67884730b09b7464b39f434e26696d807c2ff629e779f2539ce1337c4ced3900"})}
+                                         "ed707f206b8c333290e8186217f07bc36cdc07d5c470470663976d7b4af2db32"})}
 FLUX_TRAFFIC = {"bytes_per_cell": 207.4, "profile": "profiles/pointvalue_flux_vortex2048.md",
                 "sha256": dict(_SHARED, **{_KSRC + "af_flux.cu":
                                            "0a6795c5641e75f5ddeb809da2b20eac719378e73a8c240509406ffd11c0b9b9"})}

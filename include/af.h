@@ -82,7 +82,9 @@ enum {
   AF_OPT_FLUX_LIMITER = 9, /* 1: cell-average flux limiter (Sec. 3.5 names one without printing it): each
                               face flux blended with the Rusanov flux of the two averages by the largest
                               weight that keeps the convex-decomposition face states of both cells
-                              admissible (Hu, Adams & Shu 2013); AF_ST_FLUX_LIMITED when it acts */
+                              admissible (Hu, Adams & Shu 2013); AF_ST_FLUX_LIMITED when it acts.
+                              Turning it on allocates a copy of the cell averages (4 planes), which
+                              the limiter reads as the t^n state while the update overwrites them */
   AF_OPT_SHOCK_BLEND = 10, /* 1: Sec. 3.4 shock-indicator blend theta U^ho + (1 - theta) U^lo of the point
                               values, theta = exp(-phi1 phi2), U^lo from Alg. 3's low-order chain */
   AF_OPT_TILE_H = 11       /* point-value tile height: 4, 8 (default) or 16 rows of 32 cells; the result

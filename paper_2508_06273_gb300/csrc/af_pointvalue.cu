@@ -22,9 +22,14 @@
 // integral is taken exactly from the arc's end points with the recurrences
 //   (m+n) J_mn = [cos^(m-1) sin^(n+1)] + (m-1) J_(m-2)n
 //   (m+n) J_mn = -[cos^(m+1) sin^(n-1)] + (n-1) J_m(n-2)
-// for J_mn = int cos^m sin^n dtheta.  All data are taken relative to the
-// node's own t^n value, which the operators reproduce exactly, so FP32 keeps
-// its relative accuracy in the perturbations.
+// for J_mn = int cos^m sin^n dtheta.  The sum over the cells' arcs is taken
+// by inclusion-exclusion (one cell's coefficients over the whole circle, plus
+// differences of coefficients over the two half-circles cut off by the grid
+// lines and over their intersection; see "EG2 arc sums by inclusion-
+// exclusion" below), which needs no crossing sort and makes half of the
+// integrals vanish by symmetry.  All data are taken relative to the node's
+// own t^n value, which the operators reproduce exactly, so FP32 keeps its
+// relative accuracy in the perturbations.
 #include <type_traits>
 
 #include "af_common.cuh"
