@@ -126,6 +126,29 @@ int af_set_state_host(af_ctx *h, const float *avg, const float *vtx, const float
 int af_get_state(af_ctx *h, float *avg, float *vtx, float *xe, float *ye, void *stream);
 /* Same into HOST memory; synchronous. */
 int af_get_state_host(af_ctx *h, float *avg, float *vtx, float *xe, float *ye);
+/* Asynchronous host transfers, for programs that move the whole state
+ * through host memory every step (the paper has no counterpart: this is
+ * plumbing).  af_set_state_host_async enqueues the four host-to-device copies
+ * (one copy stream per array) and the unpacking into the state, ordered
+ * before later work on the handle's stream, and returns at once;
+ * af_get_state_host_async enqueues the packing of the current state (after
+ * the work already on the handle's stream) and the four device-to-host
+ * copies, on streams of their own, so that a download overlaps the next
+ * upload and the step between them.  The host arrays must stay untouched
+ * (and the output arrays unread) until af_host_sync returns; with pageable
+ * memory the copies are staged by the driver and do not overlap, so pass
+ * page-locked (pinned) memory.  An upload whose periodic duplicate line
+ * differs from the first is reported by af_host_sync (AF_ERR_ARG, no state)
+ * rather than by the call.  The synchronous host calls first wait for
+ * pending asynchronous ones.  Library memory: two more staging areas the size
+ * of the state (downloads alternate between them), allocated on the first
+ * asynchronous call. */
+int af_set_state_host_async(af_ctx *h, const float *avg, const float *vtx, const float *xe,
+                            const float *ye);
+int af_get_state_host_async(af_ctx *h, float *avg, float *vtx, float *xe, float *ye);
+/* Wait for every asynchronous host transfer of the handle (and the work
+ * before it on the handle's stream). */
+int af_host_sync(af_ctx *h);
 /* FP32 low words of the cell averages [4][ny][nx] (device / host memory). */
 int af_get_avg_lo(af_ctx *h, float *avg_lo, void *stream);
 int af_set_avg_lo(af_ctx *h, const float *avg_lo, void *stream);

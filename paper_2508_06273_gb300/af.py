@@ -27,6 +27,7 @@ ST_CFL, ST_AVG_NONPOS, ST_NONFINITE, ST_KEPT, ST_TIMEOUT, ST_STOPPED, ST_FLUX_LI
 EXPORTS = [
     "af_create", "af_destroy", "af_last_error", "af_set_stream", "af_set_option",
     "af_get_option", "af_set_state", "af_set_state_host", "af_get_state", "af_get_state_host",
+    "af_set_state_host_async", "af_get_state_host_async", "af_host_sync",
     "af_get_avg_lo", "af_set_avg_lo", "af_get_half", "af_step", "af_run", "af_status",
     "af_counters", "af_conserved_totals", "af_max_speed", "af_profile",
     "af_conserved_totals_noalloc",
@@ -66,6 +67,9 @@ def lib():
                 "af_set_state_host": (i, [vp, fp, fp, fp, fp]),
                 "af_get_state": (i, [vp, fp, fp, fp, fp, vp]),
                 "af_get_state_host": (i, [vp, fp, fp, fp, fp]),
+                "af_set_state_host_async": (i, [vp, fp, fp, fp, fp]),
+                "af_get_state_host_async": (i, [vp, fp, fp, fp, fp]),
+                "af_host_sync": (i, [vp]),
                 "af_get_avg_lo": (i, [vp, fp, vp]),
                 "af_set_avg_lo": (i, [vp, fp, vp]),
                 "af_get_half": (i, [vp, fp, fp, fp, vp]),
@@ -201,6 +205,29 @@ class Solver:
         out = out or [np.empty(s, dtype=np.float32) for s in self.shapes()]
         _check(self.L.af_get_state_host(self.h, *[C.c_void_p(a.ctypes.data) for a in out]))
         return tuple(out)
+
+    def set_state_host_async(self, avg, vtx, xe, ye):
+        """Enqueue the upload of a state held in host numpy arrays (pinned
+        memory for overlap); the arrays must stay untouched until host_sync()."""
+        arrs = (avg, vtx, xe, ye)
+        for a, s in zip(arrs, self.shapes()):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.shape == s
+                    and a.flags["C_CONTIGUOUS"]):
+                raise ValueError(f"need C-contiguous float32 arrays of shape {s}")
+        _check(self.L.af_set_state_host_async(self.h, *[C.c_void_p(a.ctypes.data) for a in arrs]))
+
+    def get_state_host_async(self, out):
+        """Enqueue the download of the current state into host numpy arrays
+        (pinned memory for overlap); their contents are valid after host_sync()."""
+        for a, s in zip(out, self.shapes()):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.shape == s
+                    and a.flags["C_CONTIGUOUS"] and a.flags["WRITEABLE"]):
+                raise ValueError(f"need writeable C-contiguous float32 arrays of shape {s}")
+        _check(self.L.af_get_state_host_async(self.h, *[C.c_void_p(a.ctypes.data) for a in out]))
+
+    def host_sync(self):
+        """Wait for the asynchronous host transfers."""
+        _check(self.L.af_host_sync(self.h))
 
     def get_avg_lo(self):
         t = self.torch.empty(self.shapes()[0], dtype=self.torch.float32, device=self.device)

@@ -224,7 +224,9 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
     }
   }
   const size_t small = 64 + 64 + 64 + 64 + sizeof(double) * (TOTALS_BLOCKS * NV + NV);
-  e = cudaMalloc(&h->small, small);
+  e = cudaHostAlloc(&h->host_words, 64, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&h->host_words_dev, h->host_words, 0);
+  if (e == cudaSuccess) e = cudaMalloc(&h->small, small);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
@@ -232,6 +234,7 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   if (e != cudaSuccess) {
     cuda_fail(e, "af_create");
     if (h->small) cudaFree(h->small);
+    if (h->host_words) cudaFreeHost(h->host_words);
     cudaFree(h->base);
     delete h;
     return nullptr;
@@ -239,6 +242,7 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   char *sp = (char *)h->small;
   h->d_status = (int *)sp;
   h->d_bad = (int *)(sp + 64);
+  h->d_bad_async = (int *)(sp + 96);
   h->d_speed = (unsigned *)(sp + 128);
   h->d_speed_bad = (int *)(sp + 160);
   h->d_counters = (unsigned long long *)(sp + 192);
@@ -256,7 +260,19 @@ void af_destroy(af_ctx *h) {
   if (!h) return;
   DeviceGuard dg(h->device);
   cudaStreamSynchronize(h->stream);
+  if (h->async_init) {
+    for (int w = 0; w < 4; w++) cudaStreamSynchronize(h->xo[w]);
+    cudaFree(h->staging_out);
+    for (int w = 0; w < 4; w++) {
+      cudaStreamDestroy(h->xo[w]);
+      cudaEventDestroy(h->out_done[0][w]);
+      cudaEventDestroy(h->out_done[1][w]);
+    }
+    cudaEventDestroy(h->in_free);
+    cudaEventDestroy(h->out_ready);
+  }
   if (h->staging) {
+    for (int w = 0; w < 4; w++) cudaStreamSynchronize(h->xs[w]);
     cudaFree(h->staging);
     for (int w = 0; w < 4; w++) cudaStreamDestroy(h->xs[w]);
     for (int k = 0; k < 5; k++) cudaEventDestroy(h->xev[k]);
@@ -264,6 +280,7 @@ void af_destroy(af_ctx *h) {
   for (int p = 0; p < 2; p++)
     if (h->run_exec[p]) cudaGraphExecDestroy(h->run_exec[p]);
   cudaFree(h->small);
+  if (h->host_words) cudaFreeHost(h->host_words);
   cudaFree(h->base);
   if (h->surr_ubar) cudaFree(h->surr_ubar);
   if (h->shock_theta) cudaFree(h->shock_theta);
@@ -385,8 +402,12 @@ int af_set_state(af_ctx *h, const float *avg, const float *vtx, const float *xe,
 
 int af_set_state_host(af_ctx *h, const float *avg, const float *vtx, const float *xe,
                       const float *ye) {
-  h->speed_valid = false;
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (h->async_pending) {
+    const int rc = af_host_sync(h);
+    if (rc) return rc;
+  }
+  h->speed_valid = false;
   if (!avg || !vtx || !xe || !ye) return fail(AF_ERR_ARG, "af_set_state_host: null array%s");
   DeviceGuard dg(h->device);
   int rc = ensure_staging(h);
@@ -473,9 +494,126 @@ int af_get_state(af_ctx *h, float *avg, float *vtx, float *xe, float *ye, void *
 int af_get_state_host(af_ctx *h, float *avg, float *vtx, float *xe, float *ye) {
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  if (h->async_pending) {
+    const int rc = af_host_sync(h);
+    if (rc) return rc;
+  }
   DeviceGuard dg(h->device);
   float *dst[4] = {avg, vtx, xe, ye};
   return get_arrays(h, h->lev[0], h->hi, dst, true, nullptr);
+}
+
+// ---------------------------------------------------------------- asynchronous host transfers
+static int ensure_async(af_ctx *h) {
+  int rc = ensure_staging(h);
+  if (rc) return rc;
+  if (h->async_init) return AF_OK;
+  CK(cudaMalloc(&h->staging_out, 2 * h->staging_off[4] * sizeof(float)), "cudaMalloc(download staging)");
+  for (int w = 0; w < 4; w++) {
+    CK(cudaStreamCreateWithFlags(&h->xo[w], cudaStreamNonBlocking), "copy streams");
+    for (int b = 0; b < 2; b++)
+      CK(cudaEventCreateWithFlags(&h->out_done[b][w], cudaEventDisableTiming), "copy events");
+  }
+  CK(cudaEventCreateWithFlags(&h->in_free, cudaEventDisableTiming), "copy events");
+  CK(cudaEventCreateWithFlags(&h->out_ready, cudaEventDisableTiming), "copy events");
+  // nothing is pending yet: the first waits on these pass at once
+  CK(cudaEventRecord(h->in_free, h->stream), "event");
+  for (int w = 0; w < 4; w++)
+    for (int b = 0; b < 2; b++) CK(cudaEventRecord(h->out_done[b][w], h->xo[w]), "event");
+  h->out_slot = 0;
+  h->async_init = true;
+  return AF_OK;
+}
+
+int af_set_state_host_async(af_ctx *h, const float *avg, const float *vtx, const float *xe,
+                            const float *ye) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (!avg || !vtx || !xe || !ye) return fail(AF_ERR_ARG, "af_set_state_host_async: null array%s");
+  DeviceGuard dg(h->device);
+  int rc = ensure_async(h);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  const float *src[4] = {avg, vtx, xe, ye};
+  float *dst[4] = {h->hi, h->lev[0].k[VTX], h->lev[0].k[XE], h->lev[0].k[YE]};
+  // each copy waits until the previous upload's unpack has read the staging
+  for (int w = 0; w < 4; w++) {
+    int ni, nj;
+    extents(h, w, ni, nj);
+    CK(cudaStreamWaitEvent(h->xs[w], h->in_free, 0), "event");
+    CK(cudaMemcpyAsync(h->staging + h->staging_off[w], src[w], sizeof(float) * NV * ni * nj,
+                       cudaMemcpyHostToDevice, h->xs[w]),
+       "af_set_state_host_async: H2D");
+    CK(cudaEventRecord(h->xev[w], h->xs[w]), "event");
+  }
+  for (int w = 0; w < 4; w++) {
+    int ni, nj;
+    extents(h, w, ni, nj);
+    float *stg = h->staging + h->staging_off[w];
+    CK(cudaStreamWaitEvent(s, h->xev[w], 0), "event");
+    const int dup_x = h->g.per_x && (w == 1 || w == 2), dup_y = h->g.per_y && (w == 1 || w == 3);
+    if (dup_x || dup_y) CK(launch_check_dup(stg, ni, nj, dup_x, dup_y, h->d_bad_async, s), "check_dup");
+    CK(launch_pack(h->g, stg, dst[w], ni, nj, true, s), "pack");
+  }
+  CK(cudaEventRecord(h->in_free, s), "event");
+  CK(cudaMemsetAsync(h->lo, 0, sizeof(float) * NV * h->g.plane, s), "memset lo");
+  CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), s), "memset status");
+  h->speed_valid = false;
+  h->has_state = true;
+  h->async_pending = true;
+  return AF_OK;
+}
+
+int af_get_state_host_async(af_ctx *h, float *avg, float *vtx, float *xe, float *ye) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  if (!avg || !vtx || !xe || !ye) return fail(AF_ERR_ARG, "af_get_state_host_async: null array%s");
+  DeviceGuard dg(h->device);
+  int rc = ensure_async(h);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  float *dst[4] = {avg, vtx, xe, ye};
+  const float *src[4] = {h->hi, h->lev[0].k[VTX], h->lev[0].k[XE], h->lev[0].k[YE]};
+  // pack into the download staging area used two downloads ago, once that
+  // download has left it
+  const int b = h->out_slot;
+  float *stg = h->staging_out + (size_t)b * h->staging_off[4];
+  for (int w = 0; w < 4; w++) CK(cudaStreamWaitEvent(s, h->out_done[b][w], 0), "event");
+  for (int w = 0; w < 4; w++) {
+    int ni, nj;
+    extents(h, w, ni, nj);
+    CK(launch_pack(h->g, src[w], stg + h->staging_off[w], ni, nj, false, s), "pack");
+  }
+  CK(cudaEventRecord(h->out_ready, s), "event");
+  for (int w = 0; w < 4; w++) {
+    int ni, nj;
+    extents(h, w, ni, nj);
+    CK(cudaStreamWaitEvent(h->xo[w], h->out_ready, 0), "event");
+    CK(cudaMemcpyAsync(dst[w], stg + h->staging_off[w], sizeof(float) * NV * ni * nj, cudaMemcpyDeviceToHost,
+                       h->xo[w]),
+       "af_get_state_host_async: D2H");
+    CK(cudaEventRecord(h->out_done[b][w], h->xo[w]), "event");
+  }
+  h->out_slot = b ^ 1;
+  h->async_pending = true;
+  return AF_OK;
+}
+
+int af_host_sync(af_ctx *h) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (!h->async_init) return AF_OK;
+  DeviceGuard dg(h->device);
+  for (int w = 0; w < 4; w++) CK(cudaStreamSynchronize(h->xs[w]), "sync");
+  for (int w = 0; w < 4; w++) CK(cudaStreamSynchronize(h->xo[w]), "sync");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  h->async_pending = false;
+  int bad = 0;
+  CK(cudaMemcpy(&bad, h->d_bad_async, sizeof(int), cudaMemcpyDeviceToHost), "memcpy");
+  if (bad) {
+    CK(cudaMemset(h->d_bad_async, 0, sizeof(int)), "memset");
+    h->has_state = false;
+    return fail(AF_ERR_ARG, "periodic state: the duplicated last node line differs from the first%s");
+  }
+  return AF_OK;
 }
 
 int af_get_half(af_ctx *h, float *vtx, float *xe, float *ye, void *stream) {
@@ -679,11 +817,10 @@ int af_run(af_ctx *h, int nsteps, double dt) {
 int af_status(af_ctx *h) {
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
   DeviceGuard dg(h->device);
-  int st = 0;
-  CK(cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status");
-  CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream), "status");
+  CK(launch_export_words(reinterpret_cast<unsigned *>(h->d_status), nullptr, 1, h->host_words_dev, h->stream),
+     "status");
   CK(cudaStreamSynchronize(h->stream), "sync");
-  return st;
+  return (int)reinterpret_cast<volatile unsigned *>(h->host_words)[0];
 }
 
 int af_counters(af_ctx *h, int64_t out[4]) {
@@ -709,6 +846,19 @@ int af_conserved_totals(af_ctx *h, double out[4]) {
   return AF_OK;
 }
 
+// the max-speed words, through mapped host memory (no copy engine: a large
+// asynchronous download must not delay this read)
+static cudaError_t read_speed(af_ctx *h, unsigned &bits, int &bad) {
+  cudaError_t e = launch_export_words(h->d_speed, reinterpret_cast<unsigned *>(h->d_speed_bad), 0,
+                                      h->host_words_dev, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return e;
+  volatile unsigned *w = h->host_words;
+  bits = w[0];
+  bad = (int)w[1];
+  return cudaSuccess;
+}
+
 int af_max_speed(af_ctx *h, float *out) {
   if (!h || !out) return fail(AF_ERR_ARG, "null argument%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
@@ -716,9 +866,7 @@ int af_max_speed(af_ctx *h, float *out) {
   if (h->speed_valid) {  // computed by the last step's flux kernel
     unsigned bits = 0;
     int bad = 0;
-    CK(cudaMemcpyAsync(&bits, h->d_speed, sizeof(bits), cudaMemcpyDeviceToHost, h->stream), "speed");
-    CK(cudaMemcpyAsync(&bad, h->d_speed_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "speed");
-    CK(cudaStreamSynchronize(h->stream), "sync");
+    CK(read_speed(h, bits, bad), "speed");
     float m;
     std::memcpy(&m, &bits, sizeof(m));
     *out = bad ? NAN : m;
@@ -736,9 +884,7 @@ int af_max_speed(af_ctx *h, float *out) {
   if (h->profile) cudaEventRecord(e1, h->stream);
   unsigned bits = 0;
   int bad = 0;
-  CK(cudaMemcpyAsync(&bits, h->d_speed, sizeof(bits), cudaMemcpyDeviceToHost, h->stream), "speed");
-  CK(cudaMemcpyAsync(&bad, h->d_speed_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "speed");
-  CK(cudaStreamSynchronize(h->stream), "sync");
+  CK(read_speed(h, bits, bad), "speed");
   if (h->profile) {
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) h->stage_ms[AF_STAGE_REDUCE] += ms;

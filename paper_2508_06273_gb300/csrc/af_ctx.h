@@ -38,6 +38,17 @@ struct af_ctx {
   size_t staging_off[5];
   cudaStream_t xs[4];
   cudaEvent_t xev[5];
+  // asynchronous host transfers: downloads use their own staging area and
+  // streams, so that a download overlaps the next upload
+  float *staging_out;  // two areas, used in turn, so that a pack need not wait for the last download
+  int out_slot;
+  cudaStream_t xo[4];
+  cudaEvent_t in_free, out_ready, out_done[2][4];
+  bool async_init, async_pending;
+  int *d_bad_async;
+  // two words of mapped pinned host memory (host and device addresses) for
+  // the small reads (status, max speed)
+  unsigned *host_words, *host_words_dev;  // a periodic duplicate line differed in an asynchronous upload
   bool has_state;
   // af_run: two captured steps per parity of the t^n buffer, with the dt and
   // options they were captured with

@@ -177,6 +177,10 @@ cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &
                                double lamy, int *status, unsigned *speed, int *speed_bad, int flux_limiter,
                                const float *q0, cudaStream_t s);
 // max over averages and owned point values of max(|u|,|v|) + c (as float bits)
+// words a and b (b may be null) into mapped host memory dst, clearing a if
+// clear_a: small results reach the host without a copy engine, so that they
+// do not queue behind a large transfer
+cudaError_t launch_export_words(unsigned *a, unsigned *b, int clear_a, unsigned *dst, cudaStream_t s);
 cudaError_t launch_max_speed(const Grid &g, const float *avg_hi, const NodeSet &n,
                              unsigned *out_bits, int *bad, cudaStream_t s);
 // fixed-order FP64 sums of hi + lo per variable: partials[nblk][4] -> out[4]

@@ -212,6 +212,15 @@ __global__ void batch_dt_kernel(BatchCtl *ctl, int n, double *hist, int hist_cap
   }
 }
 
+__global__ void export_words_kernel(unsigned *a, unsigned *b, int clear_a, unsigned *dst) {
+  if (threadIdx.x != 0) return;
+  volatile unsigned *d = dst;
+  d[0] = *a;
+  d[1] = b ? *b : 0u;
+  if (clear_a) *a = 0u;
+  __threadfence_system();
+}
+
 __global__ void max_speed_kernel(Grid g, const float *__restrict__ avg, const float *__restrict__ V,
                                  const float *__restrict__ X, const float *__restrict__ Y,
                                  unsigned *out, int *badflag) {
@@ -365,6 +374,11 @@ cudaError_t launch_shock_theta_batch(const BatchCtl *ctl, const Grid *grids, con
 cudaError_t launch_batch_dt(BatchCtl *ctl, int n, double *hist, int hist_cap, int mode, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   batch_dt_kernel<<<(n + 127) / 128, 128, 0, s>>>(ctl, n, hist, hist_cap, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_words(unsigned *a, unsigned *b, int clear_a, unsigned *dst, cudaStream_t s) {
+  export_words_kernel<<<1, 32, 0, s>>>(a, b, clear_a, dst);
   return cudaGetLastError();
 }
 

@@ -311,6 +311,54 @@ def test_host_transfer_roundtrip(env):
         assert np.array_equal(a, b)
 
 
+def _pinned(torch, shapes, fill=None):
+    out = []
+    for k, sh in enumerate(shapes):
+        a = torch.empty(sh, dtype=torch.float32, pin_memory=True).numpy()
+        a[...] = 0.0 if fill is None else fill[k]
+        out.append(a)
+    return out
+
+
+def test_async_host_pipeline_matches_synchronous_transfers(env):
+    """Uploads, steps and downloads pipelined through the asynchronous host
+    calls (the download of one step overlapping the upload of the next) give
+    bitwise the states of the synchronous calls; the inputs change every
+    step, so a stale staging area would show."""
+    torch, af, _ = env
+    prob = W.shu_vortex(64)
+    base = [np.asarray(a, dtype=np.float32) for a in W.discretise(prob)]
+    ins = [[(a * (1.0 + 1e-3 * k)).astype(np.float32) for a in base] for k in range(3)]
+    dt = 0.3 * prob.dx / 2.5
+    sync = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, bc=prob.bc)
+    want = []
+    for st in ins:
+        sync.set_state(*st)
+        sync.step(dt)
+        want.append(sync.get_state_host())
+    a = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, bc=prob.bc)
+    shapes = a.shapes()
+    pin_in = [_pinned(torch, shapes, st) for st in ins]
+    pin_out = [_pinned(torch, shapes) for _ in ins]
+    for k in range(3):
+        a.set_state_host_async(*pin_in[k])
+        a.step(dt)
+        a.get_state_host_async(pin_out[k])
+    a.host_sync()
+    for k in range(3):
+        for x, y in zip(pin_out[k], want[k]):
+            assert np.array_equal(x, y), k
+    # a periodic duplicate line that differs is reported by host_sync
+    bad = [x.copy() for x in pin_in[0]]
+    bad[1][0, -1, 3] += 1.0
+    bad = _pinned(torch, shapes, bad)
+    a.set_state_host_async(*bad)
+    with pytest.raises(af.AFError):
+        a.host_sync()
+    sync.close()
+    a.close()
+
+
 def test_full_size_sampled_windows(env):
     """The 8192^2 seeded vortex in the benchmark's launch configuration: one
     step on the GPU; windows of 16x16 cells are recomputed by the oracle
