@@ -51,7 +51,7 @@ FLUX_BYTES_PER_CELL = 208
 # were taken on (sha256 of the files below); otherwise reported as null
 _KSRC = "paper_2508_06273_gb300/csrc/"
 _SHARED = {_KSRC + "af_common.cuh": "ad367efa0749a42a00411129d4ba9b0879db4f6774a017f6d6f5cb31c8be357c",
-           _KSRC + "af_kernels.h": "55362771c9930cc6c18b944182879d2ec6126ad00a5d42986992e368199d4b7a"}
+           _KSRC + "af_kernels.h": "c59d6e0309e759a0e3d3b52afbcb4cb19fad58711b5fd792c3dfde83d5177102"}
 PV_TRAFFIC = {"bytes_per_cell": 150.7, "profile": "profiles/pointvalue_flux_vortex2048.md",
               "sha256": dict(_SHARED, **{_KSRC + "af_pointvalue.cu":
                                          "ed707f206b8c333290e8186217f07bc36cdc07d5c470470663976d7b4af2db32"})}
