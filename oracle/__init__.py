@@ -26,6 +26,7 @@ from .afo import (  # noqa: F401
     OPT_THREADS,
     OPT_FLUX_LIMITER,
     OPT_SHOCK_BLEND,
+    OPT_NODE_BOUNDS,
     ST_FLUX_LIMITED,
     ST_CFL,
     ST_AVG_NONPOS,

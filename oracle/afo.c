@@ -47,7 +47,7 @@ struct afo_ctx {
   double dx, dy, gam;
   int bc[4];
   double inflow[4][4]; /* primitive inflow state per side (Sec. 4.3) */
-  int lin_mode, tsw, limiter, correction, force_lo, threads, flux_limiter, shock_blend;
+  int lin_mode, tsw, limiter, correction, force_lo, threads, flux_limiter, shock_blend, node_bounds;
   double *avg;        /* conservative averages, [4][H][W] */
   double *nd[3][3];   /* point values [level][kind] -> [4][H][W]; level 0 t^n, 1 t^{n+1/2}, 2 t^{n+1} */
   double *uc, *ub;    /* cell-centre value U_c and primitive average Ubar, [4][H][W] */
@@ -592,6 +592,38 @@ static void eg_node(afo_ctx *c, int kind, int i, int j, int op, const double ul[
   eg_apply(&s, op, ul, tau, c->gam, out);
 }
 
+/* Node bounds (reading of Alg. 3 for data far from the linearisation, with
+ * the option on): the high-order value's rho and p must lie in
+ * [NB_ETA min, max / NB_ETA] of the node's own t^n value and the Ubar of the
+ * cells around it (4 for a vertex, 2 for an edge midpoint).  Positivity alone
+ * lets through the huge positive values that EG2 gives when the full step is
+ * linearised about a near-vacuum half-step state (terms in 1/c'^2). */
+#define NB_ETA 0.1
+static int in_node_bounds(const afo_ctx *c, int kind, int i, int j, const double U0[4], const double U[4]) {
+  double lo[2] = {U0[0], U0[3]}, hi[2] = {U0[0], U0[3]};
+  const int ncell = kind == AFO_VTX ? 4 : 2;
+  for (int q = 0; q < ncell; q++) {
+    int ci, cj;
+    if (kind == AFO_VTX) {
+      ci = i - 1 + (q & 1);
+      cj = j - 1 + (q >> 1);
+    } else if (kind == AFO_XE) {
+      ci = i - 1 + q;
+      cj = j;
+    } else {
+      ci = i;
+      cj = j - 1 + q;
+    }
+    double a[4];
+    get4(c, c->ub, ci, cj, a);
+    lo[0] = fmin(lo[0], a[0]);
+    hi[0] = fmax(hi[0], a[0]);
+    lo[1] = fmin(lo[1], a[3]);
+    hi[1] = fmax(hi[1], a[3]);
+  }
+  return U[0] >= NB_ETA * lo[0] && U[0] <= hi[0] / NB_ETA && U[3] >= NB_ETA * lo[1] && U[3] <= hi[1] / NB_ETA;
+}
+
 /* Alg. 3: keep the high-order value if it is admissible, else EG1 on pc data
  * with the averaged linearisation, else Lax-Friedrichs; if even that fails in
  * floating point, keep the node's t^n value.  A high-order value whose Mach
@@ -599,7 +631,13 @@ static void eg_node(afo_ctx *c, int kind, int i, int j, int op, const double ul[
  * operator assumes the CFL bound of its linearisation state. */
 static void limit_node(afo_ctx *c, int kind, int i, int j, double tau, const double ho[4], int inb,
                        double out[4], nstat *st, int force_lo) {
-  int go_lo = force_lo == 1 || (c->limiter && !(inb && admissible(ho)));
+  int ok = inb && admissible(ho);
+  if (ok && c->node_bounds) {
+    double U0[4];
+    get4(c, c->nd[0][kind], i, j, U0);
+    ok = in_node_bounds(c, kind, i, j, U0, ho);
+  }
+  int go_lo = force_lo == 1 || (c->limiter && !ok);
   if (force_lo != 2 && !go_lo) {
     for (int v = 0; v < NV; v++) out[v] = ho[v];
     return;
@@ -773,6 +811,7 @@ int afo_set_option(afo_ctx *c, int key, double val) {
   case AFO_OPT_THREADS: c->threads = iv; return 0;
   case AFO_OPT_FLUX_LIMITER: c->flux_limiter = iv != 0; return 0;
   case AFO_OPT_SHOCK_BLEND: c->shock_blend = iv != 0; return 0;
+  case AFO_OPT_NODE_BOUNDS: c->node_bounds = iv != 0; return 0;
   default: return -1;
   }
 }
