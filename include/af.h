@@ -87,8 +87,12 @@ enum {
                               the limiter reads as the t^n state while the update overwrites them */
   AF_OPT_SHOCK_BLEND = 10, /* 1: Sec. 3.4 shock-indicator blend theta U^ho + (1 - theta) U^lo of the point
                               values, theta = exp(-phi1 phi2), U^lo from Alg. 3's low-order chain */
-  AF_OPT_TILE_H = 11       /* point-value tile height: 4, 8 (default) or 16 rows of 32 cells; the result
+  AF_OPT_TILE_H = 11,      /* point-value tile height: 4, 8 (default) or 16 rows of 32 cells; the result
                               does not depend on it */
+  AF_OPT_NODE_BOUNDS = 12  /* 1: Alg. 3 also rejects a high-order point value whose rho or p lies outside
+                              [0.1 min, 10 max] of the node's t^n value and the primitive averages of the
+                              cells around it (own reading: positivity alone keeps the huge positive values
+                              EG2 returns when the full step is linearised about a near-vacuum state) */
 };
 
 /* stages reported by af_profile */

@@ -344,6 +344,7 @@ int af_set_option(af_ctx *h, int key, double value) {
       }
       h->opt.shock_blend = iv != 0;
       return AF_OK;
+    case AF_OPT_NODE_BOUNDS: h->opt.node_bounds = iv != 0; return AF_OK;
     case AF_OPT_TILE_H: {
       if (iv != 4 && iv != 8 && iv != 16) return fail(AF_ERR_ARG, "tile height must be 4, 8 or 16%s");
       if (iv == h->tile_h) return AF_OK;
@@ -382,6 +383,7 @@ int af_get_option(af_ctx *h, int key, double *value) {
     case AF_OPT_SURR_ABS: *value = h->opt.surr_abs; return AF_OK;
     case AF_OPT_FLUX_LIMITER: *value = h->opt.flux_limiter; return AF_OK;
     case AF_OPT_SHOCK_BLEND: *value = h->opt.shock_blend; return AF_OK;
+    case AF_OPT_NODE_BOUNDS: *value = h->opt.node_bounds; return AF_OK;
     case AF_OPT_TILE_H: *value = h->tile_h; return AF_OK;
     default: return fail(AF_ERR_ARG, "unknown option%s");
   }
@@ -751,7 +753,7 @@ static bool same_options(const Options &a, const Options &b) {
   return a.lin_mode == b.lin_mode && a.tsw == b.tsw && a.limiter == b.limiter &&
          a.correction == b.correction && a.force_lo == b.force_lo && a.surrogate == b.surrogate &&
          a.surr_tol == b.surr_tol && a.surr_abs == b.surr_abs && a.flux_limiter == b.flux_limiter &&
-         a.shock_blend == b.shock_blend;
+         a.shock_blend == b.shock_blend && a.node_bounds == b.node_bounds;
 }
 
 // Capture two steps on the handle's own stream (the t^n and t^{n+1} buffers

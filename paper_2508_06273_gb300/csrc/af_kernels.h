@@ -25,6 +25,7 @@ struct Options {
   float surr_abs = 2e-3f;
   int flux_limiter = 0;  // cell-average flux limiter (Sec. 3.5)
   int shock_blend = 0;   // Sec. 3.4 shock-indicator blend of point values
+  int node_bounds = 0;   // Alg. 3 also bounds rho, p by the node's cells (see node_update)
 };
 
 // TMA descriptors of the t^n node arrays and the cell averages (one set per
@@ -41,7 +42,7 @@ struct PointValueArgs {
   float *n1[3];
   float *n2[3];
   float dt;
-  int lin_mode, tsw, limiter, correction, force_lo;
+  int lin_mode, tsw, limiter, correction, force_lo, node_bounds;
   int *status;
   unsigned long long *counters;
   // exact operator as the surrogate's fallback: only nodes with a nonzero
@@ -68,6 +69,7 @@ inline PointValueArgs pointvalue_args(const Grid &g, const NodeSet &n0, const fl
   A.limiter = o.limiter;
   A.correction = o.correction;
   A.force_lo = o.force_lo;
+  A.node_bounds = o.node_bounds;
   A.status = status;
   A.counters = counters;
   A.mask[0] = A.mask[1] = A.mask[2] = nullptr;

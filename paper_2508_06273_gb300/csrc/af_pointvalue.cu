@@ -722,6 +722,26 @@ __device__ __noinline__ void limit(const Args &A, const float *sm, int i, int j,
   cnt[CNT_KEPT]++;
 }
 
+// node bounds (with the option on): rho and p within [NB_ETA min, max / NB_ETA]
+// of the node's own t^n value U0 and the primitive averages of its cells
+constexpr float NB_ETA = 0.1f;
+template <int K>
+__device__ __forceinline__ bool in_node_bounds(const float *sm, int li, int lj, const float *U0, const float *U) {
+  const int a = li + 1, b = lj + 1;
+  float rlo = U0[0], rhi = U0[0], plo = U0[3], phi = U0[3];
+  const int ncell = K == VTX ? 4 : 2;
+  for (int q = 0; q < ncell; q++) {
+    const int ca = K == VTX ? a - 1 + (q & 1) : (K == XE ? a - 1 + q : a);
+    const int cb = K == VTX ? b - 1 + (q >> 1) : (K == XE ? b : b - 1 + q);
+    const float4 w = ubar4(sm, ca, cb);
+    rlo = fminf(rlo, w.x);
+    rhi = fmaxf(rhi, w.x);
+    plo = fminf(plo, w.w);
+    phi = fmaxf(phi, w.w);
+  }
+  return U[0] >= NB_ETA * rlo && U[0] <= rhi / NB_ETA && U[3] >= NB_ETA * plo && U[3] <= phi / NB_ETA;
+}
+
 // Alg. 2 indicator of the vertex at tile-local cell corner (a, b): the
 // primitive averages of cells (a-1, b-1), (a, b-1), (a-1, b), (a, b)
 __device__ __forceinline__ bool tsw_vertex(const float *sm, float gam, int a, int b) {
@@ -850,8 +870,11 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
     const float ht = 0.5f * tau * tau;
 #pragma unroll
     for (int v = 0; v < NV; v++) ho[v] = fmaf(ht, T[v], ho[v]);
-    // Alg. 3 (a value from a Mach cone outside the block counts as not admissible)
-    if (A.force_lo || (A.limiter && !(inb && admissible(ho)))) {
+    // Alg. 3 (a value from a Mach cone outside the block counts as not
+    // admissible, and, with the option, one outside the node's bounds)
+    bool ok = inb && admissible(ho);
+    if (ok && A.node_bounds) ok = in_node_bounds<K>(sm, li, lj, U0, ho);
+    if (A.force_lo || (A.limiter && !ok)) {
       limit<K>(A, sm, i, j, li, lj, tau, U0, res, cnt);
     } else {
 #pragma unroll

@@ -305,8 +305,8 @@ def four_quadrant(n=64, seed=0, t_end=0.25, cfl=0.3, states=None):
     """Four-quadrant Riemann data on [0,1]^2 split at (0.5,0.5), outflow
     boundaries; rho in [0.1,1.5], p in [0.01,1.5], u, v in [-1.2,1.2] drawn
     from ``seed``, unless ``states`` (lower-left, lower-right, upper-left,
-    upper-right; each rho, u, v, p) is given.  Run with Alg. 2, Alg. 3, the
-    Sec. 3.4 blend and the cell-average flux limiter."""
+    upper-right; each rho, u, v, p) is given.  Run with Alg. 2, Alg. 3 (with
+    the node bounds), the Sec. 3.4 blend and the cell-average flux limiter."""
     if states is None:
         rng = np.random.default_rng(seed)
         st = np.stack([rng.uniform(0.1, 1.5, 4), rng.uniform(-1.2, 1.2, 4),
@@ -315,7 +315,7 @@ def four_quadrant(n=64, seed=0, t_end=0.25, cfl=0.3, states=None):
         st = np.asarray(states, dtype=np.float64)
     p = Problem(f"four_quadrant_seed{seed}", n, n, 0.0, 0.0, 1.0, 1.0, (1, 1, 1, 1),
                 _piecewise(st, 0.5, 0.5), t_end, cfl=cfl,
-                options={"tsw": 1, "limiter": 1, "flux_limiter": 1, "shock_blend": 1})
+                options={"tsw": 1, "limiter": 1, "flux_limiter": 1, "shock_blend": 1, "node_bounds": 1})
     p.states = st
     return p
 
@@ -325,7 +325,8 @@ def double_rarefaction(n=64, t_end=0.25, cfl=0.3, rho=1.0, p=0.4, speed=2.0):
     line), v = 0; outflow at x = 0, 1 and solid walls at y = 0, 1."""
     st = [(rho, -speed, 0.0, p), (rho, speed, 0.0, p), (rho, -speed, 0.0, p), (rho, speed, 0.0, p)]
     return Problem("double_rarefaction", n, n, 0.0, 0.0, 1.0, 1.0, (1, 1, 2, 2),
-                   _piecewise(st, 0.5, -1.0), t_end, cfl=cfl, options={"limiter": 1, "flux_limiter": 1})
+                   _piecewise(st, 0.5, -1.0), t_end, cfl=cfl,
+                   options={"limiter": 1, "flux_limiter": 1, "node_bounds": 1})
 
 
 def kelvin_helmholtz(n=64, t_end=1.0, cfl=0.3):
