@@ -671,6 +671,40 @@ def test_limiters_leave_smooth_data_alone(oracle_mod):
         assert np.array_equal(x, y)
 
 
+def test_node_bounds_leave_smooth_data_alone(oracle_mod):
+    """The node bounds of Alg. 3 (reading: rho, p of a high-order point value
+    within [0.1 min, 10 max] of its node's t^n value and cell averages) never
+    act on the smooth vortex: the steps equal the plain ones bit for bit."""
+    prob = W.shu_vortex(24)
+    a = make_oracle(oracle_mod, prob)
+    b = make_oracle(oracle_mod, prob, opts={"node_bounds": 1})
+    for _ in range(3):
+        dt = 0.3 * prob.dx / a.max_speed()
+        a.step(dt)
+        b.step(dt)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+
+
+def test_node_bounds_cut_the_first_step_overshoot(oracle_mod):
+    """Seeded four-quadrant data (seed 0): without the bounds the first step
+    leaves a vertex pressure of about 13 at the quadrant corner (the data's
+    pressures are at most 1.29); with them every new vertex pressure stays
+    within 10 times the largest pressure of the data, and the low-order chain
+    takes the rejected nodes (more EG1 evaluations)."""
+    prob = W.four_quadrant(24, seed=0)
+    st = W.discretise(prob)
+    pmax = max(float(np.max(a[3])) for a in st[1:])
+    a = make_oracle(oracle_mod, prob, opts={"node_bounds": 0}, state=st)
+    b = make_oracle(oracle_mod, prob, opts={"node_bounds": 1}, state=st)
+    dt = 0.3 * prob.dx / a.max_speed()
+    a.step(dt)
+    b.step(dt)
+    assert max(float(np.max(x[3])) for x in a.get_state()[1:]) > 10 * pmax
+    assert max(float(np.max(x[3])) for x in b.get_state()[1:]) <= 10 * pmax
+    assert b.counters()[0] > a.counters()[0]
+
+
 def test_flux_limiter_conserves(oracle_mod):
     """Periodic near-vacuum data with the flux limiter acting: the totals
     are conserved to round-off (each face keeps one flux)."""
