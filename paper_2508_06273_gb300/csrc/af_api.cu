@@ -942,7 +942,10 @@ int af_set_surrogate(af_ctx *h, af_mlp *vertex_net, af_mlp *edge_net) {
     const int tx = (h->g.nxv + 31) / 32, ty = (h->g.nyv + 3) / 4;  // enough for every tile height
     const size_t mask_bytes = (3 * (size_t)h->g.plane + 255) & ~size_t(255);
     const size_t ub_bytes = sizeof(float) * NV * (size_t)h->g.plane;
-    const size_t bytes = ub_bytes + mask_bytes + sizeof(int) * (size_t)tx * ty + 2 * sizeof(unsigned long long);
+    // the 64-bit counters after the tile flags start on a 256-byte boundary
+    // (tx * ty is odd on some grids: 65 x 513 tiles for 2049 x 2049 nodes)
+    const size_t tile_bytes = (sizeof(int) * (size_t)tx * ty + 255) & ~size_t(255);
+    const size_t bytes = ub_bytes + mask_bytes + tile_bytes + 2 * sizeof(unsigned long long);
     void *p = nullptr;
     CK(cudaMalloc(&p, bytes), "af_set_surrogate: cudaMalloc");
     cudaMemset(p, 0, bytes);
@@ -951,7 +954,7 @@ int af_set_surrogate(af_ctx *h, af_mlp *vertex_net, af_mlp *edge_net) {
     h->surr_tiles = (int *)((char *)h->surr_mask + mask_bytes);
     h->surr_ntiles = tx * ty;
     h->surr_tiles_x = tx;
-    h->surr_stats = (unsigned long long *)(h->surr_tiles + (size_t)tx * ty);
+    h->surr_stats = (unsigned long long *)((char *)h->surr_tiles + tile_bytes);
     CK(prepare_surrogate(), "af_set_surrogate: kernel attributes");
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
   }

@@ -83,6 +83,33 @@ def test_a_network_that_never_passes_falls_back_to_the_exact_operator(env):
         s.close()
 
 
+def test_fallback_on_a_transmissive_grid_with_an_odd_tile_count(env):
+    """Non-periodic 64^2 four-quadrant data with its limiters: 65 x 65 nodes
+    give 3 x 17 tiles, an odd count (the counters behind the tile flags must
+    still be 8-byte aligned).  A network that never passes falls back at
+    every node, bit for bit the plain method."""
+    torch, af, _ = env
+    prob = W.four_quadrant(64, states=MILD)
+    nets = [af.Mlp(seed=s) for s in (1, 2)]
+    for n in nets:
+        p = n.get_params()
+        p[-8:] = np.nan
+        n.set_params(p)
+    plain, surr = solver(env, prob), solver(env, prob)
+    surr.set_surrogate(*nets)
+    dt = 0.3 * prob.dx / plain.max_speed()
+    for _ in range(3):
+        plain.step(dt)
+        surr.step(dt)
+    for a, c in zip(plain.get_state(), surr.get_state()):
+        assert torch.equal(a, c)
+    n_net, n_fall = surr.surrogate_stats()
+    assert n_net == 0 and n_fall > 0
+    assert not surr.status() & (af.ST_AVG_NONPOS | af.ST_NONFINITE)
+    for s in (plain, surr):
+        s.close()
+
+
 def _training_set(env, seeds, n_lo=48, n_hi=96, steps=12, rate=0.08):
     torch, af, _ = env
     rng = np.random.default_rng(seeds[0])
