@@ -472,21 +472,17 @@ def run_batch_leg(args, torch, af, W):
     }
 
 
-def run_surrogate_leg(args, torch, af, W):
-    """Learned surrogate + exact fallback against the plain path on one grid
-    (default: 4096^2 isentropic vortex, centre and strength from seed 5).
-    The networks are trained here, on the GPU, from (features, exact
-    targets) pairs sampled from a batched ensemble of small seeded vortices;
-    both paths then start from the same state and take the same dt."""
-    import numpy as np
+def _train_surrogate(args, af, W, probs, seed):
+    """Both networks, trained on the GPU from (features, exact targets) pairs
+    sampled from a batched ensemble of the given small problems."""
+    import torch
 
-    t0 = time.perf_counter()
-    rng = np.random.default_rng(17)
-    probs = [W.shu_vortex_seeded(int(rng.integers(64, 129)), seed=200 + k, t_end=np.inf) for k in range(16)]
     b = af.Batch([(p.nx, p.ny) for p in probs], [(p.dx, p.dy) for p in probs], bcs=[p.bc for p in probs])
     for k, p in enumerate(probs):
+        for key, v in p.options.items():
+            b.set_option(key, v, k)
         b.set_state(k, *W.discretise_torch(p, "cuda"))
-    b.set_sampler(600000, 1200000, seed=23, rate=0.08)
+    b.set_sampler(600000, 1200000, seed=seed, rate=0.08)
     b.run(12)
     Xv, Tv, _, Xe, Te, _ = (t.clone() for t in b.samples())
     b.close()
@@ -497,13 +493,16 @@ def run_surrogate_leg(args, torch, af, W):
         hist = m.train(X, T, steps=args.surr_train_steps, batch=4096, lr=2e-3, seed=3)
         nets.append((m, float(hist[:10].mean()), float(hist[-10:].mean())))
     torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
+    return nets, int(Xv.shape[0]), int(Xe.shape[0])
 
-    n = args.surr_grid
-    prob = W.shu_vortex_seeded(n, seed=5)
+
+def _surrogate_case(args, torch, af, W, prob, nets, steps):
+    """Surrogate + exact fallback against the plain path on one grid: both
+    start from the same state and take the same dt."""
+    n = prob.nx
     dev = W.discretise_torch(prob, "cuda")
-    plain = af.Solver(n, n, prob.dx, prob.dy, prob.gamma, prob.bc)
-    surr = af.Solver(n, n, prob.dx, prob.dy, prob.gamma, prob.bc)
+    plain = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=prob.options)
+    surr = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=prob.options)
     plain.set_state(*dev)
     surr.set_state(*dev)
     del dev
@@ -517,10 +516,10 @@ def run_surrogate_leg(args, torch, af, W):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         ev0.record(stream)
-        s.run(args.surr_steps, dt)
+        s.run(steps, dt)
         ev1.record(stream)
         torch.cuda.synchronize()
-        times[name] = ev0.elapsed_time(ev1) / args.surr_steps
+        times[name] = ev0.elapsed_time(ev1) / steps
     n_net, n_fall = surr.surrogate_stats()
     a, c = surr.get_state(), plain.get_state()
     rel = 0.0
@@ -530,23 +529,60 @@ def run_surrogate_leg(args, torch, af, W):
     status = surr.status()
     for s in (plain, surr):
         s.close()
-    for m, _, _ in nets:
-        m.close()
-    cells = n * n
-    return {
+    cells = prob.nx * prob.ny
+    return {"value": cells / (times["surrogate"] / 1e3), "plain_value": cells / (times["plain"] / 1e3),
+            "unit": UNIT, "ms_per_step": times["surrogate"], "plain_ms_per_step": times["plain"],
+            "speedup_vs_plain": times["plain"] / times["surrogate"], "rel_l1_vs_plain": rel,
+            "fallback_fraction": n_fall / max(1, n_net + n_fall), "status": status}
+
+
+def run_surrogate_leg(args, torch, af, W):
+    """Learned surrogate + exact fallback against the plain path: the 4096^2
+    isentropic vortex (centre and strength from seed 5), networks trained on
+    small seeded vortices; and the 2048^2 four-quadrant Riemann problem (seed
+    6, with its limiters), networks trained on small seeded four-quadrant
+    problems.  Training runs here, on the GPU."""
+    import numpy as np
+
+    t0 = time.perf_counter()
+    rng = np.random.default_rng(17)
+    probs = [W.shu_vortex_seeded(int(rng.integers(64, 129)), seed=200 + k, t_end=np.inf) for k in range(16)]
+    nets, nv, ne = _train_surrogate(args, af, W, probs, seed=23)
+    train_s = time.perf_counter() - t0
+    n = args.surr_grid
+    out = _surrogate_case(args, torch, af, W, W.shu_vortex_seeded(n, seed=5), nets, args.surr_steps)
+    out.update({
         "workload": f"isentropic vortex, periodic [0,10]^2, {n}x{n} cells, centre and strength from seed 5, "
                     f"CFL 0.3, {args.warmup + args.surr_steps} steps of fixed dt",
-        "value": cells / (times["surrogate"] / 1e3), "plain_value": cells / (times["plain"] / 1e3),
-        "unit": UNIT, "ms_per_step": times["surrogate"], "plain_ms_per_step": times["plain"],
-        "speedup_vs_plain": times["plain"] / times["surrogate"],
-        "rel_l1_vs_plain": rel, "fallback_fraction": n_fall / max(1, n_net + n_fall), "status": status,
         "network": "64-128-128-128-16 GELU, BF16 weights, tcgen05 MMA with FP32 accumulation",
-        "training": {"samples_vertex": int(Xv.shape[0]), "samples_edge": int(Xe.shape[0]),
+        "training": {"samples_vertex": nv, "samples_edge": ne,
                      "steps": args.surr_train_steps, "batch": 4096, "seconds_incl_sampling": train_s,
                      "loss_first_last_vertex": [nets[0][1], nets[0][2]],
                      "loss_first_last_edge": [nets[1][1], nets[1][2]],
                      "data": "16 seeded vortices of 64^2 to 128^2, 12 batched steps, 8% of nodes sampled"},
-    }
+    })
+    for m, _, _ in nets:
+        m.close()
+    # the Riemann case
+    t0 = time.perf_counter()
+    probs = [W.four_quadrant(int(rng.integers(64, 129)), seed=300 + k) for k in range(16)]
+    nets, nv, ne = _train_surrogate(args, af, W, probs, seed=29)
+    train_s = time.perf_counter() - t0
+    nr = args.surr_grid // 2
+    rie = _surrogate_case(args, torch, af, W, W.four_quadrant(nr, seed=6), nets, args.surr_steps)
+    rie.update({
+        "workload": f"four-quadrant Riemann problem, transmissive [0,1]^2, {nr}x{nr} cells, states from seed 6, "
+                    f"Alg. 2, Alg. 3 with node bounds, Sec. 3.4 blend, flux limiter, CFL 0.3, "
+                    f"{args.warmup + args.surr_steps} steps of fixed dt",
+        "training": {"samples_vertex": nv, "samples_edge": ne, "seconds_incl_sampling": train_s,
+                     "loss_first_last_vertex": [nets[0][1], nets[0][2]],
+                     "loss_first_last_edge": [nets[1][1], nets[1][2]],
+                     "data": "16 seeded four-quadrant problems of 64^2 to 128^2, 12 batched steps, 8% of nodes sampled"},
+    })
+    for m, _, _ in nets:
+        m.close()
+    out["riemann"] = rie
+    return out
 
 
 def run_reference(args):
