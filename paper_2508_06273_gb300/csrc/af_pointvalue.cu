@@ -726,7 +726,7 @@ __device__ __noinline__ void limit(const Args &A, const float *sm, int i, int j,
 // of the node's own t^n value U0 and the primitive averages of its cells
 constexpr float NB_ETA = 0.1f;
 template <int K>
-__device__ __forceinline__ bool in_node_bounds(const float *sm, int li, int lj, const float *U0, const float *U) {
+__device__ __noinline__ bool in_node_bounds(const float *sm, int li, int lj, const float *U0, const float *U) {
   const int a = li + 1, b = lj + 1;
   float rlo = U0[0], rhi = U0[0], plo = U0[3], phi = U0[3];
   const int ncell = K == VTX ? 4 : 2;

@@ -15,8 +15,9 @@ sizes):
   outflow speed (the wall nodes' own linearisation departs from y-
   independence);
 * the isentropic vortex at 128^2 to t = 2 (the smallest grid of the
-  convergence sweep) against the FP64 oracle, and the conserved totals of
-  the 2048^2 grid over 100 steps."""
+  convergence sweep) against the FP64 oracle, the conserved totals of the
+  2048^2 grid over 100 steps, and third-order convergence to the exact
+  vortex on 32^2 to 128^2."""
 import numpy as np
 import pytest
 
@@ -111,3 +112,25 @@ def test_vortex_2048_conservation_per_step(env):
     assert s.status() == 0
     assert np.all(np.abs(t1 - t0) <= 1e-12 * np.maximum(1.0, np.abs(t0))), (t0, t1)
     s.close()
+
+
+def test_vortex_converges_at_third_order(env):
+    """Closed-form vortex (centre (5, 5), strength 5), t = 1, L1(rho) of the
+    cell averages against the exact cell means: order about 3 with the
+    correction term (the FP32 path reaches the oracle's order)."""
+    torch, af, _ = env
+    err = {}
+    for n in (32, 64, 128):
+        p = W.shu_vortex(n, t_end=1.0)
+        s = _gpu_solver(af, p)
+        t = 0.0
+        while t < 1.0 - 1e-12:
+            dt = min(p.cfl * p.dx / s.max_speed(), 1.0 - t)
+            s.step(dt)
+            t += dt
+        assert s.status() == 0
+        ex = W.discretise(p, p.exact(1.0))[0]
+        err[n] = float(np.mean(np.abs(s.get_state()[0][0].double().cpu().numpy() - ex[0])))
+        s.close()
+    eoc1, eoc2 = np.log2(err[32] / err[64]), np.log2(err[64] / err[128])
+    assert eoc1 > 2.75 and eoc2 > 2.75, (err, eoc1, eoc2)
