@@ -51,11 +51,11 @@ FLUX_BYTES_PER_CELL = 208
 # were taken on (sha256 of the files below); otherwise reported as null
 _KSRC = "paper_2508_06273_gb300/csrc/"
 _SHARED = {_KSRC + "af_common.cuh": "ad367efa0749a42a00411129d4ba9b0879db4f6774a017f6d6f5cb31c8be357c",
-           _KSRC + "af_kernels.h": "c59d6e0309e759a0e3d3b52afbcb4cb19fad58711b5fd792c3dfde83d5177102"}
+           _KSRC + "af_kernels.h": "d5aff27a26ae46f6b5620629ef955e376c2932218d3d34ab60bc23c6d5ae1b0f"}
 PV_TRAFFIC = {"bytes_per_cell": 150.7, "profile": "profiles/pointvalue_flux_vortex2048.md",
               "sha256": dict(_SHARED, **{_KSRC + "af_pointvalue.cu":
-                                         "ed707f206b8c333290e8186217f07bc36cdc07d5c470470663976d7b4af2db32"})}
-FLUX_TRAFFIC = {"bytes_per_cell": 207.4, "profile": "profiles/pointvalue_flux_vortex2048.md",
+                                         "1de54a4c5d302de7795d3f54228efc325f4967210deeec38990dd5282e6ee538"})}
+FLUX_TRAFFIC = {"bytes_per_cell": 207.3, "profile": "profiles/pointvalue_flux_vortex2048.md",
                 "sha256": dict(_SHARED, **{_KSRC + "af_flux.cu":
                                            "0a6795c5641e75f5ddeb809da2b20eac719378e73a8c240509406ffd11c0b9b9"})}
 
