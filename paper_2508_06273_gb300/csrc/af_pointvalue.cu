@@ -429,12 +429,12 @@ __device__ __forceinline__ void node_in_cell(int right, int top, float &xn, floa
 // linearisation state fails; the value is then not an EG2 value).
 template <int K>
 __device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int lj, const float Kr[4],
-                                    const float ul[4], float tau, float out[4]) {
-  if (!(ul[0] > 0.0f && ul[3] > 0.0f && tau > 0.0f)) {
-#pragma unroll
-    for (int v = 0; v < NV; v++) out[v] = __int_as_float(0x7fc00000);
-    return true;
-  }
+                                    const float ul_in[4], float tau, float out[4]) {
+  // an inadmissible linearisation state gives NaN outputs; the arithmetic
+  // runs on a harmless substitute so that no branch splits the evaluation
+  const bool good = ul_in[0] > 0.0f && ul_in[3] > 0.0f && tau > 0.0f;
+  const float ul[4] = {good ? ul_in[0] : 1.0f, good ? ul_in[1] : 0.0f, good ? ul_in[2] : 0.0f,
+                       good ? ul_in[3] : 1.0f};
   const float cp = sqrtf(g.gamma * ul[3] / ul[0]);
   const float R = cp * tau, icp = 1.0f / cp;
   const float am = ul[1] * icp, bm = ul[2] * icp;
@@ -563,6 +563,11 @@ __device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int 
   out[1] = Kr[1] + INV_PI * o[1];
   out[2] = Kr[2] + INV_PI * o[2];
   out[3] = Kr[3] - dpP + INV_PI * o[3];
+  if (!good) {
+#pragma unroll
+    for (int v = 0; v < NV; v++) out[v] = __int_as_float(0x7fc00000);
+    return true;
+  }
   return inside;
 }
 
