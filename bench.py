@@ -54,7 +54,7 @@ _SHARED = {_KSRC + "af_common.cuh": "ad367efa0749a42a00411129d4ba9b0879db4f6774a
            _KSRC + "af_kernels.h": "d5aff27a26ae46f6b5620629ef955e376c2932218d3d34ab60bc23c6d5ae1b0f"}
 PV_TRAFFIC = {"bytes_per_cell": 150.7, "profile": "profiles/pointvalue_flux_vortex2048.md",
               "sha256": dict(_SHARED, **{_KSRC + "af_pointvalue.cu":
-                                         "1de54a4c5d302de7795d3f54228efc325f4967210deeec38990dd5282e6ee538"})}
+                                         "19aad50c8609d27f94141de41e79747e75e702385c731e541fcc4490d3fc540a"})}
 FLUX_TRAFFIC = {"bytes_per_cell": 207.3, "profile": "profiles/pointvalue_flux_vortex2048.md",
                 "sha256": dict(_SHARED, **{_KSRC + "af_flux.cu":
                                            "0a6795c5641e75f5ddeb809da2b20eac719378e73a8c240509406ffd11c0b9b9"})}
