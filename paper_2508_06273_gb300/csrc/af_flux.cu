@@ -24,6 +24,7 @@ namespace af {
 namespace {
 
 constexpr int TX = 32, TY = 8;
+constexpr int NTHR = TX * (TY + 2);  // threads of a block: every node loop takes one round
 
 using Args = FluxArgs;
 
@@ -121,8 +122,8 @@ struct FluxSmem {
   float vf[NV][TY + 1][TX + 1], vg[NV][TY + 1][TX + 1];
   float xf[NV][TY][TX + 1], yg[NV][TY + 1][TX];
   float Fx[NV][TY][TX + 1], Gy[NV][TY + 1][TX];
-  float wmax[TX * TY / 32];
-  int wbad[TX * TY / 32];
+  float wmax[NTHR / 32];
+  int wbad[NTHR / 32];
 };
 
 // ---- cell-average flux limiter (Sec. 3.5; the convex-decomposition
@@ -214,7 +215,7 @@ __device__ __noinline__ void limit_tile(const Args &A, FluxSmem &S, LimSmem &L, 
   const Grid &g = A.g;
   const int tid = threadIdx.y * TX + threadIdx.x;
   const float gam = g.gamma, gm1 = gam - 1.0f;
-  for (int k = tid; k < LW * LH; k += TX * TY) {
+  for (int k = tid; k < LW * LH; k += NTHR) {
     const int a = k % LW, b = k / LW, ci = i0 - 2 + a, cj = j0 - 2 + b;
     float Q[4] = {1.0f, 0.0f, 0.0f, 1.0f};  // cells beyond the ghost layers feed no face of the domain
     if (ci <= g.nx + 1 && cj <= g.ny + 1)
@@ -230,14 +231,14 @@ __device__ __noinline__ void limit_tile(const Args &A, FluxSmem &S, LimSmem &L, 
     L.ay[b][a] = ok ? fabsf(U[2]) + c : 0.0f;
   }
   __syncthreads();
-  for (int k = tid; k < (LW - 2) * (LH - 2); k += TX * TY) {
+  for (int k = tid; k < (LW - 2) * (LH - 2); k += NTHR) {
     const int a = k % (LW - 2) + 1, b = k / (LW - 2) + 1;
     L.sum[b - 1][a - 1] = A.lx * (fmaxf(L.ax[b][a - 1], L.ax[b][a]) + fmaxf(L.ax[b][a], L.ax[b][a + 1])) +
                           A.ly * (fmaxf(L.ay[b - 1][a], L.ay[b][a]) + fmaxf(L.ay[b][a], L.ay[b + 1][a]));
   }
   __syncthreads();
   bool limited = false;
-  for (int k = tid; k < (TX + 1) * TY; k += TX * TY) {  // x-faces (i0 + fa - 1/2, j0 + fb)
+  for (int k = tid; k < (TX + 1) * TY; k += NTHR) {  // x-faces (i0 + fa - 1/2, j0 + fb)
     const int fa = k % (TX + 1), fb = k / (TX + 1);
     if (i0 + fa > g.nx || j0 + fb >= g.ny) continue;
     float QL[4], QR[4];
@@ -250,7 +251,7 @@ __device__ __noinline__ void limit_tile(const Args &A, FluxSmem &S, LimSmem &L, 
     const float al = fmaxf(L.ax[fb + 2][fa + 1], L.ax[fb + 2][fa + 2]);
     limited |= limit_face(F, QL, QR, al, L.sum[fb + 1][fa], L.sum[fb + 1][fa + 1], 0, gam);
   }
-  for (int k = tid; k < TX * (TY + 1); k += TX * TY) {  // y-faces (i0 + fa, j0 + fb - 1/2)
+  for (int k = tid; k < TX * (TY + 1); k += NTHR) {  // y-faces (i0 + fa, j0 + fb - 1/2)
     const int fa = k % TX, fb = k / TX;
     if (i0 + fa >= g.nx || j0 + fb > g.ny) continue;
     float QS[4], QN[4];
@@ -283,7 +284,7 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L
 
   // time-integrated node fluxes; nodes up to index nx / ny (periodic
   // duplicates included)
-  for (int k = tid; k < (TX + 1) * (TY + 1); k += TX * TY) {
+  for (int k = tid; k < (TX + 1) * (TY + 1); k += NTHR) {
     const int a = k % (TX + 1), b = k / (TX + 1), i = i0 + a, j = j0 + b;
     float F[4] = {0, 0, 0, 0}, Gf[4] = {0, 0, 0, 0};
     if (i <= g.nx && j <= g.ny) time_flux_fg(A, i, j, gm1i, F, Gf, smax, sbad);
@@ -293,14 +294,14 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L
       vg[v][b][a] = Gf[v];
     }
   }
-  for (int k = tid; k < (TX + 1) * TY; k += TX * TY) {
+  for (int k = tid; k < (TX + 1) * TY; k += NTHR) {
     const int a = k % (TX + 1), b = k / (TX + 1), i = i0 + a, j = j0 + b;
     float F[4] = {0, 0, 0, 0};
     if (i <= g.nx && j < g.ny) time_flux(A, XE, i, j, 0, true, gm1i, F, smax, sbad);
 #pragma unroll
     for (int v = 0; v < NV; v++) xf[v][b][a] = F[v];
   }
-  for (int k = tid; k < TX * (TY + 1); k += TX * TY) {
+  for (int k = tid; k < TX * (TY + 1); k += NTHR) {
     const int a = k % TX, b = k / TX, i = i0 + a, j = j0 + b;
     float F[4] = {0, 0, 0, 0};
     if (i < g.nx && j <= g.ny) time_flux(A, YE, i, j, 1, true, gm1i, F, smax, sbad);
@@ -310,12 +311,12 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L
   __syncthreads();
   // face fluxes, each formed once per tile
   const float w36 = 1.0f / 36.0f;
-  for (int k = tid; k < (TX + 1) * TY; k += TX * TY) {
+  for (int k = tid; k < (TX + 1) * TY; k += NTHR) {
     const int a = k % (TX + 1), b = k / (TX + 1);
 #pragma unroll
     for (int v = 0; v < NV; v++) Fx[v][b][a] = (vf[v][b][a] + 4.0f * xf[v][b][a] + vf[v][b + 1][a]) * w36;
   }
-  for (int k = tid; k < TX * (TY + 1); k += TX * TY) {
+  for (int k = tid; k < TX * (TY + 1); k += NTHR) {
     const int a = k % TX, b = k / TX;
 #pragma unroll
     for (int v = 0; v < NV; v++) Gy[v][b][a] = (vg[v][b][a] + 4.0f * yg[v][b][a] + vg[v][b][a + 1]) * w36;
@@ -327,7 +328,7 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L
   }
   // finite-volume update on the (hi, lo) pair in double-word arithmetic
   const int a = threadIdx.x, b = threadIdx.y, i = i0 + a, j = j0 + b;
-  const bool inside = i < g.nx && j < g.ny;
+  const bool inside = b < TY && i < g.nx && j < g.ny;
   float qh[4] = {1.0f, 0.0f, 0.0f, 1.0f};
   bool bad = false;
   if (inside) {
@@ -365,7 +366,7 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L
   if (tid == 0) {
     float m = 0.0f;
     int b = 0;
-    for (int w = 0; w < TX * TY / 32; w++) {
+    for (int w = 0; w < NTHR / 32; w++) {
       m = fmaxf(m, wmax[w]);
       b |= wbad[w];
     }
@@ -374,14 +375,16 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L
   }
 }
 
-// 6 resident blocks per SM (40 registers a thread): the kernel streams
-// ~200 B a cell, and the extra warps keep more loads in flight
-__global__ void __launch_bounds__(TX *TY, 6) flux_update_kernel(Args A) {
+// 320 threads for a 32 x 8-cell tile: each of the three node loops (297,
+// 264 and 288 nodes) takes one round of loads, where 256 threads needed a
+// second, serial round for some; the two extra warps skip the cell update.
+// 32 registers a thread: six resident blocks per SM keep the loads in flight.
+__global__ void __launch_bounds__(NTHR, 4) flux_update_kernel(Args A) {
   __shared__ FluxSmem S;
   flux_tile<false>(A, S, nullptr, blockIdx.x * TX, blockIdx.y * TY);
 }
 
-__global__ void __launch_bounds__(TX *TY) flux_limited_kernel(Args A) {
+__global__ void __launch_bounds__(NTHR) flux_limited_kernel(Args A) {
   __shared__ FluxSmem S;
   __shared__ LimSmem L;
   flux_tile<true>(A, S, &L, blockIdx.x * TX, blockIdx.y * TY);
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(TX *TY) flux_limited_kernel(Args A) {
 
 // batched form: tile B.tiles[b] = (instance, i0, j0); the instance's dt
 // ratios come from its control block
-__global__ void __launch_bounds__(TX *TY, 6) flux_batch_kernel(FluxBatch B) {
+__global__ void __launch_bounds__(NTHR, 4) flux_batch_kernel(FluxBatch B) {
   __shared__ FluxSmem S;
   __shared__ Args A;
   const int4 t = B.tiles[blockIdx.x];
@@ -421,7 +424,7 @@ __global__ void __launch_bounds__(256) snapshot_batch_kernel(FluxBatch B) {
     dst[e] = src[e];
 }
 
-__global__ void __launch_bounds__(TX *TY) flux_batch_limited_kernel(FluxBatch B) {
+__global__ void __launch_bounds__(NTHR) flux_batch_limited_kernel(FluxBatch B) {
   __shared__ FluxSmem S;
   __shared__ LimSmem L;
   __shared__ Args A;
@@ -480,7 +483,7 @@ cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &
   }
   cudaMemsetAsync(speed, 0, sizeof(unsigned), s);
   cudaMemsetAsync(speed_bad, 0, sizeof(int), s);
-  dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY), blk(TX, TY);
+  dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY), blk(TX, TY + 2);
   if (flux_limiter) flux_limited_kernel<<<grd, blk, 0, s>>>(A);
   else flux_update_kernel<<<grd, blk, 0, s>>>(A);
   return cudaGetLastError();
@@ -495,11 +498,11 @@ cudaError_t launch_snapshot_batch(const FluxBatch &B, int n, cudaStream_t s) {
 cudaError_t launch_flux_batch(const FluxBatch &B, int nplain, int ntiles, cudaStream_t s) {
   static_assert(TX == FLUX_TX && TY == FLUX_TY, "tile list shape");
   if (nplain < 0 || nplain > ntiles) return cudaErrorInvalidValue;
-  if (nplain > 0) flux_batch_kernel<<<nplain, dim3(TX, TY), 0, s>>>(B);
+  if (nplain > 0) flux_batch_kernel<<<nplain, dim3(TX, TY + 2), 0, s>>>(B);
   if (ntiles > nplain) {
     FluxBatch L = B;
     L.tiles = B.tiles + nplain;
-    flux_batch_limited_kernel<<<ntiles - nplain, dim3(TX, TY), 0, s>>>(L);
+    flux_batch_limited_kernel<<<ntiles - nplain, dim3(TX, TY + 2), 0, s>>>(L);
   }
   return cudaGetLastError();
 }
