@@ -57,7 +57,7 @@ PV_TRAFFIC = {"bytes_per_cell": 150.7, "profile": "profiles/pointvalue_flux_vort
                                          "19aad50c8609d27f94141de41e79747e75e702385c731e541fcc4490d3fc540a"})}
 FLUX_TRAFFIC = {"bytes_per_cell": 207.3, "profile": "profiles/pointvalue_flux_vortex2048.md",
                 "sha256": dict(_SHARED, **{_KSRC + "af_flux.cu":
-                                           "0a6795c5641e75f5ddeb809da2b20eac719378e73a8c240509406ffd11c0b9b9"})}
+                                           "a11ef8610691fb3a956c0141ca3bcc6bf70eed63fcd9b11ee0ac548df8c4e706"})}
 
 
 def measured_traffic(spec, cells):
