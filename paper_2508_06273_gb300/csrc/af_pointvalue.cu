@@ -195,90 +195,6 @@ __device__ __forceinline__ void jtable(float t0, float c0, float s0, float t1, f
   J[2][4] = (Dcs5 + J[0][4]) * (1.0f / 6.0f);
 }
 
-__device__ __forceinline__ float pick(const float v[4], int k) {
-  return k == 0 ? v[0] : (k == 1 ? v[1] : (k == 2 ? v[2] : v[3]));
-}
-__device__ __forceinline__ void cswap(float t[4], float c[4], float s[4], int a, int b) {
-  if (t[b] < t[a]) {
-    float x = t[a]; t[a] = t[b]; t[b] = x;
-    x = c[a]; c[a] = c[b]; c[b] = x;
-    x = s[a]; s[a] = s[b]; s[b] = x;
-  }
-}
-
-// Crossings of the circle with the grid lines through the node, sorted by
-// angle in (-pi, pi]; am = u'/c' (vertical line), bm = v'/c' (horizontal
-// line).  Also returns al = acos(am) (0 when the vertical line is not
-// crossed) and be = asin(bm) (when the horizontal line is crossed).
-template <int K>
-__device__ __forceinline__ int crossings(float am, float bm, float t[4], float c[4], float s[4],
-                                         float &al, float &be) {
-  int n = 0;
-  al = 0.0f;
-  be = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    t[k] = 1e30f;
-    c[k] = 0.0f;
-    s[k] = 0.0f;
-  }
-  if (K != YE && fabsf(am) < 1.0f) {
-    al = acosf(am);
-    const float sq = sqrtf(fmaxf(0.0f, 1.0f - am * am));
-    t[0] = al; c[0] = am; s[0] = sq;
-    t[1] = -al; c[1] = am; s[1] = -sq;
-    n = 2;
-  }
-  if (K != XE && fabsf(bm) < 1.0f) {
-    be = asinf(bm);
-    const float sq = sqrtf(fmaxf(0.0f, 1.0f - bm * bm));
-    float t2 = PI_F - be;
-    if (t2 > PI_F) t2 -= 2.0f * PI_F;
-    t[2] = be; c[2] = sq; s[2] = bm;
-    t[3] = t2; c[3] = -sq; s[3] = bm;
-    n += 2;
-  }
-  cswap(t, c, s, 0, 1);
-  cswap(t, c, s, 2, 3);
-  cswap(t, c, s, 0, 2);
-  cswap(t, c, s, 1, 3);
-  cswap(t, c, s, 1, 2);
-  return n;
-}
-
-// angle d - 2 pi floor(d / 2 pi), in [0, 2 pi)
-__device__ __forceinline__ float wrap_2pi(float d) {
-  return fmaf(-2.0f * PI_F, floorf(d * (0.5f / PI_F)), d);
-}
-
-// End points of arc k (of narcs) and the side of each line it lies on.  The
-// circle point at angle theta is right of the vertical line iff theta is in
-// (-al, al) and above the horizontal line iff theta is in (be, pi - be), mod
-// 2 pi; the test is made at the arc's mid angle, which lies strictly inside
-// one cell for every arc of positive length.
-template <int K>
-__device__ __forceinline__ void arc(int k, int ncross, float am, float bm, float al, float be,
-                                    const float t[4], const float c[4], const float s[4], float &t0,
-                                    float &c0, float &s0, float &t1, float &c1, float &s1, int &right,
-                                    int &top) {
-  if (ncross == 0) {  // whole circle on one side of every line
-    t0 = -PI_F; c0 = -1.0f; s0 = 0.0f;
-    t1 = PI_F; c1 = -1.0f; s1 = 0.0f;
-    right = am < 0.0f;
-    top = bm < 0.0f;
-    return;
-  }
-  t0 = pick(t, k); c0 = pick(c, k); s0 = pick(s, k);
-  const int k1 = k + 1 < ncross ? k + 1 : 0;
-  t1 = pick(t, k1); c1 = pick(c, k1); s1 = pick(s, k1);
-  if (k1 == 0) t1 += 2.0f * PI_F;
-  const float mid = 0.5f * (t0 + t1);
-  if (K != YE) right = fabsf(am) < 1.0f ? (wrap_2pi(mid + al) < 2.0f * al) : (am < 0.0f);
-  else right = 0;
-  if (K != XE) top = fabsf(bm) < 1.0f ? (wrap_2pi(mid - be) < PI_F - 2.0f * be) : (bm < 0.0f);
-  else top = 0;
-}
-
 // Taylor shift of q(x) = a0 + a1 x + a2 x^2 to x = x0 + r c:  q = b0 + b1 c + b2 c^2
 __device__ __forceinline__ void shift(float a0, float a1, float a2, float x0, float r, float r2,
                                       float &b0, float &b1, float &b2) {
@@ -584,7 +500,7 @@ __device__ __forceinline__ float centre(const float *sm, int a, int b, int v) {
 
 // EG1 (Sec. 3.3) on piecewise-constant primitive averages, relative to Kr
 template <int K>
-__device__ __noinline__ void eg1_pc(const Grid &g, const float *sm, int li, int lj, const float *Kr,
+__device__ __forceinline__ void eg1_pc(const Grid &g, const float *sm, int li, int lj, const float *Kr,
                                     const float *ul, float tau, float *out) {
   if (!(ul[0] > 0.0f && ul[3] > 0.0f && tau > 0.0f)) {
     for (int v = 0; v < NV; v++) out[v] = __int_as_float(0x7fc00000);
@@ -592,31 +508,80 @@ __device__ __noinline__ void eg1_pc(const Grid &g, const float *sm, int li, int 
   }
   const float cp = sqrtf(g.gamma * ul[3] / ul[0]), icp = 1.0f / cp;
   const float am = ul[1] * icp, bm = ul[2] * icp;
-  float t[4], c[4], s[4], al, be;
-  const int ncross = crossings<K>(am, bm, t, c, s, al, be);
-  const int narcs = ncross > 0 ? ncross : 1;
-  float P0 = 0, P10 = 0, P01 = 0, UC = 0, VS = 0, U20 = 0, U00 = 0, U11 = 0, V11 = 0, V02 = 0, V00 = 0;
-  for (int k = 0; k < narcs; k++) {
-    float t0, c0, s0, t1, c1, s1;
-    int right, top, a, b;
-    arc<K>(k, ncross, am, bm, al, be, t, c, s, t0, c0, s0, t1, c1, s1, right, top);
+  // the arc sums by inclusion-exclusion, as for EG2 (see "EG2 arc sums by
+  // inclusion-exclusion"): with constant data per cell only cos^m sin^n,
+  // m + n <= 2, enter; whole circle (1, cos^2, sin^2) = (2 pi, pi, pi); the
+  // X half-circle (-al, al) and the Y half-circle (asin b, pi - asin b) give
+  // theirs in closed form, zero for a line the circle misses; the quarter arc
+  // X and Y from its end points
+  const float fx = (K != YE && ul[1] < 0.0f) ? -1.0f : 1.0f, fy = (K != XE && ul[2] < 0.0f) ? -1.0f : 1.0f;
+  const float ax = fminf(fabsf(am), 1.0f), by = fminf(fabsf(bm), 1.0f);
+  const float alx = acosf(ax), snx = sqrtf(fmaxf(0.0f, fmaf(-ax, ax, 1.0f)));
+  const float aly = acosf(by), sny = sqrtf(fmaxf(0.0f, fmaf(-by, by, 1.0f)));
+  // [J00, J10, J01, J20, J11, J02] of each set, reflected frame
+  const float X[6] = {2.0f * alx, 2.0f * snx, 0.0f, fmaf(ax, snx, alx), 0.0f, fmaf(-ax, snx, alx)};
+  const float Y[6] = {2.0f * aly, 0.0f, 2.0f * sny, fmaf(-by, sny, aly), 0.0f, fmaf(by, sny, aly)};
+  float Q[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  if (K == VTX && fmaf(ax, ax, by * by) < 1.0f) {
+    // from (cos, sin) = (sny, by) at pi/2 - aly to (ax, snx) at alx
+    Q[0] = alx + aly - 0.5f * PI_F;
+    Q[1] = snx - by;
+    Q[2] = sny - ax;
+    Q[3] = 0.5f * (ax * snx - sny * by + Q[0]);
+    Q[4] = 0.5f * (snx * snx - by * by);
+    Q[5] = Q[0] - Q[3];
+  }
+  // cell values relative to Kr by side (px, py) of the reflected frame
+  auto dval = [&](int px, int py, float d[4]) {
+    const int right = px ? (fx > 0.0f) : (fx < 0.0f), top = py ? (fy > 0.0f) : (fy < 0.0f);
+    int a, b;
     arc_cell<K>(li, lj, right, top, a, b);
     const float4 w = ubar4(sm, a, b);
-    const float d[4] = {w.x - Kr[0], w.y - Kr[1], w.z - Kr[2], w.w - Kr[3]};
-    const float J00 = t1 - t0, J10 = s1 - s0, J01 = c0 - c1;
-    const float J20 = 0.5f * (c1 * s1 - c0 * s0 + J00), J02 = J00 - J20, J11 = 0.5f * (s1 * s1 - s0 * s0);
-    P0 += d[3] * J00;
-    P10 += d[3] * J10;
-    P01 += d[3] * J01;
-    UC += d[1] * J10;
-    VS += d[2] * J01;
-    U20 += d[1] * J20;
-    U00 += d[1] * J00;
-    U11 += d[1] * J11;
-    V11 += d[2] * J11;
-    V02 += d[2] * J02;
-    V00 += d[2] * J00;
+    d[0] = w.x - Kr[0];
+    d[1] = w.y - Kr[1];
+    d[2] = w.z - Kr[2];
+    d[3] = w.w - Kr[3];
+  };
+  // M[w][v] = sum over the cells' arcs of d_v J_w
+  float M[6][4], d0[4], dx[4], dy[4], dq[4];
+  dval(0, 0, d0);
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    M[0][v] = 2.0f * PI_F * d0[v];
+    M[1][v] = M[2][v] = M[4][v] = 0.0f;
+    M[3][v] = M[5][v] = PI_F * d0[v];
   }
+  if (K != YE) {
+    dval(1, 0, dx);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const float e = dx[v] - d0[v];
+#pragma unroll
+      for (int w = 0; w < 6; w++) M[w][v] = fmaf(e, X[w], M[w][v]);
+    }
+  }
+  if (K != XE) {
+    dval(0, 1, dy);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const float e = dy[v] - d0[v];
+#pragma unroll
+      for (int w = 0; w < 6; w++) M[w][v] = fmaf(e, Y[w], M[w][v]);
+    }
+  }
+  if (K == VTX) {
+    dval(1, 1, dq);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const float e = dq[v] - dx[v] - dy[v] + d0[v];
+#pragma unroll
+      for (int w = 0; w < 6; w++) M[w][v] = fmaf(e, Q[w], M[w][v]);
+    }
+  }
+  // back to the grid frame: odd in cos changes sign with fx, odd in sin with fy
+  const float P0 = M[0][3], P10 = fx * M[1][3], P01 = fy * M[2][3];
+  const float UC = fx * M[1][1], VS = fy * M[2][2], U20 = M[3][1], U00 = M[0][1], U11 = fx * fy * M[4][1];
+  const float V11 = fx * fy * M[4][2], V02 = M[5][2], V00 = M[0][2];
   // value at P'; on a grid line the mean of the cells whose closure holds it
   float dP[4] = {0, 0, 0, 0};
   {
@@ -745,6 +710,25 @@ __device__ __noinline__ bool in_node_bounds(const float *sm, int li, int lj, con
     phi = fmaxf(phi, w.w);
   }
   return U[0] >= NB_ETA * rlo && U[0] <= rhi / NB_ETA && U[3] >= NB_ETA * plo && U[3] <= phi / NB_ETA;
+}
+
+// the blend's low-order value: EG1 on pc data inline (it is short and
+// branch-free), the rest of Alg. 3's chain behind a call only if that fails
+template <int K>
+__device__ __forceinline__ void blend_low(const Args &A, const float *sm, int i, int j, int li, int lj, float tau,
+                                          const float *Kr, float *res, unsigned *cnt) {
+  if (A.force_lo != 2) {
+    float ul[4], lo[4];
+    lin_avg<K>(sm, li, lj, ul);
+    eg1_pc<K>(A.g, sm, li, lj, Kr, ul, tau, lo);
+    if (admissible(lo)) {
+      cnt[CNT_EG1]++;
+#pragma unroll
+      for (int v = 0; v < NV; v++) res[v] = lo[v];
+      return;
+    }
+  }
+  limit<K>(A, sm, i, j, li, lj, tau, Kr, res, cnt);
 }
 
 // Alg. 2 indicator of the vertex at tile-local cell corner (a, b): the
@@ -889,7 +873,7 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
       // blend with the low-order value of Alg. 3's chain (EG1 on pc data,
       // else Lax-Friedrichs, else the t^n value): both ends admissible
       float lo[4];
-      limit<K>(A, sm, i, j, li, lj, tau, U0, lo, cnt);
+      blend_low<K>(A, sm, i, j, li, lj, tau, U0, lo, cnt);
 #pragma unroll
       for (int v = 0; v < NV; v++) res[v] = th * res[v] + (1.0f - th) * lo[v];
     }

@@ -226,16 +226,21 @@ MILD = [(1.0, 0.1, -0.1, 1.0), (0.9, -0.15, 0.05, 1.1), (1.1, 0.05, 0.15, 0.95),
 
 
 @pytest.mark.parametrize("force", [1, 2])
-@pytest.mark.parametrize("data", ["mild_quadrants", "fourier"])
+@pytest.mark.parametrize("data", ["mild_quadrants", "fourier", "supersonic_xy", "supersonic_y", "outside_neg",
+                                  "inside_neg"])
 def test_low_order_paths_parity(env, force, data):
     """Alg. 3's EG1-on-pc and Lax-Friedrichs updates, forced at every node,
     on data where every EG1 value is clearly admissible (so FP32 and FP64
-    take the same branches)."""
+    take the same branches); the flows cover every way the Mach circle can
+    meet the grid lines (no line, one line, both with the node outside or
+    inside the circle) and both signs of the velocity."""
     torch, af, oracle = env
     if data == "fourier":
         prob = W.fourier_smooth(30, 26, seed=7)
-    else:
+    elif data == "mild_quadrants":
         prob = W.four_quadrant(24, states=MILD)
+    else:
+        prob = SMOOTH[data]()
     st = W.to_f32(W.discretise(prob))
     opts = {"force_lo": force, "tsw": 0, "shock_blend": 0, "flux_limiter": 0}
     o = make_oracle(oracle, prob, opts, state=st)
