@@ -91,6 +91,14 @@ __device__ __forceinline__ void ld4(const Args &A, const float *p, int i, int j,
   for (int v = 0; v < NV; v++) U[v] = ld(A, p, v, i, j);
 }
 
+__device__ __forceinline__ float4 pack4(const float U[4]) { return make_float4(U[0], U[1], U[2], U[3]); }
+__device__ __forceinline__ void unpack4(float4 w, float U[4]) {
+  U[0] = w.x;
+  U[1] = w.y;
+  U[2] = w.z;
+  U[3] = w.w;
+}
+
 // shared-memory cell record of tile-local cell (a, b), a in [0, HX), b in [0, HY)
 __device__ __forceinline__ const float *cell_rec(const float *sm, int a, int b) {
   return sm + (b * HX + a) * CELL_F;
@@ -628,7 +636,7 @@ __device__ __forceinline__ void rusanov(const float *L, const float *R, float ga
 // Lax-Friedrichs update of a point value from the same-type point values one
 // mesh width away (Alg. 3, last resort), converted back to primitive form
 template <int K>
-__device__ __noinline__ void lf_node(const Args &A, int i, int j, float tau, float *out) {
+__device__ __noinline__ float4 lf_node(const Args &A, int i, int j, float tau) {
   const Grid &g = A.g;
   const float *a = A.n0[K];
   float U0[4], W[4], E[4], S[4], N[4], FW[4], FE[4], GS[4], GN[4], Q[4];
@@ -644,7 +652,9 @@ __device__ __noinline__ void lf_node(const Args &A, int i, int j, float tau, flo
   p2c(U0, 1.0f / (g.gamma - 1.0f), Q);
   const float lx = tau * g.idx, ly = tau * g.idy;
   for (int v = 0; v < NV; v++) Q[v] = Q[v] - lx * (FE[v] - FW[v]) - ly * (GN[v] - GS[v]);
+  float out[4];
   c2p(Q, g.gamma - 1.0f, out);
+  return pack4(out);
 }
 
 // averaged linearisation state, eq. (Un+1/2)
@@ -667,38 +677,38 @@ __device__ __forceinline__ void lin_avg(const float *sm, int li, int lj, float u
 }
 
 // Alg. 3 for one time level: EG1 on pc data with the averaged linearisation,
-// else Lax-Friedrichs, else the node's t^n value (the high-order value failed)
+// else Lax-Friedrichs, else the node's t^n value Kr (the high-order value
+// failed).  The calls behind which the rare paths sit take and return values,
+// never addresses: an array whose address is passed lives in local memory for
+// the whole kernel, taken path or not.  The events met here are counted with
+// atomics (they are rare).
 template <int K>
-__device__ __noinline__ void limit(const Args &A, const float *sm, int i, int j, int li, int lj,
-                                   float tau, const float *Kr, float *res, unsigned *cnt) {
+__device__ __noinline__ float4 limit(const Args &A, const float *sm, int i, int j, int li, int lj, float tau,
+                                     float4 Kr4) {
+  const float Kr[4] = {Kr4.x, Kr4.y, Kr4.z, Kr4.w};
   if (A.force_lo != 2) {
     float ul[4], lo[4];
     lin_avg<K>(sm, li, lj, ul);
     eg1_pc<K>(A.g, sm, li, lj, Kr, ul, tau, lo);
-    cnt[CNT_EG1]++;
-    if (admissible(lo)) {
-      for (int v = 0; v < NV; v++) res[v] = lo[v];
-      return;
-    }
+    atomicAdd(&A.counters[CNT_EG1], 1ull);
+    if (admissible(lo)) return pack4(lo);
   }
-  float lf[4];
-  lf_node<K>(A, i, j, tau, lf);
-  cnt[CNT_LF]++;
-  if (admissible(lf)) {
-    for (int v = 0; v < NV; v++) res[v] = lf[v];
-    return;
-  }
-  for (int v = 0; v < NV; v++) res[v] = Kr[v];
-  cnt[CNT_KEPT]++;
+  const float4 lf4 = lf_node<K>(A, i, j, tau);
+  const float lf[4] = {lf4.x, lf4.y, lf4.z, lf4.w};
+  atomicAdd(&A.counters[CNT_LF], 1ull);
+  if (admissible(lf)) return lf4;
+  atomicAdd(&A.counters[CNT_KEPT], 1ull);
+  atomicOr(A.status, ST_KEPT);
+  return Kr4;
 }
 
 // node bounds (with the option on): rho and p within [NB_ETA min, max / NB_ETA]
 // of the node's own t^n value U0 and the primitive averages of its cells
 constexpr float NB_ETA = 0.1f;
 template <int K>
-__device__ __noinline__ bool in_node_bounds(const float *sm, int li, int lj, const float *U0, const float *U) {
+__device__ __noinline__ bool in_node_bounds(const float *sm, int li, int lj, float4 U0, float4 U) {
   const int a = li + 1, b = lj + 1;
-  float rlo = U0[0], rhi = U0[0], plo = U0[3], phi = U0[3];
+  float rlo = U0.x, rhi = U0.x, plo = U0.w, phi = U0.w;
   const int ncell = K == VTX ? 4 : 2;
   for (int q = 0; q < ncell; q++) {
     const int ca = K == VTX ? a - 1 + (q & 1) : (K == XE ? a - 1 + q : a);
@@ -709,7 +719,7 @@ __device__ __noinline__ bool in_node_bounds(const float *sm, int li, int lj, con
     plo = fminf(plo, w.w);
     phi = fmaxf(phi, w.w);
   }
-  return U[0] >= NB_ETA * rlo && U[0] <= rhi / NB_ETA && U[3] >= NB_ETA * plo && U[3] <= phi / NB_ETA;
+  return U.x >= NB_ETA * rlo && U.x <= rhi / NB_ETA && U.w >= NB_ETA * plo && U.w <= phi / NB_ETA;
 }
 
 // the blend's low-order value: EG1 on pc data inline (it is short and
@@ -728,7 +738,7 @@ __device__ __forceinline__ void blend_low(const Args &A, const float *sm, int i,
       return;
     }
   }
-  limit<K>(A, sm, i, j, li, lj, tau, Kr, res, cnt);
+  unpack4(limit<K>(A, sm, i, j, li, lj, tau, pack4(Kr)), res);
 }
 
 // Alg. 2 indicator of the vertex at tile-local cell corner (a, b): the
@@ -862,9 +872,9 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
     // Alg. 3 (a value from a Mach cone outside the block counts as not
     // admissible, and, with the option, one outside the node's bounds)
     bool ok = inb && admissible(ho);
-    if (ok && A.node_bounds) ok = in_node_bounds<K>(sm, li, lj, U0, ho);
+    if (ok && A.node_bounds) ok = in_node_bounds<K>(sm, li, lj, pack4(U0), pack4(ho));
     if (A.force_lo || (A.limiter && !ok)) {
-      limit<K>(A, sm, i, j, li, lj, tau, U0, res, cnt);
+      unpack4(limit<K>(A, sm, i, j, li, lj, tau, pack4(U0)), res);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; v++) res[v] = ho[v];
@@ -910,7 +920,8 @@ __device__ __forceinline__ void tile_nodes(const Args &A, const float *sm, const
   node_update<VTX, TY>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
   node_update<XE, TY>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
   node_update<YE, TY>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite);
-  const int st = (cfl_bad ? ST_CFL : 0) | (nonfinite ? ST_NONFINITE : 0) | (cnt[CNT_KEPT] ? ST_KEPT : 0);
+  // (the limiter reports its own kept values and Lax-Friedrichs fall-backs)
+  const int st = (cfl_bad ? ST_CFL : 0) | (nonfinite ? ST_NONFINITE : 0);
   if (st) atomicOr(A.status, st);
 #pragma unroll
   for (int k = 0; k < 4; k++)
@@ -985,8 +996,18 @@ __device__ __forceinline__ float *tile_smem(float4 *smem4) {
   return reinterpret_cast<float *>((reinterpret_cast<size_t>(smem4) + 127) & ~size_t(127));
 }
 
+// Blocks per SM that the register budget is sized for, the most that the
+// tile's shared memory allows: two for 8 rows (128 registers a thread, 16
+// warps), one for 16 rows (the 512 threads cap it at 128 anyway), three for
+// 4 rows (170 registers, 12 warps).  Without the bound the compiler may take
+// more registers than two 8-row blocks can share.
 template <int TY>
-__global__ void __launch_bounds__(TX *TY) pointvalue_kernel(Args A, const __grid_constant__ TileMaps T) {
+constexpr int min_blocks() {
+  return TY == 4 ? 3 : (TY == 8 ? 2 : 1);
+}
+
+template <int TY>
+__global__ void __launch_bounds__(TX *TY, min_blocks<TY>()) pointvalue_kernel(Args A, const __grid_constant__ TileMaps T) {
   extern __shared__ float4 smem4[];
   __shared__ alignas(8) unsigned long long bar;
   if (A.tile_flag && !A.tile_flag[blockIdx.y * gridDim.x + blockIdx.x]) return;
@@ -997,7 +1018,7 @@ __global__ void __launch_bounds__(TX *TY) pointvalue_kernel(Args A, const __grid
 // instance's arguments and descriptors for the buffer now holding its t^n;
 // instances that have stopped are skipped.
 template <int TY>
-__global__ void __launch_bounds__(TX *TY) pointvalue_batch_kernel(PointValueBatch B) {
+__global__ void __launch_bounds__(TX *TY, min_blocks<TY>()) pointvalue_batch_kernel(PointValueBatch B) {
   extern __shared__ float4 smem4[];
   __shared__ alignas(8) unsigned long long bar;
   __shared__ Args A;
