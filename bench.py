@@ -52,9 +52,9 @@ FLUX_BYTES_PER_CELL = 208
 _KSRC = "paper_2508_06273_gb300/csrc/"
 _SHARED = {_KSRC + "af_common.cuh": "ad367efa0749a42a00411129d4ba9b0879db4f6774a017f6d6f5cb31c8be357c",
            _KSRC + "af_kernels.h": "d5aff27a26ae46f6b5620629ef955e376c2932218d3d34ab60bc23c6d5ae1b0f"}
-PV_TRAFFIC = {"bytes_per_cell": 150.7, "profile": "profiles/pointvalue_flux_vortex2048.md",
+PV_TRAFFIC = {"bytes_per_cell": 150.2, "profile": "profiles/pointvalue_flux_vortex2048.md",
               "sha256": dict(_SHARED, **{_KSRC + "af_pointvalue.cu":
-                                         "8af2163446df58f03d57b175bca520cb63a89c7f3f4584df1c8565566ae80642"})}
+                                         "913514e67d83e4270e8a1c6c57a05d56552a8ca9238e4bf8d630d35c2d9aeb74"})}
 FLUX_TRAFFIC = {"bytes_per_cell": 207.3, "profile": "profiles/pointvalue_flux_vortex2048.md",
                 "sha256": dict(_SHARED, **{_KSRC + "af_flux.cu":
                                            "a11ef8610691fb3a956c0141ca3bcc6bf70eed63fcd9b11ee0ac548df8c4e706"})}
