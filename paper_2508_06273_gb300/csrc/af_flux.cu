@@ -156,9 +156,12 @@ __device__ __forceinline__ bool fl_ok(const float A[4], const float B[4], float 
 }
 
 // largest admissible theta of the face state of a cell with average Q
-__device__ __noinline__ float fl_theta(const float *Q, int dir, float k, const float *Fho, const float *Flo,
-                                       float gam) {
+// (arguments by value: an array whose address a call takes lives in local
+// memory)
+__device__ __noinline__ float fl_theta(float4 Q4, int dir, float k, float4 Fho4, float4 Flo4, float gam) {
   const float gm1 = gam - 1.0f;
+  const float Q[4] = {Q4.x, Q4.y, Q4.z, Q4.w}, Fho[4] = {Fho4.x, Fho4.y, Fho4.z, Fho4.w},
+              Flo[4] = {Flo4.x, Flo4.y, Flo4.z, Flo4.w};
   float U[4], fn[4], A[4], B[4], UA[4];
   c2p(Q, gm1, U);
   phys_flux(U, 1.0f / gm1, dir, fn);
@@ -200,8 +203,9 @@ __device__ __forceinline__ bool limit_face(float *const F[4], const float QL[4],
   for (int v = 0; v < NV; v++) finite = finite && isfinite(Fho[v]);
   float th = 0.0f;
   if (finite) {
-    const float tl = fl_theta(QL, dir, sL / al, Fho, Flo, gam);
-    const float tr = fl_theta(QR, dir, -sR / al, Fho, Flo, gam);
+    const float4 ho = make_float4(Fho[0], Fho[1], Fho[2], Fho[3]), lo = make_float4(Flo[0], Flo[1], Flo[2], Flo[3]);
+    const float tl = fl_theta(make_float4(QL[0], QL[1], QL[2], QL[3]), dir, sL / al, ho, lo, gam);
+    const float tr = fl_theta(make_float4(QR[0], QR[1], QR[2], QR[3]), dir, -sR / al, ho, lo, gam);
     th = fminf(tl, tr);
     if (th >= 1.0f) return false;
   }
@@ -384,7 +388,9 @@ __global__ void __launch_bounds__(NTHR, 4) flux_update_kernel(Args A) {
   flux_tile<false>(A, S, nullptr, blockIdx.x * TX, blockIdx.y * TY);
 }
 
-__global__ void __launch_bounds__(NTHR) flux_limited_kernel(Args A) {
+// (the arguments are grid constants so that the limiter's call can take
+// their address without a local copy)
+__global__ void __launch_bounds__(NTHR, 4) flux_limited_kernel(const __grid_constant__ Args A) {
   __shared__ FluxSmem S;
   __shared__ LimSmem L;
   flux_tile<true>(A, S, &L, blockIdx.x * TX, blockIdx.y * TY);
@@ -392,7 +398,7 @@ __global__ void __launch_bounds__(NTHR) flux_limited_kernel(Args A) {
 
 // batched form: tile B.tiles[b] = (instance, i0, j0); the instance's dt
 // ratios come from its control block
-__global__ void __launch_bounds__(NTHR, 4) flux_batch_kernel(FluxBatch B) {
+__global__ void __launch_bounds__(NTHR, 6) flux_batch_kernel(FluxBatch B) {
   __shared__ FluxSmem S;
   __shared__ Args A;
   const int4 t = B.tiles[blockIdx.x];
@@ -424,7 +430,7 @@ __global__ void __launch_bounds__(256) snapshot_batch_kernel(FluxBatch B) {
     dst[e] = src[e];
 }
 
-__global__ void __launch_bounds__(NTHR) flux_batch_limited_kernel(FluxBatch B) {
+__global__ void __launch_bounds__(NTHR, 4) flux_batch_limited_kernel(FluxBatch B) {
   __shared__ FluxSmem S;
   __shared__ LimSmem L;
   __shared__ Args A;
