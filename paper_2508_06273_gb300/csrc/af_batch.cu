@@ -53,7 +53,10 @@ struct af_batch {
   int4 *d_pv_tiles = nullptr, *d_fx_tiles = nullptr;
   int n_pv_tiles = 0, n_fx_tiles = 0, pv_tiles_h = 0;
   int n_fx_plain = -1;  // flux tiles of instances without the flux limiter (listed first)
-  long long ghost_max = 0;
+  int4 *d_ghost_chunks = nullptr;  // (instance, array, first entry) per ghost-fill block
+  int n_ghost_chunks = 0;
+  int4 *d_theta_tiles = nullptr;   // (instance, a0, b0): shock-indicator tiles of the blending instances
+  int n_theta_tiles = 0, theta_tiles_cap = 0;
   bool maps_ok = false;
   std::vector<GraphEntry> graphs;
   bool any_limiter = false;  // some instance has the flux limiter on
@@ -172,8 +175,28 @@ int upload_args(af_batch *b) {
   if (!b->d_fx_tiles) BCK(cudaMalloc(&b->d_fx_tiles, sizeof(int4) * fxt.size()), "batch: cudaMalloc(tiles)");
   BCK(cudaMemcpy(b->d_fx_tiles, fxt.data(), sizeof(int4) * fxt.size(), cudaMemcpyHostToDevice), "batch: tiles");
   b->n_fx_tiles = (int)fxt.size();
+  // shock-indicator tiles of the instances with the blend on
+  std::vector<int4> tht;
+  for (int k = 0; k < b->n; k++) {
+    const af_ctx *h = b->inst[k];
+    if (!h->opt.shock_blend) continue;
+    for (int b0 = 0; b0 <= h->g.ny + 1; b0 += 8)
+      for (int a0 = 0; a0 <= h->g.nx + 1; a0 += 32) tht.push_back(make_int4(k, a0, b0, 0));
+  }
+  if ((int)tht.size() > b->theta_tiles_cap) {
+    cudaFree(b->d_theta_tiles);
+    b->d_theta_tiles = nullptr;
+    BCK(cudaMalloc(&b->d_theta_tiles, sizeof(int4) * tht.size()), "batch: cudaMalloc(tiles)");
+    b->theta_tiles_cap = (int)tht.size();
+  }
+  if (!tht.empty())
+    BCK(cudaMemcpy(b->d_theta_tiles, tht.data(), sizeof(int4) * tht.size(), cudaMemcpyHostToDevice), "batch: tiles");
+  const int n_theta = (int)tht.size();
   // captured launches differ
-  if (any_lim != b->any_limiter || any_blend != b->any_blend || n_plain != b->n_fx_plain) drop_graphs(b);
+  if (any_lim != b->any_limiter || any_blend != b->any_blend || n_plain != b->n_fx_plain ||
+      n_theta != b->n_theta_tiles)
+    drop_graphs(b);
+  b->n_theta_tiles = n_theta;
   b->n_fx_plain = n_plain;
   b->any_limiter = any_lim;
   b->any_blend = any_blend;
@@ -224,9 +247,12 @@ int enqueue_batch_step(af_batch *b, double *hist, int hist_steps, cudaStream_t s
   G.ctl = b->d_ctl;
   G.grids = b->d_grids;
   G.arrays = b->d_arrays;
-  BCK(launch_ghost_batch(G, b->n, b->ghost_max, s), "batch: ghost fill");
+  G.chunks = b->d_ghost_chunks;
+  BCK(launch_ghost_batch(G, b->n_ghost_chunks, s), "batch: ghost fill");
   if (b->any_blend)
-    BCK(launch_shock_theta_batch(b->d_ctl, b->d_grids, b->d_arrays, b->d_theta, b->n, s), "batch: shock indicator");
+    BCK(launch_shock_theta_batch(b->d_theta_tiles, b->n_theta_tiles, b->d_ctl, b->d_grids, b->d_arrays, b->d_theta,
+                                 s),
+        "batch: shock indicator");
   BCK(launch_pointvalue_batch(pv_batch(b), b->n_pv_tiles, b->tile_h, s), "batch: point values");
   if (b->sampling)
     BCK(launch_sample_batch(b->sampler, b->d_pv_tiles, b->n_pv_tiles, b->tile_h, b->d_ctl, b->d_pv, s),
@@ -297,6 +323,8 @@ void free_batch(af_batch *b) {
   cudaFree(b->d_fx);
   cudaFree(b->d_maps);
   cudaFree(b->d_grids);
+  cudaFree(b->d_ghost_chunks);
+  cudaFree(b->d_theta_tiles);
   cudaFree(b->d_arrays);
   cudaFree(b->d_theta);
   cudaFree(b->d_pv_tiles);
@@ -342,6 +370,7 @@ af_batch *af_batch_create(int n, const int *nx, const int *ny, const double *dx,
   b->speed_ok.assign(n, 0);
   b->stopped.assign(n, 0);
   std::vector<Grid> grids(n);
+  std::vector<int4> chunks;
   for (int k = 0; k < n; k++) {
     BatchCtl &c = b->ctl_h[k];
     std::memset(&c, 0, sizeof(c));
@@ -352,9 +381,11 @@ af_batch *af_batch_create(int n, const int *nx, const int *ny, const double *dx,
     c.h = dx[k] < dy[k] ? dx[k] : dy[k];
     c.cur = b->inst[k]->tmap_cur;
     grids[k] = b->inst[k]->g;
-    const long long gc = ghost_count(grids[k]);
-    if (gc > b->ghost_max) b->ghost_max = gc;
+    for (int arr = 0; arr < 5; arr++)
+      for (long long e = 0; e < ghost_total(grids[k], arr); e += GHOST_CHUNK)
+        chunks.push_back(make_int4(k, arr, (int)e, 0));
   }
+  b->n_ghost_chunks = (int)chunks.size();
   cudaError_t e = cudaMalloc(&b->d_ctl, sizeof(BatchCtl) * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_pv, sizeof(PointValueArgs) * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_fx, sizeof(FluxArgs) * 2 * n);
@@ -363,6 +394,9 @@ af_batch *af_batch_create(int n, const int *nx, const int *ny, const double *dx,
   if (e == cudaSuccess) e = cudaMalloc(&b->d_arrays, sizeof(float *) * 10 * n);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_theta, sizeof(float *) * 2 * n);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_grids, grids.data(), sizeof(Grid) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_ghost_chunks, sizeof(int4) * chunks.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_ghost_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     bcuda(e, "af_batch_create");
     free_batch(b);

@@ -136,6 +136,7 @@ struct GhostBatch {
   const BatchCtl *ctl;
   const Grid *grids;       // [instance]
   float *const *arrays;    // [instance][buffer][5]: avg hi, avg lo, vtx, xe, ye of t^n
+  const int4 *chunks;      // one block each: (instance, array, first ghost entry, 0), 256 entries
 };
 
 // ghost layers of the t^n state (cell averages hi/lo and the three node arrays)
@@ -155,14 +156,17 @@ cudaError_t launch_snapshot_batch(const FluxBatch &B, int n, cudaStream_t s);
 // with the limited one
 cudaError_t launch_flux_batch(const FluxBatch &B, int nplain, int ntiles, cudaStream_t s);
 constexpr int FLUX_TX = 32, FLUX_TY = 8;
-// batched ghost fill; max_per: the largest per-instance ghost count
-cudaError_t launch_ghost_batch(const GhostBatch &B, int n, long long max_per, cudaStream_t s);
-long long ghost_count(const Grid &g);
+// batched ghost fill over nchunks chunks of 256 ghost entries
+cudaError_t launch_ghost_batch(const GhostBatch &B, int nchunks, cudaStream_t s);
+// number of ghost entries of array arr (0 averages hi, 1 averages lo, 2..4 node arrays)
+long long ghost_total(const Grid &g, int arr);
+constexpr int GHOST_CHUNK = 256;
 // Sec. 3.4 blend weights of the edge midpoints (planes of the padded layout)
 cudaError_t launch_shock_theta(const Grid &g, const float *avg_hi, float *tx, float *ty, cudaStream_t s);
-// batched: theta[2k], theta[2k+1] the planes of instance k (NULL: skipped)
-cudaError_t launch_shock_theta_batch(const BatchCtl *ctl, const Grid *grids, const float *const *arrays,
-                                     float *const *theta, int n, cudaStream_t s);
+// batched over tiles (instance, a0, b0) of 32 x 8 entries (a <= nx + 1,
+// b <= ny + 1); theta[2k], theta[2k+1] the planes of instance k (NULL: skipped)
+cudaError_t launch_shock_theta_batch(const int4 *tiles, int ntiles, const BatchCtl *ctl, const Grid *grids,
+                                     const float *const *arrays, float *const *theta, cudaStream_t s);
 // per-instance dt for the coming step (mode DT_STEP; records it into
 // hist[step * n + k] if hist), only the buffer flip of the last step
 // (DT_SETTLE), or dt without advancing anything (DT_PROBE)

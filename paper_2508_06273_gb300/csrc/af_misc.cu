@@ -102,15 +102,18 @@ __global__ void ghost_kernel(GhostArgs A) {
     ghost_entry(A.g, R, A.a[arr], arr, k);
 }
 
-// batched: blockIdx.z is the instance
-__global__ void ghost_batch_kernel(GhostBatch B) {
-  const int inst = blockIdx.z, arr = blockIdx.y;
+// batched: block b fills chunk B.chunks[b] = (instance, array, first entry)
+// (a list of exactly the blocks that have work, where a grid sized for the
+// largest instance left most blocks of the small ones empty)
+__global__ void __launch_bounds__(GHOST_CHUNK) ghost_batch_kernel(GhostBatch B) {
+  const int4 c = B.chunks[blockIdx.x];
+  const int inst = c.x, arr = c.y;
   if (!B.ctl[inst].active) return;
-  const Grid g = B.grids[inst];
+  const Grid &g = B.grids[inst];
   const GhostRange R(g, arr);
   float *p = B.arrays[(2 * inst + B.ctl[inst].cur) * 5 + arr];
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < R.total; k += gridDim.x * blockDim.x)
-    ghost_entry(g, R, p, arr, k);
+  const int k = c.z + threadIdx.x;
+  if (k < R.total) ghost_entry(g, R, p, arr, k);
 }
 
 // ---- Sec. 3.4 shock indicator: theta = exp(-phi1 phi2) per edge midpoint,
@@ -151,15 +154,18 @@ __global__ void shock_theta_kernel(Grid g, const float *avg, float *tx, float *t
   if (a > g.nx + 1 || b > g.ny + 1) return;
   theta_entry(g, avg, tx, ty, a, b);
 }
-__global__ void shock_theta_batch_kernel(const BatchCtl *ctl, const Grid *grids, const float *const *avg,
-                                         float *const *theta) {
-  const int inst = blockIdx.z;
+// batched: block k takes tile tiles[k] = (instance, a0, b0) of 32 x 8 entries
+// (tiles only for the instances with the blend on)
+__global__ void __launch_bounds__(256) shock_theta_batch_kernel(const int4 *tiles, const BatchCtl *ctl,
+                                                                const Grid *grids, const float *const *avg,
+                                                                float *const *theta) {
+  const int4 t = tiles[blockIdx.x];
+  const int inst = t.x;
   if (!ctl[inst].active || !theta[2 * inst]) return;
-  const Grid g = grids[inst];
-  const float *hi = avg[(2 * inst + ctl[inst].cur) * 5];
-  for (int b = blockIdx.y * blockDim.y + threadIdx.y; b <= g.ny + 1; b += gridDim.y * blockDim.y)
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a <= g.nx + 1; a += gridDim.x * blockDim.x)
-      theta_entry(g, hi, theta[2 * inst], theta[2 * inst + 1], a, b);
+  const Grid &g = grids[inst];
+  const int a = t.y + threadIdx.x, b = t.z + threadIdx.y;
+  if (a > g.nx + 1 || b > g.ny + 1) return;
+  theta_entry(g, avg[(2 * inst + ctl[inst].cur) * 5], theta[2 * inst], theta[2 * inst + 1], a, b);
 }
 
 // Per-instance dt for the coming step from the wave speed of the current
@@ -341,20 +347,11 @@ cudaError_t launch_ghost_fill(const Grid &g, float *avg_hi, float *avg_lo, const
   return cudaGetLastError();
 }
 
-long long ghost_count(const Grid &g) {
-  long long m = 0;
-  for (int arr = 0; arr < 5; arr++) {
-    const GhostRange R(g, arr);
-    if (R.total > m) m = R.total;
-  }
-  return m;
-}
+long long ghost_total(const Grid &g, int arr) { return GhostRange(g, arr).total; }
 
-cudaError_t launch_ghost_batch(const GhostBatch &B, int n, long long max_per, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  int blocks = (int)((max_per + 255) / 256);
-  if (blocks < 1) blocks = 1;
-  ghost_batch_kernel<<<dim3(blocks, 5, n), 256, 0, s>>>(B);
+cudaError_t launch_ghost_batch(const GhostBatch &B, int nchunks, cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  ghost_batch_kernel<<<nchunks, GHOST_CHUNK, 0, s>>>(B);
   return cudaGetLastError();
 }
 
@@ -364,10 +361,10 @@ cudaError_t launch_shock_theta(const Grid &g, const float *avg_hi, float *tx, fl
   return cudaGetLastError();
 }
 
-cudaError_t launch_shock_theta_batch(const BatchCtl *ctl, const Grid *grids, const float *const *arrays,
-                                     float *const *theta, int n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  shock_theta_batch_kernel<<<dim3(8, 8, n), dim3(32, 8), 0, s>>>(ctl, grids, arrays, theta);
+cudaError_t launch_shock_theta_batch(const int4 *tiles, int ntiles, const BatchCtl *ctl, const Grid *grids,
+                                     const float *const *arrays, float *const *theta, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  shock_theta_batch_kernel<<<ntiles, dim3(32, 8), 0, s>>>(tiles, ctl, grids, arrays, theta);
   return cudaGetLastError();
 }
 
