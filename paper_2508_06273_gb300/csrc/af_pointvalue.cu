@@ -43,6 +43,14 @@ constexpr float PI_F = 3.14159265358979f;
 constexpr float INV_PI = 0.318309886183791f;
 constexpr float INV_2PI = 0.159154943091895f;
 
+// The divisions and square roots on the EG2 / EG1 / correction path use the
+// hardware approximations (__fdividef and rsqrtf, a few ulp) instead of the
+// correctly rounded sequences: they sit on the dependency chain that starts
+// every evaluation (c' -> 1/c' -> the half-circle tables), and the kernel is
+// bound by latency.  sqrt(t) for t >= 0 from the reciprocal square root (0 at
+// t = 0):
+__device__ __forceinline__ float sqrt_nn(float t) { return t > 0.0f ? t * rsqrtf(t) : 0.0f; }
+
 // A tile is TX x TY cells: TX = 32 (one warp along x) and TY rows, TY one
 // of the heights in tile_heights (the batched path picks one by timing).
 constexpr int TX = 32;
@@ -359,8 +367,8 @@ __device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int 
   const bool good = ul_in[0] > 0.0f && ul_in[3] > 0.0f && tau > 0.0f;
   const float ul[4] = {good ? ul_in[0] : 1.0f, good ? ul_in[1] : 0.0f, good ? ul_in[2] : 0.0f,
                        good ? ul_in[3] : 1.0f};
-  const float cp = sqrtf(g.gamma * ul[3] / ul[0]);
-  const float R = cp * tau, icp = 1.0f / cp;
+  const float cp2 = __fdividef(g.gamma * ul[3], ul[0]), icp = rsqrtf(cp2), cp = cp2 * icp;
+  const float R = cp * tau;
   const float am = ul[1] * icp, bm = ul[2] * icp;
   bool inside;
   {
@@ -383,13 +391,13 @@ __device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int 
   if (hx) {
     const float a = fminf(ax, 1.0f);
     alx = acosf(a);
-    snx = sqrtf(fmaxf(0.0f, fmaf(-a, a, 1.0f)));
+    snx = sqrt_nn(fmaf(-a, a, 1.0f));
     half_table(a, snx, alx, Tx);
   }
   if (hy) {
     const float b = fminf(by, 1.0f);
     aly = acosf(b);
-    sny = sqrtf(fmaxf(0.0f, fmaf(-b, b, 1.0f)));
+    sny = sqrt_nn(fmaf(-b, b, 1.0f));
     half_table(b, sny, aly, Ty);
   }
   // X and Y meet in (asin b, acos a): (cos, sin) = (sin aly, b) to (a, sin alx)
@@ -450,7 +458,7 @@ __device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int 
   };
   // the moments enter the result as soon as each variable is done (moments
   // odd in cos change sign with fx, odd in sin with fy, back in the grid frame)
-  const float rp = ul[0], rc = rp * cp, irc = 1.0f / rc, icp2 = icp * icp, rpi = rp * icp;
+  const float rp = ul[0], rc = rp * cp, irc = __fdividef(icp, rp), icp2 = icp * icp, rpi = rp * icp;
   float o[4], M[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   var_moments(std::integral_constant<int, 0>(), 36, Kr[3], M);  // p0, pc, ps
   o[0] = M[0] * icp2;
@@ -514,7 +522,7 @@ __device__ __forceinline__ void eg1_pc(const Grid &g, const float *sm, int li, i
     for (int v = 0; v < NV; v++) out[v] = __int_as_float(0x7fc00000);
     return;
   }
-  const float cp = sqrtf(g.gamma * ul[3] / ul[0]), icp = 1.0f / cp;
+  const float cp2 = __fdividef(g.gamma * ul[3], ul[0]), icp = rsqrtf(cp2), cp = cp2 * icp;
   const float am = ul[1] * icp, bm = ul[2] * icp;
   // the arc sums by inclusion-exclusion, as for EG2 (see "EG2 arc sums by
   // inclusion-exclusion"): with constant data per cell only cos^m sin^n,
@@ -524,8 +532,8 @@ __device__ __forceinline__ void eg1_pc(const Grid &g, const float *sm, int li, i
   // X and Y from its end points
   const float fx = (K != YE && ul[1] < 0.0f) ? -1.0f : 1.0f, fy = (K != XE && ul[2] < 0.0f) ? -1.0f : 1.0f;
   const float ax = fminf(fabsf(am), 1.0f), by = fminf(fabsf(bm), 1.0f);
-  const float alx = acosf(ax), snx = sqrtf(fmaxf(0.0f, fmaf(-ax, ax, 1.0f)));
-  const float aly = acosf(by), sny = sqrtf(fmaxf(0.0f, fmaf(-by, by, 1.0f)));
+  const float alx = acosf(ax), snx = sqrt_nn(fmaf(-ax, ax, 1.0f));
+  const float aly = acosf(by), sny = sqrt_nn(fmaf(-by, by, 1.0f));
   // [J00, J10, J01, J20, J11, J02] of each set, reflected frame
   const float X[6] = {2.0f * alx, 2.0f * snx, 0.0f, fmaf(ax, snx, alx), 0.0f, fmaf(-ax, snx, alx)};
   const float Y[6] = {2.0f * aly, 0.0f, 2.0f * sny, fmaf(-by, sny, aly), 0.0f, fmaf(by, sny, aly)};
@@ -784,7 +792,7 @@ __device__ __forceinline__ void correction(const Grid &g, const float *sm, const
       Uy[v] = (centre(sm, a, b, v) - centre(sm, a, b - 1, v)) * g.idy;
     }
   }
-  const float r = U[0], u = U[1], v = U[2], p = U[3], gm = g.gamma, ir = 1.0f / r;
+  const float r = U[0], u = U[1], v = U[2], p = U[3], gm = g.gamma, ir = __fdividef(1.0f, r);
   const float rx = Ux[0], ux = Ux[1], vx = Ux[2], px = Ux[3];
   const float ry = Uy[0], uy = Uy[1], vy = Uy[2], py = Uy[3];
   const float f1 = ux * ux + uy * vx, f2 = uy * vx + vy * vy;
