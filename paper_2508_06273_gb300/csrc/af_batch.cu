@@ -240,9 +240,9 @@ PointValueBatch pv_batch(const af_batch *b) {
   return B;
 }
 
-// one step of every active instance on stream s
-int enqueue_batch_step(af_batch *b, double *hist, int hist_steps, cudaStream_t s) {
-  BCK(launch_batch_dt(b->d_ctl, b->n, hist, hist_steps, DT_STEP, s), "batch: dt");
+// what a step does before its point values: the ghost layers of t^n and the
+// Sec. 3.4 blend weights (both functions of the t^n state alone)
+int enqueue_pre_pointvalue(af_batch *b, cudaStream_t s) {
   GhostBatch G;
   G.ctl = b->d_ctl;
   G.grids = b->d_grids;
@@ -253,6 +253,14 @@ int enqueue_batch_step(af_batch *b, double *hist, int hist_steps, cudaStream_t s
     BCK(launch_shock_theta_batch(b->d_theta_tiles, b->n_theta_tiles, b->d_ctl, b->d_grids, b->d_arrays, b->d_theta,
                                  s),
         "batch: shock indicator");
+  return AF_OK;
+}
+
+// one step of every active instance on stream s
+int enqueue_batch_step(af_batch *b, double *hist, int hist_steps, cudaStream_t s) {
+  BCK(launch_batch_dt(b->d_ctl, b->n, hist, hist_steps, DT_STEP, s), "batch: dt");
+  const int pre = enqueue_pre_pointvalue(b, s);
+  if (pre) return pre;
   BCK(launch_pointvalue_batch(pv_batch(b), b->n_pv_tiles, b->tile_h, s), "batch: point values");
   if (b->sampling)
     BCK(launch_sample_batch(b->sampler, b->d_pv_tiles, b->n_pv_tiles, b->tile_h, b->d_ctl, b->d_pv, s),
@@ -568,6 +576,10 @@ int af_batch_autotune(af_batch *b, int *tile_h, double *ms) {
   if (rc) return rc;
   const std::vector<BatchCtl> saved = b->ctl_h;
   rc = ensure_speeds(b);
+  if (rc) return rc;
+  // the timed launches see what a step's point values see: ghost layers and
+  // blend weights of the current state (both recomputed by every step)
+  rc = enqueue_pre_pointvalue(b, b->stream);
   if (rc) return rc;
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0), "event");
