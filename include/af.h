@@ -140,7 +140,7 @@ int af_get_state_host(af_ctx *h, float *avg, float *vtx, float *xe, float *ye);
  * copies, on streams of their own, so that a download overlaps the next
  * upload and the step between them.  The host arrays must stay untouched
  * (and the output arrays unread) until af_host_sync returns; with pageable
- * memory the copies are staged by the driver and do not overlap, so pass
+ * memory the CUDA driver stages the copies and they do not overlap, so pass
  * page-locked (pinned) memory.  An upload whose periodic duplicate line
  * differs from the first is reported by af_host_sync (AF_ERR_ARG, no state)
  * rather than by the call.  The synchronous host calls first wait for
