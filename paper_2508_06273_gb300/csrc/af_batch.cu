@@ -258,7 +258,7 @@ int enqueue_pre_pointvalue(af_batch *b, cudaStream_t s) {
 
 // one step of every active instance on stream s
 int enqueue_batch_step(af_batch *b, double *hist, int hist_steps, cudaStream_t s) {
-  BCK(launch_batch_dt(b->d_ctl, b->n, hist, hist_steps, DT_STEP, s), "batch: dt");
+  BCK(launch_batch_dt(b->d_ctl, b->n, hist, hist_steps, DT_STEP, b->d_pv, s), "batch: dt");
   const int pre = enqueue_pre_pointvalue(b, s);
   if (pre) return pre;
   BCK(launch_pointvalue_batch(pv_batch(b), b->n_pv_tiles, b->tile_h, s), "batch: point values");
@@ -286,7 +286,7 @@ int graph_for(af_batch *b, int steps, double *hist, int hist_steps, cudaGraphExe
   int rc = AF_OK;
   for (int k = 0; k < steps && rc == AF_OK; k++) rc = enqueue_batch_step(b, hist, hist_steps, b->own_stream);
   if (rc == AF_OK) {
-    cudaError_t e = launch_batch_dt(b->d_ctl, b->n, hist, hist_steps, DT_SETTLE, b->own_stream);
+    cudaError_t e = launch_batch_dt(b->d_ctl, b->n, hist, hist_steps, DT_SETTLE, b->d_pv, b->own_stream);
     if (e != cudaSuccess) rc = bcuda(e, "batch: settle");
   }
   cudaError_t e = cudaStreamEndCapture(b->own_stream, &graph);
@@ -591,7 +591,7 @@ int af_batch_autotune(af_batch *b, int *tile_h, double *ms) {
     rc = build_tiles(b);
     if (rc) break;
     // dt of the coming step, nothing advanced
-    cudaError_t e = launch_batch_dt(b->d_ctl, b->n, nullptr, 0, DT_PROBE, b->stream);
+    cudaError_t e = launch_batch_dt(b->d_ctl, b->n, nullptr, 0, DT_PROBE, b->d_pv, b->stream);
     if (e == cudaSuccess) e = launch_pointvalue_batch(pv_batch(b), b->n_pv_tiles, b->tile_h, b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
     for (int r = 0; r < 3 && e == cudaSuccess; r++)

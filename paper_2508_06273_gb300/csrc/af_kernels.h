@@ -169,8 +169,11 @@ cudaError_t launch_shock_theta_batch(const int4 *tiles, int ntiles, const BatchC
                                      const float *const *arrays, float *const *theta, cudaStream_t s);
 // per-instance dt for the coming step (mode DT_STEP; records it into
 // hist[step * n + k] if hist), only the buffer flip of the last step
-// (DT_SETTLE), or dt without advancing anything (DT_PROBE)
-cudaError_t launch_batch_dt(BatchCtl *ctl, int n, double *hist, int hist_cap, int mode, cudaStream_t s);
+// (DT_SETTLE), or dt without advancing anything (DT_PROBE); the dt is also
+// written into both point-value argument records of the instance (pv_args,
+// [instance][buffer], if not null), which the batched kernel reads in place
+cudaError_t launch_batch_dt(BatchCtl *ctl, int n, double *hist, int hist_cap, int mode, PointValueArgs *pv_args,
+                            cudaStream_t s);
 // cell prep and point values at t^{n+1/2} (n1) and t^{n+1} (n2)
 cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,

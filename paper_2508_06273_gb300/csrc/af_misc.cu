@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) shock_theta_batch_kernel(const int4 *tile
 // state has no finite positive wave speed (flagged ST_STOPPED).  The flip of
 // the t^n buffer of the previous step is applied first; the speed is zeroed
 // for the coming step's flux kernel, which refills it.
-__global__ void batch_dt_kernel(BatchCtl *ctl, int n, double *hist, int hist_cap, int mode) {
+__global__ void batch_dt_kernel(BatchCtl *ctl, int n, double *hist, int hist_cap, int mode, PointValueArgs *pv) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   BatchCtl &c = ctl[k];
@@ -202,6 +202,7 @@ __global__ void batch_dt_kernel(BatchCtl *ctl, int n, double *hist, int hist_cap
     }
   }
   c.dt = (float)dt;
+  if (pv) pv[2 * k].dt = pv[2 * k + 1].dt = c.dt;
   const double lx = dt / c.dx, ly = dt / c.dy;
   c.lxh = (float)lx;
   c.lxl = (float)(lx - (double)c.lxh);
@@ -368,9 +369,10 @@ cudaError_t launch_shock_theta_batch(const int4 *tiles, int ntiles, const BatchC
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_dt(BatchCtl *ctl, int n, double *hist, int hist_cap, int mode, cudaStream_t s) {
+cudaError_t launch_batch_dt(BatchCtl *ctl, int n, double *hist, int hist_cap, int mode, PointValueArgs *pv_args,
+                            cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  batch_dt_kernel<<<(n + 127) / 128, 128, 0, s>>>(ctl, n, hist, hist_cap, mode);
+  batch_dt_kernel<<<(n + 127) / 128, 128, 0, s>>>(ctl, n, hist, hist_cap, mode, pv_args);
   return cudaGetLastError();
 }
 

@@ -1029,16 +1029,14 @@ template <int TY>
 __global__ void __launch_bounds__(TX *TY, min_blocks<TY>()) pointvalue_batch_kernel(PointValueBatch B) {
   extern __shared__ float4 smem4[];
   __shared__ alignas(8) unsigned long long bar;
-  __shared__ Args A;
   const int4 t = B.tiles[blockIdx.x];
   const BatchCtl &c = B.ctl[t.x];
   if (!c.active) return;
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    A = B.args[2 * t.x + c.cur];
-    A.dt = c.dt;
-  }
-  __syncthreads();
-  tile_body<TY>(A, B.maps[2 * t.x + c.cur], tile_smem(smem4), &bar, t.y, t.z);
+  // the instance's arguments are read in place (the step's dt is in them):
+  // read-only, so the compiler may load a field again where a copy in shared
+  // memory held it in a register (half the spills)
+  const Args *__restrict__ A = B.args + 2 * t.x + c.cur;
+  tile_body<TY>(*A, B.maps[2 * t.x + c.cur], tile_smem(smem4), &bar, t.y, t.z);
 }
 
 }  // namespace
