@@ -53,11 +53,11 @@ FLUX_BYTES_PER_CELL = 208
 # were taken on (sha256 of the files below); otherwise reported as null
 _KSRC = "paper_2508_06273_gb300/csrc/"
 _SHARED = {_KSRC + "af_common.cuh": "ad367efa0749a42a00411129d4ba9b0879db4f6774a017f6d6f5cb31c8be357c",
-           _KSRC + "af_kernels.h": "173082c6909ad133e2877806f0cfd06b09134ced6793313f07e41345012386f4"}
+           _KSRC + "af_kernels.h": "041e3fe48d6b08f2ecd47e0aec35013ec68a10463e4ddcb5cc5357a501e7884e"}
 PV_TRAFFIC = {"bytes_per_cell": 150.9, "profile": "profiles/pointvalue_flux_vortex2048.md",
               "sha256": dict(_SHARED, **{_KSRC + "af_pointvalue.cu":
-                                         "c0495ef135a6c18c53050465ff839f5b1fae9634db451926fed0e5eddf8f9e99"})}
-FLUX_TRAFFIC = {"bytes_per_cell": 207.4, "profile": "profiles/pointvalue_flux_vortex2048.md",
+                                         "c96b3e1d3f33b818e2c71aa8ddcf36a346c45b8c0db561dbb80348c8b6804876"})}
+FLUX_TRAFFIC = {"bytes_per_cell": 207.3, "profile": "profiles/pointvalue_flux_vortex2048.md",
                 "sha256": dict(_SHARED, **{_KSRC + "af_flux.cu":
                                            "213f4a4a6ac472c9376c2a5a58a1b991d0577593a37d6c3ad426ed128e9579ca"})}
 
