@@ -7,8 +7,8 @@
  * in device memory (FP32 storage, cell averages with an FP32 low word), and
  * a CUDA stream.  Every numerical step runs in the library's CUDA kernels.
  *
- * Degrees of freedom (Sec. 2 of the paper, "Let (x_{i-1/2}, x_{i+1/2}) x
- * (y_{j-1/2}, y_{j+1/2}) be the grid cell (i,j)..."):
+ * Degrees of freedom (Sec. 2 of the paper; cell (i, j) is the rectangle
+ * (x_{i-1/2}, x_{i+1/2}) x (y_{j-1/2}, y_{j+1/2})):
  *   cell averages of the conserved variables (rho, rho u, rho v, E),
  *   point values of the primitive variables (rho, u, v, p) at the vertices
  *   (x_{i-1/2}, y_{j-1/2}), the x-edge midpoints (x_{i-1/2}, y_j) and the
