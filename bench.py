@@ -607,7 +607,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(n), "cells": n * n, "grid": [n, n]},
+        "data": "synthetic",
+        "config": {"workload": workload_name(n), "grid": [n, n], "cells": w.cells,
+                   "sample": f"{w.window}x{w.window}-cell window of the {n}x{n} grid around the vortex "
+                             f"(outflow ghosts at its edge): {w.cells} cells timed per step, not the full grid"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": w.threads, "kind": "oracle",
                          "sample": w.describe(n, args.steps) + ", one step per bench step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

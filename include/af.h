@@ -58,8 +58,13 @@ enum {
   AF_ST_NONFINITE = 4,  /* a non-finite point value or cell average */
   AF_ST_KEPT = 8,       /* Alg. 3's Lax-Friedrichs value was not admissible in FP32;
                            the node kept its old value */
-  AF_ST_TIMEOUT = 16,   /* a block's wait for its staged tile timed out; the tile was
-                           not updated (the step's result is invalid) */
+  AF_ST_TIMEOUT = 16,   /* a block's bounded wait for its staged tile (or the surrogate's
+                           wait for its tensor-core MMAs) ran out; the tile was not
+                           updated and the step's result is invalid.  Fatal and sticky:
+                           once af_status has returned it, every later af_status returns
+                           it and af_step / af_run refuse (AF_ERR_STATE).  A block that
+                           times out waits 16 times longer for its copy to land before it
+                           exits; if even that runs out it exits with the copy unfinished */
   AF_ST_STOPPED = 32,   /* batch only: the instance's state had no finite positive wave
                            speed, so it was stopped before its end time */
   AF_ST_FLUX_LIMITED = 64 /* the flux limiter blended at least one face flux (informational) */
@@ -89,10 +94,20 @@ enum {
                               values, theta = exp(-phi1 phi2), U^lo from Alg. 3's low-order chain */
   AF_OPT_TILE_H = 11,      /* point-value tile height: 4, 8 (default) or 16 rows of 32 cells; the result
                               does not depend on it */
-  AF_OPT_NODE_BOUNDS = 12  /* 1: Alg. 3 also rejects a high-order point value whose rho or p lies outside
+  AF_OPT_NODE_BOUNDS = 12, /* 1: Alg. 3 also rejects a high-order point value whose rho or p lies outside
                               [0.1 min, 10 max] of the node's t^n value and the primitive averages of the
                               cells around it (own reading: positivity alone keeps the huge positive values
                               EG2 returns when the full step is linearised about a near-vacuum state) */
+  AF_OPT_UBAR = 13,        /* primitive cell average Ubar (used by the averaged linearisation, Alg. 2,
+                              Alg. 3's piecewise-constant data, the Sec. 3.4 indicator and the node
+                              bounds): 0 (default) Sec. 2's definition, Simpson's rule over the primitive
+                              point values and U_c = C2P(Q_c); 1 the primitive state of the conservative
+                              cell average, C2P(Qbar) (reading of Sec. 3.5, which keeps discontinuous
+                              data admissible) */
+  AF_OPT_TEST_TIMEOUT = 14  /* test hook: 1 makes every later step's waits for staged data (the point-value
+                               tiles' TMA copies) and for the surrogate's tensor-core MMAs run out after a
+                               short bound with nothing in flight (the barrier is armed, no copy or MMA is
+                               issued): the step returns normally with AF_ST_TIMEOUT set */
 };
 
 /* stages reported by af_profile */
@@ -202,11 +217,19 @@ int af_profile(af_ctx *h, double ms[4], int64_t launches[4], int reset);
  *   out     device double[4]: dx dy * sum over the cells, per variable
  *   stream  cudaStream_t to run on (0: the legacy default stream); the call
  *           is asynchronous on it and calls no cudaMalloc or cudaFree.
+ * avg_lo and out must be device memory of avg's device (or managed memory);
+ * a host pointer or another GPU's memory is rejected with AF_ERR_ARG before
+ * anything runs.
  * Scratch: a static device array of AF_TOTALS_NOALLOC_MAX_ROWS x 4 doubles
  * (512 KiB) that every GPU loading the library holds until exit; ny above
- * the limit is rejected with AF_ERR_ARG before anything runs.  The first
- * call on a device looks the array's device address up (cudaGetSymbolAddress)
- * and should come before any stream capture.  All calls share the array:
+ * the limit is rejected with AF_ERR_ARG before anything runs.  Set-up on the
+ * first call on each device: the call looks the array's device address up
+ * (cudaGetSymbolAddress), and with CUDA's default lazy module loading that
+ * is when the driver loads this entry point's device code and the array onto
+ * the device, which allocates device memory and may synchronise.  Make that
+ * first call on every device during set-up, before the region that must not
+ * allocate and before any stream capture; later calls allocate nothing.
+ * All calls share the array:
  * calls that overlap on the GPU race.  Nothing in it needs to start at zero
  * (each call writes every row partial it reads).  Fixed-order summation, so
  * a repeated call gives the same bits; it differs from af_conserved_totals

@@ -27,6 +27,7 @@ from .afo import (  # noqa: F401
     OPT_FLUX_LIMITER,
     OPT_SHOCK_BLEND,
     OPT_NODE_BOUNDS,
+    OPT_UBAR,
     ST_FLUX_LIMITED,
     ST_CFL,
     ST_AVG_NONPOS,

@@ -12,6 +12,7 @@
  *   P2C / C2P, fluxes f and g ............. Sec. 2, conservative form and EOS, gamma = 1.4
  *   cell prep: invert Simpson for Q_c,
  *     U_c = C2P(Q_c), Simpson for Ubar .... Sec. 2, paragraph on primitive cell averages
+ *                                            (AFO_OPT_UBAR = 1: C2P of the average, after Sec. 3.5)
  *   cpq reconstruction ..................... Sec. 2: continuous piecewise quadratic; read as the
  *                                            biquadratic Lagrange interpolant of the 8 boundary point
  *                                            values and U_c (Simpson is exact for it, so its mean is Ubar)
@@ -48,6 +49,7 @@ struct afo_ctx {
   int bc[4];
   double inflow[4][4]; /* primitive inflow state per side (Sec. 4.3) */
   int lin_mode, tsw, limiter, correction, force_lo, threads, flux_limiter, shock_blend, node_bounds;
+  int ubar_c2p;       /* Ubar: 0 Simpson over primitive point values (Sec. 2), 1 C2P(Qbar) */
   double *avg;        /* conservative averages, [4][H][W] */
   double *nd[3][3];   /* point values [level][kind] -> [4][H][W]; level 0 t^n, 1 t^{n+1/2}, 2 t^{n+1} */
   double *uc, *ub;    /* cell-centre value U_c and primitive average Ubar, [4][H][W] */
@@ -177,16 +179,19 @@ static void fill_cells(afo_ctx *c, double *a) {
 /* Q_c from inverting Simpson's rule in conservative variables, U_c = C2P(Q_c)
  * (the reconstruction's centre value).  Ubar, the primitive cell average that
  * the linearisation, Alg. 2, Alg. 3's piecewise-constant data and Sec. 3.4's
- * indicator use, is the primitive state of the conservative cell average,
- * C2P(Qbar): Sec. 3.5 speaks of density and pressure computed from the cell
- * averages of the conserved quantities as the values the linearisation is
- * built from. */
+ * indicator use, is by default the one Sec. 2 defines: Simpson's rule applied
+ * to the primitive point values (the 8 boundary nodes and U_c), i.e. the mean
+ * of the primitive reconstruction.  With AFO_OPT_UBAR = 1 it is the primitive
+ * state of the conservative cell average, C2P(Qbar): Sec. 3.5 speaks of density
+ * and pressure computed from the cell averages of the conserved quantities as
+ * the values the linearisation is built from, and discontinuous data keep
+ * their positivity with it. */
 static void prep_cells(afo_ctx *c) {
   const double *V = c->nd[0][0], *X = c->nd[0][1], *Y = c->nd[0][2];
 #pragma omp parallel for schedule(static)
   for (int j = -G; j < c->ny + G; j++) {
     for (int i = -G; i < c->nx + G; i++) {
-      double Qs[4] = {0, 0, 0, 0};
+      double Qs[4] = {0, 0, 0, 0}, Us[4] = {0, 0, 0, 0};
       const struct { const double *a; int i, j; double w; } nodes[8] = {
           {V, i, j, 1.0},     {V, i + 1, j, 1.0}, {V, i, j + 1, 1.0}, {V, i + 1, j + 1, 1.0},
           {X, i, j, 4.0},     {X, i + 1, j, 4.0}, {Y, i, j, 4.0},     {Y, i, j + 1, 4.0}};
@@ -194,13 +199,20 @@ static void prep_cells(afo_ctx *c) {
         double U[4], Q[4];
         get4(c, nodes[n].a, nodes[n].i, nodes[n].j, U);
         p2c(U, c->gam, Q);
-        for (int v = 0; v < NV; v++) Qs[v] += nodes[n].w * Q[v];
+        for (int v = 0; v < NV; v++) {
+          Qs[v] += nodes[n].w * Q[v];
+          Us[v] += nodes[n].w * U[v];
+        }
       }
       double Qc[4], Uc[4], Ub[4], Qa[4];
       for (int v = 0; v < NV; v++) Qc[v] = (36.0 * AT(c, c->avg, v, i, j) - Qs[v]) / 16.0;
       c2p(Qc, c->gam, Uc);
-      get4(c, c->avg, i, j, Qa);
-      c2p(Qa, c->gam, Ub);
+      if (c->ubar_c2p) {
+        get4(c, c->avg, i, j, Qa);
+        c2p(Qa, c->gam, Ub);
+      } else {
+        for (int v = 0; v < NV; v++) Ub[v] = (Us[v] + 16.0 * Uc[v]) / 36.0;
+      }
       put4(c, c->uc, i, j, Uc);
       put4(c, c->ub, i, j, Ub);
     }
@@ -812,6 +824,10 @@ int afo_set_option(afo_ctx *c, int key, double val) {
   case AFO_OPT_FLUX_LIMITER: c->flux_limiter = iv != 0; return 0;
   case AFO_OPT_SHOCK_BLEND: c->shock_blend = iv != 0; return 0;
   case AFO_OPT_NODE_BOUNDS: c->node_bounds = iv != 0; return 0;
+  case AFO_OPT_UBAR:
+    if (iv < 0 || iv > 1) return -1;
+    c->ubar_c2p = iv;
+    return 0;
   default: return -1;
   }
 }

@@ -42,6 +42,8 @@ enum {
   AFO_OPT_SHOCK_BLEND = 10,  /* Sec. 3.4 shock-indicator blend of point values with EG1 (0/1) */
   AFO_OPT_NODE_BOUNDS = 12,  /* Alg. 3 also rejects rho, p outside [0.1 min, 10 max] of the node's t^n value
                                 and the Ubar of its cells (0/1; own reading, see limit_node) */
+  AFO_OPT_UBAR = 13,         /* primitive cell average Ubar: 0 = Simpson's rule over the primitive point values
+                                and U_c (Sec. 2, default); 1 = C2P of the conservative average (Sec. 3.5 reading) */
   AFO_OPT_THREADS = 16    /* OpenMP threads (oracle only; 0 = runtime default) */
 };
 enum { AFO_LIN_AVG = 0, AFO_LIN_POINT = 1, AFO_LIN_ALG1 = 2 };

@@ -24,7 +24,7 @@ _LIB = None
 VTX, XE, YE = 0, 1, 2
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING, BC_INFLOW = 0, 1, 2, 3
 OPT_LIN_MODE, OPT_TSW, OPT_LIMITER, OPT_CORRECTION, OPT_FORCE_LO, OPT_THREADS = 0, 1, 2, 3, 4, 16
-OPT_FLUX_LIMITER, OPT_SHOCK_BLEND, OPT_NODE_BOUNDS = 9, 10, 12
+OPT_FLUX_LIMITER, OPT_SHOCK_BLEND, OPT_NODE_BOUNDS, OPT_UBAR = 9, 10, 12, 13
 ST_FLUX_LIMITED = 64
 ST_CFL, ST_AVG_NONPOS, ST_NONFINITE, ST_KEPT = 1, 2, 4, 8
 

@@ -98,14 +98,25 @@ def p2c(U, gamma=GAMMA):
     return np.stack([r, r * u, r * v, p / (gamma - 1) + 0.5 * r * (u * u + v * v)])
 
 
-def ubar(ext, gamma=GAMMA):
-    """Primitive cell averages Ubar of the cells -1 .. n: the primitive state of
-    the conservative cell average (the reading the C oracle uses, after
-    Sec. 3.5).  Returned at [v, j + 1, i + 1]."""
-    avg = ext[0]
+def ubar(ext, gamma=GAMMA, c2p_mode=0):
+    """Primitive cell averages Ubar of the cells -1 .. n, returned at
+    [v, j + 1, i + 1].  Default (Sec. 2): invert Simpson's rule for the
+    conserved centre value Q_c, U_c = C2P(Q_c), then Simpson's rule over the
+    primitive point values and U_c.  c2p_mode = 1: the primitive state of the
+    conservative cell average (the reading after Sec. 3.5)."""
+    avg, vtx, xe, ye = ext
     ny, nx = avg.shape[1] - 2 * G, avg.shape[2] - 2 * G
     o = G - 1  # extended index of cell -1
-    return c2p(avg[:, o:o + ny + 2, o:o + nx + 2], gamma)
+    cy, cx = slice(o, o + ny + 2), slice(o, o + nx + 2)
+    cy1, cx1 = slice(o + 1, o + ny + 3), slice(o + 1, o + nx + 3)
+    Qa = avg[:, cy, cx]
+    if c2p_mode:
+        return c2p(Qa, gamma)
+    corners = [vtx[:, cy, cx], vtx[:, cy, cx1], vtx[:, cy1, cx], vtx[:, cy1, cx1]]
+    edges = [xe[:, cy, cx], xe[:, cy, cx1], ye[:, cy, cx], ye[:, cy1, cx]]
+    Qs = sum(p2c(U, gamma) for U in corners) + 4 * sum(p2c(U, gamma) for U in edges)
+    Uc = c2p((36 * Qa - Qs) / 16, gamma)
+    return (sum(corners) + 4 * sum(edges) + 16 * Uc) / 36
 
 
 # --------------------------------------------------------------- features
@@ -115,12 +126,13 @@ def _scale(ut, gamma):
     return np.stack([rho, c, c, rho * c * c]), c
 
 
-def features(state, bc, kind, I, J, dt, h, gamma=GAMMA):
+def features(state, bc, kind, I, J, dt, h, gamma=GAMMA, ubar_c2p=0):
     """Features (n, 64), linearisation states (n, 4) and scales (n, 4) of the
-    nodes (kind, I[k], J[k]) (array indices of that kind)."""
+    nodes (kind, I[k], J[k]) (array indices of that kind); ubar_c2p selects
+    the definition of Ubar (see ubar)."""
     ext = extend(state, bc)
     avg, vtx, xe, ye = ext
-    ub = ubar(ext, gamma)  # cells -1..n at [j + 1, i + 1]
+    ub = ubar(ext, gamma, ubar_c2p)  # cells -1..n at [j + 1, i + 1]
     I = np.asarray(I)
     J = np.asarray(J)
     cb = lambda i, j: ub[:, j + 1, i + 1]  # noqa: E731

@@ -345,6 +345,19 @@ int af_set_option(af_ctx *h, int key, double value) {
       h->opt.shock_blend = iv != 0;
       return AF_OK;
     case AF_OPT_NODE_BOUNDS: h->opt.node_bounds = iv != 0; return AF_OK;
+    case AF_OPT_TEST_TIMEOUT: h->opt.test_timeout = iv != 0; return AF_OK;
+    case AF_OPT_UBAR:
+      if (iv < 0 || iv > 1) return fail(AF_ERR_ARG, "ubar must be 0 or 1%s");
+      if (iv != h->g.ubar_c2p) {
+        for (int p = 0; p < 2; p++)  // captured steps hold the old grid description
+          if (h->run_exec[p]) {
+            DeviceGuard dg(h->device);
+            cudaGraphExecDestroy(h->run_exec[p]);
+            h->run_exec[p] = nullptr;
+          }
+      }
+      h->g.ubar_c2p = iv;
+      return AF_OK;
     case AF_OPT_TILE_H: {
       if (iv != 4 && iv != 8 && iv != 16) return fail(AF_ERR_ARG, "tile height must be 4, 8 or 16%s");
       if (iv == h->tile_h) return AF_OK;
@@ -384,6 +397,8 @@ int af_get_option(af_ctx *h, int key, double *value) {
     case AF_OPT_FLUX_LIMITER: *value = h->opt.flux_limiter; return AF_OK;
     case AF_OPT_SHOCK_BLEND: *value = h->opt.shock_blend; return AF_OK;
     case AF_OPT_NODE_BOUNDS: *value = h->opt.node_bounds; return AF_OK;
+    case AF_OPT_UBAR: *value = h->g.ubar_c2p; return AF_OK;
+    case AF_OPT_TEST_TIMEOUT: *value = h->opt.test_timeout; return AF_OK;
     case AF_OPT_TILE_H: *value = h->tile_h; return AF_OK;
     default: return fail(AF_ERR_ARG, "unknown option%s");
   }
@@ -673,7 +688,8 @@ static int enqueue_step(af_ctx *h, double dt) {
   if (h->opt.shock_blend) {
     theta[0] = h->shock_theta;
     theta[1] = h->shock_theta + h->g.plane;
-    CK(launch_shock_theta(h->g, h->hi, h->shock_theta, h->shock_theta + h->g.plane, s), "shock indicator");
+    CK(launch_shock_theta(h->g, h->hi, h->lev[0], h->shock_theta, h->shock_theta + h->g.plane, s),
+       "shock indicator");
   }
   if (prof) cudaEventRecord(h->ev_stage[1], s);
   if (h->opt.surrogate) {
@@ -705,6 +721,8 @@ static int enqueue_step(af_ctx *h, double dt) {
       A.tile_rows = h->tile_h;
       A.stats = h->surr_stats;
       A.status = h->d_status;
+      A.test_no_issue = h->opt.test_timeout != 0;
+      A.wait_limit = h->opt.test_timeout ? kTestWaitLimit : kWaitLimit;
       CK(launch_surrogate(k, A, h->sms, s), "surrogate");
     }
     CK(launch_pointvalue_masked(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
@@ -741,10 +759,15 @@ static int enqueue_step(af_ctx *h, double dt) {
   return AF_OK;
 }
 
+static const char *kTimedOut =
+    "a wait for staged data or for the tensor cores timed out (AF_ST_TIMEOUT): the state is invalid and the "
+    "handle takes no further steps%s";
+
 int af_step(af_ctx *h, double dt) {
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(AF_ERR_ARG, "af_step: dt must be positive%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  if (h->timed_out) return fail(AF_ERR_STATE, kTimedOut);
   DeviceGuard dg(h->device);
   return enqueue_step(h, dt);
 }
@@ -792,6 +815,7 @@ int af_run(af_ctx *h, int nsteps, double dt) {
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
   if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(AF_ERR_ARG, "af_run: bad arguments%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  if (h->timed_out) return fail(AF_ERR_STATE, kTimedOut);
   DeviceGuard dg(h->device);
   if (h->profile || nsteps < 4) {  // profiled runs time every stage: plain launches
     for (int k = 0; k < nsteps; k++) {
@@ -822,7 +846,9 @@ int af_status(af_ctx *h) {
   CK(launch_export_words(reinterpret_cast<unsigned *>(h->d_status), nullptr, 1, h->host_words_dev, h->stream),
      "status");
   CK(cudaStreamSynchronize(h->stream), "sync");
-  return (int)reinterpret_cast<volatile unsigned *>(h->host_words)[0];
+  const int bits = (int)reinterpret_cast<volatile unsigned *>(h->host_words)[0];
+  if (bits & AF_ST_TIMEOUT) h->timed_out = true;
+  return h->timed_out ? bits | AF_ST_TIMEOUT : bits;  // sticky
 }
 
 int af_counters(af_ctx *h, int64_t out[4]) {

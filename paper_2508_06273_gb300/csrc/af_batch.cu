@@ -58,6 +58,7 @@ struct af_batch {
   int4 *d_theta_tiles = nullptr;   // (instance, a0, b0): shock-indicator tiles of the blending instances
   int n_theta_tiles = 0, theta_tiles_cap = 0;
   bool maps_ok = false;
+  bool timed_out = false;  // an instance reported AF_ST_TIMEOUT: no further runs
   std::vector<GraphEntry> graphs;
   bool any_limiter = false;  // some instance has the flux limiter on
   bool any_blend = false;    // some instance has the Sec. 3.4 blend on
@@ -110,6 +111,7 @@ int sync_ctl(af_batch *b) {
     h->lev[2] = h->tbuf[c.cur ^ 1];
     h->speed_valid = false;
     if (!c.active && (c.status & ST_STOPPED)) b->stopped[k] = 1;
+    if (c.status & ST_TIMEOUT) b->timed_out = true;
   }
   return AF_OK;
 }
@@ -443,6 +445,9 @@ int af_batch_set_option(af_batch *b, int k, int key, double value) {
     if (rc) return rc;
   }
   BCK(cudaStreamSynchronize(b->stream), "batch: sync");
+  if (key == AF_OPT_UBAR)  // the option lives in the grid description
+    for (int q = k0; q < k1; q++)
+      BCK(cudaMemcpy(b->d_grids + q, &b->inst[q]->g, sizeof(Grid), cudaMemcpyHostToDevice), "batch: grid");
   return upload_args(b);
 }
 
@@ -511,6 +516,9 @@ int af_batch_run(af_batch *b, int nsteps, double *hist, int hist_steps) {
   if (!b || nsteps < 0 || hist_steps < 0) return bfail(AF_ERR_ARG, "af_batch_run: bad arguments");
   for (int k = 0; k < b->n; k++)
     if (!b->has_state[k]) return bfail(AF_ERR_STATE, "af_batch_run: an instance has no state");
+  if (b->timed_out)
+    return bfail(AF_ERR_STATE, "af_batch_run: a wait for staged data timed out (AF_ST_TIMEOUT): the states are "
+                               "invalid and the batch takes no further steps");
   if (nsteps == 0) return AF_OK;
   Dev d(b->device);
   int rc = build_tiles(b);

@@ -34,6 +34,11 @@ struct Grid {
   float dx, dy, idx, idy;
   float gamma;
   float inflow[4][4];  // primitive inflow state of each side (BC_INFLOW sides)
+  // definition of the primitive cell average Ubar (a method option, kept here
+  // so that every kernel that forms Ubar sees it): 0 Simpson's rule over the
+  // primitive point values (Sec. 2), 1 the primitive state of the
+  // conservative cell average (Sec. 3.5 reading)
+  int ubar_c2p;
 };
 
 __host__ __device__ __forceinline__ long long at(const Grid &g, int v, int i, int j) {
@@ -54,6 +59,60 @@ __device__ __forceinline__ void c2p(const float Q[4], float gm1, float U[4]) {
   U[2] = Q[2] * ir;
   U[3] = gm1 * (Q[3] - 0.5f * (Q[1] * Q[1] + Q[2] * Q[2]) * ir);
 }
+// Cell prep of Sec. 2 from a cell's 8 boundary point values N (primitive;
+// corners ll, lr, ul, ur, then edge midpoints left, right, bottom, top) and
+// its conservative average Qa: the centre value U_c = C2P(Q_c), with Q_c from
+// Simpson's rule solved for the centre in conservative variables, and the
+// primitive cell average Ubar: Simpson's rule over the primitive point values
+// and U_c, or C2P(Qa) with ubar_c2p.
+__device__ __forceinline__ void cell_prep(const float N[8][4], const float Qa[4], float gamma, int ubar_c2p,
+                                          float Uc[4], float Ub[4]) {
+  const float gm1 = gamma - 1.0f, gm1i = 1.0f / gm1;
+  float Qs[4] = {0.0f, 0.0f, 0.0f, 0.0f}, Us[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int n = 0; n < 8; n++) {
+    float Q[4];
+    p2c(N[n], gm1i, Q);
+    const float w = n < 4 ? 1.0f : 4.0f;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      Qs[v] += w * Q[v];
+      Us[v] += w * N[n][v];
+    }
+  }
+  float Qc[4];
+#pragma unroll
+  for (int v = 0; v < NV; v++) Qc[v] = (36.0f * Qa[v] - Qs[v]) * 0.0625f;
+  c2p(Qc, gm1, Uc);
+  if (ubar_c2p) {
+    c2p(Qa, gm1, Ub);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; v++) Ub[v] = fmaf(16.0f, Uc[v], Us[v]) * (1.0f / 36.0f);
+  }
+}
+
+// Ubar of cell (i, j) read from the t^n arrays in global memory (the
+// point-value kernel forms the same values from its staged tile)
+__device__ __forceinline__ void cell_ubar_global(const Grid &g, const float *avg, const float *vtx,
+                                                 const float *xe, const float *ye, int i, int j, float Ub[4]) {
+  float Qa[4];
+#pragma unroll
+  for (int v = 0; v < NV; v++) Qa[v] = __ldg(avg + at(g, v, i, j));
+  if (g.ubar_c2p) {
+    c2p(Qa, g.gamma - 1.0f, Ub);
+    return;
+  }
+  float N[8][4], Uc[4];
+  const float *src[8] = {vtx, vtx, vtx, vtx, xe, xe, ye, ye};
+  const int di[8] = {0, 1, 0, 1, 0, 1, 0, 0}, dj[8] = {0, 0, 1, 1, 0, 0, 0, 1};
+#pragma unroll
+  for (int n = 0; n < 8; n++)
+#pragma unroll
+    for (int v = 0; v < NV; v++) N[n][v] = __ldg(src[n] + at(g, v, i + di[n], j + dj[n]));
+  cell_prep(N, Qa, g.gamma, 0, Uc, Ub);
+}
+
 // Alg. 3's test: positive density and pressure, every component finite
 __device__ __forceinline__ bool admissible(const float U[4]) {
   return U[0] > 0.0f && U[3] > 0.0f && isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]);

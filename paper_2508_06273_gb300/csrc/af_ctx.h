@@ -50,6 +50,9 @@ struct af_ctx {
   // the small reads (status, max speed)
   unsigned *host_words, *host_words_dev;  // a periodic duplicate line differed in an asynchronous upload
   bool has_state;
+  // a block's wait for staged data or for the tensor cores ran out (seen by
+  // af_status): the state is invalid and the handle refuses further steps
+  bool timed_out;
   // af_run: two captured steps per parity of the t^n buffer, with the dt and
   // options they were captured with
   cudaGraphExec_t run_exec[2];

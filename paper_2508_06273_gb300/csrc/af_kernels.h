@@ -26,7 +26,16 @@ struct Options {
   int flux_limiter = 0;  // cell-average flux limiter (Sec. 3.5)
   int shock_blend = 0;   // Sec. 3.4 shock-indicator blend of point values
   int node_bounds = 0;   // Alg. 3 also bounds rho, p by the node's cells (see node_update)
+  int test_timeout = 0;  // test hook: waits for staged data run out with nothing in flight
 };
+
+// Bounded waits on an mbarrier (polls of try_wait, which suspends in hardware
+// between polls): the normal limit, the short one the timeout test hook uses,
+// and how many times the limit a block that timed out still waits for its
+// copies to land before it exits.
+constexpr unsigned kWaitLimit = 1u << 22;
+constexpr unsigned kTestWaitLimit = 256;
+constexpr unsigned kDrainFactor = 16;
 
 // TMA descriptors of the t^n node arrays and the cell averages (one set per
 // physical buffer that can hold t^n)
@@ -43,6 +52,11 @@ struct PointValueArgs {
   float *n2[3];
   float dt;
   int lin_mode, tsw, limiter, correction, force_lo, node_bounds;
+  // polls of the tile barrier before a block gives up (ST_TIMEOUT); test
+  // hook: arm the barrier but issue no copy, so the wait runs out with
+  // nothing in flight
+  unsigned wait_limit;
+  int test_no_copy;
   int *status;
   unsigned long long *counters;
   // exact operator as the surrogate's fallback: only nodes with a nonzero
@@ -70,6 +84,8 @@ inline PointValueArgs pointvalue_args(const Grid &g, const NodeSet &n0, const fl
   A.correction = o.correction;
   A.force_lo = o.force_lo;
   A.node_bounds = o.node_bounds;
+  A.test_no_copy = o.test_timeout != 0;
+  A.wait_limit = o.test_timeout ? kTestWaitLimit : kWaitLimit;
   A.status = status;
   A.counters = counters;
   A.mask[0] = A.mask[1] = A.mask[2] = nullptr;
@@ -162,7 +178,8 @@ cudaError_t launch_ghost_batch(const GhostBatch &B, int nchunks, cudaStream_t s)
 long long ghost_total(const Grid &g, int arr);
 constexpr int GHOST_CHUNK = 256;
 // Sec. 3.4 blend weights of the edge midpoints (planes of the padded layout)
-cudaError_t launch_shock_theta(const Grid &g, const float *avg_hi, float *tx, float *ty, cudaStream_t s);
+cudaError_t launch_shock_theta(const Grid &g, const float *avg_hi, const NodeSet &n0, float *tx, float *ty,
+                               cudaStream_t s);
 // batched over tiles (instance, a0, b0) of 32 x 8 entries (a <= nx + 1,
 // b <= ny + 1); theta[2k], theta[2k+1] the planes of instance k (NULL: skipped)
 cudaError_t launch_shock_theta_batch(const int4 *tiles, int ntiles, const BatchCtl *ctl, const Grid *grids,
@@ -241,6 +258,10 @@ struct SurrogateArgs {
   int tiles_x, tile_rows;
   unsigned long long *stats;  // [0] nodes from the network, [1] nodes sent to the exact operator
   int *status;
+  // polls of a layer's MMA barrier before the group gives up (ST_TIMEOUT);
+  // test hook: issue no MMA, so the wait runs out with nothing in flight
+  unsigned wait_limit = kWaitLimit;
+  int test_no_issue = 0;
 };
 cudaError_t prepare_surrogate();
 // Ubar of the cells -1 .. nx, -1 .. ny of the t^n state into ub (4 planes)

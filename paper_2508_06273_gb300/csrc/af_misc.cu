@@ -119,24 +119,24 @@ __global__ void __launch_bounds__(GHOST_CHUNK) ghost_batch_kernel(GhostBatch B) 
 // ---- Sec. 3.4 shock indicator: theta = exp(-phi1 phi2) per edge midpoint,
 // phi1 the larger normalised second difference of the averaged pressure on
 // either side of the edge, phi2 = 2^(max |u_n| + c of its two cells), the
-// "bar" quantities from the primitive state of the cell averages.
-__device__ __forceinline__ void cell_prim(const Grid &g, const float *avg, int i, int j, float U[4]) {
-  float Q[4];
-#pragma unroll
-  for (int v = 0; v < NV; v++) Q[v] = avg[at(g, v, i, j)];
-  c2p(Q, g.gamma - 1.0f, U);
+// "bar" quantities from the primitive cell averages Ubar.
+struct TnArrays {
+  const float *avg, *vtx, *xe, *ye;
+};
+__device__ __forceinline__ void cell_prim(const Grid &g, const TnArrays &t, int i, int j, float U[4]) {
+  cell_ubar_global(g, t.avg, t.vtx, t.xe, t.ye, i, j, U);
 }
 __device__ __forceinline__ float d2ratio(float a, float b, float c) {
   return fabsf((a - 2.0f * b + c) / (a + 2.0f * b + c));
 }
 // x-edge (i - 1/2, j) (dir 0) or y-edge (i, j - 1/2) (dir 1)
-__device__ __forceinline__ float shock_theta(const Grid &g, const float *avg, int dir, int i, int j) {
+__device__ __forceinline__ float shock_theta(const Grid &g, const TnArrays &t, int dir, int i, int j) {
   const int di = dir == 0 ? 1 : 0, dj = 1 - di;
   float Um2[4], Um1[4], U0[4], Up1[4];
-  cell_prim(g, avg, i - 2 * di, j - 2 * dj, Um2);
-  cell_prim(g, avg, i - di, j - dj, Um1);
-  cell_prim(g, avg, i, j, U0);
-  cell_prim(g, avg, i + di, j + dj, Up1);
+  cell_prim(g, t, i - 2 * di, j - 2 * dj, Um2);
+  cell_prim(g, t, i - di, j - dj, Um1);
+  cell_prim(g, t, i, j, U0);
+  cell_prim(g, t, i + di, j + dj, Up1);
   const float phi1 = fmaxf(d2ratio(Up1[3], U0[3], Um1[3]), d2ratio(U0[3], Um1[3], Um2[3]));
   const float s0 = fabsf(U0[1 + dir]) + sqrtf(g.gamma * U0[3] / U0[0]);
   const float s1 = fabsf(Um1[1 + dir]) + sqrtf(g.gamma * Um1[3] / Um1[0]);
@@ -145,27 +145,30 @@ __device__ __forceinline__ float shock_theta(const Grid &g, const float *avg, in
 // thread (a, b), a <= nx + 1, b <= ny + 1: x-edge (a, b - 1) for a < nxv,
 // b - 1 in -1 .. ny, and y-edge (a - 1, b) for a - 1 in -1 .. nx, b < nyv: the
 // edges of every owned vertex (a vertex takes the minimum of its 4 edges)
-__device__ __forceinline__ void theta_entry(const Grid &g, const float *avg, float *tx, float *ty, int a, int b) {
-  if (a < g.nxv && b <= g.ny + 1) tx[at(g, 0, a, b - 1)] = shock_theta(g, avg, 0, a, b - 1);
-  if (a <= g.nx + 1 && b < g.nyv) ty[at(g, 0, a - 1, b)] = shock_theta(g, avg, 1, a - 1, b);
+__device__ __forceinline__ void theta_entry(const Grid &g, const TnArrays &t, float *tx, float *ty, int a, int b) {
+  if (a < g.nxv && b <= g.ny + 1) tx[at(g, 0, a, b - 1)] = shock_theta(g, t, 0, a, b - 1);
+  if (a <= g.nx + 1 && b < g.nyv) ty[at(g, 0, a - 1, b)] = shock_theta(g, t, 1, a - 1, b);
 }
-__global__ void shock_theta_kernel(Grid g, const float *avg, float *tx, float *ty) {
+__global__ void shock_theta_kernel(Grid g, TnArrays t, float *tx, float *ty) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
   if (a > g.nx + 1 || b > g.ny + 1) return;
-  theta_entry(g, avg, tx, ty, a, b);
+  theta_entry(g, t, tx, ty, a, b);
 }
 // batched: block k takes tile tiles[k] = (instance, a0, b0) of 32 x 8 entries
-// (tiles only for the instances with the blend on)
+// (tiles only for the instances with the blend on); the instance's arrays
+// (averages hi, lo, then the three node arrays) for its current t^n buffer
 __global__ void __launch_bounds__(256) shock_theta_batch_kernel(const int4 *tiles, const BatchCtl *ctl,
-                                                                const Grid *grids, const float *const *avg,
+                                                                const Grid *grids, const float *const *arrays,
                                                                 float *const *theta) {
-  const int4 t = tiles[blockIdx.x];
-  const int inst = t.x;
+  const int4 tl = tiles[blockIdx.x];
+  const int inst = tl.x;
   if (!ctl[inst].active || !theta[2 * inst]) return;
   const Grid &g = grids[inst];
-  const int a = t.y + threadIdx.x, b = t.z + threadIdx.y;
+  const int a = tl.y + threadIdx.x, b = tl.z + threadIdx.y;
   if (a > g.nx + 1 || b > g.ny + 1) return;
-  theta_entry(g, avg[(2 * inst + ctl[inst].cur) * 5], theta[2 * inst], theta[2 * inst + 1], a, b);
+  const float *const *arr = arrays + (2 * inst + ctl[inst].cur) * 5;
+  const TnArrays t = {arr[0], arr[2], arr[3], arr[4]};
+  theta_entry(g, t, theta[2 * inst], theta[2 * inst + 1], a, b);
 }
 
 // Per-instance dt for the coming step from the wave speed of the current
@@ -356,9 +359,11 @@ cudaError_t launch_ghost_batch(const GhostBatch &B, int nchunks, cudaStream_t s)
   return cudaGetLastError();
 }
 
-cudaError_t launch_shock_theta(const Grid &g, const float *avg_hi, float *tx, float *ty, cudaStream_t s) {
+cudaError_t launch_shock_theta(const Grid &g, const float *avg_hi, const NodeSet &n0, float *tx, float *ty,
+                               cudaStream_t s) {
   dim3 blk(32, 8), grd((g.nx + 2 + 31) / 32, (g.ny + 2 + 7) / 8);
-  shock_theta_kernel<<<grd, blk, 0, s>>>(g, avg_hi, tx, ty);
+  const TnArrays t = {avg_hi, n0.k[VTX], n0.k[XE], n0.k[YE]};
+  shock_theta_kernel<<<grd, blk, 0, s>>>(g, t, tx, ty);
   return cudaGetLastError();
 }
 

@@ -88,6 +88,17 @@ cudaError_t scratch_on(int dev, double **ptr) {
   return cudaSuccess;
 }
 
+// p is memory that kernels on device dev can read and write: device memory
+// of that device, or managed memory
+bool reachable_on(const void *p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
+}
+
 }  // namespace
 
 extern "C" int af_conserved_totals_noalloc(const float *avg, const float *avg_lo, int nx, int ny,
@@ -108,6 +119,10 @@ extern "C" int af_conserved_totals_noalloc(const float *avg, const float *avg_lo
     cudaGetLastError();
     return af::set_error(AF_ERR_ARG, "af_conserved_totals_noalloc: avg must be device memory");
   }
+  // the kernels run on avg's device: out and avg_lo must be reachable there
+  if (!reachable_on(out, a.device) || (avg_lo && !reachable_on(avg_lo, a.device)))
+    return af::set_error(AF_ERR_ARG,
+                         "af_conserved_totals_noalloc: out and avg_lo must be device memory on avg's device");
   double *rows = nullptr;
   cudaError_t e = scratch_on(a.device, &rows);
   if (e != cudaSuccess) {

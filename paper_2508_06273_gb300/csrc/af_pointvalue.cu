@@ -7,8 +7,9 @@
 // midpoint (i-1/2, j) and the y-edge midpoint (i, j-1/2).
 //
 // Prologue: for every cell of the tile and a one-cell halo the block forms
-// the cell prep (Q_c by inverting Simpson's rule, U_c = C2P(Q_c), Ubar the
-// primitive state of the cell average) and stores, per variable, the cell's biquadratic
+// the cell prep (Q_c by inverting Simpson's rule, U_c = C2P(Q_c), Ubar by
+// Simpson's rule over the primitive point values, or optionally the primitive
+// state of the cell average) and stores, per variable, the cell's biquadratic
 // reconstruction as monomial coefficients about the cell centre in shared
 // memory, plus Ubar.
 //
@@ -74,8 +75,6 @@ struct Tile {
   static constexpr int SMEM_BYTES = (RAW_FLOATS + REC_FLOATS) * 4 + 128;  // + alignment slack
 };
 enum { RAW_VTX = 0, RAW_XE = 1, RAW_YE = 2, RAW_AVG = 3 };
-// bound on the mbarrier wait (try_wait suspends in hardware between polls)
-constexpr unsigned WAIT_LIMIT = 1u << 22;
 
 using Args = PointValueArgs;
 
@@ -135,7 +134,6 @@ __device__ __forceinline__ void to_monomial(const float f[3][3], float m[3][3]) 
 template <int TY>
 __device__ __forceinline__ void build_cell(const Grid &g, const float *raw, int i0, int j0, int ci, int cj,
                                            float *rec) {
-  const float gm1 = g.gamma - 1.0f, gm1i = 1.0f / gm1;
   float N[8][4];  // corners (ll, lr, ul, ur), then edges (left, right, bottom, top)
   raw4<TY>(raw, RAW_VTX, ci, cj, i0, j0, N[0]);
   raw4<TY>(raw, RAW_VTX, ci + 1, cj, i0, j0, N[1]);
@@ -145,23 +143,10 @@ __device__ __forceinline__ void build_cell(const Grid &g, const float *raw, int 
   raw4<TY>(raw, RAW_XE, ci + 1, cj, i0, j0, N[5]);
   raw4<TY>(raw, RAW_YE, ci, cj, i0, j0, N[6]);
   raw4<TY>(raw, RAW_YE, ci, cj + 1, i0, j0, N[7]);
-  float Qs[4] = {0, 0, 0, 0};
+  float Qa[4], Uc[4], Ub[4];
 #pragma unroll
-  for (int n = 0; n < 8; n++) {
-    float Q[4];
-    p2c(N[n], gm1i, Q);
-    const float w = n < 4 ? 1.0f : 4.0f;
-#pragma unroll
-    for (int v = 0; v < NV; v++) Qs[v] += w * Q[v];
-  }
-  float Qa[4], Qc[4], Uc[4], Ub[4];
-#pragma unroll
-  for (int v = 0; v < NV; v++) {
-    Qa[v] = raw_at<TY>(raw, RAW_AVG, v, ci, cj, i0, j0);
-    Qc[v] = (36.0f * Qa[v] - Qs[v]) * 0.0625f;
-  }
-  c2p(Qc, gm1, Uc);
-  c2p(Qa, gm1, Ub);  // Ubar: the primitive state of the cell average (Sec. 3.5)
+  for (int v = 0; v < NV; v++) Qa[v] = raw_at<TY>(raw, RAW_AVG, v, ci, cj, i0, j0);
+  cell_prep(N, Qa, g.gamma, g.ubar_c2p, Uc, Ub);
 #pragma unroll
   for (int v = 0; v < NV; v++) {
     const float f[3][3] = {{N[0][v], N[4][v], N[2][v]}, {N[6][v], Uc[v], N[7][v]}, {N[1][v], N[5][v], N[3][v]}};
@@ -941,15 +926,17 @@ __device__ __forceinline__ unsigned smem_addr(const void *p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-// one thread: arm the barrier with the byte count and issue the four box loads
+// one thread: arm the barrier with the byte count and issue the four box
+// loads (no_copy: the timeout test hook, which arms it and issues nothing)
 template <int TY>
 __device__ __forceinline__ void tile_fetch(const TileMaps &T, float *raw, unsigned long long *bar, int i0,
-                                           int j0) {
+                                           int j0, int no_copy) {
   const unsigned b = smem_addr(bar);
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(Tile<TY>::RAW_BYTES) : "memory");
+  if (no_copy) return;
   // box origin: column i0 (grid index i0 - 4), row j0 + 1 (grid index j0 - 1), variable 0
   const int x = i0, y = j0 + OY - 1;
   const CUtensorMap *maps[4] = {&T.vtx, &T.xe, &T.ye, &T.avg};
@@ -964,9 +951,9 @@ __device__ __forceinline__ void tile_fetch(const TileMaps &T, float *raw, unsign
 }
 
 // bounded wait for phase 0 of the barrier; false on time-out
-__device__ __forceinline__ bool tile_wait(unsigned long long *bar) {
+__device__ __forceinline__ bool tile_wait(unsigned long long *bar, unsigned limit) {
   const unsigned b = smem_addr(bar);
-  for (unsigned it = 0; it < WAIT_LIMIT; it++) {
+  for (unsigned it = 0; it < limit; it++) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
@@ -984,14 +971,20 @@ __device__ __forceinline__ void tile_body(const Args &A, const TileMaps &T, floa
                                           int i0, int j0) {
   float *sm = raw + Tile<TY>::RAW_FLOATS;
   const int tid = threadIdx.y * TX + threadIdx.x;
-  if (tid == 0) tile_fetch<TY>(T, raw, bar, i0, j0);
+  if (tid == 0) tile_fetch<TY>(T, raw, bar, i0, j0, A.test_no_copy);
   __syncthreads();
-  if (!tile_wait(bar)) {
-    // the copy did not land in time: report it, give it one more bounded
-    // wait so that nothing is still writing this block's shared memory, and
-    // leave the tile alone
-    if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
-    tile_wait(bar);
+  const bool landed = tile_wait(bar, A.wait_limit);
+  if (!__syncthreads_and(landed)) {
+    // the copy did not land in time: report it (the host then refuses further
+    // steps of the handle) and leave the tile alone.  The block's shared
+    // memory stays allocated until its last thread exits, so thread 0 first
+    // waits kDrainFactor times longer for the copy to land; if even that runs
+    // out, the block exits with its copy unfinished.  Under the test hook no
+    // copy was issued and nothing is in flight.
+    if (tid == 0) {
+      atomicOr(A.status, ST_TIMEOUT);
+      if (!landed && !A.test_no_copy) tile_wait(bar, kDrainFactor * A.wait_limit);
+    }
     return;
   }
   tile_prologue<TY>(A, raw, sm, i0, j0, tid);

@@ -33,13 +33,11 @@ __device__ __forceinline__ void ld4g(const Grid &g, const float *p, int i, int j
   for (int v = 0; v < NV; v++) U[v] = __ldg(p + at(g, v, i, j));
 }
 
-// primitive cell average Ubar of cell (ci, cj): the primitive state of the
-// conservative cell average (the reading of Sec. 3.5 the point-value kernel uses)
-__device__ __forceinline__ void cell_ubar(const Grid &g, const float *avg, const float *, const float *,
-                                          const float *, int ci, int cj, float Ub[4]) {
-  float A[4];
-  ld4g(g, avg, ci, cj, A);
-  c2p(A, g.gamma - 1.0f, Ub);
+// primitive cell average Ubar of cell (ci, cj), as the point-value kernel
+// forms it (the grid's Ubar definition)
+__device__ __forceinline__ void cell_ubar(const Grid &g, const float *avg, const float *vtx, const float *xe,
+                                          const float *ye, int ci, int cj, float Ub[4]) {
+  cell_ubar_global(g, avg, vtx, xe, ye, ci, cj, Ub);
 }
 
 // values of the node's stencil (cells first, then points) in template order
@@ -264,7 +262,6 @@ constexpr unsigned O_W1 = 0, O_W2 = O_W1 + SZ_W1, O_W3 = O_W2 + SZ_W2, O_W4 = O_
 constexpr unsigned O_BUF = O_W4 + SZ_W4, O_B = O_BUF + NG * SZ_BUF;
 constexpr int NBIAS = 3 * NH + NOUT_PAD + NIN + NOUT;
 constexpr unsigned SURR_SMEM = O_B + NBIAS * 4 + 128;
-constexpr unsigned SURR_WAIT = 1u << 20;
 static_assert(SURR_SMEM <= 227 * 1024, "shared memory");
 
 // weights of one layer (R x Kd, row-major BF16) into the K-major core layout
@@ -447,9 +444,9 @@ __global__ void __launch_bounds__(NG *TM, 1) surrogate_kernel(SurrogateArgs A) {
       if (row == 0) {
         tc::fence_after_sync();
         const unsigned char *w = l == 0 ? W1s : (l == 1 ? W2s : (l == 2 ? W3s : W4s));
-        issue_layer(tcol, tc::smem_u32(buf), tc::smem_u32(w), Kd, l < 3 ? NH : NOUT_PAD, bar);
+        if (!A.test_no_issue) issue_layer(tcol, tc::smem_u32(buf), tc::smem_u32(w), Kd, l < 3 ? NH : NOUT_PAD, bar);
       }
-      if (!tc::bar_wait(bar, phase, SURR_WAIT)) gfail[grp] = 1;
+      if (!tc::bar_wait(bar, phase, A.wait_limit)) gfail[grp] = 1;
       phase ^= 1;
       group_sync(grp);
       if (gfail[grp]) {
@@ -469,10 +466,14 @@ __global__ void __launch_bounds__(NG *TM, 1) surrogate_kernel(SurrogateArgs A) {
       }
     }
     if (!ok) {
-      // the tensor cores did not finish in time: flag the step as invalid,
-      // give them one more bounded wait, and stop this group
+      // the tensor cores did not finish in time: flag the step as invalid
+      // (the host then refuses further steps of the handle), wait
+      // kDrainFactor times longer for the MMAs in flight before the tensor
+      // memory is released, and stop this group; if even that runs out, the
+      // group goes on with an MMA unfinished.  Under the test hook no MMA was
+      // issued and nothing is in flight.
       if (row == 0) atomicOr(A.status, ST_TIMEOUT);
-      tc::bar_wait(bar, phase ^ 1, SURR_WAIT);
+      if (!A.test_no_issue) tc::bar_wait(bar, phase ^ 1, kDrainFactor * A.wait_limit);
       break;
     }
     float y[32];

@@ -315,7 +315,8 @@ def four_quadrant(n=64, seed=0, t_end=0.25, cfl=0.3, states=None):
         st = np.asarray(states, dtype=np.float64)
     p = Problem(f"four_quadrant_seed{seed}", n, n, 0.0, 0.0, 1.0, 1.0, (1, 1, 1, 1),
                 _piecewise(st, 0.5, 0.5), t_end, cfl=cfl,
-                options={"tsw": 1, "limiter": 1, "flux_limiter": 1, "shock_blend": 1, "node_bounds": 1})
+                options={"tsw": 1, "limiter": 1, "flux_limiter": 1, "shock_blend": 1, "node_bounds": 1,
+                         "ubar": 1})
     p.states = st
     return p
 
@@ -326,7 +327,7 @@ def double_rarefaction(n=64, t_end=0.25, cfl=0.3, rho=1.0, p=0.4, speed=2.0):
     st = [(rho, -speed, 0.0, p), (rho, speed, 0.0, p), (rho, -speed, 0.0, p), (rho, speed, 0.0, p)]
     return Problem("double_rarefaction", n, n, 0.0, 0.0, 1.0, 1.0, (1, 1, 2, 2),
                    _piecewise(st, 0.5, -1.0), t_end, cfl=cfl,
-                   options={"limiter": 1, "flux_limiter": 1, "node_bounds": 1})
+                   options={"limiter": 1, "flux_limiter": 1, "node_bounds": 1, "ubar": 1})
 
 
 def kelvin_helmholtz(n=64, t_end=1.0, cfl=0.3):
@@ -342,7 +343,7 @@ def kelvin_helmholtz(n=64, t_end=1.0, cfl=0.3):
         return rho, u, v, 2.5 + 0.0 * x
 
     return Problem("kelvin_helmholtz", n, n, -0.5, -0.5, 1.0, 1.0, (0, 0, 0, 0), f, t_end,
-                   cfl=cfl, options={"limiter": 1})
+                   cfl=cfl, options={"limiter": 1, "ubar": 1})
 
 
 def shock_reflection(nx=120, ny=30, t_end=6.0, cfl=0.3):
@@ -360,7 +361,7 @@ def shock_reflection(nx=120, ny=30, t_end=6.0, cfl=0.3):
         return tuple(a + (b - a) * top for a, b in zip(A, B))
 
     p = Problem("shock_reflection", nx, ny, 0.0, 0.0, 4.0, 1.0, (3, 1, 2, 3), f, t_end, cfl=cfl,
-                options={"limiter": 0}, inflow={0: A, 3: B})
+                options={"limiter": 0, "ubar": 1}, inflow={0: A, 3: B})
     return p
 
 

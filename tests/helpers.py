@@ -4,7 +4,7 @@ import numpy as np
 from paper_2508_06273_gb300 import workloads as W
 
 OPTS = {"lin_mode": 0, "tsw": 1, "limiter": 2, "correction": 3, "force_lo": 4, "flux_limiter": 9,
-        "shock_blend": 10, "node_bounds": 12}
+        "shock_blend": 10, "node_bounds": 12, "ubar": 13}
 
 
 def make_oracle(oracle, prob, opts=None, state=None):

@@ -8,7 +8,7 @@ import pytest
 
 from helpers import make_oracle
 from paper_2508_06273_gb300 import workloads as W
-from test_gpu_parity import MILD, env, host, solver, state_err, to_dev  # noqa: F401
+from test_gpu_parity import MILD, assert_parity, env, host, solver, state_err, to_dev  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -60,8 +60,7 @@ def test_batch_matches_each_grid_stepped_alone(env):
             s.step(hist[n, k])
         want = host(s.get_state())
         got = host(b.get_state(k))
-        err = state_err(got, want)
-        assert err <= 1e-6, (k, p.name, err)
+        assert_parity(got, want, 1e-6, what=f"instance {k} ({p.name})")
         assert s.status() & ~8 == 0 and status[k] & ~8 == 0, (k, status[k])
         s.close()
     b.close()
@@ -76,8 +75,7 @@ def test_batch_instances_match_the_oracle(env, oracle_mod):
         o = make_oracle(oracle_mod, p, state=W.to_f32(W.discretise(p)))
         for n in range(3):
             o.step(hist[n, k])
-        err = state_err(host(b.get_state(k)), o.get_state())
-        assert err <= 3e-5, (k, p.name, err)
+        assert_parity(host(b.get_state(k)), o.get_state(), 3e-5, what=f"instance {k} ({p.name})")
     b.close()
 
 
@@ -149,7 +147,7 @@ def test_a_failing_instance_stops_alone(env):
     s = solver(env, probs[0])
     for n in range(12):
         s.step(hist[n, 0])
-    assert state_err(host(b.get_state(0)), host(s.get_state())) <= 1e-6
+    assert_parity(host(b.get_state(0)), host(s.get_state()), 1e-6, what="running instance")
     s.close()
     b.close()
 

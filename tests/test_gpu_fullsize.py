@@ -23,7 +23,7 @@ import pytest
 
 from helpers import make_oracle
 from paper_2508_06273_gb300 import workloads as W
-from test_gpu_parity import FINAL_TOL, env, host, solver, state_err  # noqa: F401
+from test_gpu_parity import FINAL_TOL, assert_parity, env, host, solver, state_err  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -94,8 +94,7 @@ def test_vortex_sweep_128_to_t2_follows_the_oracle(env):
         s.step(dt)
         t += dt
     assert s.status() == 0
-    err = state_err(host(s.get_state()), o.get_state())
-    assert err < FINAL_TOL, err
+    assert_parity(host(s.get_state()), o.get_state(), FINAL_TOL, what="128^2 vortex at t = 2")
 
 
 def test_vortex_2048_conservation_per_step(env):

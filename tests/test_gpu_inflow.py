@@ -7,7 +7,7 @@ import pytest
 
 from helpers import make_oracle
 from paper_2508_06273_gb300 import workloads as W
-from test_gpu_parity import env, host, solver, state_err  # noqa: F401
+from test_gpu_parity import assert_parity, env, host, solver  # noqa: F401
 from test_oracle_pins import _regular_reflection
 
 pytestmark = pytest.mark.gpu
@@ -21,7 +21,7 @@ def test_constant_inflow_state_is_preserved(env):
     s0 = host(s.get_state())
     for _ in range(5):
         s.step(0.3 * prob.dx / s.max_speed())
-    assert state_err(host(s.get_state()), s0) < 1e-6
+    assert_parity(host(s.get_state()), s0, 1e-6, what="constant inflow")
     assert s.status() == 0
 
 
@@ -35,8 +35,7 @@ def test_shock_reflection_follows_the_oracle(env):
         dt = 0.3 * prob.dx / o.max_speed()
         o.step(dt)
         s.step(dt)
-    err = state_err(host(s.get_state()), o.get_state())
-    assert err < 8e-5, err
+    assert_parity(host(s.get_state()), o.get_state(), 8e-5, what="shock reflection")
     assert s.status() == 0
 
 

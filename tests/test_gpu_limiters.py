@@ -7,7 +7,7 @@ import pytest
 
 from helpers import make_oracle
 from paper_2508_06273_gb300 import workloads as W
-from test_gpu_parity import env, host, solver, state_err  # noqa: F401
+from test_gpu_parity import assert_parity, env, host, solver, state_err  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -34,8 +34,7 @@ def test_flux_limiter_matches_the_oracle_while_acting(env):
         so, sg = o.status(), s.status()
         assert bool(so & oracle.ST_FLUX_LIMITED) == bool(sg & af.ST_FLUX_LIMITED), k
         assert not sg & (af.ST_AVG_NONPOS | af.ST_NONFINITE)
-    err = state_err(host(s.get_state()), o.get_state())
-    assert err < 1e-4, err
+    assert_parity(host(s.get_state()), o.get_state(), 1e-4, what="flux limiter")
     assert _admissible(host(s.get_state()))
 
 
@@ -58,7 +57,7 @@ def test_shock_blend_matches_the_oracle(env):
         s.step(dt)
     # the blend changes the result measurably, and the GPU follows the oracle
     assert state_err(o.get_state(), plain.get_state()) > 1e-4
-    assert state_err(host(s.get_state()), o.get_state()) < 3e-5
+    assert_parity(host(s.get_state()), o.get_state(), 3e-5, what="shock blend")
 
 
 def test_limiters_leave_smooth_data_bitwise_alone(env):
@@ -119,8 +118,7 @@ def test_flux_limiter_on_tile_boundaries(env):
     assert acted_o and acted_g
     t1 = s.totals()
     assert np.all(np.abs(t1 - t0) <= 1e-9 * np.maximum(1.0, np.abs(t0))), (t0, t1)
-    err = state_err(host(s.get_state()), o.get_state())
-    assert err < 1e-4, err
+    assert_parity(host(s.get_state()), o.get_state(), 1e-4, what="flux limiter on tile boundaries")
 
 
 @pytest.mark.parametrize("seed", range(8))

@@ -48,7 +48,8 @@ def test_sampled_features_and_targets_match_the_oracle(env, oracle_mod):
                 if not m.any():
                     continue
                 I, J = ids[m, 3] & 0xFFFF, ids[m, 3] >> 16
-                Xo, ut, sc = S.features(st, p.bc, kind, I, J, dts[k], p.dx)
+                Xo, ut, sc = S.features(st, p.bc, kind, I, J, dts[k], p.dx,
+                                        ubar_c2p=p.options.get("ubar", 0))
                 U0 = S.node_values(st, kind, I, J)
                 U1 = np.asarray(half[kind])[:, J, I].T
                 U2 = np.asarray(new[1 + kind])[:, J, I].T

@@ -35,9 +35,9 @@ def _run(env, prob, opts):
     return q
 
 
-def _table(env, make, ns, per_row):
-    errs = {c: [] for c in VARIANTS}
-    for col, opts in VARIANTS.items():
+def _table(env, make, ns, per_row, variants=VARIANTS):
+    errs = {c: [] for c in variants}
+    for col, opts in variants.items():
         for n in ns:
             c, f = make(n, False), make(n, True)
             e = np.abs(_run(env, c, opts)[0] - restrict2(_run(env, f, opts))[0])
@@ -70,6 +70,23 @@ def test_table2_example2(env):
     _check(_table(env, make, ns, per_row=False), tab, ns)
 
 
+@pytest.mark.parametrize("ubar", [0, 1])
+@pytest.mark.parametrize("table", [1, 2])
+def test_tables_with_the_averaged_linearisation(env, table, ubar):
+    """The averaged linearisation of eq. (Un+1/2) with the correction gives
+    almost the errors of the tables' first column (Sec. 3.1 says so), under
+    either definition of Ubar (Sec. 2's Simpson mean, or C2P of the average)."""
+    name = "table1_ex1.txt" if table == 1 else "table2_ex2.txt"
+    tab = read_table(os.path.join(GOLDEN, name))
+    ns = [32, 64, 128, 256]
+    if table == 1:
+        make = lambda n, fine: W.gaussian_pulse(2 * n if fine else n, 16 if fine else 8, cfl=0.25)  # noqa: E731
+    else:
+        make = lambda n, fine: W.compact_vortex(2 * n if fine else n)  # noqa: E731
+    variants = {1: {"lin_mode": 0, "correction": 1, "ubar": ubar}}
+    _check(_table(env, make, ns, per_row=table == 1, variants=variants), tab, ns)
+
+
 @pytest.mark.parametrize("limited", [False, True])
 def test_kelvin_helmholtz_to_t1(env, limited):
     """Sec. 4.2's shear layer on 128^2 cells, periodic, to t = 1, without and
@@ -77,7 +94,8 @@ def test_kelvin_helmholtz_to_t1(env, limited):
     value stays admissible and the totals are conserved to round-off."""
     torch, af, _ = env
     prob = W.kelvin_helmholtz(128)
-    opts = {"limiter": 1, "shock_blend": 1} if limited else {"limiter": 0}
+    opts = dict(prob.options)
+    opts.update({"limiter": 1, "shock_blend": 1} if limited else {"limiter": 0})
     s = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=opts)
     s.set_state(*[torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
                   for a in W.to_f32(W.discretise(prob))])

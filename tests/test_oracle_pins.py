@@ -61,14 +61,30 @@ def node_xy(prob, kind, i, j):
 
 
 # ------------------------------------------------------------ reconstruction
-def test_recon_reproduces_biquadratic(oracle_mod):
-    """cpq is exact for biquadratic data, its centre value inverts Simpson's
-    rule on the cell average, and Ubar is the primitive state of the average."""
+def _gauss_cell_mean(f, x0, y0, dx, dy, npts=3):
+    """Mean of f over [x0, x0 + dx] x [y0, y0 + dy] by tensor Gauss-Legendre
+    (npts points per axis: exact for degree <= 2 npts - 1 in each variable)."""
+    t, w = np.polynomial.legendre.leggauss(npts)
+    t, w = 0.5 * (t + 1.0), 0.5 * w
+    out = 0.0
+    for a in range(npts):
+        for b in range(npts):
+            out = out + w[a] * w[b] * np.array(f(x0 + dx * t[a], y0 + dy * t[b]), dtype=np.float64)
+    return out
+
+
+@pytest.mark.parametrize("ubar", [0, 1])
+def test_recon_reproduces_biquadratic(oracle_mod, ubar):
+    """cpq is exact for biquadratic data and its centre value inverts
+    Simpson's rule on the cell average.  Ubar: with the default (Sec. 2,
+    Simpson's rule over the primitive point values) it is the exact primitive
+    cell mean of the biquadratic field; with ubar = 1 it is the primitive
+    state of the conservative average."""
     rng = np.random.default_rng(3)
     prob = box()
     coef = random_poly(rng)
     f = poly_field(coef)
-    o = make_oracle(oracle_mod, prob, state=q2_state(prob, f))
+    o = make_oracle(oracle_mod, prob, opts={"ubar": ubar}, state=q2_state(prob, f))
     o.prepare()
     for _ in range(40):
         i, j = rng.integers(0, 6, size=2)
@@ -77,8 +93,7 @@ def test_recon_reproduces_biquadratic(oracle_mod):
         want = np.array(f(prob.dx * (i + xi), prob.dy * (j + eta)))
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
     # the centre value inverts Simpson's rule in conservative variables: the
-    # Simpson mean of the 9 conserved nodal values is the cell average; Ubar
-    # is the primitive state of the cell average
+    # Simpson mean of the 9 conserved nodal values is the cell average
     avg, vtx, xe, ye = o.get_state()
     g = prob.gamma
 
@@ -92,9 +107,70 @@ def test_recon_reproduces_biquadratic(oracle_mod):
              + 4 * (p2c(xe[:, j, i]) + p2c(xe[:, j, i + 1]) + p2c(ye[:, j, i]) + p2c(ye[:, j + 1, i]))
              + 16 * p2c(uc)) / 36
         np.testing.assert_allclose(Q, avg[:, j, i], rtol=1e-13, atol=1e-13)
-        Qa = avg[:, j, i]
-        want = [Qa[0], Qa[1] / Qa[0], Qa[2] / Qa[0], (g - 1) * (Qa[3] - 0.5 * (Qa[1] ** 2 + Qa[2] ** 2) / Qa[0])]
-        np.testing.assert_allclose(ub, want, rtol=1e-13)
+        if ubar == 0:
+            want = _gauss_cell_mean(f, prob.dx * i, prob.dy * j, prob.dx, prob.dy)
+            np.testing.assert_allclose(ub, want, rtol=0, atol=1e-13)
+        else:
+            Qa = avg[:, j, i]
+            want = [Qa[0], Qa[1] / Qa[0], Qa[2] / Qa[0], (g - 1) * (Qa[3] - 0.5 * (Qa[1] ** 2 + Qa[2] ** 2) / Qa[0])]
+            np.testing.assert_allclose(ub, want, rtol=1e-13)
+
+
+def test_ubar_definitions_on_biquadratic_conserved_data(oracle_mod):
+    """rho = 1, u = a + b x, v = c + d y, p biquadratic: both the primitive and
+    the conserved fields are biquadratic (E = p/(gamma-1) + (u^2 + v^2)/2), so
+    cell averages are exact Gauss means and Simpson's rule is exact for both.
+    Sec. 2's Ubar (default) is then the exact primitive cell mean; C2P of the
+    average (ubar = 1) has the exact rho, u, v but a pressure above the mean
+    by (gamma - 1)/2 (var u + var v) = (gamma - 1)/24 (b^2 dx^2 + d^2 dy^2).
+    The two definitions differ exactly by that closed form."""
+    prob = box(nx=5, ny=4, dx=0.3, dy=0.2)
+    g = prob.gamma
+    a, b, c, d = 0.4, 1.3, -0.2, -0.9
+    pc = np.array([[1.2, 0.3, -0.4], [0.2, -0.1, 0.05], [0.3, 0.1, -0.2]])
+
+    def f(x, y):
+        x, y = np.broadcast_arrays(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
+        p = sum(pc[k][l] * x ** k * y ** l for k in range(3) for l in range(3))
+        return 1.0 + 0 * x, a + b * x, c + d * y, p
+
+    def q(x, y):
+        r, u, v, p = f(x, y)
+        return r, r * u, r * v, p / (g - 1) + 0.5 * r * (u * u + v * v)
+
+    _, vtx, xe, ye = W.discretise(prob, f)
+    avg = np.zeros((4, prob.ny, prob.nx))
+    for j in range(prob.ny):
+        for i in range(prob.nx):
+            avg[:, j, i] = _gauss_cell_mean(q, prob.dx * i, prob.dy * j, prob.dx, prob.dy)
+    excess = (g - 1) / 24 * (b * b * prob.dx ** 2 + d * d * prob.dy ** 2)
+    for ubar in (0, 1):
+        o = make_oracle(oracle_mod, prob, opts={"ubar": ubar}, state=(avg, vtx, xe, ye))
+        o.prepare()
+        for (i, j) in [(0, 0), (2, 1), (4, 3)]:
+            _, ub = o.cell_prim(i, j)
+            mean = _gauss_cell_mean(f, prob.dx * i, prob.dy * j, prob.dx, prob.dy)
+            np.testing.assert_allclose(ub[:3], mean[:3], rtol=0, atol=1e-13)
+            np.testing.assert_allclose(ub[3] - mean[3], excess * ubar, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("ubar", [0, 1])
+def test_averaged_linearisation_reproduces_tables(oracle_mod, ubar):
+    """The averaged linearisation (eq. (Un+1/2)) gives almost the same errors as
+    Tables 1 and 2 (Sec. 3.1 says so), under either definition of Ubar: Table 1
+    (with correction) within 5% at 32 and 64 cells and its EOC within 0.1,
+    Table 2 at 32 cells within 10%."""
+    t1 = read_table(os.path.join(GOLDEN, "table1_ex1.txt"))
+    t2 = read_table(os.path.join(GOLDEN, "table2_ex2.txt"))
+    opts = {"lin_mode": 0, "ubar": ubar}
+    pulse = lambda nx, ny: W.gaussian_pulse(nx, ny, cfl=0.25)  # noqa: E731
+    e32 = _paper_l1(oracle_mod, pulse(32, 8), pulse(64, 16), opts, per_row=True)
+    e64 = _paper_l1(oracle_mod, pulse(64, 8), pulse(128, 16), opts, per_row=True)
+    assert abs(e32 / t1[0, 1] - 1) < 0.05, (e32, t1[0, 1])
+    assert abs(e64 / t1[1, 1] - 1) < 0.05, (e64, t1[1, 1])
+    assert abs(np.log2(e32 / e64) - t1[1, 2]) < 0.1
+    v32 = _paper_l1(oracle_mod, W.compact_vortex(32), W.compact_vortex(64), opts)
+    assert abs(v32 / t2[0, 1] - 1) < 0.1, (v32, t2[0, 1])
 
 
 def test_recon_continuous_across_faces(oracle_mod):
@@ -626,7 +702,8 @@ def test_ex2_pressure_is_pressure_balance():
 def test_shock_theta_formula(oracle_mod):
     """theta = exp(-phi1 phi2) of Sec. 3.4 on averages that vary in x only:
     1 where the pressure is linear, the hand-computed value next to a jump,
-    and a vertex takes the smallest theta of its four edges."""
+    and a vertex takes the smallest theta of its four edges.  Ubar is taken
+    as C2P of the averages (ubar = 1), so the averages set it directly."""
     g = 1.4
     n = 8
     pbar = np.array([1.0, 1.0, 1.0, 1.0, 2.0, 2.0, 2.5, 3.0])  # cells 0..7 (periodic in y)
@@ -637,7 +714,7 @@ def test_shock_theta_formula(oracle_mod):
     avg[1] = ubar[None, :]
     avg[3] = pbar[None, :] / (g - 1) + 0.5 * ubar[None, :] ** 2
     vtx, xe, ye = np.ones((4, 5, n + 1)), np.ones((4, 4, n + 1)), np.ones((4, 5, n))
-    o = make_oracle(oracle_mod, prob, state=(avg, vtx, xe, ye))
+    o = make_oracle(oracle_mod, prob, opts={"ubar": 1}, state=(avg, vtx, xe, ye))
     o.prepare()
     c = np.sqrt(g * pbar)
 

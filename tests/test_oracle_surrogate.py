@@ -9,15 +9,17 @@ from oracle import surrogate as S
 from paper_2508_06273_gb300 import workloads as W
 
 
-def test_ubar_matches_the_c_oracle(oracle_mod):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_ubar_matches_the_c_oracle(oracle_mod, mode):
     prob = W.four_quadrant(12, states=[(1.0, 0.1, -0.2, 1.0), (0.8, 0.3, 0.1, 0.7),
                                        (1.2, -0.1, 0.2, 1.1), (0.9, 0.0, 0.3, 0.9)])
     prob.bc = (1, 2, 2, 1)  # outflow and walls: ghost cells of both kinds
     st = W.discretise(prob)
     o = oracle_mod.Oracle(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc)
+    o.set_option(oracle_mod.OPT_UBAR, mode)
     o.set_state(*st)
     o.prepare()
-    ub = S.ubar(S.extend(st, prob.bc))
+    ub = S.ubar(S.extend(st, prob.bc), c2p_mode=mode)
     for j in range(-1, prob.ny + 1):
         for i in range(-1, prob.nx + 1):
             _, want = o.cell_prim(i, j)
