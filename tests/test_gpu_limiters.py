@@ -21,7 +21,12 @@ def _admissible(state, g=1.4):
 
 def test_flux_limiter_matches_the_oracle_while_acting(env):
     """Near-vacuum double rarefaction (u = -+2, p = 0.1): both sides limit
-    fluxes on the same steps; the states agree to FP32 level."""
+    fluxes on the same steps; the states agree to FP32 level in L1.  The
+    element gate is 2e-2 here: next to the vacuum (p about 1.5e-3 at the
+    walls) hundreds of point values a step take Alg. 3's EG1 or
+    Lax-Friedrichs branch, and which branch a marginal node takes is decided
+    by FP32 or FP64 rounding; such a node differs by about 1% of its own tiny
+    value (measured 9e-3), while the whole state stays within 1e-4."""
     torch, af, oracle = env
     prob = W.double_rarefaction(32, p=0.1)
     st = W.to_f32(W.discretise(prob))
@@ -34,7 +39,7 @@ def test_flux_limiter_matches_the_oracle_while_acting(env):
         so, sg = o.status(), s.status()
         assert bool(so & oracle.ST_FLUX_LIMITED) == bool(sg & af.ST_FLUX_LIMITED), k
         assert not sg & (af.ST_AVG_NONPOS | af.ST_NONFINITE)
-    assert_parity(host(s.get_state()), o.get_state(), 1e-4, what="flux limiter")
+    assert_parity(host(s.get_state()), o.get_state(), 1e-4, elem_tol=2e-2, what="flux limiter")
     assert _admissible(host(s.get_state()))
 
 
