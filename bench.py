@@ -424,14 +424,185 @@ def run_ours(args):
         line["accuracy"] = accuracy_leg(torch, af, W, n)
     if world == 1 and args.batch_steps > 0:
         line["batch"] = run_batch_leg(args, torch, af, W)
-    if world == 1 and args.surr_steps > 0:
-        line["surrogate"] = run_surrogate_leg(args, torch, af, W)
+    refs = None
+    if world == 1 and not args.no_cpu and (args.surrogate or args.convergence):
+        refs = oracle_references(af, W, args)
+    if world == 1 and not args.no_cpu and args.convergence:
+        line["convergence"] = convergence_leg(torch, af, W, refs)
+    if world == 1 and args.surrogate:
+        line["surrogate"] = run_surrogate_leg(args, torch, af, W, refs)
     if world == 1 and not args.no_cpu:
         v, threads, desc, _ = cpu_sample(n, min_seconds=args.cpu_seconds)
         v1, _, desc1, _ = cpu_sample(n, min_seconds=0.5 * args.cpu_seconds, threads=1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
                                 "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": desc1}}
     print(json.dumps(line), flush=True)
+
+
+def _oracle_run(af, W, prob, t_end, max_steps=1_000_000):
+    """FP64 oracle from the FP32-rounded initial data of ``prob`` to t_end,
+    dt = cfl h / (max speed) each step (the last step clipped), on all host
+    cores.  Returns (state, dts, seconds)."""
+    import oracle
+
+    o = oracle.Oracle(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc)
+    o.set_option(oracle.OPT_THREADS, len(os.sched_getaffinity(0)))
+    for k, v in prob.options.items():
+        o.set_option(af.OPT[k], v)
+    o.set_state(*W.to_f32(W.discretise(prob)))
+    t, dts, t0 = 0.0, [], time.perf_counter()
+    while t < t_end * (1 - 1e-12) and len(dts) < max_steps:
+        speed = o.max_speed()
+        if not speed > 0.0 or speed == float("inf"):
+            raise RuntimeError(f"oracle: wave speed {speed} at step {len(dts)}, t = {t:.6g}")
+        dt = min(prob.cfl * min(prob.dx, prob.dy) / speed, t_end - t)
+        o.step(dt)
+        dts.append(dt)
+        t += dt
+    return o.get_state(), dts, time.perf_counter() - t0
+
+
+def _gpu_replay(torch, af, W, prob, dts, nets=None):
+    """GPU run of ``prob`` from the same FP32 initial data with the given dt
+    sequence (plain, or the surrogate with exact fallback when nets are
+    given).  Returns (state as float64 arrays, status, fallback fraction)."""
+    import numpy as np
+
+    s = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=prob.options)
+    s.set_state(*[torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+                  for a in W.to_f32(W.discretise(prob))])
+    if nets:
+        s.set_surrogate(nets[0], nets[1])
+    status = 0
+    for dt in dts:
+        s.step(dt)
+    status |= s.status()
+    frac = None
+    if nets:
+        n_net, n_fall = s.surrogate_stats()
+        frac = n_fall / max(1, n_net + n_fall)
+    out = [a.double().cpu().numpy() for a in s.get_state()]
+    s.close()
+    return out, status, frac
+
+
+def _rel_l1(a_state, b_state):
+    """max over the four arrays and variables of sum|a - b| / scale, the
+    scale sum|b| for rho and p (E), sum(|u| + |v| + 1) for the velocities
+    (momenta): the relative L1 the accuracy figures use."""
+    import numpy as np
+
+    worst = 0.0
+    for a, b in zip(a_state, b_state):
+        for v in range(4):
+            scale = np.abs(b[v]).sum() if v in (0, 3) else (np.abs(b[1]) + np.abs(b[2]) + 1.0).sum()
+            worst = max(worst, float(np.abs(a[v] - b[v]).sum() / scale))
+    return worst
+
+
+def _vortex_l1_vs_exact(W, prob, rho, t, radius=2.5):
+    """mean |rho - rho_exact| over the cell averages: the whole box, and the
+    cells within ``radius`` of the moving vortex centre (periodic distance)."""
+    import numpy as np
+
+    ex = W.discretise(prob, prob.exact(t))[0][0]
+    err = np.abs(rho - ex)
+    xc = prob.x0 + prob.dx * (np.arange(prob.nx) + 0.5)
+    yc = prob.y0 + prob.dy * (np.arange(prob.ny) + 0.5)
+    cx, cy = prob.vortex_centre(t)
+    L = prob.lx
+    dx = (xc[None, :] - cx + 0.5 * L) % L - 0.5 * L
+    dy = (yc[:, None] - cy + 0.5 * L) % L - 0.5 * L
+    near = dx * dx + dy * dy <= radius * radius
+    return float(err.mean()), float(err[near].mean())
+
+
+def oracle_references(af, W, args):
+    """FP64 oracle runs the accuracy legs compare with (host cores, FP32
+    initial data): the seeded vortex at 128^2 and 256^2 to t = 2 (K2), the
+    four-quadrant problem of seed 6 at 256^2 to the Riemann leg's final time."""
+    refs = {}
+    for n in (128, 256):
+        prob = W.shu_vortex_seeded(n, t_end=2.0)
+        refs[f"vortex{n}"] = (prob,) + _oracle_run(af, W, prob, 2.0)
+    prob = W.four_quadrant(256, seed=6)
+    refs["riemann256"] = (prob,) + _oracle_run(af, W, prob, args.riemann_t)
+    return refs
+
+
+def convergence_leg(torch, af, W, refs, seg_steps=400):
+    """Isentropic-vortex sweep (seed 2508 law): 128^2 and 256^2 to t = 2
+    against the FP64 oracle (same dt sequence) and the exact solution; 512^2
+    and 2048^2 to t = 2 on the GPU against the exact solution, the 2048^2 run
+    with its conserved totals every step; 8192^2 for ``seg_steps`` steps of
+    fixed dt."""
+    import numpy as np
+
+    out = {}
+    for n in (128, 256):
+        prob, ora, dts, osec = refs[f"vortex{n}"]
+        gpu, status, _ = _gpu_replay(torch, af, W, prob, dts)
+        t = float(sum(dts))
+        g_all, g_near = _vortex_l1_vs_exact(W, prob, gpu[0][0], t)
+        o_all, o_near = _vortex_l1_vs_exact(W, prob, ora[0][0], t)
+        out[f"{n}^2"] = {"t": t, "steps": len(dts), "rel_l1_vs_oracle": _rel_l1(gpu, ora),
+                         "l1_rho_vs_exact": g_all, "l1_rho_vs_exact_near_vortex": g_near,
+                         "oracle_l1_rho_vs_exact": o_all, "oracle_l1_rho_vs_exact_near_vortex": o_near,
+                         "status": status, "oracle_seconds": osec}
+    for n in (512, 2048):
+        prob = W.shu_vortex_seeded(n, t_end=2.0)
+        s = af.Solver(n, n, prob.dx, prob.dy, prob.gamma, prob.bc)
+        s.set_state(*W.discretise_torch(prob, "cuda"))
+        absq = np.abs(W.discretise(prob)[0]).sum(axis=(1, 2)) * prob.dx * prob.dy if n <= 2048 else None
+        tot = [s.totals()]
+        t, k, failed = 0.0, 0, None
+        while t < 2.0 * (1 - 1e-12):
+            speed = s.max_speed()
+            if not speed > 0.0 or not np.isfinite(speed):
+                failed = f"wave speed {speed} at step {k}, t = {t:.6g}"
+                break
+            dt = min(prob.cfl * prob.dx / speed, 2.0 - t)
+            s.step(dt)
+            t += dt
+            k += 1
+            if n == 2048:
+                tot.append(s.totals())
+        status = s.status()
+        if failed:
+            s.close()
+            out[f"{n}^2"] = {"failed": failed, "status": status, "steps": k, "t": t}
+            continue
+        rho = s.get_state()[0][0].double().cpu().numpy()
+        s.close()
+        e_all, e_near = _vortex_l1_vs_exact(W, prob, rho, t)
+        rec = {"t": t, "steps": k, "l1_rho_vs_exact": e_all, "l1_rho_vs_exact_near_vortex": e_near,
+               "status": status}
+        if n == 2048:
+            tot = np.array(tot)
+            rec["drift_per_step_max"] = float((np.abs(np.diff(tot, axis=0)) / absq).max())
+            rec["drift_total"] = [float(x) for x in np.abs(tot[-1] - tot[0]) / absq]
+        out[f"{n}^2"] = rec
+    n = 8192
+    prob = W.shu_vortex_seeded(n)
+    s = af.Solver(n, n, prob.dx, prob.dy, prob.gamma, prob.bc)
+    s.set_state(*W.discretise_torch(prob, "cuda"))
+    t0 = s.totals()
+    dt = prob.cfl * prob.dx / s.max_speed()
+    s.run(seg_steps, dt)
+    t1 = s.totals()
+    status = s.status()
+    rho = s.get_state()[0][0]
+    s.close()
+    mass = float(np.abs(t0[0]))
+    e_all, e_near = _vortex_l1_vs_exact(W, prob, rho.double().cpu().numpy(), seg_steps * dt)
+    out["8192^2"] = {"t": seg_steps * dt, "steps": seg_steps, "fixed_dt": dt, "l1_rho_vs_exact": e_all,
+                     "l1_rho_vs_exact_near_vortex": e_near, "status": status,
+                     "mass_drift_total": abs(float(t1[0] - t0[0])) / mass}
+    out["note"] = ("mean |rho - rho_exact| over cell averages, whole box and within 2.5 of the vortex centre; "
+                   "the vortex is not periodic: its minimum-image data have a kink at distance 5 from the "
+                   "centre (size about eps e^-12 / 2 pi, 3e-5 in velocity), whose waves set the whole-box "
+                   "floor; FP32 point values set a second floor near 1e-7 at the finest grids")
+    return out
 
 
 def run_batch_leg(args, torch, af, W):
@@ -501,52 +672,110 @@ def _train_surrogate(args, af, W, probs, seed):
     return nets, int(Xv.shape[0]), int(Xe.shape[0])
 
 
-def _surrogate_case(args, torch, af, W, prob, nets, steps):
-    """Surrogate + exact fallback against the plain path on one grid: both
-    start from the same state and take the same dt."""
-    n = prob.nx
+def _surrogate_full(args, torch, af, W, prob, nets, t_end):
+    """Plain path and surrogate + exact fallback on the full-size grid from
+    the same state to t_end: the plain run takes dt = cfl h / (its max speed)
+    each step (the last one clipped); the surrogate run takes the same dt
+    sequence, or its own CFL dt where that is smaller, until it reaches t_end.
+    Each run is timed with CUDA events around all its steps (the per-step
+    max-speed reads included, as in the plain run)."""
     dev = W.discretise_torch(prob, "cuda")
     plain = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=prob.options)
     surr = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=prob.options)
-    plain.set_state(*dev)
-    surr.set_state(*dev)
+    surr.set_surrogate(nets[0], nets[1])
+    h = min(prob.dx, prob.dy)
+    for s in (plain, surr):  # warm-up steps, then the initial state again
+        s.set_state(*dev)
+        s.run(args.warmup, prob.cfl * h / s.max_speed())
+        s.set_state(*dev)
+        s.status()
     del dev
-    surr.set_surrogate(nets[0][0], nets[1][0])
-    dt = prob.cfl * prob.dx / plain.max_speed()
+    surr.surrogate_stats(reset=True)
     stream = torch.cuda.current_stream()
-    times = {}
+    runs = {}
+    dts = []
     for name, s in (("plain", plain), ("surrogate", surr)):
-        s.run(args.warmup, dt)
-        s.surrogate_stats(reset=True)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         ev0.record(stream)
-        s.run(steps, dt)
+        t, k = 0.0, 0
+        while t < t_end * (1 - 1e-12):
+            speed = s.max_speed()
+            if not speed > 0.0 or speed == float("inf"):
+                runs["failed"] = f"{name}: wave speed {speed} at step {k}, t = {t:.6g}"
+                break
+            dt = prob.cfl * h / speed
+            if name == "surrogate" and k < len(dts):
+                dt = min(dt, dts[k])
+            dt = min(dt, t_end - t)
+            s.step(dt)
+            if name == "plain":
+                dts.append(dt)
+            t += dt
+            k += 1
         ev1.record(stream)
         torch.cuda.synchronize()
-        times[name] = ev0.elapsed_time(ev1) / steps
+        runs[name] = (ev0.elapsed_time(ev1), k, s.status())
+        if "failed" in runs:
+            break
     n_net, n_fall = surr.surrogate_stats()
     a, c = surr.get_state(), plain.get_state()
     rel = 0.0
     for x, y in zip(a, c):
         for v in (0, 3):  # density and energy / pressure: no vanishing components
             rel = max(rel, float((x[v].double() - y[v].double()).abs().sum() / y[v].double().abs().sum()))
-    status = surr.status()
     for s in (plain, surr):
         s.close()
     cells = prob.nx * prob.ny
-    return {"value": cells / (times["surrogate"] / 1e3), "plain_value": cells / (times["plain"] / 1e3),
-            "unit": UNIT, "ms_per_step": times["surrogate"], "plain_ms_per_step": times["plain"],
-            "speedup_vs_plain": times["plain"] / times["surrogate"], "rel_l1_vs_plain": rel,
-            "fallback_fraction": n_fall / max(1, n_net + n_fall), "status": status}
+    if "failed" in runs:
+        return {"grid": [prob.nx, prob.ny], "final_time": t_end, "failed": runs["failed"],
+                "status": sst_or_none(runs, "surrogate"), "plain_status": sst_or_none(runs, "plain")}
+    (pm, pk, pst), (sm, sk, sst) = runs["plain"], runs["surrogate"]
+    allowed = af.ST_FLUX_LIMITED
+    out = {"grid": [prob.nx, prob.ny], "final_time": t_end, "steps_plain": pk, "steps_surrogate": sk,
+           "value": cells * sk / (sm / 1e3), "plain_value": cells * pk / (pm / 1e3), "unit": UNIT,
+           "ms_per_step": sm / sk, "plain_ms_per_step": pm / pk,
+           "speedup_vs_plain": (cells * sk / sm) / (cells * pk / pm),
+           "rel_l1_vs_plain": rel, "fallback_fraction": n_fall / max(1, n_net + n_fall),
+           "status": sst, "plain_status": pst}
+    bad = (pst | sst) & ~allowed
+    if bad:
+        out["failed"] = f"status bits {bad} other than AF_ST_FLUX_LIMITED"
+    return out
 
 
-def run_surrogate_leg(args, torch, af, W):
-    """Learned surrogate + exact fallback against the plain path: the 4096^2
-    isentropic vortex (centre and strength from seed 5), networks trained on
-    small seeded vortices; and the 2048^2 four-quadrant Riemann problem (seed
-    6, with its limiters), networks trained on small seeded four-quadrant
-    problems.  Training runs here, on the GPU."""
+def sst_or_none(runs, name):
+    return runs[name][2] if name in runs else None
+
+
+def _surrogate_vs_oracle(torch, af, W, ref, nets, vortex):
+    """Plain and surrogate GPU runs at the oracle's size, with the oracle's dt
+    sequence, against the FP64 oracle at its final time."""
+    prob, ora, dts, osec = ref
+    plain, pst, _ = _gpu_replay(torch, af, W, prob, dts)
+    surr, sst, frac = _gpu_replay(torch, af, W, prob, dts, nets)
+    rp, rs = _rel_l1(plain, ora), _rel_l1(surr, ora)
+    out = {"grid": [prob.nx, prob.ny], "final_time": float(sum(dts)), "steps": len(dts),
+           "rel_l1_plain_vs_oracle": rp, "rel_l1_surrogate_vs_oracle": rs,
+           "surrogate_within_2x_of_plain": bool(rs <= 2.0 * rp), "surrogate_fallback_fraction": frac,
+           "status": sst, "plain_status": pst, "oracle_seconds": osec,
+           "norm": "relative L1, all arrays (averages and the three point-value arrays), worst variable"}
+    if vortex:
+        t = float(sum(dts))
+        out["l1_rho_vs_exact"] = {"oracle": _vortex_l1_vs_exact(W, prob, ora[0][0], t)[0],
+                                  "plain": _vortex_l1_vs_exact(W, prob, plain[0][0], t)[0],
+                                  "surrogate": _vortex_l1_vs_exact(W, prob, surr[0][0], t)[0]}
+    return out
+
+
+def run_surrogate_leg(args, torch, af, W, refs):
+    """Learned surrogate + exact fallback (K5): the 4096^2 isentropic vortex
+    (seed 5) to t = --vortex-t and the 2048^2 four-quadrant problem (seed 6)
+    to t = --riemann-t, each against the plain path on the same grid, and
+    both paths against the FP64 oracle at an oracle-sized grid of the same
+    law (256^2; the vortex of seed 2508 to t = 2, the four-quadrant problem of
+    seed 6 to --riemann-t).  Networks are trained here, on the GPU, from
+    samples of small seeded problems of each kind."""
     import numpy as np
 
     t0 = time.perf_counter()
@@ -555,10 +784,13 @@ def run_surrogate_leg(args, torch, af, W):
     nets, nv, ne = _train_surrogate(args, af, W, probs, seed=23)
     train_s = time.perf_counter() - t0
     n = args.surr_grid
-    out = _surrogate_case(args, torch, af, W, W.shu_vortex_seeded(n, seed=5), nets, args.surr_steps)
+    pair = (nets[0][0], nets[1][0])
+    out = _surrogate_full(args, torch, af, W, W.shu_vortex_seeded(n, seed=5), pair, args.vortex_t)
+    if refs:
+        out["oracle_check"] = _surrogate_vs_oracle(torch, af, W, refs["vortex256"], pair, vortex=True)
     out.update({
         "workload": f"isentropic vortex, periodic [0,10]^2, {n}x{n} cells, centre and strength from seed 5, "
-                    f"CFL 0.3, {args.warmup + args.surr_steps} steps of fixed dt",
+                    f"CFL 0.3, dt from the max speed every step, to t = {args.vortex_t}",
         "network": "64-128-128-128-16 GELU, BF16 weights, tcgen05 MMA with FP32 accumulation",
         "training": {"samples_vertex": nv, "samples_edge": ne,
                      "steps": args.surr_train_steps, "batch": 4096, "seconds_incl_sampling": train_s,
@@ -574,11 +806,14 @@ def run_surrogate_leg(args, torch, af, W):
     nets, nv, ne = _train_surrogate(args, af, W, probs, seed=29)
     train_s = time.perf_counter() - t0
     nr = args.surr_grid // 2
-    rie = _surrogate_case(args, torch, af, W, W.four_quadrant(nr, seed=6), nets, args.surr_steps)
+    pair = (nets[0][0], nets[1][0])
+    rie = _surrogate_full(args, torch, af, W, W.four_quadrant(nr, seed=6), pair, args.riemann_t)
+    if refs:
+        rie["oracle_check"] = _surrogate_vs_oracle(torch, af, W, refs["riemann256"], pair, vortex=False)
     rie.update({
         "workload": f"four-quadrant Riemann problem, transmissive [0,1]^2, {nr}x{nr} cells, states from seed 6, "
-                    f"Alg. 2, Alg. 3 with node bounds, Sec. 3.4 blend, flux limiter, CFL 0.3, "
-                    f"{args.warmup + args.surr_steps} steps of fixed dt",
+                    f"Alg. 2, Alg. 3 with node bounds, Sec. 3.4 blend, flux limiter, Ubar = C2P of the average, "
+                    f"CFL 0.3, dt from the max speed every step, to t = {args.riemann_t}",
         "training": {"samples_vertex": nv, "samples_edge": ne, "seconds_incl_sampling": train_s,
                      "loss_first_last_vertex": [nets[0][1], nets[0][2]],
                      "loss_first_last_edge": [nets[1][1], nets[1][2]],
@@ -627,15 +862,25 @@ def main(argv=None):
     ap.add_argument("--grid", type=int, default=8192, help="cells per side (default: 8192)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip every leg that runs the FP64 oracle on the host (CPU baseline, accuracy, "
+                         "convergence, the surrogate leg's oracle checks)")
     ap.add_argument("--batch-steps", type=int, default=200,
                     help="steps of the batched-ensemble leg (0: skip it)")
-    ap.add_argument("--surr-steps", type=int, default=10, help="timed steps of the surrogate leg (0: skip it)")
-    ap.add_argument("--surr-grid", type=int, default=4096, help="cells per side of the surrogate leg")
+    ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",
+                    help="skip the surrogate leg (K5: surrogate vs plain vs FP64 oracle at a final time)")
+    ap.add_argument("--no-convergence", dest="convergence", action="store_false",
+                    help="skip the convergence leg (K2: vortex sweep 128^2 to 8192^2)")
+    ap.add_argument("--surr-steps", type=int, default=None, help="0: skip the surrogate leg (as --no-surrogate)")
+    ap.add_argument("--surr-grid", type=int, default=4096, help="cells per side of the surrogate leg's vortex")
+    ap.add_argument("--vortex-t", type=float, default=0.25, help="final time of the surrogate leg's vortex")
+    ap.add_argument("--riemann-t", type=float, default=0.05, help="final time of the surrogate leg's Riemann case")
     ap.add_argument("--surr-train-steps", type=int, default=2000, help="Adam steps per surrogate network")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.surr_steps == 0:
+        args.surrogate = False
     if args.impl == "reference":
         run_reference(args)
     else:

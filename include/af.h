@@ -104,10 +104,15 @@ enum {
                               point values and U_c = C2P(Q_c); 1 the primitive state of the conservative
                               cell average, C2P(Qbar) (reading of Sec. 3.5, which keeps discontinuous
                               data admissible) */
-  AF_OPT_TEST_TIMEOUT = 14  /* test hook: 1 makes every later step's waits for staged data (the point-value
+  AF_OPT_TEST_TIMEOUT = 14, /* test hook: 1 makes every later step's waits for staged data (the point-value
                                tiles' TMA copies) and for the surrogate's tensor-core MMAs run out after a
                                short bound with nothing in flight (the barrier is armed, no copy or MMA is
                                issued): the step returns normally with AF_ST_TIMEOUT set */
+  AF_OPT_KEEP_HALF = 15     /* 1: steps also keep the t^{n+1/2} point values for af_get_half (48 more bytes
+                               written a cell).  Default 0: the point-value kernel writes, in place of that
+                               level, each node's Simpson-in-time flux f(U^n) + 4 f(U^{n+1/2}) + f(U^{n+1})
+                               (eq. (F)), which is all the flux kernel needs (the surrogate path keeps the
+                               level regardless) */
 };
 
 /* stages reported by af_profile */
@@ -171,7 +176,9 @@ int af_host_sync(af_ctx *h);
 /* FP32 low words of the cell averages [4][ny][nx] (device / host memory). */
 int af_get_avg_lo(af_ctx *h, float *avg_lo, void *stream);
 int af_set_avg_lo(af_ctx *h, const float *avg_lo, void *stream);
-/* Point values at t^{n+1/2} computed by the last step (device memory). */
+/* Point values at t^{n+1/2} computed by the last step (device memory).
+ * AF_ERR_STATE unless that step kept them (AF_OPT_KEEP_HALF, or the
+ * surrogate path). */
 int af_get_half(af_ctx *h, float *vtx, float *xe, float *ye, void *stream);
 
 /* One time step of size dt (Alg. 1 with the options above): ghost fill,

@@ -122,6 +122,7 @@ int load_state(af_ctx *h, const float *const src[4]) {
   CK(cudaMemsetAsync(h->lo, 0, sizeof(float) * NV * h->g.plane, s), "memset lo");
   CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), s), "memset status");
   h->has_state = true;
+  h->half_valid = false;
   return AF_OK;
 }
 
@@ -182,8 +183,8 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   h->dx = dx;
   h->dy = dy;
   cudaGetDevice(&h->device);
-  // hi, lo and 3 levels x 3 node kinds: 11 arrays of 4 planes
-  const size_t state_bytes = 11 * (size_t)NV * (size_t)g.plane * sizeof(float);
+  // hi, lo, 3 levels x 3 node kinds and 4 node-flux arrays: 15 arrays of 4 planes
+  const size_t state_bytes = 15 * (size_t)NV * (size_t)g.plane * sizeof(float);
   cudaError_t e = cudaMalloc(&h->base, state_bytes);
   if (e != cudaSuccess) {
     cuda_fail(e, "af_create: cudaMalloc(state)");
@@ -200,6 +201,7 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   h->lo = take();
   for (int l = 0; l < 3; l++)
     for (int k = 0; k < 3; k++) h->lev[l].k[k] = take();
+  for (int q = 0; q < 4; q++) h->nflux[q] = take();
   h->tbuf[0] = h->lev[0];
   h->tbuf[1] = h->lev[2];
   h->tmap_cur = 0;
@@ -346,6 +348,17 @@ int af_set_option(af_ctx *h, int key, double value) {
       return AF_OK;
     case AF_OPT_NODE_BOUNDS: h->opt.node_bounds = iv != 0; return AF_OK;
     case AF_OPT_TEST_TIMEOUT: h->opt.test_timeout = iv != 0; return AF_OK;
+    case AF_OPT_KEEP_HALF:
+      if ((iv != 0) != (h->keep_half != 0)) {
+        for (int p = 0; p < 2; p++)  // captured steps hold the old launch arguments
+          if (h->run_exec[p]) {
+            DeviceGuard dg(h->device);
+            cudaGraphExecDestroy(h->run_exec[p]);
+            h->run_exec[p] = nullptr;
+          }
+      }
+      h->keep_half = iv != 0;
+      return AF_OK;
     case AF_OPT_UBAR:
       if (iv < 0 || iv > 1) return fail(AF_ERR_ARG, "ubar must be 0 or 1%s");
       if (iv != h->g.ubar_c2p) {
@@ -399,6 +412,7 @@ int af_get_option(af_ctx *h, int key, double *value) {
     case AF_OPT_NODE_BOUNDS: *value = h->opt.node_bounds; return AF_OK;
     case AF_OPT_UBAR: *value = h->g.ubar_c2p; return AF_OK;
     case AF_OPT_TEST_TIMEOUT: *value = h->opt.test_timeout; return AF_OK;
+    case AF_OPT_KEEP_HALF: *value = h->keep_half; return AF_OK;
     case AF_OPT_TILE_H: *value = h->tile_h; return AF_OK;
     default: return fail(AF_ERR_ARG, "unknown option%s");
   }
@@ -464,6 +478,7 @@ int af_set_state_host(af_ctx *h, const float *avg, const float *vtx, const float
     return fail(AF_ERR_ARG, "periodic state: the duplicated last node line differs from the first%s");
   }
   h->has_state = true;
+  h->half_valid = false;
   return AF_OK;
 }
 
@@ -576,6 +591,7 @@ int af_set_state_host_async(af_ctx *h, const float *avg, const float *vtx, const
   CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), s), "memset status");
   h->speed_valid = false;
   h->has_state = true;
+  h->half_valid = false;
   h->async_pending = true;
   return AF_OK;
 }
@@ -636,6 +652,8 @@ int af_host_sync(af_ctx *h) {
 int af_get_half(af_ctx *h, float *vtx, float *xe, float *ye, void *stream) {
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  if (!h->half_valid)
+    return fail(AF_ERR_STATE, "af_get_half: the last step kept no t^{n+1/2} level (set AF_OPT_KEEP_HALF before it)%s");
   DeviceGuard dg(h->device);
   float *dst[4] = {nullptr, vtx, xe, ye};
   return get_arrays(h, h->lev[1], nullptr, dst, false, (cudaStream_t)stream);
@@ -729,11 +747,22 @@ static int enqueue_step(af_ctx *h, double dt) {
                                 h->opt, h->d_status, h->d_counters, mask, h->surr_tiles, theta, h->tile_h, s),
        "point values (fallback)");
     h->launches[AF_STAGE_POINTVALUE] += 5;
+    h->half_valid = true;
   } else {
+    // plain path: the point-value kernel writes the node fluxes (and folds
+    // the new point values into the wave speed) for the flux kernel
+    NodeFluxOut nf;
+    for (int q = 0; q < 4; q++) nf.q[q] = h->nflux[q];
+    nf.speed = h->d_speed;
+    nf.speed_bad = h->d_speed_bad;
+    nf.write_half = h->keep_half;
+    CK(cudaMemsetAsync(h->d_speed, 0, sizeof(unsigned), s), "memset speed");
+    CK(cudaMemsetAsync(h->d_speed_bad, 0, sizeof(int), s), "memset speed");
     CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
-                         h->opt, h->d_status, h->d_counters, theta, h->tile_h, s),
+                         h->opt, h->d_status, h->d_counters, theta, h->tile_h, &nf, s),
        "point values");
     h->launches[AF_STAGE_POINTVALUE] += 1;
+    h->half_valid = h->keep_half != 0;
   }
   if (prof) {
     cudaEventRecord(h->ev_stage[2], s);
@@ -743,9 +772,16 @@ static int enqueue_step(af_ctx *h, double dt) {
   if (h->opt.flux_limiter)
     CK(cudaMemcpyAsync(h->q0, h->hi, sizeof(float) * NV * (size_t)h->g.plane, cudaMemcpyDeviceToDevice, s),
        "flux limiter snapshot");
-  CK(launch_flux_update(h->g, h->lev[0], h->lev[1], h->lev[2], h->hi, h->lo, dt / h->dx, dt / h->dy,
-                        h->d_status, h->d_speed, h->d_speed_bad, h->opt.flux_limiter, h->q0, s),
-     "flux update");
+  if (h->opt.surrogate) {
+    CK(launch_flux_update(h->g, h->lev[0], h->lev[1], h->lev[2], h->hi, h->lo, dt / h->dx, dt / h->dy,
+                          h->d_status, h->d_speed, h->d_speed_bad, h->opt.flux_limiter, h->q0, s),
+       "flux update");
+  } else {
+    const float *nf[4] = {h->nflux[0], h->nflux[1], h->nflux[2], h->nflux[3]};
+    CK(launch_flux_nf(h->g, nf, h->hi, h->lo, dt / h->dx, dt / h->dy, h->d_status, h->d_speed, h->d_speed_bad,
+                      h->opt.flux_limiter, h->q0, s),
+       "flux update");
+  }
   h->speed_valid = true;
   h->launches[AF_STAGE_FLUX] += 1;
   if (prof) {
@@ -776,7 +812,7 @@ static bool same_options(const Options &a, const Options &b) {
   return a.lin_mode == b.lin_mode && a.tsw == b.tsw && a.limiter == b.limiter &&
          a.correction == b.correction && a.force_lo == b.force_lo && a.surrogate == b.surrogate &&
          a.surr_tol == b.surr_tol && a.surr_abs == b.surr_abs && a.flux_limiter == b.flux_limiter &&
-         a.shock_blend == b.shock_blend && a.node_bounds == b.node_bounds;
+         a.shock_blend == b.shock_blend && a.node_bounds == b.node_bounds && a.test_timeout == b.test_timeout;
 }
 
 // Capture two steps on the handle's own stream (the t^n and t^{n+1} buffers

@@ -59,6 +59,26 @@ __device__ __forceinline__ void c2p(const float Q[4], float gm1, float U[4]) {
   U[2] = Q[2] * ir;
   U[3] = gm1 * (Q[3] - 0.5f * (Q[1] * Q[1] + Q[2] * Q[2]) * ir);
 }
+// f (dir 0) or g (dir 1) of the conservative form (Sec. 2) at primitive U
+__device__ __forceinline__ void phys_flux(const float U[4], float gm1i, int dir, float F[4]) {
+  const float r = U[0], u = U[1], v = U[2], p = U[3];
+  const float un = dir == 0 ? u : v;
+  const float E = p * gm1i + 0.5f * r * (u * u + v * v);
+  F[0] = r * un;
+  F[1] = r * u * un + (dir == 0 ? p : 0.0f);
+  F[2] = r * v * un + (dir == 1 ? p : 0.0f);
+  F[3] = un * (E + p);
+}
+// the Simpson weights in time of eq. (F): F += w f(U), w = 1, 4, 1 for
+// t^n, t^{n+1/2}, t^{n+1}, accumulated in that order (the point-value kernel
+// and the flux kernel form node fluxes with this same sequence of operations)
+__device__ __forceinline__ void add_time_flux(const float U[4], float gm1i, int dir, float w, float F[4]) {
+  float f[4];
+  phys_flux(U, gm1i, dir, f);
+#pragma unroll
+  for (int v = 0; v < NV; v++) F[v] += w * f[v];
+}
+
 // Cell prep of Sec. 2 from a cell's 8 boundary point values N (primitive;
 // corners ll, lr, ul, ur, then edge midpoints left, right, bottom, top) and
 // its conservative average Qa: the centre value U_c = C2P(Q_c), with Q_c from

@@ -20,6 +20,12 @@ struct af_ctx {
   float *base;  // all planes in one allocation
   float *hi, *lo;
   NodeSet lev[3];  // 0: t^n, 1: t^{n+1/2}, 2: t^{n+1}
+  // node fluxes of the last step (f, g at vertices, f at x-edges, g at
+  // y-edges; Simpson in time), written by the point-value kernel for the flux
+  // kernel on the plain path
+  float *nflux[4];
+  int keep_half;    // the plain path also writes the t^{n+1/2} level
+  bool half_valid;  // lev[1] holds the t^{n+1/2} level of the last step
   // TMA descriptors for t^n held in either of the two buffers that swap
   // roles each step; tmap_cur selects the one now holding t^n
   TileMaps tmaps[2];

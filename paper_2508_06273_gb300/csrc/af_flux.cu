@@ -63,17 +63,6 @@ __device__ __forceinline__ void dw_add(float ah, float al, float bh, float bl, f
   h = two_sum(s, e, l);
 }
 
-// f (dir 0) or g (dir 1) of the conservative form at primitive U
-__device__ __forceinline__ void phys_flux(const float U[4], float gm1i, int dir, float F[4]) {
-  const float r = U[0], u = U[1], v = U[2], p = U[3];
-  const float un = dir == 0 ? u : v;
-  const float E = p * gm1i + 0.5f * r * (u * u + v * v);
-  F[0] = r * un;
-  F[1] = r * u * un + (dir == 0 ? p : 0.0f);
-  F[2] = r * v * un + (dir == 1 ? p : 0.0f);
-  F[3] = un * (E + p);
-}
-
 // Simpson in time at one node: f(U^n) + 4 f(U^{n+1/2}) + f(U^{n+1}); with
 // fold set, also folds the node's new value into the running wave-speed
 // maximum (set on one visit of each node only)
@@ -82,13 +71,10 @@ __device__ __forceinline__ void time_flux(const Args &A, int kind, int i, int j,
   F[0] = F[1] = F[2] = F[3] = 0.0f;
 #pragma unroll
   for (int l = 0; l < 3; l++) {
-    float U[4], f[4];
+    float U[4];
 #pragma unroll
     for (int v = 0; v < NV; v++) U[v] = __ldg(A.n[l][kind] + at(A.g, v, i, j));
-    phys_flux(U, gm1i, dir, f);
-    const float w = l == 1 ? 4.0f : 1.0f;
-#pragma unroll
-    for (int v = 0; v < NV; v++) F[v] += w * f[v];
+    add_time_flux(U, gm1i, dir, l == 1 ? 4.0f : 1.0f, F);
     if (l == 2 && fold) smax = fmaxf(smax, wave_speed(U, A.g.gamma, bad));
   }
 }
@@ -105,15 +91,8 @@ __device__ __forceinline__ void time_flux_fg(const Args &A, int i, int j, float 
   for (int v = 0; v < NV; v++) F[v] = G[v] = 0.0f;
 #pragma unroll
   for (int l = 0; l < 3; l++) {
-    float f[4], gf[4];
-    phys_flux(U[l], gm1i, 0, f);
-    phys_flux(U[l], gm1i, 1, gf);
-    const float w = l == 1 ? 4.0f : 1.0f;
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-      F[v] += w * f[v];
-      G[v] += w * gf[v];
-    }
+    add_time_flux(U[l], gm1i, 0, l == 1 ? 4.0f : 1.0f, F);
+    add_time_flux(U[l], gm1i, 1, l == 1 ? 4.0f : 1.0f, G);
   }
   smax = fmaxf(smax, wave_speed(U[2], A.g.gamma, bad));
 }
@@ -271,8 +250,18 @@ __device__ __noinline__ void limit_tile(const Args &A, FluxSmem &S, LimSmem &L, 
   if (limited) atomicOr(A.status, ST_FLUX_LIMITED);
 }
 
-// the tile of cells with origin (i0, j0)
-template <bool LIM>
+// time-integrated node fluxes written by the point-value kernel (NF): node
+// (i, j) of array q (0 f at vertices, 1 g at vertices, 2 f at x-edges, 3 g at
+// y-edges)
+__device__ __forceinline__ void ld_nf(const Args &A, int q, int i, int j, float F[4]) {
+#pragma unroll
+  for (int v = 0; v < NV; v++) F[v] = __ldg(A.nf[q] + at(A.g, v, i, j));
+}
+
+// the tile of cells with origin (i0, j0); NF: the node fluxes come from the
+// point-value kernel (which also folded the new point values into the wave
+// speed), else they are formed here from the three time levels
+template <bool LIM, bool NF>
 __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L, int i0, int j0) {
   const Grid &g = A.g;
   auto &vf = S.vf;
@@ -291,7 +280,14 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L
   for (int k = tid; k < (TX + 1) * (TY + 1); k += NTHR) {
     const int a = k % (TX + 1), b = k / (TX + 1), i = i0 + a, j = j0 + b;
     float F[4] = {0, 0, 0, 0}, Gf[4] = {0, 0, 0, 0};
-    if (i <= g.nx && j <= g.ny) time_flux_fg(A, i, j, gm1i, F, Gf, smax, sbad);
+    if (i <= g.nx && j <= g.ny) {
+      if (NF) {
+        ld_nf(A, 0, i, j, F);
+        ld_nf(A, 1, i, j, Gf);
+      } else {
+        time_flux_fg(A, i, j, gm1i, F, Gf, smax, sbad);
+      }
+    }
 #pragma unroll
     for (int v = 0; v < NV; v++) {
       vf[v][b][a] = F[v];
@@ -301,14 +297,20 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L
   for (int k = tid; k < (TX + 1) * TY; k += NTHR) {
     const int a = k % (TX + 1), b = k / (TX + 1), i = i0 + a, j = j0 + b;
     float F[4] = {0, 0, 0, 0};
-    if (i <= g.nx && j < g.ny) time_flux(A, XE, i, j, 0, true, gm1i, F, smax, sbad);
+    if (i <= g.nx && j < g.ny) {
+      if (NF) ld_nf(A, 2, i, j, F);
+      else time_flux(A, XE, i, j, 0, true, gm1i, F, smax, sbad);
+    }
 #pragma unroll
     for (int v = 0; v < NV; v++) xf[v][b][a] = F[v];
   }
   for (int k = tid; k < TX * (TY + 1); k += NTHR) {
     const int a = k % TX, b = k / TX, i = i0 + a, j = j0 + b;
     float F[4] = {0, 0, 0, 0};
-    if (i < g.nx && j <= g.ny) time_flux(A, YE, i, j, 1, true, gm1i, F, smax, sbad);
+    if (i < g.nx && j <= g.ny) {
+      if (NF) ld_nf(A, 3, i, j, F);
+      else time_flux(A, YE, i, j, 1, true, gm1i, F, smax, sbad);
+    }
 #pragma unroll
     for (int v = 0; v < NV; v++) yg[v][b][a] = F[v];
   }
@@ -385,7 +387,13 @@ __device__ __forceinline__ void flux_tile(const Args &A, FluxSmem &S, LimSmem *L
 // 32 registers a thread: six resident blocks per SM keep the loads in flight.
 __global__ void __launch_bounds__(NTHR, 4) flux_update_kernel(Args A) {
   __shared__ FluxSmem S;
-  flux_tile<false>(A, S, nullptr, blockIdx.x * TX, blockIdx.y * TY);
+  flux_tile<false, false>(A, S, nullptr, blockIdx.x * TX, blockIdx.y * TY);
+}
+// the same from the point-value kernel's node fluxes: 64 B of node data a cell
+// read instead of 144 B of point values at three time levels
+__global__ void __launch_bounds__(NTHR, 4) flux_nf_kernel(Args A) {
+  __shared__ FluxSmem S;
+  flux_tile<false, true>(A, S, nullptr, blockIdx.x * TX, blockIdx.y * TY);
 }
 
 // (the arguments are grid constants so that the limiter's call can take
@@ -393,7 +401,12 @@ __global__ void __launch_bounds__(NTHR, 4) flux_update_kernel(Args A) {
 __global__ void __launch_bounds__(NTHR, 4) flux_limited_kernel(const __grid_constant__ Args A) {
   __shared__ FluxSmem S;
   __shared__ LimSmem L;
-  flux_tile<true>(A, S, &L, blockIdx.x * TX, blockIdx.y * TY);
+  flux_tile<true, false>(A, S, &L, blockIdx.x * TX, blockIdx.y * TY);
+}
+__global__ void __launch_bounds__(NTHR, 4) flux_nf_limited_kernel(const __grid_constant__ Args A) {
+  __shared__ FluxSmem S;
+  __shared__ LimSmem L;
+  flux_tile<true, true>(A, S, &L, blockIdx.x * TX, blockIdx.y * TY);
 }
 
 // batched form: tile B.tiles[b] = (instance, i0, j0); the instance's dt
@@ -412,7 +425,7 @@ __global__ void __launch_bounds__(NTHR, 6) flux_batch_kernel(FluxBatch B) {
     A.lyl = c.lyl;
   }
   __syncthreads();
-  flux_tile<false>(A, S, nullptr, t.y, t.z);
+  flux_tile<false, false>(A, S, nullptr, t.y, t.z);
 }
 
 // instance blockIdx.y: its t^n averages (hi, all planes) into its snapshot
@@ -447,8 +460,8 @@ __global__ void __launch_bounds__(NTHR, 4) flux_batch_limited_kernel(FluxBatch B
     A.ly = c.lyh;
   }
   __syncthreads();
-  if (A.flux_limiter) flux_tile<true>(A, S, &L, t.y, t.z);
-  else flux_tile<false>(A, S, nullptr, t.y, t.z);
+  if (A.flux_limiter) flux_tile<true, false>(A, S, &L, t.y, t.z);
+  else flux_tile<false, false>(A, S, nullptr, t.y, t.z);
 }
 
 }  // namespace
@@ -465,6 +478,7 @@ FluxArgs flux_args(const Grid &g, const NodeSet &n0, const NodeSet &n1, const No
   A.hi = avg_hi;
   A.lo = avg_lo;
   A.q0 = avg_hi;
+  for (int q = 0; q < 4; q++) A.nf[q] = nullptr;
   A.lxh = A.lxl = A.lyh = A.lyl = A.lx = A.ly = 0.0f;
   A.flux_limiter = 0;
   A.status = status;
@@ -492,6 +506,27 @@ cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &
   dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY), blk(TX, TY + 2);
   if (flux_limiter) flux_limited_kernel<<<grd, blk, 0, s>>>(A);
   else flux_update_kernel<<<grd, blk, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flux_nf(const Grid &g, const float *const nf[4], float *avg_hi, float *avg_lo, double lamx,
+                           double lamy, int *status, unsigned *speed, int *speed_bad, int flux_limiter,
+                           const float *q0, cudaStream_t s) {
+  NodeSet none = {{nullptr, nullptr, nullptr}};
+  Args A = flux_args(g, none, none, none, avg_hi, avg_lo, status, speed, speed_bad);
+  for (int q = 0; q < 4; q++) A.nf[q] = nf[q];
+  split_double(lamx, A.lxh, A.lxl);
+  split_double(lamy, A.lyh, A.lyl);
+  A.lx = A.lxh;
+  A.ly = A.lyh;
+  A.flux_limiter = flux_limiter;
+  if (flux_limiter) {
+    if (!q0 || q0 == avg_hi) return cudaErrorInvalidValue;
+    A.q0 = q0;
+  }
+  dim3 grd((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY), blk(TX, TY + 2);
+  if (flux_limiter) flux_nf_limited_kernel<<<grd, blk, 0, s>>>(A);
+  else flux_nf_kernel<<<grd, blk, 0, s>>>(A);
   return cudaGetLastError();
 }
 

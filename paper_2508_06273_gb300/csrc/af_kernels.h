@@ -65,6 +65,15 @@ struct PointValueArgs {
   const int *tile_flag;
   // Sec. 3.4 blend weights of the x- and y-edge midpoints (NULL: no blend)
   const float *theta[2];
+  // node fluxes for the flux kernel, f(U^n) + 4 f(U^{n+1/2}) + f(U^{n+1}) in
+  // conservative form ([0] f and [1] g at vertices, [2] f at x-edges, [3] g
+  // at y-edges), with the wave speed of the new point values folded into
+  // speed / speed_bad; NULL: the t^{n+1/2} level is written instead, for the
+  // flux kernel that reads three levels
+  float *nflux[4];
+  unsigned *speed;
+  int *speed_bad;
+  int write_half;  // with nflux: also write the t^{n+1/2} level into n1
 };
 inline PointValueArgs pointvalue_args(const Grid &g, const NodeSet &n0, const float *avg_hi, const NodeSet &n1,
                                       const NodeSet &n2, const Options &o, int *status,
@@ -91,6 +100,10 @@ inline PointValueArgs pointvalue_args(const Grid &g, const NodeSet &n0, const fl
   A.mask[0] = A.mask[1] = A.mask[2] = nullptr;
   A.tile_flag = nullptr;
   A.theta[0] = A.theta[1] = nullptr;
+  for (int q = 0; q < 4; q++) A.nflux[q] = nullptr;
+  A.speed = nullptr;
+  A.speed_bad = nullptr;
+  A.write_half = 1;
   return A;
 }
 
@@ -105,6 +118,9 @@ struct FluxArgs {
   const float *q0;
   float lxh, lxl, lyh, lyl;  // dt/dx and dt/dy as double-word FP32 (hi + lo)
   float lx, ly;              // the same in FP32 (flux limiter)
+  // node fluxes of the point-value kernel (f and g at vertices, f at x-edges,
+  // g at y-edges, Simpson in time), or NULL: formed here from the levels n
+  const float *__restrict__ nf[4];
   int flux_limiter;          // cell-average flux limiter on
   int *status;
   unsigned *speed;  // max of max(|u|,|v|) + c over the new state, as float bits
@@ -191,17 +207,31 @@ cudaError_t launch_shock_theta_batch(const int4 *tiles, int ntiles, const BatchC
 // [instance][buffer], if not null), which the batched kernel reads in place
 cudaError_t launch_batch_dt(BatchCtl *ctl, int n, double *hist, int hist_cap, int mode, PointValueArgs *pv_args,
                             cudaStream_t s);
-// cell prep and point values at t^{n+1/2} (n1) and t^{n+1} (n2)
+// node fluxes for the flux kernel (see PointValueArgs::nflux)
+struct NodeFluxOut {
+  float *q[4];
+  unsigned *speed;
+  int *speed_bad;
+  int write_half;
+};
+// cell prep and point values at t^{n+1/2} (n1) and t^{n+1} (n2); with nf the
+// node fluxes instead of the t^{n+1/2} level (which is kept if write_half)
 cudaError_t launch_pointvalue(const Grid &g, const NodeSet &n0, const float *avg_hi, const TileMaps &maps,
                               const NodeSet &n1, const NodeSet &n2, float dt, const Options &o,
                               int *status, unsigned long long *counters, const float *const theta[2],
-                              int tile_h, cudaStream_t s);
+                              int tile_h, const NodeFluxOut *nf, cudaStream_t s);
 // Simpson fluxes and the finite-volume update of the averages (compensated
 // hi/lo); also the max wave speed of the new state into *speed (float bits)
 cudaError_t launch_flux_update(const Grid &g, const NodeSet &n0, const NodeSet &n1,
                                const NodeSet &n2, float *avg_hi, float *avg_lo, double lamx,
                                double lamy, int *status, unsigned *speed, int *speed_bad, int flux_limiter,
                                const float *q0, cudaStream_t s);
+// the same from the node fluxes nf[4] that the point-value kernel wrote (see
+// PointValueArgs::nflux); folds only the new averages into *speed, which the
+// caller cleared before the point-value kernel
+cudaError_t launch_flux_nf(const Grid &g, const float *const nf[4], float *avg_hi, float *avg_lo, double lamx,
+                           double lamy, int *status, unsigned *speed, int *speed_bad, int flux_limiter,
+                           const float *q0, cudaStream_t s);
 // max over averages and owned point values of max(|u|,|v|) + c (as float bits)
 // words a and b (b may be null) into mapped host memory dst, clearing a if
 // clear_a: small results reach the host without a copy engine, so that they

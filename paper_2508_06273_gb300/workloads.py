@@ -55,6 +55,12 @@ class Problem:
     options: dict = dataclasses.field(default_factory=dict)
     exact: Optional[Callable[[float], Field]] = None
     inflow: dict = dataclasses.field(default_factory=dict)  # side (0..3) -> primitive state, for BC 3
+    centre: Optional[tuple] = None  # vortex centre at t = 0 (moving with velocity (1, 1))
+
+    def vortex_centre(self, t):
+        """Centre of the translating vortex at time t, wrapped into the box."""
+        cx, cy = self.centre
+        return self.x0 + (cx + t - self.x0) % self.lx, self.y0 + (cy + t - self.y0) % self.ly
 
     @property
     def dx(self):
@@ -209,7 +215,7 @@ def shu_vortex(n=32, eps=5.0, xc=5.0, yc=5.0, L=10.0, t_end=10.0, ny=None, cfl=0
         return f
 
     return Problem("shu_vortex", n, ny or n, 0.0, 0.0, L, L, (0, 0, 0, 0), at(0.0), t_end,
-                   cfl=cfl, exact=at)
+                   cfl=cfl, exact=at, centre=(xc, yc))
 
 
 def shu_vortex_seeded(n, seed=2508, t_end=2.0):

@@ -160,7 +160,7 @@ def test_one_step_parity(env, case, mode):
     o = make_oracle(oracle, prob, MODES[mode], state=st)
     dt = prob.cfl * min(prob.dx, prob.dy) / o.max_speed()
     o.step(dt)
-    s = solver(env, prob, MODES[mode], st)
+    s = solver(env, prob, dict(MODES[mode], keep_half=1), st)
     s.step(dt)
     assert s.status() == 0
     assert_parity(host(s.get_state()), o.get_state(), STEP_TOL, what="t^n+1")
@@ -286,7 +286,7 @@ def test_low_order_paths_parity(env, force, data):
     o = make_oracle(oracle, prob, opts, state=st)
     dt = 0.3 * min(prob.dx, prob.dy) / o.max_speed()
     o.step(dt)
-    s = solver(env, prob, opts, st)
+    s = solver(env, prob, dict(opts, keep_half=1), st)
     s.step(dt)
     assert_parity(host(s.get_half()), o.get_half(), STEP_TOL, first_conservative=False, what="t^n+1/2")
     assert_parity(host(s.get_state())[1:], o.get_state()[1:], STEP_TOL, first_conservative=False, what="t^n+1")
@@ -518,3 +518,29 @@ def test_checkpoint_resume_is_bitwise(env, prob_name):
     assert a.status() == b.status()
     for s in (a, b, c):
         s.close()
+
+
+def test_node_flux_path_matches_the_three_level_flux_kernel(env):
+    """The single-grid step writes each node's Simpson-in-time flux from the
+    point-value kernel and the flux kernel reads those; a batch instance takes
+    the other design (t^{n+1/2} written, fluxes formed from three levels in
+    the flux kernel).  Both form every node flux with the same sequence of
+    operations, so the states agree to FP32 round-off (the compilers may
+    contract differently in the two kernels); the half level is refused unless
+    it was kept."""
+    torch, af, _ = env
+    prob = W.fourier_smooth(45, 38, seed=31, lx=1.0, ly=0.84)
+    st = W.to_f32(W.discretise(prob))
+    s = solver(env, prob, state=st)
+    b = af.Batch([(prob.nx, prob.ny)], [(prob.dx, prob.dy)], bcs=[prob.bc])
+    b.set_state(0, *to_dev(torch, st))
+    hist = torch.zeros((4, 1), dtype=torch.float64, device="cuda")
+    b.run(3, hist)
+    for dt in hist[:3, 0].cpu().numpy():
+        s.step(float(dt))
+    assert s.status() == 0
+    assert_parity(host(s.get_state()), host(b.get_state(0)), 1e-6, what="node fluxes vs three levels")
+    with pytest.raises(af.AFError, match="KEEP_HALF"):
+        s.get_half()
+    b.close()
+    s.close()
