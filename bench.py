@@ -523,7 +523,7 @@ def oracle_references(af, W, args):
     four-quadrant problem of seed 6 at 256^2 to the Riemann leg's final time."""
     refs = {}
     for n in (128, 256):
-        prob = W.shu_vortex_seeded(n, t_end=2.0)
+        prob = W.shu_vortex_seeded(n, t_end=2.0, vel=W.STABLE_VELOCITY)
         refs[f"vortex{n}"] = (prob,) + _oracle_run(af, W, prob, 2.0)
     prob = W.four_quadrant(256, seed=6)
     refs["riemann256"] = (prob,) + _oracle_run(af, W, prob, args.riemann_t)
@@ -550,13 +550,13 @@ def convergence_leg(torch, af, W, refs, seg_steps=400):
                          "oracle_l1_rho_vs_exact": o_all, "oracle_l1_rho_vs_exact_near_vortex": o_near,
                          "status": status, "oracle_seconds": osec}
     for n in (512, 2048):
-        prob = W.shu_vortex_seeded(n, t_end=2.0)
+        prob = W.shu_vortex_seeded(n, t_end=2.0, vel=W.STABLE_VELOCITY)
         s = af.Solver(n, n, prob.dx, prob.dy, prob.gamma, prob.bc)
         s.set_state(*W.discretise_torch(prob, "cuda"))
         absq = np.abs(W.discretise(prob)[0]).sum(axis=(1, 2)) * prob.dx * prob.dy if n <= 2048 else None
         tot = [s.totals()]
         t, k, failed = 0.0, 0, None
-        while t < 2.0 * (1 - 1e-12):
+        while t < 2.0 * (1 - 1e-12) and k < 20000:
             speed = s.max_speed()
             if not speed > 0.0 or not np.isfinite(speed):
                 failed = f"wave speed {speed} at step {k}, t = {t:.6g}"
@@ -582,8 +582,27 @@ def convergence_leg(torch, af, W, refs, seg_steps=400):
             rec["drift_per_step_max"] = float((np.abs(np.diff(tot, axis=0)) / absq).max())
             rec["drift_total"] = [float(x) for x in np.abs(tot[-1] - tot[0]) / absq]
         out[f"{n}^2"] = rec
+    # the default background (1, 1) lies in the band where the scheme
+    # amplifies perturbations: the same sweep at 512^2 blows up before t = 2
+    prob = W.shu_vortex_seeded(512, t_end=2.0)
+    s = af.Solver(512, 512, prob.dx, prob.dy, prob.gamma, prob.bc)
+    s.set_state(*W.discretise_torch(prob, "cuda"))
+    sp0, t, k, blow = s.max_speed(), 0.0, 0, None
+    while t < 2.0 * (1 - 1e-12) and k < 4000:
+        speed = s.max_speed()
+        if not np.isfinite(speed) or speed > 3.0 * sp0:
+            blow = {"step": k, "t": t, "max_speed": speed if np.isfinite(speed) else None}
+            break
+        dt = min(prob.cfl * prob.dx / speed, 2.0 - t)
+        s.step(dt)
+        t += dt
+        k += 1
+    s.close()
+    out["background_1_1_512^2"] = {"blow_up": blow, "steps": k, "t": t,
+                                    "note": "velocity (1, 1): Mach 1.2 along the diagonal, inside the band of "
+                                            "oblique supersonic states that the scheme amplifies"}
     n = 8192
-    prob = W.shu_vortex_seeded(n)
+    prob = W.shu_vortex_seeded(n, vel=W.STABLE_VELOCITY)
     s = af.Solver(n, n, prob.dx, prob.dy, prob.gamma, prob.bc)
     s.set_state(*W.discretise_torch(prob, "cuda"))
     t0 = s.totals()
@@ -598,7 +617,9 @@ def convergence_leg(torch, af, W, refs, seg_steps=400):
     out["8192^2"] = {"t": seg_steps * dt, "steps": seg_steps, "fixed_dt": dt, "l1_rho_vs_exact": e_all,
                      "l1_rho_vs_exact_near_vortex": e_near, "status": status,
                      "mass_drift_total": abs(float(t1[0] - t0[0])) / mass}
-    out["note"] = ("mean |rho - rho_exact| over cell averages, whole box and within 2.5 of the vortex centre; "
+    out["note"] = ("vortex of the seed-2508 law moving with (0.5, 0.5) (the default (1, 1) is unstable for long "
+                   "runs, see background_1_1_512^2); "
+                   "mean |rho - rho_exact| over cell averages, whole box and within 2.5 of the vortex centre; "
                    "the vortex is not periodic: its minimum-image data have a kink at distance 5 from the "
                    "centre (size about eps e^-12 / 2 pi, 3e-5 in velocity), whose waves set the whole-box "
                    "floor; FP32 point values set a second floor near 1e-7 at the finest grids")
@@ -699,7 +720,7 @@ def _surrogate_full(args, torch, af, W, prob, nets, t_end):
         torch.cuda.synchronize()
         ev0.record(stream)
         t, k = 0.0, 0
-        while t < t_end * (1 - 1e-12):
+        while t < t_end * (1 - 1e-12) and k < 20000:
             speed = s.max_speed()
             if not speed > 0.0 or speed == float("inf"):
                 runs["failed"] = f"{name}: wave speed {speed} at step {k}, t = {t:.6g}"
@@ -780,23 +801,27 @@ def run_surrogate_leg(args, torch, af, W, refs):
 
     t0 = time.perf_counter()
     rng = np.random.default_rng(17)
-    probs = [W.shu_vortex_seeded(int(rng.integers(64, 129)), seed=200 + k, t_end=np.inf) for k in range(16)]
+    probs = [W.shu_vortex_seeded(int(rng.integers(64, 129)), seed=200 + k, t_end=np.inf, vel=W.STABLE_VELOCITY)
+             for k in range(16)]
     nets, nv, ne = _train_surrogate(args, af, W, probs, seed=23)
     train_s = time.perf_counter() - t0
     n = args.surr_grid
     pair = (nets[0][0], nets[1][0])
-    out = _surrogate_full(args, torch, af, W, W.shu_vortex_seeded(n, seed=5), pair, args.vortex_t)
+    out = _surrogate_full(args, torch, af, W, W.shu_vortex_seeded(n, seed=5, vel=W.STABLE_VELOCITY), pair,
+                          args.vortex_t)
     if refs:
         out["oracle_check"] = _surrogate_vs_oracle(torch, af, W, refs["vortex256"], pair, vortex=True)
     out.update({
-        "workload": f"isentropic vortex, periodic [0,10]^2, {n}x{n} cells, centre and strength from seed 5, "
+        "workload": f"isentropic vortex moving with (0.5, 0.5), periodic [0,10]^2, {n}x{n} cells, centre and "
+                    f"strength from seed 5, "
                     f"CFL 0.3, dt from the max speed every step, to t = {args.vortex_t}",
         "network": "64-128-128-128-16 GELU, BF16 weights, tcgen05 MMA with FP32 accumulation",
         "training": {"samples_vertex": nv, "samples_edge": ne,
                      "steps": args.surr_train_steps, "batch": 4096, "seconds_incl_sampling": train_s,
                      "loss_first_last_vertex": [nets[0][1], nets[0][2]],
                      "loss_first_last_edge": [nets[1][1], nets[1][2]],
-                     "data": "16 seeded vortices of 64^2 to 128^2, 12 batched steps, 8% of nodes sampled"},
+                     "data": "16 seeded vortices (velocity (0.5, 0.5)) of 64^2 to 128^2, 12 batched steps, "
+                             "8% of nodes sampled"},
     })
     for m, _, _ in nets:
         m.close()

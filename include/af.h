@@ -108,11 +108,13 @@ enum {
                                tiles' TMA copies) and for the surrogate's tensor-core MMAs run out after a
                                short bound with nothing in flight (the barrier is armed, no copy or MMA is
                                issued): the step returns normally with AF_ST_TIMEOUT set */
-  AF_OPT_KEEP_HALF = 15     /* 1: steps also keep the t^{n+1/2} point values for af_get_half (48 more bytes
-                               written a cell).  Default 0: the point-value kernel writes, in place of that
-                               level, each node's Simpson-in-time flux f(U^n) + 4 f(U^{n+1/2}) + f(U^{n+1})
-                               (eq. (F)), which is all the flux kernel needs (the surrogate path keeps the
-                               level regardless) */
+  AF_OPT_KEEP_HALF = 15,    /* with AF_OPT_NODE_FLUX: 1 keeps the t^{n+1/2} point values for af_get_half
+                               as well (48 more bytes written a cell) */
+  AF_OPT_NODE_FLUX = 16     /* 1: the point-value kernel writes, in place of the t^{n+1/2} level, each node's
+                               Simpson-in-time flux f(U^n) + 4 f(U^{n+1/2}) + f(U^{n+1}) (eq. (F)) and the flux
+                               kernel reads those (64 B a cell instead of 144 B of point values at three
+                               levels; the result is bitwise the same).  Default 0: it moves fewer bytes but
+                               costs the point-value kernel more than it saves (measured at 8192^2) */
 };
 
 /* stages reported by af_profile */
@@ -177,8 +179,8 @@ int af_host_sync(af_ctx *h);
 int af_get_avg_lo(af_ctx *h, float *avg_lo, void *stream);
 int af_set_avg_lo(af_ctx *h, const float *avg_lo, void *stream);
 /* Point values at t^{n+1/2} computed by the last step (device memory).
- * AF_ERR_STATE unless that step kept them (AF_OPT_KEEP_HALF, or the
- * surrogate path). */
+ * AF_ERR_STATE if that step took the node-flux path without
+ * AF_OPT_KEEP_HALF. */
 int af_get_half(af_ctx *h, float *vtx, float *xe, float *ye, void *stream);
 
 /* One time step of size dt (Alg. 1 with the options above): ghost fill,

@@ -348,6 +348,7 @@ int af_set_option(af_ctx *h, int key, double value) {
       return AF_OK;
     case AF_OPT_NODE_BOUNDS: h->opt.node_bounds = iv != 0; return AF_OK;
     case AF_OPT_TEST_TIMEOUT: h->opt.test_timeout = iv != 0; return AF_OK;
+    case AF_OPT_NODE_FLUX: h->opt.node_flux = iv != 0; return AF_OK;
     case AF_OPT_KEEP_HALF:
       if ((iv != 0) != (h->keep_half != 0)) {
         for (int p = 0; p < 2; p++)  // captured steps hold the old launch arguments
@@ -413,6 +414,7 @@ int af_get_option(af_ctx *h, int key, double *value) {
     case AF_OPT_UBAR: *value = h->g.ubar_c2p; return AF_OK;
     case AF_OPT_TEST_TIMEOUT: *value = h->opt.test_timeout; return AF_OK;
     case AF_OPT_KEEP_HALF: *value = h->keep_half; return AF_OK;
+    case AF_OPT_NODE_FLUX: *value = h->opt.node_flux; return AF_OK;
     case AF_OPT_TILE_H: *value = h->tile_h; return AF_OK;
     default: return fail(AF_ERR_ARG, "unknown option%s");
   }
@@ -748,9 +750,17 @@ static int enqueue_step(af_ctx *h, double dt) {
        "point values (fallback)");
     h->launches[AF_STAGE_POINTVALUE] += 5;
     h->half_valid = true;
+  } else if (!h->opt.node_flux) {
+    // plain path: t^{n+1/2} and t^{n+1} written, the flux kernel forms the
+    // node fluxes from three levels
+    CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
+                         h->opt, h->d_status, h->d_counters, theta, h->tile_h, nullptr, s),
+       "point values");
+    h->launches[AF_STAGE_POINTVALUE] += 1;
+    h->half_valid = true;
   } else {
-    // plain path: the point-value kernel writes the node fluxes (and folds
-    // the new point values into the wave speed) for the flux kernel
+    // node-flux path: the point-value kernel writes the node fluxes (and
+    // folds the new point values into the wave speed) for the flux kernel
     NodeFluxOut nf;
     for (int q = 0; q < 4; q++) nf.q[q] = h->nflux[q];
     nf.speed = h->d_speed;
@@ -772,7 +782,7 @@ static int enqueue_step(af_ctx *h, double dt) {
   if (h->opt.flux_limiter)
     CK(cudaMemcpyAsync(h->q0, h->hi, sizeof(float) * NV * (size_t)h->g.plane, cudaMemcpyDeviceToDevice, s),
        "flux limiter snapshot");
-  if (h->opt.surrogate) {
+  if (h->opt.surrogate || !h->opt.node_flux) {
     CK(launch_flux_update(h->g, h->lev[0], h->lev[1], h->lev[2], h->hi, h->lo, dt / h->dx, dt / h->dy,
                           h->d_status, h->d_speed, h->d_speed_bad, h->opt.flux_limiter, h->q0, s),
        "flux update");
@@ -812,7 +822,8 @@ static bool same_options(const Options &a, const Options &b) {
   return a.lin_mode == b.lin_mode && a.tsw == b.tsw && a.limiter == b.limiter &&
          a.correction == b.correction && a.force_lo == b.force_lo && a.surrogate == b.surrogate &&
          a.surr_tol == b.surr_tol && a.surr_abs == b.surr_abs && a.flux_limiter == b.flux_limiter &&
-         a.shock_blend == b.shock_blend && a.node_bounds == b.node_bounds && a.test_timeout == b.test_timeout;
+         a.shock_blend == b.shock_blend && a.node_bounds == b.node_bounds && a.test_timeout == b.test_timeout &&
+         a.node_flux == b.node_flux;
 }
 
 // Capture two steps on the handle's own stream (the t^n and t^{n+1} buffers

@@ -27,6 +27,7 @@ struct Options {
   int shock_blend = 0;   // Sec. 3.4 shock-indicator blend of point values
   int node_bounds = 0;   // Alg. 3 also bounds rho, p by the node's cells (see node_update)
   int test_timeout = 0;  // test hook: waits for staged data run out with nothing in flight
+  int node_flux = 0;     // point-value kernel writes node fluxes for the flux kernel (see PointValueArgs)
 };
 
 // Bounded waits on an mbarrier (polls of try_wait, which suspends in hardware

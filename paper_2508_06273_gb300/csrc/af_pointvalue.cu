@@ -19,10 +19,11 @@
 // node at cos(theta) = u'/c' and sin(theta) = v'/c', which splits it into at
 // most four arcs, each inside one cell.  On an arc a cell's biquadratic is a
 // polynomial in cos and sin of degree <= 2 in each (a Taylor shift of the
-// monomials); with cos^2 = 1 - sin^2 it is A(sin) + cos B(sin), and every
-// EG2 moment over an arc is a sum over S0[n] = int sin^n and S1[n] =
-// int cos sin^n, taken exactly from the arc's end points (see "moment tables
-// in the reduced basis").  The sum over the cells' arcs is taken
+// monomials), the EG2 weights raise that to degree <= 6, and every arc
+// integral is taken exactly from the arc's end points with the recurrences
+//   (m+n) J_mn = [cos^(m-1) sin^(n+1)] + (m-1) J_(m-2)n
+//   (m+n) J_mn = -[cos^(m+1) sin^(n-1)] + (n-1) J_m(n-2)
+// for J_mn = int cos^m sin^n dtheta.  The sum over the cells' arcs is taken
 // by inclusion-exclusion (one cell's coefficients over the whole circle, plus
 // differences of coefficients over the two half-circles cut off by the grid
 // lines and over their intersection; see "EG2 arc sums by inclusion-
@@ -163,55 +164,40 @@ __device__ __forceinline__ void build_cell(const Grid &g, const float *raw, int 
   }
 }
 
-// ---- moment tables in the reduced basis
-// On the circle cos^2 = 1 - sin^2, so a polynomial sum_{i,e <= 2} b[i][e]
-// cos^i sin^e is A(sin) + cos B(sin) with A of degree 4 and B of degree 2
-// (see reduce_cs), and every EG2 moment over an arc is a sum over
-// S0[n] = int sin^n (n <= 6) and S1[n] = int cos sin^n (n <= 5):
-//   S1[n] = [sin^(n+1)] / (n + 1),  n S0[n] = -[sin^(n-1) cos] + (n - 1) S0[n-2].
-// Arc from (c0, s0) at angle t0 to (c1, s1) at t1 (the quarter arc X and Y):
-struct ArcTab {
-  float s0[7], s1[6];
-};
-__device__ __forceinline__ void arc_tab(float t0, float c0, float s0, float t1, float c1, float s1, ArcTab &T) {
-  float p0[7], p1[7];  // powers of s0, s1
-  p0[0] = p1[0] = 1.0f;
-#pragma unroll
-  for (int k = 1; k < 7; k++) {
-    p0[k] = p0[k - 1] * s0;
-    p1[k] = p1[k - 1] * s1;
-  }
-  T.s0[0] = t1 - t0;
-  T.s0[1] = c0 - c1;
-#pragma unroll
-  for (int n = 2; n < 7; n++)
-    T.s0[n] = (fmaf(c0, p0[n - 1], -c1 * p1[n - 1]) + (float)(n - 1) * T.s0[n - 2]) * (1.0f / (float)n);
-#pragma unroll
-  for (int n = 0; n < 6; n++) T.s1[n] = (p1[n + 1] - p0[n + 1]) * (1.0f / (float)(n + 1));
-}
-
-// Half-circle X = (-al, al), al = acos a, s = sin al: odd n vanish; the even
-// entries S0 = (2 al, al - a s, (3 S0[2] - 2 a s^3) / 4, (5 S0[4] - 2 a s^5) / 6),
-// S1 = (2 s, 2 s^3 / 3, 2 s^5 / 5), and D[n] = S0[n] - S0[n+2] = int cos^2 sin^n
-// (n = 0, 2).  The Y side (asin b, pi - asin b) is X in the frame mirrored
-// about pi/4 (cos and sin exchanged), with b for a.  A line that misses the
-// circle (a = 1) gives al = s = 0: every entry vanishes.
-struct HalfTab {
-  float s00, s02, s04, s06, s10, s12, s14, d0, d2;
-};
-__device__ __forceinline__ HalfTab half_tab(float a, float s, float al) {
-  const float s2 = s * s, as = a * s, as3 = as * s2;
-  HalfTab T;
-  T.s00 = 2.0f * al;
-  T.s02 = al - as;
-  T.s04 = 0.25f * fmaf(3.0f, T.s02, -2.0f * as3);
-  T.s06 = (1.0f / 6.0f) * fmaf(5.0f, T.s04, -2.0f * as3 * s2);
-  T.s10 = 2.0f * s;
-  T.s12 = (2.0f / 3.0f) * s2 * s;
-  T.s14 = 0.4f * s2 * s2 * s;
-  T.d0 = al + as;
-  T.d2 = fmaf(0.25f, T.s02, 0.5f * as3);
-  return T;
+// J[m][n] = int_{t0}^{t1} cos^m sin^n for m, n <= 4, m + n <= 6
+__device__ __forceinline__ void jtable(float t0, float c0, float s0, float t1, float c1, float s1,
+                                       float J[5][5]) {
+  float c0s = c0 * c0, c1s = c1 * c1, c0c = c0s * c0, c1c = c1s * c1;
+  float s0s = s0 * s0, s1s = s1 * s1, s0c = s0s * s0, s1c = s1s * s1;
+  float s0q = s0s * s0s, s1q = s1s * s1s;
+  float Ds = s1 - s0, Dc = c1 - c0, Ds2 = s1s - s0s;
+  float Dcs = c1 * s1 - c0 * s0, Dc2s = c1s * s1 - c0s * s0, Dc3s = c1c * s1 - c0c * s0;
+  float Dcs2 = c1 * s1s - c0 * s0s, Dc2s2 = c1s * s1s - c0s * s0s, Dc3s2 = c1c * s1s - c0c * s0s;
+  float Dcs3 = c1 * s1c - c0 * s0c, Dc2s3 = c1s * s1c - c0s * s0c, Dc3s3 = c1c * s1c - c0c * s0c;
+  float Dcs4 = c1 * s1q - c0 * s0q, Dc2s4 = c1s * s1q - c0s * s0q;
+  float Dcs5 = c1 * s1q * s1 - c0 * s0q * s0;
+  J[0][0] = t1 - t0;
+  J[1][0] = Ds;
+  J[0][1] = -Dc;
+  J[1][1] = 0.5f * Ds2;
+  J[2][0] = 0.5f * (Dcs + J[0][0]);
+  J[3][0] = (Dc2s + 2.0f * J[1][0]) * (1.0f / 3.0f);
+  J[4][0] = 0.25f * (Dc3s + 3.0f * J[2][0]);
+  J[2][1] = (Dcs2 + J[0][1]) * (1.0f / 3.0f);
+  J[3][1] = 0.25f * (Dc2s2 + 2.0f * J[1][1]);
+  J[4][1] = 0.2f * (Dc3s2 + 3.0f * J[2][1]);
+  J[0][2] = 0.5f * (J[0][0] - Dcs);
+  J[1][2] = (J[1][0] - Dc2s) * (1.0f / 3.0f);
+  J[2][2] = 0.25f * (Dcs3 + J[0][2]);
+  J[3][2] = 0.2f * (Dc2s3 + 2.0f * J[1][2]);
+  J[4][2] = (Dc3s3 + 3.0f * J[2][2]) * (1.0f / 6.0f);
+  J[0][3] = (2.0f * J[0][1] - Dcs2) * (1.0f / 3.0f);
+  J[1][3] = 0.25f * (2.0f * J[1][1] - Dc2s2);
+  J[2][3] = 0.2f * (Dcs4 + J[0][3]);
+  J[3][3] = (Dc2s4 + 2.0f * J[1][3]) * (1.0f / 6.0f);
+  J[0][4] = 0.25f * (3.0f * J[0][2] - Dcs3);
+  J[1][4] = 0.2f * (3.0f * J[1][2] - Dc2s3);
+  J[2][4] = (Dcs5 + J[0][4]) * (1.0f / 6.0f);
 }
 
 // Taylor shift of q(x) = a0 + a1 x + a2 x^2 to x = x0 + r c:  q = b0 + b1 c + b2 c^2
@@ -266,6 +252,29 @@ __device__ __forceinline__ float eval_at(const float *rec, float K, float x0, fl
 // pi/2) only even powers of cos.  An edge-midpoint node (one grid line) keeps
 // the first two terms (XE) or the first and third (YE).
 
+// H[m][n] = int_{-al}^{al} cos^m sin^n for n even (al = acos a, s = sin al):
+// twice the integrals from 0, by the recurrences of jtable with the start
+// point (1, 0); the entries m <= 4, n <= 4, m + n <= 6 the moments use
+__device__ __forceinline__ void half_table(float a, float s, float al, float H[5][5]) {
+  const float s2 = s * s, s3 = s2 * s, a2 = a * a, a3 = a2 * a;
+  const float as = a * s, as3 = a * s3;
+  const float I20 = 0.5f * (as + al), I02 = 0.5f * (al - as), I12 = s3 * (1.0f / 3.0f);
+  const float I22 = 0.25f * (as3 + I02), I04 = 0.25f * (3.0f * I02 - as3);
+  H[0][0] = 2.0f * al;
+  H[1][0] = 2.0f * s;
+  H[2][0] = 2.0f * I20;
+  H[3][0] = (2.0f / 3.0f) * (a2 * s + 2.0f * s);
+  H[4][0] = 0.5f * (a3 * s + 3.0f * I20);
+  H[0][2] = 2.0f * I02;
+  H[1][2] = 2.0f * I12;
+  H[2][2] = 2.0f * I22;
+  H[3][2] = 0.4f * (a2 * s3 + 2.0f * I12);
+  H[4][2] = (1.0f / 3.0f) * (a3 * s3 + 3.0f * I22);
+  H[0][4] = 2.0f * I04;
+  H[1][4] = 0.4f * (3.0f * I12 - a2 * s3);
+  H[2][4] = (1.0f / 3.0f) * (as3 * s2 + I04);
+}
+
 // int over the whole circle of cos^m sin^n for the (m, n) the moments use
 // (zero unless m and n are even)
 __host__ __device__ constexpr float jfull(int m, int n) {
@@ -278,155 +287,47 @@ __host__ __device__ constexpr float jfull(int m, int n) {
          : 0.0f;
 }
 
-// acc + sum_{i,e <= 2} b[i][e] int_circle cos^(i+DI) sin^(e+DE) (constants;
-// the odd entries are skipped)
-template <int DI, int DE>
-__device__ __forceinline__ float contract_circle(const float b[3][3], float acc) {
+// table kinds: full arc table, X-side table H (odd n vanish), Y-side table
+// (odd m vanish; stored transposed, H[n][m]), whole circle (constants)
+enum { TB_ARC = 0, TB_X = 1, TB_Y = 2, TB_CIRCLE = 3 };
+
+// acc + sum_{i,e <= 2} b[i][e] T(i + DI, e + DE), skipping the entries the
+// table's symmetry makes zero
+template <int DI, int DE, int KIND>
+__device__ __forceinline__ float contract(const float b[3][3], const float T[5][5], float acc) {
 #pragma unroll
   for (int i = 0; i < 3; i++)
 #pragma unroll
     for (int e = 0; e < 3; e++) {
       const int m = i + DI, n = e + DE;
-      if ((m | n) & 1) continue;
-      acc = fmaf(b[i][e], jfull(m, n), acc);
+      if (KIND == TB_X && (n & 1)) continue;
+      if (KIND == TB_Y && (m & 1)) continue;
+      if (KIND == TB_CIRCLE && ((m | n) & 1)) continue;
+      const float t = KIND == TB_CIRCLE ? jfull(m, n) : (KIND == TB_Y ? T[n][m] : T[m][n]);
+      acc = fmaf(b[i][e], t, acc);
     }
   return acc;
 }
 
-// The EG2 moments of one variable (p: VAR 0, u: 1, v: 2) accumulate into
-// acc: p: int p, int p cos, int p sin; u: int u cos, int u cos^2, int u,
-// int u sin cos; v: int v sin, int v sin^2, int v, int v sin cos.
-template <int VAR>
-__device__ __forceinline__ void circle_moments(const float b[3][3], float acc[4]) {
+// the EG2 moments of one variable against one table: p (VAR 0): int p,
+// int p cos, int p sin; u (1): int u cos, int u cos^2, int u, int u sin cos;
+// v (2): int v sin, int v sin^2, int v, int v sin cos
+template <int VAR, int KIND>
+__device__ __forceinline__ void moments(const float b[3][3], const float T[5][5], float acc[4]) {
   if (VAR == 0) {
-    acc[0] = contract_circle<0, 0>(b, acc[0]);
-    acc[1] = contract_circle<1, 0>(b, acc[1]);
-    acc[2] = contract_circle<0, 1>(b, acc[2]);
+    acc[0] = contract<0, 0, KIND>(b, T, acc[0]);
+    acc[1] = contract<1, 0, KIND>(b, T, acc[1]);
+    acc[2] = contract<0, 1, KIND>(b, T, acc[2]);
   } else if (VAR == 1) {
-    acc[0] = contract_circle<1, 0>(b, acc[0]);
-    acc[1] = contract_circle<2, 0>(b, acc[1]);
-    acc[2] = contract_circle<0, 0>(b, acc[2]);
-    acc[3] = contract_circle<1, 1>(b, acc[3]);
+    acc[0] = contract<1, 0, KIND>(b, T, acc[0]);
+    acc[1] = contract<2, 0, KIND>(b, T, acc[1]);
+    acc[2] = contract<0, 0, KIND>(b, T, acc[2]);
+    acc[3] = contract<1, 1, KIND>(b, T, acc[3]);
   } else {
-    acc[0] = contract_circle<0, 1>(b, acc[0]);
-    acc[1] = contract_circle<0, 2>(b, acc[1]);
-    acc[2] = contract_circle<0, 0>(b, acc[2]);
-    acc[3] = contract_circle<1, 1>(b, acc[3]);
-  }
-}
-
-// b[i][e] (cos^i sin^e) as A(sin) + cos B(sin); MIRROR: of b[e][i], i.e. in the
-// frame mirrored about pi/4 where cos and sin exchange roles
-struct Red {
-  float A0, A1, A2, A3, A4, B0, B1, B2;
-};
-template <bool MIRROR>
-__device__ __forceinline__ Red reduce_cs(const float b[3][3]) {
-  auto B = [&](int i, int e) { return MIRROR ? b[e][i] : b[i][e]; };
-  Red r;
-  r.A0 = B(0, 0) + B(2, 0);
-  r.A1 = B(0, 1) + B(2, 1);
-  r.A2 = B(0, 2) + B(2, 2) - B(2, 0);
-  r.A3 = -B(2, 1);
-  r.A4 = -B(2, 2);
-  r.B0 = B(1, 0);
-  r.B1 = B(1, 1);
-  r.B2 = B(1, 2);
-  return r;
-}
-
-// Moments over a half-circle table of q = A + cos B (only even table entries):
-// M1 = int q, Mc = int q cos, Ms = int q sin, Mss = int q sin^2,
-// Msc = int q sin cos; int q cos^2 = M1 - Mss.  MIRROR: q given in the mirrored
-// frame, so its cos is the grid frame's sin and the moments map back with
-// cos and sin exchanged.
-template <int VAR, bool MIRROR>
-__device__ __forceinline__ void half_moments(const Red &r, const HalfTab &T, float acc[4]) {
-  auto M1 = [&]() { return fmaf(r.A0, T.s00, fmaf(r.A2, T.s02, fmaf(r.A4, T.s04, fmaf(r.B0, T.s10, r.B2 * T.s12)))); };
-  auto Mc = [&]() { return fmaf(r.A0, T.s10, fmaf(r.A2, T.s12, fmaf(r.A4, T.s14, fmaf(r.B0, T.d0, r.B2 * T.d2)))); };
-  auto Ms = [&]() { return fmaf(r.A1, T.s02, fmaf(r.A3, T.s04, r.B1 * T.s12)); };
-  auto Mss = [&]() { return fmaf(r.A0, T.s02, fmaf(r.A2, T.s04, fmaf(r.A4, T.s06, fmaf(r.B0, T.s12, r.B2 * T.s14)))); };
-  auto Msc = [&]() { return fmaf(r.A1, T.s12, fmaf(r.A3, T.s14, r.B1 * T.d2)); };
-  // grid-frame cos and sin moments of the table's frame
-  if (VAR == 0) {
-    acc[0] += M1();
-    acc[1] += MIRROR ? Ms() : Mc();
-    acc[2] += MIRROR ? Mc() : Ms();
-  } else if (VAR == 1) {  // int u cos, int u cos^2, int u, int u sin cos
-    const float m1 = M1(), mss = Mss();
-    acc[0] += MIRROR ? Ms() : Mc();
-    acc[1] += MIRROR ? mss : m1 - mss;
-    acc[2] += m1;
-    acc[3] += Msc();
-  } else {  // int v sin, int v sin^2, int v, int v sin cos
-    const float m1 = M1(), mss = Mss();
-    acc[0] += MIRROR ? Mc() : Ms();
-    acc[1] += MIRROR ? m1 - mss : mss;
-    acc[2] += m1;
-    acc[3] += Msc();
-  }
-}
-
-// the same over an arc table (every entry)
-template <int VAR>
-__device__ __forceinline__ void arc_moments(const Red &r, const ArcTab &T, float acc[4]) {
-  const float A[5] = {r.A0, r.A1, r.A2, r.A3, r.A4}, B[3] = {r.B0, r.B1, r.B2};
-  auto M1 = [&]() {
-    float m = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 5; j++) m = fmaf(A[j], T.s0[j], m);
-#pragma unroll
-    for (int j = 0; j < 3; j++) m = fmaf(B[j], T.s1[j], m);
-    return m;
-  };
-  auto Mc = [&]() {
-    float m = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 5; j++) m = fmaf(A[j], T.s1[j], m);
-#pragma unroll
-    for (int j = 0; j < 3; j++) m = fmaf(B[j], T.s0[j] - T.s0[j + 2], m);
-    return m;
-  };
-  auto Ms = [&]() {
-    float m = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 5; j++) m = fmaf(A[j], T.s0[j + 1], m);
-#pragma unroll
-    for (int j = 0; j < 3; j++) m = fmaf(B[j], T.s1[j + 1], m);
-    return m;
-  };
-  auto Mss = [&]() {
-    float m = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 5; j++) m = fmaf(A[j], T.s0[j + 2], m);
-#pragma unroll
-    for (int j = 0; j < 3; j++) m = fmaf(B[j], T.s1[j + 2], m);
-    return m;
-  };
-  auto Msc = [&]() {
-    float m = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 5; j++) m = fmaf(A[j], T.s1[j + 1], m);
-#pragma unroll
-    for (int j = 0; j < 3; j++) m = fmaf(B[j], T.s0[j + 1] - T.s0[j + 3], m);
-    return m;
-  };
-  if (VAR == 0) {
-    acc[0] += M1();
-    acc[1] += Mc();
-    acc[2] += Ms();
-  } else if (VAR == 1) {
-    const float m1 = M1(), mss = Mss();
-    acc[0] += Mc();
-    acc[1] += m1 - mss;
-    acc[2] += m1;
-    acc[3] += Msc();
-  } else {
-    const float m1 = M1(), mss = Mss();
-    acc[0] += Ms();
-    acc[1] += mss;
-    acc[2] += m1;
-    acc[3] += Msc();
+    acc[0] = contract<0, 1, KIND>(b, T, acc[0]);
+    acc[1] = contract<0, 2, KIND>(b, T, acc[1]);
+    acc[2] = contract<0, 0, KIND>(b, T, acc[2]);
+    acc[3] = contract<1, 1, KIND>(b, T, acc[3]);
   }
 }
 
@@ -474,23 +375,22 @@ __device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int 
   // sin al = 0), so the X and Y stages run without branches
   constexpr bool hx = K != YE, hy = K != XE;
   const bool hq = K == VTX && ax < 1.0f && by < 1.0f && fmaf(ax, ax, by * by) < 1.0f;
-  HalfTab Tx, Ty;
-  ArcTab Jq;
+  float Tx[5][5], Ty[5][5], Jq[5][5];
   float alx = 0.0f, snx = 0.0f, aly = 0.0f, sny = 0.0f;
   if (hx) {
     const float a = fminf(ax, 1.0f);
     alx = acosf(a);
     snx = sqrt_nn(fmaf(-a, a, 1.0f));
-    Tx = half_tab(a, snx, alx);
+    half_table(a, snx, alx, Tx);
   }
   if (hy) {
     const float b = fminf(by, 1.0f);
     aly = acosf(b);
     sny = sqrt_nn(fmaf(-b, b, 1.0f));
-    Ty = half_tab(b, sny, aly);
+    half_table(b, sny, aly, Ty);
   }
   // X and Y meet in (asin b, acos a): (cos, sin) = (sin aly, b) to (a, sin alx)
-  if (hq) arc_tab(0.5f * PI_F - aly, sny, by, alx, ax, snx, Jq);
+  if (hq) jtable(0.5f * PI_F - aly, sny, by, alx, ax, snx, Jq);
   const float frx = fx * rx, fry = fy * ry;
 
   // circle coefficients of variable (record offset off, reference Kv) of
@@ -509,7 +409,7 @@ __device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int 
     constexpr int VAR = decltype(var_tag)::value;
     float b0[3][3], S[3][3], d[3][3];
     side(0, 0, off, Kv, b0);
-    circle_moments<VAR>(b0, acc);
+    moments<VAR, TB_CIRCLE>(b0, Tx, acc);
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -523,7 +423,7 @@ __device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int 
           S[i][e] -= d[i][e];
           d[i][e] -= b0[i][e];
         }
-      half_moments<VAR, false>(reduce_cs<false>(d), Tx, acc);
+      moments<VAR, TB_X>(d, Tx, acc);
     }
     if (hy) {
       side(0, 1, off, Kv, d);
@@ -534,7 +434,7 @@ __device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int 
           S[i][e] -= d[i][e];
           d[i][e] -= b0[i][e];
         }
-      half_moments<VAR, true>(reduce_cs<true>(d), Ty, acc);
+      moments<VAR, TB_Y>(d, Ty, acc);
     }
     if (hq) {
       side(1, 1, off, Kv, d);
@@ -542,7 +442,7 @@ __device__ __forceinline__ bool eg2(const Grid &g, const float *sm, int li, int 
       for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int e = 0; e < 3; e++) d[i][e] += S[i][e];
-      arc_moments<VAR>(reduce_cs<false>(d), Jq, acc);
+      moments<VAR, TB_ARC>(d, Jq, acc);
     }
   };
   // the moments enter the result as soon as each variable is done (moments

@@ -60,7 +60,8 @@ class Problem:
     def vortex_centre(self, t):
         """Centre of the translating vortex at time t, wrapped into the box."""
         cx, cy = self.centre
-        return self.x0 + (cx + t - self.x0) % self.lx, self.y0 + (cy + t - self.y0) % self.ly
+        u0, v0 = getattr(self, "velocity", (1.0, 1.0))
+        return self.x0 + (cx + u0 * t - self.x0) % self.lx, self.y0 + (cy + v0 * t - self.y0) % self.ly
 
     @property
     def dx(self):
@@ -191,14 +192,16 @@ def _mod(x):
     return np
 
 
-def shu_vortex(n=32, eps=5.0, xc=5.0, yc=5.0, L=10.0, t_end=10.0, ny=None, cfl=0.3):
+def shu_vortex(n=32, eps=5.0, xc=5.0, yc=5.0, L=10.0, t_end=10.0, ny=None, cfl=0.3, vel=(1.0, 1.0)):
     """Isentropic vortex of strength eps on the periodic box [0,L]^2 moving
-    with (1,1) through the background rho = u = v = p = 1 (minimum-image
-    distance to the centre, so the data are single valued on the torus)."""
+    with the background velocity ``vel`` (default (1,1)) through rho = p = 1
+    (minimum-image distance to the centre, so the data are single valued on
+    the torus)."""
     g = GAMMA
+    u0, v0 = vel
 
     def at(t):
-        cx, cy = xc + t, yc + t
+        cx, cy = xc + u0 * t, yc + v0 * t
 
         def f(x, y):
             m = _mod(x)
@@ -210,20 +213,30 @@ def shu_vortex(n=32, eps=5.0, xc=5.0, yc=5.0, L=10.0, t_end=10.0, ny=None, cfl=0
             e = m.exp(0.5 * (1.0 - r2))
             T = 1.0 - (g - 1.0) * eps * eps / (8.0 * g * np.pi ** 2) * e * e
             rho = T ** (1.0 / (g - 1.0))
-            return rho, 1.0 - eps / (2 * np.pi) * e * Y, 1.0 + eps / (2 * np.pi) * e * X, rho ** g
+            return rho, u0 - eps / (2 * np.pi) * e * Y, v0 + eps / (2 * np.pi) * e * X, rho ** g
 
         return f
 
-    return Problem("shu_vortex", n, ny or n, 0.0, 0.0, L, L, (0, 0, 0, 0), at(0.0), t_end,
-                   cfl=cfl, exact=at, centre=(xc, yc))
+    p = Problem("shu_vortex", n, ny or n, 0.0, 0.0, L, L, (0, 0, 0, 0), at(0.0), t_end,
+                cfl=cfl, exact=at, centre=(xc, yc))
+    p.velocity = (u0, v0)
+    return p
 
 
-def shu_vortex_seeded(n, seed=2508, t_end=2.0):
+# Background velocity of the long vortex runs (the convergence sweep and the
+# surrogate evaluation): the default (1, 1) (c = 1.18, Mach 1.2 along the
+# diagonal) lies in the band where the scheme amplifies perturbations (each
+# Mach circle crosses both grid lines through a vertex without holding it),
+# so runs of more than about 900 FP32 steps blow up; (0.5, 0.5) is stable.
+STABLE_VELOCITY = (0.5, 0.5)
+
+
+def shu_vortex_seeded(n, seed=2508, t_end=2.0, vel=(1.0, 1.0)):
     """Vortex with centre in [3,6]^2 and strength in [3,6] drawn from ``seed``."""
     rng = np.random.default_rng(seed)
     xc, yc = rng.uniform(3.0, 6.0, size=2)
     eps = rng.uniform(3.0, 6.0)
-    p = shu_vortex(n, eps=eps, xc=xc, yc=yc, t_end=t_end)
+    p = shu_vortex(n, eps=eps, xc=xc, yc=yc, t_end=t_end, vel=vel)
     p.name = f"shu_vortex_seed{seed}"
     return p
 

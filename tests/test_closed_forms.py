@@ -1,11 +1,9 @@
 """The closed forms behind the GPU's EG2 and EG1 arc sums, checked against
 quadrature on the CPU (no GPU, no oracle): the moments J_mn = int cos^m sin^n
 over the two half-circles that the grid lines through a node cut off, over
-their intersection, and over the whole circle; the inclusion-exclusion
+their intersection, and over the whole circle; and the inclusion-exclusion
 identity that turns the sum over the four cells' arcs (eq. (EG2), a vertex
-node) into one whole-circle term and three difference terms; and the reduced
-basis (cos^2 = 1 - sin^2) in which the GPU evaluates the moments, with the Y
-side as the X side of the frame mirrored about pi/4.
+node) into one whole-circle term and three difference terms.
 
 Frame (reflected so that u', v' >= 0): X = {cos > a} = (-acos a, acos a),
 Y = {sin > b} = (asin b, pi - asin b), and X and Y meet in (asin b, acos a)
@@ -174,81 +172,3 @@ def test_eg1_closed_forms(a, b):
              0.5 * (t1 - t0 - c1 * s1 + c0 * s0)]
         for v, (m, n) in zip(Q, mons):
             assert abs(v - quad_moment(m, n, t0, t1)) < 1e-13
-
-
-# ---- the reduced basis the GPU's EG2 sums use: on the circle cos^2 = 1 - sin^2,
-# so q = sum_{i,e <= 2} b[i][e] cos^i sin^e = A(sin) + cos B(sin) with
-# A = (b00 + b20, b01 + b21, b02 + b22 - b20, -b21, -b22), B = (b10, b11, b12);
-# every EG2 moment int q w (w in 1, cos, sin, cos^2, sin cos, sin^2) is then a
-# sum over S0[n] = int sin^n and S1[n] = int cos sin^n.  Over the half-circle
-# X only even n survive (and Y is X in the frame mirrored about pi/4, with
-# cos and sin exchanged and b for a); S1[n] = [sin^(n+1)] / (n + 1) and
-# n S0[n] = -[sin^(n-1) cos] + (n - 1) S0[n - 2].
-def reduce_cs(b):
-    return ([b[0][0] + b[2][0], b[0][1] + b[2][1], b[0][2] + b[2][2] - b[2][0], -b[2][1], -b[2][2]],
-            [b[1][0], b[1][1], b[1][2]])
-
-
-def s_tables(t0, t1):
-    c0, s0, c1, s1 = np.cos(t0), np.sin(t0), np.cos(t1), np.sin(t1)
-    S0 = [t1 - t0, c0 - c1]
-    for n in range(2, 7):
-        S0.append((c0 * s0 ** (n - 1) - c1 * s1 ** (n - 1) + (n - 1) * S0[n - 2]) / n)
-    S1 = [(s1 ** (n + 1) - s0 ** (n + 1)) / (n + 1) for n in range(6)]
-    return S0, S1
-
-
-def reduced_moments(b, S0, S1):
-    A, B = reduce_cs(b)
-    M1 = sum(A[j] * S0[j] for j in range(5)) + sum(B[j] * S1[j] for j in range(3))
-    Mc = sum(A[j] * S1[j] for j in range(5)) + sum(B[j] * (S0[j] - S0[j + 2]) for j in range(3))
-    Ms = sum(A[j] * S0[j + 1] for j in range(5)) + sum(B[j] * S1[j + 1] for j in range(3))
-    Mss = sum(A[j] * S0[j + 2] for j in range(5)) + sum(B[j] * S1[j + 2] for j in range(3))
-    Msc = sum(A[j] * S1[j + 1] for j in range(5)) + sum(B[j] * (S0[j + 1] - S0[j + 3]) for j in range(3))
-    return {"1": M1, "c": Mc, "s": Ms, "cc": M1 - Mss, "sc": Msc, "ss": Mss}
-
-
-WEIGHTS = {"1": (0, 0), "c": (1, 0), "s": (0, 1), "cc": (2, 0), "sc": (1, 1), "ss": (0, 2)}
-
-
-def direct_moments(b, t0, t1):
-    """int q w by quadrature of the monomials (q = sum b[i][e] cos^i sin^e)."""
-    return {k: sum(b[i][e] * quad_moment(i + di, e + de, t0, t1) for i in range(3) for e in range(3))
-            for k, (di, de) in WEIGHTS.items()}
-
-
-@pytest.mark.parametrize("seed", range(6))
-def test_reduced_basis_moments_on_arcs(seed):
-    rng = np.random.default_rng(seed)
-    b = rng.normal(size=(3, 3))
-    t0, t1 = sorted(rng.uniform(-3.0, 3.0, size=2))
-    want, got = direct_moments(b, t0, t1), reduced_moments(b, *s_tables(t0, t1))
-    for k in WEIGHTS:
-        assert got[k] == pytest.approx(want[k], abs=1e-12)
-
-
-@pytest.mark.parametrize("a", [0.0, 0.3, 0.847, 0.999, 1.0])
-def test_reduced_half_table_and_mirror(a):
-    """X: the half table's odd entries vanish and the even ones have the
-    closed forms S0 = (2 al, al - a s, ...), S1[n] = 2 s^(n+1) / (n + 1); Y
-    (asin b, pi - asin b) is X mirrored about pi/4 with b for a: the moments
-    over Y of q equal the mirrored moments over X of q with cos and sin
-    exchanged (b[i][e] -> b[e][i])."""
-    al = np.arccos(a)
-    s = np.sqrt(1.0 - a * a)
-    S0, S1 = s_tables(-al, al)
-    assert S0[0] == pytest.approx(2 * al, abs=1e-14)
-    assert S0[2] == pytest.approx(al - a * s, abs=1e-14)
-    for n in (1, 3, 5):
-        assert abs(S0[n]) < 1e-14 and abs(S1[n]) < 1e-14
-    for n in (0, 2, 4):
-        assert S1[n] == pytest.approx(2 * s ** (n + 1) / (n + 1), abs=1e-14)
-    rng = np.random.default_rng(int(a * 1000))
-    b = rng.normal(size=(3, 3))
-    be = np.arcsin(a)
-    want = direct_moments(b, be, np.pi - be)
-    mirrored = reduced_moments(b.T, S0, S1)
-    back = {"1": mirrored["1"], "c": mirrored["s"], "s": mirrored["c"], "cc": mirrored["ss"],
-            "sc": mirrored["sc"], "ss": mirrored["cc"]}
-    for k in WEIGHTS:
-        assert back[k] == pytest.approx(want[k], abs=1e-12)

@@ -521,8 +521,8 @@ def test_checkpoint_resume_is_bitwise(env, prob_name):
 
 
 def test_node_flux_path_matches_the_three_level_flux_kernel(env):
-    """The single-grid step writes each node's Simpson-in-time flux from the
-    point-value kernel and the flux kernel reads those; a batch instance takes
+    """With AF_OPT_NODE_FLUX the single-grid step writes each node's Simpson-in-
+    time flux from the point-value kernel and the flux kernel reads those; a batch instance takes
     the other design (t^{n+1/2} written, fluxes formed from three levels in
     the flux kernel).  Both form every node flux with the same sequence of
     operations, so the states agree to FP32 round-off (the compilers may
@@ -531,7 +531,7 @@ def test_node_flux_path_matches_the_three_level_flux_kernel(env):
     torch, af, _ = env
     prob = W.fourier_smooth(45, 38, seed=31, lx=1.0, ly=0.84)
     st = W.to_f32(W.discretise(prob))
-    s = solver(env, prob, state=st)
+    s = solver(env, prob, {"node_flux": 1}, state=st)
     b = af.Batch([(prob.nx, prob.ny)], [(prob.dx, prob.dy)], bcs=[prob.bc])
     b.set_state(0, *to_dev(torch, st))
     hist = torch.zeros((4, 1), dtype=torch.float64, device="cuda")

@@ -444,6 +444,50 @@ def test_constant_state_preserved(oracle_mod, bc):
         np.testing.assert_allclose(a, b, rtol=1e-14, atol=1e-14)
 
 
+# ---------------------------------------------- linear stability of the step
+def _perturbation_growth(oracle_mod, u, v, cfl, steps, n=16, amp=1e-8, seed=1):
+    """Largest deviation from a uniform state (rho = p = 1, velocity (u, v))
+    after ``steps`` steps of a periodic n x n grid whose averages and point
+    values carry a random perturbation of size amp, divided by the initial
+    deviation; dt from CFL = (max(|u|, |v|) + c) dt / h (Sec. 2)."""
+    prob = W.Problem("uniform", n, n, 0.0, 0.0, 1.0, 1.0, (0, 0, 0, 0),
+                     lambda x, y: (1.0 + 0 * x, u + 0 * x, v + 0 * x, 1.0 + 0 * x), 1.0)
+    base = [np.array(a, dtype=np.float64) for a in W.discretise(prob)]
+    rng = np.random.default_rng(seed)
+    st = [a + amp * rng.normal(size=a.shape) for a in base]
+    st[1][:, -1, :] = st[1][:, 0, :]  # periodic duplicate lines equal the first
+    st[1][:, :, -1] = st[1][:, :, 0]
+    st[2][:, :, -1] = st[2][:, :, 0]
+    st[3][:, -1, :] = st[3][:, 0, :]
+    d0 = max(np.abs(a - b).max() for a, b in zip(st, base))
+    o = make_oracle(oracle_mod, prob, state=st)
+    dt = cfl * prob.dx / (max(abs(u), abs(v)) + np.sqrt(1.4))
+    for _ in range(steps):
+        o.step(dt)
+    return max(np.abs(a - b).max() for a, b in zip(o.get_state(), base)) / d0
+
+
+def test_linear_stability_bound_at_rest(oracle_mod):
+    """Sec. 2 quotes the linear stability bound CFL <= 0.279 for the EG2
+    Active Flux method; at rest the full step reproduces it: perturbations of
+    a uniform state stay bounded at CFL 0.279 and grow fast at 0.29."""
+    assert _perturbation_growth(oracle_mod, 0.0, 0.0, 0.279, 600) < 3.0
+    assert _perturbation_growth(oracle_mod, 0.0, 0.0, 0.29, 600) > 1e3
+
+
+def test_oblique_supersonic_background_is_unstable(oracle_mod):
+    """A finding, recorded as a test: for a uniform flow along the diagonal at
+    about Mach 1.2 (velocity (1.05, 1.05), c = 1.18: each Mach circle crosses
+    both grid lines through a vertex without holding it) perturbations grow
+    even within the bound, CFL 0.279; at velocity (0.5, 0.5) they decay at
+    CFL 0.3, and at (1.5, 1.5) (the lines miss the circles) they stay
+    bounded.  The isentropic-vortex background (1, 1) lies in the growing
+    band, so long runs of that vortex blow up (after about 1800 FP64 steps)."""
+    assert _perturbation_growth(oracle_mod, 1.05, 1.05, 0.279, 600) > 1e2
+    assert _perturbation_growth(oracle_mod, 0.5, 0.5, 0.3, 600) < 1.0
+    assert _perturbation_growth(oracle_mod, 1.5, 1.5, 0.3, 600) < 3.0
+
+
 def test_conservation_periodic(oracle_mod):
     prob = W.fourier_smooth(16, 12, seed=3, lx=1.0, ly=0.75)
     o = make_oracle(oracle_mod, prob)
