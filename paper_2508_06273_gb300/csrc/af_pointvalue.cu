@@ -838,7 +838,7 @@ __device__ __forceinline__ void node_flux(const Args &A, int i, int j, const flo
 }
 
 // both time levels of node (K, i, j), tile-local (li, lj)
-template <int K, int TY>
+template <int K, int TY, bool NF>
 __device__ __forceinline__ void node_update(const Args &A, const float *sm, const float *raw, int i0, int j0,
                                             int i, int j, int li, int lj, unsigned cnt[4], bool &cfl_bad,
                                             bool &nonfinite, float *scr) {
@@ -924,13 +924,13 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
     }
 #pragma unroll
     for (int v = 0; v < NV; v++) nonfinite |= !isfinite(res[v]);
-    if (lev == 1 && A.nflux[0]) {
+    if (NF && lev == 1) {
 #pragma unroll
       for (int v = 0; v < NV; v++) scr[v * (TX * TY)] = res[v];
     }
-    if (lev == 2 || A.write_half || !A.nflux[0]) st4_node<K>(lev == 1 ? A.n1[K] : A.n2[K], g, i, j, res);
+    if (!NF || lev == 2 || A.write_half) st4_node<K>(lev == 1 ? A.n1[K] : A.n2[K], g, i, j, res);
   }
-  if (A.nflux[0]) node_flux<K, TY>(A, i, j, U0, res, scr);
+  if (NF) node_flux<K, TY>(A, i, j, U0, res, scr);
 }
 
 // prologue: the block builds the records of its (TX+2) x (TY+2) cells; only
@@ -944,43 +944,50 @@ __device__ __forceinline__ void tile_prologue(const Args &A, const float *raw, f
   }
 }
 
-// node updates of the cell (i0 + tx, j0 + ty); with node fluxes, the block's
-// maximum wave speed of the new point values goes to A.speed (one atomic)
+// the block's maximum wave speed of the new point values (node-flux
+// instantiation: each thread's running maximum in scratch slot 4) into
+// A.speed, one atomic a block
 template <int TY>
+__device__ __forceinline__ void block_speed(const Args &A, const float *scr, int tid) {
+  __shared__ float wmax[TX * TY / 32];
+  __shared__ int wbad[TX * TY / 32];
+  float smax = scr[4 * TX * TY];
+  const bool sbad = isinf(smax);
+  smax = sbad ? 0.0f : smax;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  const bool anybad = __any_sync(0xffffffffu, sbad);
+  if ((tid & 31) == 0) {
+    wmax[tid >> 5] = smax;
+    wbad[tid >> 5] = anybad;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float m = 0.0f;
+    int b = 0;
+    for (int w = 0; w < TX * TY / 32; w++) {
+      m = fmaxf(m, wmax[w]);
+      b |= wbad[w];
+    }
+    atomicMax(A.speed, __float_as_uint(m));  // positive floats order like their bit patterns
+    if (b) atomicOr(A.speed_bad, 1);
+  }
+}
+
+// node updates of the cell (i0 + tx, j0 + ty); NF: the instantiation that
+// writes node fluxes (separate, so that the plain kernel carries none of it)
+template <int TY, bool NF>
 __device__ __forceinline__ void tile_nodes(const Args &A, const float *sm, const float *raw, int i0, int j0,
-                                           int tx, int ty, float *scr, float *wmax, int *wbad) {
+                                           int tx, int ty, float *scr) {
   unsigned cnt[4] = {0, 0, 0, 0};
   bool cfl_bad = false, nonfinite = false;
   const int i = i0 + tx, j = j0 + ty;
   constexpr int NT = TX * TY;
-  if (A.nflux[0]) scr[4 * NT] = 0.0f;
-  node_update<VTX, TY>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
-  node_update<XE, TY>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
-  node_update<YE, TY>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
-  if (A.nflux[0]) {
-    const int tid = ty * TX + tx;
-    float smax = scr[4 * NT];
-    const bool sbad = isinf(smax);
-    smax = sbad ? 0.0f : smax;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-    const bool anybad = __any_sync(0xffffffffu, sbad);
-    if ((tid & 31) == 0) {
-      wmax[tid >> 5] = smax;
-      wbad[tid >> 5] = anybad;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      float m = 0.0f;
-      int b = 0;
-      for (int w = 0; w < TX * TY / 32; w++) {
-        m = fmaxf(m, wmax[w]);
-        b |= wbad[w];
-      }
-      atomicMax(A.speed, __float_as_uint(m));  // positive floats order like their bit patterns
-      if (b) atomicOr(A.speed_bad, 1);
-    }
-  }
+  if (NF) scr[4 * NT] = 0.0f;
+  node_update<VTX, TY, NF>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
+  node_update<XE, TY, NF>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
+  node_update<YE, TY, NF>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
+  if (NF) block_speed<TY>(A, scr, ty * TX + tx);
   // (the limiter reports its own kept values and Lax-Friedrichs fall-backs)
   const int st = (cfl_bad ? ST_CFL : 0) | (nonfinite ? ST_NONFINITE : 0);
   if (st) atomicOr(A.status, st);
@@ -1034,7 +1041,7 @@ __device__ __forceinline__ bool tile_wait(unsigned long long *bar, unsigned limi
 }
 
 // one tile: stage the t^n box, build the cell records, update the nodes
-template <int TY>
+template <int TY, bool NF>
 __device__ __forceinline__ void tile_body(const Args &A, const TileMaps &T, float *raw, unsigned long long *bar,
                                           int i0, int j0) {
   float *sm = raw + Tile<TY>::RAW_FLOATS;
@@ -1057,9 +1064,7 @@ __device__ __forceinline__ void tile_body(const Args &A, const TileMaps &T, floa
   }
   tile_prologue<TY>(A, raw, sm, i0, j0, tid);
   __syncthreads();
-  __shared__ float wmax[TX * TY / 32];
-  __shared__ int wbad[TX * TY / 32];
-  tile_nodes<TY>(A, sm, raw, i0, j0, threadIdx.x, threadIdx.y, sm + Tile<TY>::REC_FLOATS + tid, wmax, wbad);
+  tile_nodes<TY, NF>(A, sm, raw, i0, j0, threadIdx.x, threadIdx.y, sm + Tile<TY>::REC_FLOATS + tid);
 }
 
 // TMA destinations must start on 128-byte boundaries
@@ -1095,13 +1100,13 @@ __device__ __forceinline__ void tile_prefetch_l2(const TileMaps &T) {
                  : "memory");
 }
 
-template <int TY>
+template <int TY, bool NF>
 __global__ void __launch_bounds__(TX *TY, min_blocks<TY>()) pointvalue_kernel(Args A, const __grid_constant__ TileMaps T) {
   extern __shared__ float4 smem4[];
   __shared__ alignas(8) unsigned long long bar;
   if (A.tile_flag && !A.tile_flag[blockIdx.y * gridDim.x + blockIdx.x]) return;
   if (threadIdx.x == 0 && threadIdx.y == 0) tile_prefetch_l2<TY>(T);
-  tile_body<TY>(A, T, tile_smem(smem4), &bar, blockIdx.x * TX, blockIdx.y * TY);
+  tile_body<TY, NF>(A, T, tile_smem(smem4), &bar, blockIdx.x * TX, blockIdx.y * TY);
 }
 
 // Batched form: block b takes tile B.tiles[b] = (instance, i0, j0) and the
@@ -1118,7 +1123,7 @@ __global__ void __launch_bounds__(TX *TY, min_blocks<TY>()) pointvalue_batch_ker
   // read-only, so the compiler may load a field again where a copy in shared
   // memory held it in a register (half the spills)
   const Args *__restrict__ A = B.args + 2 * t.x + c.cur;
-  tile_body<TY>(*A, B.maps[2 * t.x + c.cur], tile_smem(smem4), &bar, t.y, t.z);
+  tile_body<TY, false>(*A, B.maps[2 * t.x + c.cur], tile_smem(smem4), &bar, t.y, t.z);
 }
 
 }  // namespace
@@ -1155,34 +1160,31 @@ cudaError_t make_tile_maps(const Grid &g, float *vtx, float *xe, float *ye, floa
 }
 
 cudaError_t prepare_pointvalue() {
-  cudaError_t e = cudaFuncSetAttribute(pointvalue_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       Tile<8>::SMEM_NF_BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(pointvalue_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Tile<4>::SMEM_NF_BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(pointvalue_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Tile<16>::SMEM_NF_BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(pointvalue_batch_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Tile<4>::SMEM_BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(pointvalue_batch_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Tile<8>::SMEM_BYTES);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(pointvalue_batch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Tile<16>::SMEM_BYTES);
+  cudaError_t e = cudaSuccess;
+  auto attr = [&](const void *f, int bytes) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  };
+  attr((const void *)pointvalue_kernel<4, false>, Tile<4>::SMEM_BYTES);
+  attr((const void *)pointvalue_kernel<8, false>, Tile<8>::SMEM_BYTES);
+  attr((const void *)pointvalue_kernel<16, false>, Tile<16>::SMEM_BYTES);
+  attr((const void *)pointvalue_kernel<4, true>, Tile<4>::SMEM_NF_BYTES);
+  attr((const void *)pointvalue_kernel<8, true>, Tile<8>::SMEM_NF_BYTES);
+  attr((const void *)pointvalue_kernel<16, true>, Tile<16>::SMEM_NF_BYTES);
+  attr((const void *)pointvalue_batch_kernel<4>, Tile<4>::SMEM_BYTES);
+  attr((const void *)pointvalue_batch_kernel<8>, Tile<8>::SMEM_BYTES);
+  attr((const void *)pointvalue_batch_kernel<16>, Tile<16>::SMEM_BYTES);
   return e;
 }
 
 // tiles cover the owned nodes: up to nxv x nyv (vertex lines n + 1 on a
 // non-periodic axis); every box x coordinate is a multiple of TX floats; the
-// node-flux scratch is allocated only when node fluxes are written
+// node-flux instantiation (with its scratch) only when node fluxes are written
 template <int TY>
 static void launch_h(const Args &A, const TileMaps &maps, cudaStream_t s) {
   const Grid &g = A.g;
-  const int smem = A.nflux[0] ? Tile<TY>::SMEM_NF_BYTES : Tile<TY>::SMEM_BYTES;
-  pointvalue_kernel<TY><<<dim3((g.nxv + TX - 1) / TX, (g.nyv + TY - 1) / TY), dim3(TX, TY), smem, s>>>(A, maps);
+  const dim3 grd((g.nxv + TX - 1) / TX, (g.nyv + TY - 1) / TY), blk(TX, TY);
+  if (A.nflux[0]) pointvalue_kernel<TY, true><<<grd, blk, Tile<TY>::SMEM_NF_BYTES, s>>>(A, maps);
+  else pointvalue_kernel<TY, false><<<grd, blk, Tile<TY>::SMEM_BYTES, s>>>(A, maps);
 }
 static cudaError_t launch_single(const Args &A, const TileMaps &maps, int tile_h, cudaStream_t s) {
   switch (tile_h) {
