@@ -110,6 +110,14 @@ enum {
                                issued): the step returns normally with AF_ST_TIMEOUT set */
   AF_OPT_KEEP_HALF = 15,    /* with AF_OPT_NODE_FLUX: 1 keeps the t^{n+1/2} point values for af_get_half
                                as well (48 more bytes written a cell) */
+  AF_OPT_FP64 = 17,         /* 1: the handle steps in FP64 (state, reconstruction, EG2 with the correction,
+                               fluxes and update in double; af_set_state_f64 / af_get_state_f64 move its
+                               state) for accuracy studies below the FP32 floor of the point values (Tables 1
+                               and 2 of Sec. 2 at 512 and 1024 cells).  Alg. 1 with the linearisations of
+                               Sec. 2 and 3.1 and Corollary 1 only: af_step refuses (AF_ERR_STATE) with tsw,
+                               limiter, force_lo, surrogate, flux_limiter, shock_blend, node_bounds or
+                               node_flux on, or an inflow side.  Turning it on allocates 80 double planes;
+                               switching precision drops the state.  Many times slower than FP32 on this GPU */
   AF_OPT_NODE_FLUX = 16     /* 1: the point-value kernel writes, in place of the t^{n+1/2} level, each node's
                                Simpson-in-time flux f(U^n) + 4 f(U^{n+1/2}) + f(U^{n+1}) (eq. (F)) and the flux
                                kernel reads those (64 B a cell instead of 144 B of point values at three
@@ -178,6 +186,12 @@ int af_host_sync(af_ctx *h);
 /* FP32 low words of the cell averages [4][ny][nx] (device / host memory). */
 int af_get_avg_lo(af_ctx *h, float *avg_lo, void *stream);
 int af_set_avg_lo(af_ctx *h, const float *avg_lo, void *stream);
+/* The state of a handle in FP64 mode (AF_OPT_FP64): the layouts of
+ * af_set_state / af_get_state with double elements, device memory.
+ * AF_ERR_STATE if the handle is not in FP64 mode. */
+int af_set_state_f64(af_ctx *h, const double *avg, const double *vtx, const double *xe, const double *ye,
+                     void *stream);
+int af_get_state_f64(af_ctx *h, double *avg, double *vtx, double *xe, double *ye, void *stream);
 /* Point values at t^{n+1/2} computed by the last step (device memory).
  * AF_ERR_STATE if that step took the node-flux path without
  * AF_OPT_KEEP_HALF. */

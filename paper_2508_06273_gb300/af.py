@@ -21,13 +21,13 @@ _LIB = None
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING, BC_INFLOW = 0, 1, 2, 3
 OPT = {"lin_mode": 0, "tsw": 1, "limiter": 2, "correction": 3, "force_lo": 4, "profile": 5, "surrogate": 6,
        "surr_tol": 7, "surr_abs": 8,
-       "flux_limiter": 9, "shock_blend": 10, "tile_h": 11, "node_bounds": 12, "ubar": 13, "test_timeout": 14, "keep_half": 15, "node_flux": 16}
+       "flux_limiter": 9, "shock_blend": 10, "tile_h": 11, "node_bounds": 12, "ubar": 13, "test_timeout": 14, "keep_half": 15, "node_flux": 16, "fp64": 17}
 STAGES = ("prep", "pointvalue", "flux", "reduce")
 ST_CFL, ST_AVG_NONPOS, ST_NONFINITE, ST_KEPT, ST_TIMEOUT, ST_STOPPED, ST_FLUX_LIMITED = 1, 2, 4, 8, 16, 32, 64
 EXPORTS = [
     "af_create", "af_destroy", "af_last_error", "af_set_stream", "af_set_option",
     "af_get_option", "af_set_state", "af_set_state_host", "af_get_state", "af_get_state_host",
-    "af_set_state_host_async", "af_get_state_host_async", "af_host_sync",
+    "af_set_state_host_async", "af_get_state_host_async", "af_host_sync", "af_set_state_f64", "af_get_state_f64",
     "af_get_avg_lo", "af_set_avg_lo", "af_get_half", "af_step", "af_run", "af_status",
     "af_counters", "af_conserved_totals", "af_max_speed", "af_profile",
     "af_conserved_totals_noalloc",
@@ -70,6 +70,8 @@ def lib():
                 "af_set_state_host_async": (i, [vp, fp, fp, fp, fp]),
                 "af_get_state_host_async": (i, [vp, fp, fp, fp, fp]),
                 "af_host_sync": (i, [vp]),
+                "af_set_state_f64": (i, [vp, fp, fp, fp, fp, vp]),
+                "af_get_state_f64": (i, [vp, fp, fp, fp, fp, vp]),
                 "af_get_avg_lo": (i, [vp, fp, vp]),
                 "af_set_avg_lo": (i, [vp, fp, vp]),
                 "af_get_half": (i, [vp, fp, fp, fp, vp]),
@@ -193,6 +195,21 @@ class Solver:
                 raise ValueError(f"need CUDA float32 tensors of shape {s}")
             ts.append(a.contiguous())
         _check(self.L.af_set_state(self.h, *[_ptr(t) for t in ts], self._s()))
+
+    def set_state_f64(self, avg, vtx, xe, ye):
+        """State of a handle in FP64 mode from CUDA float64 tensors."""
+        ts = []
+        for a, s in zip((avg, vtx, xe, ye), self.shapes()):
+            if tuple(a.shape) != s or a.dtype != self.torch.float64 or not a.is_cuda:
+                raise ValueError(f"need CUDA float64 tensors of shape {s}")
+            ts.append(a.contiguous())
+        _check(self.L.af_set_state_f64(self.h, *[_ptr(t) for t in ts], self._s()))
+
+    def get_state_f64(self):
+        """Current state of a handle in FP64 mode as CUDA float64 tensors."""
+        out = [self.torch.empty(s, dtype=self.torch.float64, device=self.device) for s in self.shapes()]
+        _check(self.L.af_get_state_f64(self.h, *[_ptr(t) for t in out], self._s()))
+        return tuple(out)
 
     def get_state(self):
         """Current state as CUDA float32 tensors."""

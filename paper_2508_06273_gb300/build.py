@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libaf.so")
-SOURCES = ["af_api.cu", "af_misc.cu", "af_pointvalue.cu", "af_flux.cu", "af_noalloc.cu", "af_batch.cu", "af_gemm.cu", "af_mlp.cu", "af_surrogate.cu"]
+SOURCES = ["af_api.cu", "af_misc.cu", "af_pointvalue.cu", "af_flux.cu", "af_noalloc.cu", "af_batch.cu", "af_gemm.cu", "af_mlp.cu", "af_surrogate.cu", "af_fp64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -287,6 +287,7 @@ void af_destroy(af_ctx *h) {
   if (h->surr_ubar) cudaFree(h->surr_ubar);
   if (h->shock_theta) cudaFree(h->shock_theta);
   if (h->q0) cudaFree(h->q0);
+  if (h->f64_base) cudaFree(h->f64_base);
   cudaEventDestroy(h->ev_in);
   cudaEventDestroy(h->ev_out);
   for (int k = 0; k < 5; k++) cudaEventDestroy(h->ev_stage[k]);
@@ -349,6 +350,36 @@ int af_set_option(af_ctx *h, int key, double value) {
     case AF_OPT_NODE_BOUNDS: h->opt.node_bounds = iv != 0; return AF_OK;
     case AF_OPT_TEST_TIMEOUT: h->opt.test_timeout = iv != 0; return AF_OK;
     case AF_OPT_NODE_FLUX: h->opt.node_flux = iv != 0; return AF_OK;
+    case AF_OPT_FP64: {
+      const bool on = iv != 0;
+      if (on && !h->f64_base) {
+        DeviceGuard dg(h->device);
+        // averages (4 planes), 3 levels x 3 node arrays (36 planes), records
+        // (40 doubles a cell), then the reduction words
+        const size_t planes = (40 + REC64_DOUBLES) * (size_t)h->g.plane;
+        const size_t bytes = sizeof(double) * (planes + TOTALS64_PARTIALS + 4) + 64;
+        CK(cudaMalloc(&h->f64_base, bytes), "cudaMalloc(FP64 state)");
+        double *p = h->f64_base;
+        h->f64_avg = p;
+        p += NV * (size_t)h->g.plane;
+        for (int l = 0; l < 3; l++)
+          for (int k = 0; k < 3; k++) {
+            h->f64_lev[l][k] = p;
+            p += NV * (size_t)h->g.plane;
+          }
+        h->f64_rec = p;
+        p += REC64_DOUBLES * (size_t)h->g.plane;
+        h->f64_partials = p;
+        p += TOTALS64_PARTIALS;
+        h->f64_totals = p;
+        p += 4;
+        h->f64_speed = reinterpret_cast<unsigned long long *>(p);
+        h->f64_bad = reinterpret_cast<int *>(p + 1);
+      }
+      if (on != h->fp64) h->has_state = false;  // a state of the other precision is not carried over
+      h->fp64 = on;
+      return AF_OK;
+    }
     case AF_OPT_KEEP_HALF:
       if ((iv != 0) != (h->keep_half != 0)) {
         for (int p = 0; p < 2; p++)  // captured steps hold the old launch arguments
@@ -415,6 +446,7 @@ int af_get_option(af_ctx *h, int key, double *value) {
     case AF_OPT_TEST_TIMEOUT: *value = h->opt.test_timeout; return AF_OK;
     case AF_OPT_KEEP_HALF: *value = h->keep_half; return AF_OK;
     case AF_OPT_NODE_FLUX: *value = h->opt.node_flux; return AF_OK;
+    case AF_OPT_FP64: *value = h->fp64 ? 1.0 : 0.0; return AF_OK;
     case AF_OPT_TILE_H: *value = h->tile_h; return AF_OK;
     default: return fail(AF_ERR_ARG, "unknown option%s");
   }
@@ -423,6 +455,7 @@ int af_get_option(af_ctx *h, int key, double *value) {
 int af_set_state(af_ctx *h, const float *avg, const float *vtx, const float *xe, const float *ye,
                  void *stream) {
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (h->fp64) return fail(AF_ERR_STATE, "the handle is in FP64 mode: use af_set_state_f64%s");
   DeviceGuard dg(h->device);
   const float *src[4] = {avg, vtx, xe, ye};
   for (int w = 0; w < 4; w++)
@@ -519,10 +552,53 @@ static int get_arrays(af_ctx *h, NodeSet &ns, const float *avgsrc, float *dst[4]
 
 int af_get_state(af_ctx *h, float *avg, float *vtx, float *xe, float *ye, void *stream) {
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (h->fp64) return fail(AF_ERR_STATE, "the handle is in FP64 mode: use af_get_state_f64%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
   DeviceGuard dg(h->device);
   float *dst[4] = {avg, vtx, xe, ye};
   return get_arrays(h, h->lev[0], h->hi, dst, false, (cudaStream_t)stream);
+}
+
+// FP64 path: the compact arrays of af_set_state / af_get_state in double
+// (device memory), packed into or out of the padded FP64 planes
+int af_set_state_f64(af_ctx *h, const double *avg, const double *vtx, const double *xe, const double *ye,
+                     void *stream) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (!h->fp64) return fail(AF_ERR_STATE, "af_set_state_f64: turn AF_OPT_FP64 on first%s");
+  const double *src[4] = {avg, vtx, xe, ye};
+  for (int w = 0; w < 4; w++)
+    if (!is_device_ptr(src[w])) return fail(AF_ERR_ARG, "af_set_state_f64: arrays must be device memory%s");
+  DeviceGuard dg(h->device);
+  order_after(h, (cudaStream_t)stream);
+  double *dst[4] = {h->f64_avg, h->f64_lev[0][VTX], h->f64_lev[0][XE], h->f64_lev[0][YE]};
+  for (int w = 0; w < 4; w++) {
+    int ni, nj;
+    extents(h, w, ni, nj);
+    CK(launch_pack64(h->g, src[w], dst[w], ni, nj, true, h->stream), "pack");
+  }
+  order_before(h, (cudaStream_t)stream);
+  h->has_state = true;
+  h->half_valid = false;
+  return AF_OK;
+}
+
+int af_get_state_f64(af_ctx *h, double *avg, double *vtx, double *xe, double *ye, void *stream) {
+  if (!h) return fail(AF_ERR_ARG, "null handle%s");
+  if (!h->fp64) return fail(AF_ERR_STATE, "af_get_state_f64: the handle is not in FP64 mode%s");
+  if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  double *dst[4] = {avg, vtx, xe, ye};
+  for (int w = 0; w < 4; w++)
+    if (!is_device_ptr(dst[w])) return fail(AF_ERR_ARG, "af_get_state_f64: arrays must be device memory%s");
+  DeviceGuard dg(h->device);
+  order_after(h, (cudaStream_t)stream);
+  const double *src[4] = {h->f64_avg, h->f64_lev[0][VTX], h->f64_lev[0][XE], h->f64_lev[0][YE]};
+  for (int w = 0; w < 4; w++) {
+    int ni, nj;
+    extents(h, w, ni, nj);
+    CK(launch_pack64(h->g, src[w], dst[w], ni, nj, false, h->stream), "unpack");
+  }
+  order_before(h, (cudaStream_t)stream);
+  return AF_OK;
 }
 
 int af_get_state_host(af_ctx *h, float *avg, float *vtx, float *xe, float *ye) {
@@ -809,11 +885,45 @@ static const char *kTimedOut =
     "a wait for staged data or for the tensor cores timed out (AF_ST_TIMEOUT): the state is invalid and the "
     "handle takes no further steps%s";
 
+// one step of the FP64 path: ghost layers, cell records, point values, fluxes
+static int step64(af_ctx *h, double dt) {
+  const Options &o = h->opt;
+  if (o.tsw || o.limiter || o.force_lo || o.surrogate || o.flux_limiter || o.shock_blend || o.node_bounds ||
+      o.node_flux)
+    return fail(AF_ERR_STATE,
+                "the FP64 path has no Sec. 3 limiters or switches: set tsw, limiter, force_lo, surrogate, "
+                "flux_limiter, shock_blend, node_bounds and node_flux to 0%s");
+  for (int k = 0; k < 4; k++)
+    if (h->g.bc[k] == AF_BC_INFLOW) return fail(AF_ERR_STATE, "the FP64 path has no inflow sides%s");
+  cudaStream_t s = h->stream;
+  CK(launch_ghost_fill64(h->g, h->f64_avg, h->f64_lev[0], s), "FP64 ghost fill");
+  Step64 S;
+  S.g = h->g;
+  S.avg = h->f64_avg;
+  for (int k = 0; k < 3; k++) {
+    S.n0[k] = h->f64_lev[0][k];
+    S.n1[k] = h->f64_lev[1][k];
+    S.n2[k] = h->f64_lev[2][k];
+  }
+  S.recs = h->f64_rec;
+  S.dt = dt;
+  S.lin_mode = o.lin_mode;
+  S.correction = o.correction;
+  S.status = h->d_status;
+  CK(launch_step64(S, dt / h->dx, dt / h->dy, s), "FP64 step");
+  for (int k = 0; k < 3; k++) std::swap(h->f64_lev[0][k], h->f64_lev[2][k]);
+  return AF_OK;
+}
+
 int af_step(af_ctx *h, double dt) {
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(AF_ERR_ARG, "af_step: dt must be positive%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
   if (h->timed_out) return fail(AF_ERR_STATE, kTimedOut);
+  if (h->fp64) {
+    DeviceGuard dg(h->device);
+    return step64(h, dt);
+  }
   DeviceGuard dg(h->device);
   return enqueue_step(h, dt);
 }
@@ -864,6 +974,13 @@ int af_run(af_ctx *h, int nsteps, double dt) {
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
   if (h->timed_out) return fail(AF_ERR_STATE, kTimedOut);
   DeviceGuard dg(h->device);
+  if (h->fp64) {
+    for (int k = 0; k < nsteps; k++) {
+      int rc = step64(h, dt);
+      if (rc) return rc;
+    }
+    return AF_OK;
+  }
   if (h->profile || nsteps < 4) {  // profiled runs time every stage: plain launches
     for (int k = 0; k < nsteps; k++) {
       int rc = enqueue_step(h, dt);
@@ -912,6 +1029,12 @@ int af_conserved_totals(af_ctx *h, double out[4]) {
   if (!h || !out) return fail(AF_ERR_ARG, "null argument%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
   DeviceGuard dg(h->device);
+  if (h->fp64) {
+    CK(launch_totals64(h->g, h->f64_avg, h->f64_partials, h->dx * h->dy, h->f64_totals, h->stream), "totals");
+    CK(cudaMemcpyAsync(out, h->f64_totals, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "totals");
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    return AF_OK;
+  }
   CK(launch_totals(h->g, h->hi, h->lo, h->d_partials, h->d_totals, h->stream), "totals");
   h->launches[AF_STAGE_REDUCE] += 2;
   double t[4];
@@ -938,6 +1061,19 @@ int af_max_speed(af_ctx *h, float *out) {
   if (!h || !out) return fail(AF_ERR_ARG, "null argument%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
   DeviceGuard dg(h->device);
+  if (h->fp64) {
+    const double *n[3] = {h->f64_lev[0][VTX], h->f64_lev[0][XE], h->f64_lev[0][YE]};
+    CK(launch_speed64(h->g, h->f64_avg, n, h->f64_speed, h->f64_bad, h->stream), "FP64 max speed");
+    unsigned long long bits = 0;
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bits, h->f64_speed, sizeof(bits), cudaMemcpyDeviceToHost, h->stream), "speed");
+    CK(cudaMemcpyAsync(&bad, h->f64_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream), "speed");
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    double m;
+    std::memcpy(&m, &bits, sizeof(m));
+    *out = bad ? NAN : (float)m;
+    return AF_OK;
+  }
   if (h->speed_valid) {  // computed by the last step's flux kernel
     unsigned bits = 0;
     int bad = 0;

@@ -25,6 +25,13 @@ struct af_ctx {
   // kernel on the plain path
   float *nflux[4];
   int keep_half;    // the plain path also writes the t^{n+1/2} level
+  // FP64 path (AF_OPT_FP64): own state in double (averages, three levels of
+  // node arrays), cell records and reduction words, allocated when turned on
+  bool fp64;
+  double *f64_base, *f64_avg, *f64_rec, *f64_partials, *f64_totals;
+  double *f64_lev[3][3];  // [level][kind]
+  unsigned long long *f64_speed;
+  int *f64_bad;
   bool half_valid;  // lev[1] holds the t^{n+1/2} level of the last step
   // TMA descriptors for t^n held in either of the two buffers that swap
   // roles each step; tmap_cur selects the one now holding t^n

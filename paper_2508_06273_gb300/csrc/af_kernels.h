@@ -260,6 +260,30 @@ cudaError_t launch_gemm_bf16(const void *A, int lda, const void *B, int ldb, flo
                              int K, const float *bias, int splits, int accumulate, int *err, cudaStream_t s);
 int *gemm_default_err();
 
+// ---- FP64 path (af_fp64.cu): the step in double precision, without the
+// Sec. 3 limiters (accuracy studies below the FP32 floor)
+struct Step64 {
+  Grid g;
+  const double *avg;      // t^n averages (updated in place to t^{n+1})
+  const double *n0[3];    // t^n point values (ghost layers filled)
+  double *n1[3], *n2[3];  // t^{n+1/2} and t^{n+1} point values
+  double *recs;           // cell records, 40 doubles a cell (padded cell index)
+  double dt;
+  int lin_mode, correction;
+  int *status;
+};
+constexpr int REC64_DOUBLES = 40;
+cudaError_t launch_step64(const Step64 &S, double lamx, double lamy, cudaStream_t s);
+cudaError_t launch_speed64(const Grid &g, const double *avg, const double *const n[3], unsigned long long *out,
+                           int *bad, cudaStream_t s);
+cudaError_t launch_totals64(const Grid &g, const double *avg, double *partials, double area, double *out,
+                            cudaStream_t s);
+constexpr int TOTALS64_PARTIALS = 128 * 4;
+cudaError_t launch_pack64(const Grid &g, const double *src, double *dst, int ni, int nj, bool to_padded,
+                          cudaStream_t s);
+// ghost layers of FP64 averages and node arrays (no inflow sides)
+cudaError_t launch_ghost_fill64(const Grid &g, double *avg, double *const n[3], cudaStream_t s);
+
 // ---- learned surrogate (af_surrogate.cu)
 // training-set sampler of batched runs: a node is kept when a counter-based
 // hash of (seed, instance, step, kind, i, j) falls below threshold / 2^32

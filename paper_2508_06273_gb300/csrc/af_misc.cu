@@ -1,5 +1,7 @@
 // af_misc.cu -- ghost cells (Sec. 4.3), reductions and layout conversion
 // kernels.
+#include <type_traits>
+
 #include "af_common.cuh"
 #include "af_kernels.h"
 
@@ -54,7 +56,8 @@ struct GhostRange {
 // an inflow side the side's state (conservative for the averages, zero low
 // word).  A corner entry takes the y side's rule applied to the x side's
 // value, as two passes (x, then y) would give.
-__device__ __forceinline__ void ghost_entry(const Grid &g, const GhostRange &R, float *p, int arr, int k) {
+template <typename T>
+__device__ __forceinline__ void ghost_entry(const Grid &g, const GhostRange &R, T *p, int arr, int k) {
   int i, j, r = k;
   if (r < R.nb) {
     j = -G + r / R.wext;
@@ -76,6 +79,7 @@ __device__ __forceinline__ void ghost_entry(const Grid &g, const GhostRange &R, 
   const int xside = i < 0 ? 0 : (i >= R.ownx ? 1 : -1), yside = j < 0 ? 2 : (j >= R.owny ? 3 : -1);
   const bool xin = !g.per_x && xside >= 0 && g.bc[xside] == BC_INFLOW;
   const bool yin = !g.per_y && yside >= 0 && g.bc[yside] == BC_INFLOW;
+  if constexpr (std::is_same<T, float>::value) {  // (the FP64 path has no inflow sides)
   if (xin || yin) {
     float U[4];
 #pragma unroll
@@ -87,9 +91,10 @@ __device__ __forceinline__ void ghost_entry(const Grid &g, const GhostRange &R, 
     for (int v = 0; v < NV; v++) p[at(g, v, i, j)] = arr == 0 ? Q[v] : (arr == 1 ? 0.0f : U[v]);
     return;
   }
+  }
 #pragma unroll
   for (int v = 0; v < NV; v++) {
-    float x = p[at(g, v, si, sj)];
+    T x = p[at(g, v, si, sj)];
     if ((v == 1 && fx) || (v == 2 && fy)) x = -x;
     p[at(g, v, i, j)] = x;
   }
@@ -100,6 +105,16 @@ __global__ void ghost_kernel(GhostArgs A) {
   const GhostRange R(A.g, arr);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < R.total; k += gridDim.x * blockDim.x)
     ghost_entry(A.g, R, A.a[arr], arr, k);
+}
+
+// FP64 path: averages (no low word) and node arrays
+__global__ void ghost64_kernel(Grid g, double *avg, double *vtx, double *xe, double *ye) {
+  const int arr = blockIdx.y;
+  if (arr == 1) return;
+  double *p = arr == 0 ? avg : (arr == 2 ? vtx : (arr == 3 ? xe : ye));
+  const GhostRange R(g, arr);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < R.total; k += gridDim.x * blockDim.x)
+    ghost_entry(g, R, p, arr, k);
 }
 
 // batched: block b fills chunk B.chunks[b] = (instance, array, first entry)
@@ -334,6 +349,14 @@ __global__ void check_dup_kernel(const float *__restrict__ a, int ni, int nj, in
 }
 
 }  // namespace
+
+cudaError_t launch_ghost_fill64(const Grid &g, double *avg, double *const n[3], cudaStream_t s) {
+  const long long per = 2LL * (g.nx + g.ny + 2 * G + 2) * (2 * G + 1);
+  int blocks = (int)((per + 255) / 256);
+  if (blocks < 1) blocks = 1;
+  ghost64_kernel<<<dim3(blocks, 5), 256, 0, s>>>(g, avg, n[VTX], n[XE], n[YE]);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ghost_fill(const Grid &g, float *avg_hi, float *avg_lo, const NodeSet &n,
                               cudaStream_t s) {

@@ -1,0 +1,157 @@
+"""The FP64 path (AF_OPT_FP64) through the C ABI: one step against the FP64
+oracle on the same inputs to round-off level, element by element, in every
+linearisation mode; conservation to FP64 round-off; and Tables 1 and 2 of
+Sec. 2 reproduced on the GPU down to the rows the FP32 path cannot reach
+(its point values floor at about 3e-7 and 9e-7)."""
+import os
+
+import numpy as np
+import pytest
+
+from helpers import make_oracle, read_table, restrict2
+from paper_2508_06273_gb300 import workloads as W
+from test_gpu_parity import SMOOTH, _wall_problem, assert_parity, env  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+# the Sec. 3 limiters and switches are not part of the FP64 path
+PLAIN = {"limiter": 0, "tsw": 0, "flux_limiter": 0, "shock_blend": 0, "node_bounds": 0}
+# FP64 against FP64: the GPU's closed-form arc sums and the oracle's
+# quadrature differ by round-off only
+TOL64 = 1e-11
+
+
+def solver64(env, prob, opts=None, state=None):
+    torch, af, _ = env
+    o = dict(prob.options)
+    o.update(PLAIN)
+    o.update(opts or {})
+    s = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=o)
+    s.set_option("fp64", 1)
+    st = state if state is not None else W.discretise(prob)
+    s.set_state_f64(*[torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda() for a in st])
+    return s
+
+
+def host64(s):
+    return [t.cpu().numpy() for t in s.get_state_f64()]
+
+
+MODES64 = {"avg": {}, "point": {"lin_mode": 1}, "alg1": {"lin_mode": 2}, "nocorr": {"correction": 0},
+           "ubar_c2p": {"ubar": 1}}
+
+
+@pytest.mark.parametrize("case", ["vortex32", "fourier_ragged", "supersonic_xy", "inside_neg", "at_rest"])
+@pytest.mark.parametrize("mode", list(MODES64))
+def test_one_step_matches_the_oracle(env, case, mode):
+    if mode != "avg" and case not in ("vortex32", "inside_neg"):
+        pytest.skip("modes are covered on two cases")
+    torch, af, oracle = env
+    prob = SMOOTH[case]()
+    st = W.discretise(prob)  # FP64 initial data on both sides
+    opts = dict(PLAIN, **MODES64[mode])
+    o = make_oracle(oracle, prob, opts, state=st)
+    dt = prob.cfl * min(prob.dx, prob.dy) / o.max_speed()
+    o.step(dt)
+    s = solver64(env, prob, MODES64[mode], st)
+    assert s.max_speed() == pytest.approx(make_oracle(oracle, prob, opts, state=st).max_speed(), rel=1e-6)
+    s.step(dt)
+    assert s.status() == 0
+    assert_parity(host64(s), o.get_state(), TOL64, what="FP64 step")
+    s.close()
+
+
+def test_walls_and_final_time_match_the_oracle(env):
+    torch, af, oracle = env
+    prob = _wall_problem()
+    st = W.discretise(prob)
+    o = make_oracle(oracle, prob, PLAIN, state=st)
+    s = solver64(env, prob, state=st)
+    for _ in range(5):
+        dt = 0.3 * prob.dy / o.max_speed()
+        o.step(dt)
+        s.step(dt)
+    assert_parity(host64(s), o.get_state(), TOL64, what="walls")
+    prob = W.shu_vortex(32)
+    st = W.discretise(prob)
+    o = make_oracle(oracle, prob, PLAIN, state=st)
+    s = solver64(env, prob, state=st)
+    t = 0.0
+    while t < prob.t_end * (1 - 1e-12):
+        dt = min(prob.cfl * prob.dx / o.max_speed(), prob.t_end - t)
+        o.step(dt)
+        s.step(dt)
+        t += dt
+    assert s.status() == 0
+    assert_parity(host64(s), o.get_state(), 1e-9, what="32^2 vortex at t = 10")
+    s.close()
+
+
+def test_conservation_and_refusals(env):
+    torch, af, _ = env
+    prob = W.fourier_smooth(64, 48, seed=8, lx=1.0, ly=0.75)
+    s = solver64(env, prob)
+    t0 = s.totals()
+    absq = np.abs(W.discretise(prob)[0]).sum(axis=(1, 2)) * prob.dx * prob.dy
+    for _ in range(50):
+        s.step(0.3 * prob.dx / 2.0)
+    assert s.status() == 0
+    assert np.all(np.abs(s.totals() - t0) / absq < 1e-14)
+    with pytest.raises(af.AFError, match="FP64"):
+        s.get_state()
+    s.set_option("limiter", 1)
+    with pytest.raises(af.AFError, match="limiters"):
+        s.step(1e-3)
+    s.close()
+
+
+def _run64(env, prob, opts):
+    s = solver64(env, prob, opts)
+    t = 0.0
+    while t < prob.t_end * (1 - 1e-12):
+        dt = min(prob.cfl * min(prob.dx, prob.dy) / s.max_speed(), prob.t_end - t)
+        s.step(dt)
+        t += dt
+    assert s.status() == 0
+    q = s.get_state_f64()[0].cpu().numpy()
+    s.close()
+    return q
+
+
+def _table64(env, make, ns, col, opts, per_row):
+    errs = []
+    for n in ns:
+        c, f = make(n, False), make(n, True)
+        e = np.abs(_run64(env, c, opts)[0] - restrict2(_run64(env, f, opts))[0])
+        errs.append(e.mean() * c.lx if per_row else e.mean() * c.lx * c.ly)
+    return errs
+
+
+def _check64(errs, tab, rows, col, rel, eoc_tol):
+    for k, r in enumerate(rows):
+        assert abs(errs[k] / tab[r, col] - 1) < rel, (r, errs[k], tab[r, col])
+        if k:
+            eoc = np.log2(errs[k - 1] / errs[k])
+            assert abs(eoc - tab[r, col + 1]) < eoc_tol, (r, eoc, tab[r, col + 1])
+
+
+@pytest.mark.parametrize("col,opts", [(1, {"lin_mode": 2, "correction": 1}), (3, {"lin_mode": 2, "correction": 0}),
+                                      (5, {"lin_mode": 1, "correction": 1})])
+def test_table1_to_1024_cells(env, col, opts):
+    """Example 1 (CFL 0.25; the paper's is unstated) in FP64: every row to
+    1024 cells, values within 12% and EOC within 0.15 of Table 1."""
+    tab = read_table(os.path.join(GOLDEN, "table1_ex1.txt"))
+    ns = [32, 64, 128, 256, 512, 1024]
+    make = lambda n, fine: W.gaussian_pulse(2 * n if fine else n, 16 if fine else 8, cfl=0.25)  # noqa: E731
+    errs = _table64(env, make, ns, col, opts, per_row=True)
+    _check64(errs, tab, range(6), col, 0.12, 0.15)
+
+
+def test_table2_to_512_cells(env):
+    """Example 2 (CFL 0.3) in FP64 with the correction, rows 256 and 512
+    (the 512 row is below the FP32 floor)."""
+    tab = read_table(os.path.join(GOLDEN, "table2_ex2.txt"))
+    make = lambda n, fine: W.compact_vortex(2 * n if fine else n)  # noqa: E731
+    errs = _table64(env, make, [256, 512], 1, {"lin_mode": 2, "correction": 1}, per_row=False)
+    _check64(errs, tab, [3, 4], 1, 0.12, 0.15)
