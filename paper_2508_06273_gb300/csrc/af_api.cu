@@ -182,6 +182,7 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   }
   h->dx = dx;
   h->dy = dy;
+  h->gamma = gamma;
   cudaGetDevice(&h->device);
   // hi, lo, 3 levels x 3 node kinds and 4 node-flux arrays: 15 arrays of 4 planes
   const size_t state_bytes = 15 * (size_t)NV * (size_t)g.plane * sizeof(float);
@@ -899,6 +900,9 @@ static int step64(af_ctx *h, double dt) {
   CK(launch_ghost_fill64(h->g, h->f64_avg, h->f64_lev[0], s), "FP64 ghost fill");
   Step64 S;
   S.g = h->g;
+  S.ph.gam = h->gamma;
+  S.ph.dx = h->dx;
+  S.ph.dy = h->dy;
   S.avg = h->f64_avg;
   for (int k = 0; k < 3; k++) {
     S.n0[k] = h->f64_lev[0][k];
@@ -1063,7 +1067,7 @@ int af_max_speed(af_ctx *h, float *out) {
   DeviceGuard dg(h->device);
   if (h->fp64) {
     const double *n[3] = {h->f64_lev[0][VTX], h->f64_lev[0][XE], h->f64_lev[0][YE]};
-    CK(launch_speed64(h->g, h->f64_avg, n, h->f64_speed, h->f64_bad, h->stream), "FP64 max speed");
+    CK(launch_speed64(h->g, h->gamma, h->f64_avg, n, h->f64_speed, h->f64_bad, h->stream), "FP64 max speed");
     unsigned long long bits = 0;
     int bad = 0;
     CK(cudaMemcpyAsync(&bits, h->f64_speed, sizeof(bits), cudaMemcpyDeviceToHost, h->stream), "speed");

@@ -13,7 +13,7 @@ using af::TileMaps;
 
 struct af_ctx {
   Grid g;
-  double dx, dy;
+  double dx, dy, gamma;  // as given to af_create
   Options opt;
   int device;
   cudaStream_t own_stream, stream;

@@ -76,9 +76,9 @@ __device__ __forceinline__ void to_monomial_d(const double f[3][3], double m[3][
 // record of cell (ci, cj): Q_c by Simpson's rule solved for the centre,
 // U_c = C2P(Q_c), Ubar (Simpson over the primitive point values, or C2P of the
 // average with ubar_c2p), and the biquadratic of each primitive variable
-__device__ void build_record(const Grid &g, const double *avg, const double *vtx, const double *xe,
+__device__ void build_record(const Grid &g, double gam, const double *avg, const double *vtx, const double *xe,
                              const double *ye, int ci, int cj, double *rec) {
-  const double gam = g.gamma, gm1 = gam - 1.0, gm1i = 1.0 / gm1;
+  const double gm1 = gam - 1.0, gm1i = 1.0 / gm1;
   double N[8][4];  // corners (ll, lr, ul, ur), then edges (left, right, bottom, top)
   ld4d(g, vtx, ci, cj, N[0]);
   ld4d(g, vtx, ci + 1, cj, N[1]);
@@ -240,14 +240,14 @@ __device__ __forceinline__ const double *rec_at(const Grid &g, const double *rec
 // {sin > b}; the sum over the cells' arcs is the circle term of the cell on
 // side -- plus the differences over X, Y and X and Y (inclusion-exclusion).
 template <int K>
-__device__ bool eg2_d(const Grid &g, const double *recs, int i, int j, const double Kr[4], const double ul[4],
-                      double tau, double out[4]) {
+__device__ bool eg2_d(const Grid &g, const Phys64 &ph, const double *recs, int i, int j, const double Kr[4],
+                      const double ul[4], double tau, double out[4]) {
   if (!(ul[0] > 0.0 && ul[3] > 0.0 && tau > 0.0)) {
     for (int v = 0; v < NV; v++) out[v] = nan("");
     return true;
   }
-  const double dx = g.dx, dy = g.dy, idx = 1.0 / dx, idy = 1.0 / dy;
-  const double cp2 = g.gamma * ul[3] / ul[0], cp = sqrt(cp2), icp = 1.0 / cp;
+  const double dx = ph.dx, dy = ph.dy, idx = 1.0 / dx, idy = 1.0 / dy;
+  const double cp2 = ph.gam * ul[3] / ul[0], cp = sqrt(cp2), icp = 1.0 / cp;
   const double R = cp * tau;
   bool inside;
   {
@@ -364,7 +364,7 @@ __device__ bool eg2_d(const Grid &g, const double *recs, int i, int j, const dou
 template <int K>
 __device__ void correction_d(const Grid &g, const Step64 &S, int i, int j, const double U[4], double T[4]) {
   double Ux[4], Uy[4];
-  const double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
+  const double idx = 1.0 / S.ph.dx, idy = 1.0 / S.ph.dy;
   for (int v = 0; v < NV; v++) {
     if (K == VTX) {
       Ux[v] = (S.n0[YE][at(g, v, i, j)] - S.n0[YE][at(g, v, i - 1, j)]) * idx;
@@ -377,7 +377,7 @@ __device__ void correction_d(const Grid &g, const Step64 &S, int i, int j, const
       Uy[v] = (rec_at(g, S.recs, i, j)[9 * v] - rec_at(g, S.recs, i, j - 1)[9 * v]) * idy;
     }
   }
-  const double r = U[0], u = U[1], v = U[2], p = U[3], gm = g.gamma, ir = 1.0 / r;
+  const double r = U[0], u = U[1], v = U[2], p = U[3], gm = S.ph.gam, ir = 1.0 / r;
   const double rx = Ux[0], ux = Ux[1], vx = Ux[2], px = Ux[3];
   const double ry = Uy[0], uy = Uy[1], vy = Uy[2], py = Uy[3];
   const double f1 = ux * ux + uy * vx, f2 = uy * vx + vy * vy;
@@ -427,7 +427,7 @@ __global__ void node64_kernel(Step64 S) {
     if (S.lin_mode == 1) {
       for (int v = 0; v < NV; v++) ul[v] = U0[v];
     } else if (S.lin_mode == 2) {
-      cfl_bad |= !eg2_d<K>(g, S.recs, i, j, U0, U0, 0.25 * S.dt, ul);
+      cfl_bad |= !eg2_d<K>(g, S.ph, S.recs, i, j, U0, U0, 0.25 * S.dt, ul);
     } else {
       const bool wx = (K != YE) && ((i == 0 && g.bc[0] == BC_REFLECTING) || (i == g.nx && g.bc[1] == BC_REFLECTING));
       const bool wy = (K != XE) && ((j == 0 && g.bc[2] == BC_REFLECTING) || (j == g.ny && g.bc[3] == BC_REFLECTING));
@@ -443,7 +443,7 @@ __global__ void node64_kernel(Step64 S) {
       const double tau = lev == 1 ? 0.5 * S.dt : S.dt;
       if (lev == 2)
         for (int v = 0; v < NV; v++) ul[v] = res[v];
-      cfl_bad |= !eg2_d<K>(g, S.recs, i, j, U0, ul, tau, res);
+      cfl_bad |= !eg2_d<K>(g, S.ph, S.recs, i, j, U0, ul, tau, res);
       for (int v = 0; v < NV; v++) {
         res[v] = fma(0.5 * tau * tau, T[v], res[v]);
         nonfinite |= !isfinite(res[v]);
@@ -462,7 +462,7 @@ __global__ void record64_kernel(Step64 S) {
   const long long n = (long long)w * h;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const int ci = (int)(e % w) - 1, cj = (int)(e / w) - 1;
-    build_record(g, S.avg, S.n0[VTX], S.n0[XE], S.n0[YE], ci, cj, S.recs + REC64 * cell_index(g, ci, cj));
+    build_record(g, S.ph.gam, S.avg, S.n0[VTX], S.n0[XE], S.n0[YE], ci, cj, S.recs + REC64 * cell_index(g, ci, cj));
   }
 }
 
@@ -478,6 +478,7 @@ __device__ __forceinline__ void phys_flux_d(const double U[4], double gm1i, int 
 }
 struct Flux64 {
   Grid g;
+  Phys64 ph;
   const double *n[3][3];  // [level][kind]
   double *avg;
   double lx, ly;  // dt/dx, dt/dy
@@ -488,7 +489,7 @@ struct Flux64 {
 // 1/36; both cells sharing the face call this with the same arguments
 __device__ void face_flux(const Flux64 &A, int dir, int i, int j, double F[4]) {
   const Grid &g = A.g;
-  const double gm1i = 1.0 / (g.gamma - 1.0);
+  const double gm1i = 1.0 / (A.ph.gam - 1.0);
   for (int v = 0; v < NV; v++) F[v] = 0.0;
   for (int s = 0; s < 3; s++) {
     const int kind = s == 1 ? (dir == 0 ? XE : YE) : VTX;
@@ -521,7 +522,7 @@ __global__ void flux64_kernel(Flux64 A) {
       A.avg[k] = Q[v];
     }
     double U[4];
-    c2p_d(Q, g.gamma - 1.0, U);
+    c2p_d(Q, A.ph.gam - 1.0, U);
     const bool finite = isfinite(Q[0]) && isfinite(Q[1]) && isfinite(Q[2]) && isfinite(Q[3]);
     const int st = !finite ? ST_NONFINITE : ((U[0] > 0.0 && U[3] > 0.0) ? 0 : ST_AVG_NONPOS);
     if (st) atomicOr(A.status, st);
@@ -531,7 +532,7 @@ __global__ void flux64_kernel(Flux64 A) {
 // max over the averages and the owned point values of max(|u|, |v|) + c, as
 // the bits of a positive double (which order like the values); bad set if a
 // value is not admissible
-__global__ void speed64_kernel(Grid g, const double *avg, const double *vtx, const double *xe, const double *ye,
+__global__ void speed64_kernel(Grid g, double gam, const double *avg, const double *vtx, const double *xe, const double *ye,
                                unsigned long long *out, int *bad) {
   const long long nc = (long long)g.nx * g.ny, nv = (long long)g.nxv * g.nyv;
   const long long nxe = (long long)g.nxv * g.ny, nye = (long long)g.nx * g.nyv;
@@ -545,7 +546,7 @@ __global__ void speed64_kernel(Grid g, const double *avg, const double *vtx, con
     if (r < nc) {
       double Q[4];
       ld4d(g, avg, (int)(r % g.nx), (int)(r / g.nx), Q);
-      c2p_d(Q, g.gamma - 1.0, U);
+      c2p_d(Q, gam - 1.0, U);
     } else {
       const double *p;
       int ni;
@@ -566,7 +567,7 @@ __global__ void speed64_kernel(Grid g, const double *avg, const double *vtx, con
       b = true;
       continue;
     }
-    m = fmax(m, fmax(fabs(U[1]), fabs(U[2])) + sqrt(g.gamma * U[3] / U[0]));
+    m = fmax(m, fmax(fabs(U[1]), fabs(U[2])) + sqrt(gam * U[3] / U[0]));
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   b = __any_sync(0xffffffffu, b);
@@ -629,6 +630,7 @@ cudaError_t launch_step64(const Step64 &S, double lamx, double lamy, cudaStream_
   node64_kernel<YE><<<blocks_for((long long)g.nx * g.nyv), 256, 0, s>>>(S);
   Flux64 F;
   F.g = g;
+  F.ph = S.ph;
   for (int k = 0; k < 3; k++) {
     F.n[0][k] = S.n0[k];
     F.n[1][k] = S.n1[k];
@@ -642,11 +644,11 @@ cudaError_t launch_step64(const Step64 &S, double lamx, double lamy, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_speed64(const Grid &g, const double *avg, const double *const n[3], unsigned long long *out,
-                           int *bad, cudaStream_t s) {
+cudaError_t launch_speed64(const Grid &g, double gam, const double *avg, const double *const n[3],
+                           unsigned long long *out, int *bad, cudaStream_t s) {
   cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
   cudaMemsetAsync(bad, 0, sizeof(int), s);
-  speed64_kernel<<<1024, 256, 0, s>>>(g, avg, n[VTX], n[XE], n[YE], out, bad);
+  speed64_kernel<<<1024, 256, 0, s>>>(g, gam, avg, n[VTX], n[XE], n[YE], out, bad);
   return cudaGetLastError();
 }
 

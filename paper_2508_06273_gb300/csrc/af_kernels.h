@@ -262,8 +262,13 @@ int *gemm_default_err();
 
 // ---- FP64 path (af_fp64.cu): the step in double precision, without the
 // Sec. 3 limiters (accuracy studies below the FP32 floor)
+// gamma and the cell sizes in double (the grid description holds FP32 copies)
+struct Phys64 {
+  double gam, dx, dy;
+};
 struct Step64 {
   Grid g;
+  Phys64 ph;
   const double *avg;      // t^n averages (updated in place to t^{n+1})
   const double *n0[3];    // t^n point values (ghost layers filled)
   double *n1[3], *n2[3];  // t^{n+1/2} and t^{n+1} point values
@@ -274,8 +279,8 @@ struct Step64 {
 };
 constexpr int REC64_DOUBLES = 40;
 cudaError_t launch_step64(const Step64 &S, double lamx, double lamy, cudaStream_t s);
-cudaError_t launch_speed64(const Grid &g, const double *avg, const double *const n[3], unsigned long long *out,
-                           int *bad, cudaStream_t s);
+cudaError_t launch_speed64(const Grid &g, double gam, const double *avg, const double *const n[3],
+                           unsigned long long *out, int *bad, cudaStream_t s);
 cudaError_t launch_totals64(const Grid &g, const double *avg, double *partials, double area, double *out,
                             cudaStream_t s);
 constexpr int TOTALS64_PARTIALS = 128 * 4;
