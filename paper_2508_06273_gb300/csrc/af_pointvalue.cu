@@ -809,6 +809,15 @@ __device__ __forceinline__ void st4_node(float *p, const Grid &g, int i, int j, 
   if (dx_ && dy_) st4(p, g, g.nx, g.ny, U);
 }
 
+// Instantiations of the node update: PV_FULL takes every option (Alg. 1
+// linearisation, Alg. 2, the Sec. 3.4 blend, node bounds, masks, the test
+// hooks); PV_NF is PV_FULL that also writes node fluxes; PV_LEAN has only
+// what the plain method with the Alg. 3 limiter needs (linearisation about
+// the averages or the node value, the correction), so that its code and
+// register allocation carry none of the rest.  The host picks PV_LEAN
+// whenever the options allow it.
+enum { PV_LEAN = 0, PV_FULL = 1, PV_NF = 2 };
+
 // Simpson in time of eq. (F) at a node, for the flux kernel, once both levels
 // are known: f(U^n) + 4 f(U^{n+1/2}) + f(U^{n+1}) (f for vertices and x-edges,
 // g for vertices and y-edges; U^{n+1/2} kept in the thread's scratch, slots
@@ -838,14 +847,15 @@ __device__ __forceinline__ void node_flux(const Args &A, int i, int j, const flo
 }
 
 // both time levels of node (K, i, j), tile-local (li, lj)
-template <int K, int TY, bool NF>
+template <int K, int TY, int FT>
 __device__ __forceinline__ void node_update(const Args &A, const float *sm, const float *raw, int i0, int j0,
                                             int i, int j, int li, int lj, unsigned cnt[4], bool &cfl_bad,
                                             bool &nonfinite, float *scr) {
+  constexpr bool NF = FT == PV_NF, FULL = FT != PV_LEAN;
   const Grid &g = A.g;
   const int ni = (K == YE) ? g.nx : g.nxv, nj = (K == XE) ? g.ny : g.nyv;
   if (i >= ni || j >= nj) return;
-  if (A.mask[K] && !A.mask[K][(long long)(j + OY) * g.P + (i + OX)]) return;
+  if (FULL && A.mask[K] && !A.mask[K][(long long)(j + OY) * g.P + (i + OX)]) return;
   float U0[4], T[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   raw4<TY>(raw, K == VTX ? RAW_VTX : (K == XE ? RAW_XE : RAW_YE), i, j, i0, j0, U0);
   if (A.correction) correction<K, TY>(g, sm, raw, i, j, i0, j0, U0, T);
@@ -855,7 +865,7 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
   if (A.lin_mode == 1) {
 #pragma unroll
     for (int v = 0; v < NV; v++) ul[v] = U0[v];
-  } else if (A.lin_mode == 2) {
+  } else if (FULL && A.lin_mode == 2) {
     cfl_bad |= !eg2<K>(g, sm, li, lj, U0, U0, 0.25f * A.dt, ul);
   } else {
     const bool wx = (K != YE) && ((i == 0 && g.bc[0] == BC_REFLECTING) || (i == g.nx && g.bc[1] == BC_REFLECTING));
@@ -871,7 +881,7 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
   }
   // Sec. 3.4 blend weight (the same for both levels; from the t^n averages)
   float th = 1.0f;
-  if (A.theta[0]) {
+  if (FULL && A.theta[0]) {
     if (K == XE) th = __ldg(A.theta[0] + at(g, 0, i, j));
     else if (K == YE) th = __ldg(A.theta[1] + at(g, 0, i, j));
     else
@@ -879,7 +889,7 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
                  fminf(__ldg(A.theta[1] + at(g, 0, i, j)), __ldg(A.theta[1] + at(g, 0, i - 1, j))));
   }
   bool sw = false;
-  if (A.tsw) {
+  if (FULL && A.tsw) {
     const int a = li + 1, b = lj + 1;
     if (K == VTX) sw = tsw_vertex(sm, g.gamma, a, b);
     else if (K == XE) sw = tsw_vertex(sm, g.gamma, a, b) || tsw_vertex(sm, g.gamma, a, b + 1);
@@ -891,7 +901,7 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
   for (int lev = 1; lev <= 2; lev++) {
     const float tau = lev == 1 ? 0.5f * A.dt : A.dt;
     if (lev == 2) {
-      if (sw) {
+      if (FULL && sw) {
         lin_avg<K>(sm, li, lj, ul);
       } else {
 #pragma unroll
@@ -907,14 +917,14 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
     // Alg. 3 (a value from a Mach cone outside the block counts as not
     // admissible, and, with the option, one outside the node's bounds)
     bool ok = inb && admissible(ho);
-    if (ok && A.node_bounds) ok = in_node_bounds<K>(sm, li, lj, pack4(U0), pack4(ho));
-    if (A.force_lo || (A.limiter && !ok)) {
+    if (FULL && ok && A.node_bounds) ok = in_node_bounds<K>(sm, li, lj, pack4(U0), pack4(ho));
+    if ((FULL && A.force_lo) || (A.limiter && !ok)) {
       unpack4(limit<K>(A, sm, i, j, li, lj, tau, pack4(U0)), res);
     } else {
 #pragma unroll
       for (int v = 0; v < NV; v++) res[v] = ho[v];
     }
-    if (1.0f - th >= 1e-6f) {
+    if (FULL && 1.0f - th >= 1e-6f) {
       // blend with the low-order value of Alg. 3's chain (EG1 on pc data,
       // else Lax-Friedrichs, else the t^n value): both ends admissible
       float lo[4];
@@ -934,14 +944,22 @@ __device__ __forceinline__ void node_update(const Args &A, const float *sm, cons
 }
 
 // prologue: the block builds the records of its (TX+2) x (TY+2) cells; only
-// cells -1..nx, -1..ny can be referenced by owned nodes, the others are skipped
+// cells -1..nx, -1..ny can be referenced by owned nodes, the others are
+// skipped.  The last column and row of the halo (cells i0 + TX, j0 + TY) are
+// read only by Alg. 2's indicator at the tile's last edge nodes: without
+// Alg. 2 they are not built (297 instead of 340 records at TY = 8).
+template <int TY, int W, int H>
+__device__ __forceinline__ void build_records(const Args &A, const float *raw, float *sm, int i0, int j0, int tid) {
+  for (int k = tid; k < W * H; k += TX * TY) {
+    const int a = k % W, b = k / W, ci = i0 - 1 + a, cj = j0 - 1 + b;
+    if (ci <= A.g.nx && cj <= A.g.ny) build_cell<TY>(A.g, raw, i0, j0, ci, cj, sm + (b * HX + a) * CELL_F);
+  }
+}
 template <int TY>
 __device__ __forceinline__ void tile_prologue(const Args &A, const float *raw, float *sm, int i0, int j0,
                                               int tid) {
-  for (int k = tid; k < HX * Tile<TY>::HY; k += TX * TY) {
-    const int a = k % HX, b = k / HX, ci = i0 - 1 + a, cj = j0 - 1 + b;
-    if (ci <= A.g.nx && cj <= A.g.ny) build_cell<TY>(A.g, raw, i0, j0, ci, cj, sm + k * CELL_F);
-  }
+  if (A.tsw) build_records<TY, HX, Tile<TY>::HY>(A, raw, sm, i0, j0, tid);
+  else build_records<TY, HX - 1, Tile<TY>::HY - 1>(A, raw, sm, i0, j0, tid);
 }
 
 // the block's maximum wave speed of the new point values (node-flux
@@ -976,17 +994,18 @@ __device__ __forceinline__ void block_speed(const Args &A, const float *scr, int
 
 // node updates of the cell (i0 + tx, j0 + ty); NF: the instantiation that
 // writes node fluxes (separate, so that the plain kernel carries none of it)
-template <int TY, bool NF>
+template <int TY, int FT>
 __device__ __forceinline__ void tile_nodes(const Args &A, const float *sm, const float *raw, int i0, int j0,
                                            int tx, int ty, float *scr) {
+  constexpr bool NF = FT == PV_NF;
   unsigned cnt[4] = {0, 0, 0, 0};
   bool cfl_bad = false, nonfinite = false;
   const int i = i0 + tx, j = j0 + ty;
   constexpr int NT = TX * TY;
   if (NF) scr[4 * NT] = 0.0f;
-  node_update<VTX, TY, NF>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
-  node_update<XE, TY, NF>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
-  node_update<YE, TY, NF>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
+  node_update<VTX, TY, FT>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
+  node_update<XE, TY, FT>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
+  node_update<YE, TY, FT>(A, sm, raw, i0, j0, i, j, tx, ty, cnt, cfl_bad, nonfinite, scr);
   if (NF) block_speed<TY>(A, scr, ty * TX + tx);
   // (the limiter reports its own kept values and Lax-Friedrichs fall-backs)
   const int st = (cfl_bad ? ST_CFL : 0) | (nonfinite ? ST_NONFINITE : 0);
@@ -1041,7 +1060,7 @@ __device__ __forceinline__ bool tile_wait(unsigned long long *bar, unsigned limi
 }
 
 // one tile: stage the t^n box, build the cell records, update the nodes
-template <int TY, bool NF>
+template <int TY, int FT>
 __device__ __forceinline__ void tile_body(const Args &A, const TileMaps &T, float *raw, unsigned long long *bar,
                                           int i0, int j0) {
   float *sm = raw + Tile<TY>::RAW_FLOATS;
@@ -1064,7 +1083,7 @@ __device__ __forceinline__ void tile_body(const Args &A, const TileMaps &T, floa
   }
   tile_prologue<TY>(A, raw, sm, i0, j0, tid);
   __syncthreads();
-  tile_nodes<TY, NF>(A, sm, raw, i0, j0, threadIdx.x, threadIdx.y, sm + Tile<TY>::REC_FLOATS + tid);
+  tile_nodes<TY, FT>(A, sm, raw, i0, j0, threadIdx.x, threadIdx.y, sm + Tile<TY>::REC_FLOATS + tid);
 }
 
 // TMA destinations must start on 128-byte boundaries
@@ -1100,13 +1119,13 @@ __device__ __forceinline__ void tile_prefetch_l2(const TileMaps &T) {
                  : "memory");
 }
 
-template <int TY, bool NF>
+template <int TY, int FT>
 __global__ void __launch_bounds__(TX *TY, min_blocks<TY>()) pointvalue_kernel(Args A, const __grid_constant__ TileMaps T) {
   extern __shared__ float4 smem4[];
   __shared__ alignas(8) unsigned long long bar;
-  if (A.tile_flag && !A.tile_flag[blockIdx.y * gridDim.x + blockIdx.x]) return;
+  if (FT != PV_LEAN && A.tile_flag && !A.tile_flag[blockIdx.y * gridDim.x + blockIdx.x]) return;
   if (threadIdx.x == 0 && threadIdx.y == 0) tile_prefetch_l2<TY>(T);
-  tile_body<TY, NF>(A, T, tile_smem(smem4), &bar, blockIdx.x * TX, blockIdx.y * TY);
+  tile_body<TY, FT>(A, T, tile_smem(smem4), &bar, blockIdx.x * TX, blockIdx.y * TY);
 }
 
 // Batched form: block b takes tile B.tiles[b] = (instance, i0, j0) and the
@@ -1123,7 +1142,7 @@ __global__ void __launch_bounds__(TX *TY, min_blocks<TY>()) pointvalue_batch_ker
   // read-only, so the compiler may load a field again where a copy in shared
   // memory held it in a register (half the spills)
   const Args *__restrict__ A = B.args + 2 * t.x + c.cur;
-  tile_body<TY, false>(*A, B.maps[2 * t.x + c.cur], tile_smem(smem4), &bar, t.y, t.z);
+  tile_body<TY, PV_FULL>(*A, B.maps[2 * t.x + c.cur], tile_smem(smem4), &bar, t.y, t.z);
 }
 
 }  // namespace
@@ -1164,12 +1183,15 @@ cudaError_t prepare_pointvalue() {
   auto attr = [&](const void *f, int bytes) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   };
-  attr((const void *)pointvalue_kernel<4, false>, Tile<4>::SMEM_BYTES);
-  attr((const void *)pointvalue_kernel<8, false>, Tile<8>::SMEM_BYTES);
-  attr((const void *)pointvalue_kernel<16, false>, Tile<16>::SMEM_BYTES);
-  attr((const void *)pointvalue_kernel<4, true>, Tile<4>::SMEM_NF_BYTES);
-  attr((const void *)pointvalue_kernel<8, true>, Tile<8>::SMEM_NF_BYTES);
-  attr((const void *)pointvalue_kernel<16, true>, Tile<16>::SMEM_NF_BYTES);
+  attr((const void *)pointvalue_kernel<4, PV_LEAN>, Tile<4>::SMEM_BYTES);
+  attr((const void *)pointvalue_kernel<8, PV_LEAN>, Tile<8>::SMEM_BYTES);
+  attr((const void *)pointvalue_kernel<16, PV_LEAN>, Tile<16>::SMEM_BYTES);
+  attr((const void *)pointvalue_kernel<4, PV_FULL>, Tile<4>::SMEM_BYTES);
+  attr((const void *)pointvalue_kernel<8, PV_FULL>, Tile<8>::SMEM_BYTES);
+  attr((const void *)pointvalue_kernel<16, PV_FULL>, Tile<16>::SMEM_BYTES);
+  attr((const void *)pointvalue_kernel<4, PV_NF>, Tile<4>::SMEM_NF_BYTES);
+  attr((const void *)pointvalue_kernel<8, PV_NF>, Tile<8>::SMEM_NF_BYTES);
+  attr((const void *)pointvalue_kernel<16, PV_NF>, Tile<16>::SMEM_NF_BYTES);
   attr((const void *)pointvalue_batch_kernel<4>, Tile<4>::SMEM_BYTES);
   attr((const void *)pointvalue_batch_kernel<8>, Tile<8>::SMEM_BYTES);
   attr((const void *)pointvalue_batch_kernel<16>, Tile<16>::SMEM_BYTES);
@@ -1178,13 +1200,17 @@ cudaError_t prepare_pointvalue() {
 
 // tiles cover the owned nodes: up to nxv x nyv (vertex lines n + 1 on a
 // non-periodic axis); every box x coordinate is a multiple of TX floats; the
-// node-flux instantiation (with its scratch) only when node fluxes are written
+// node-flux instantiation (with its scratch) only when node fluxes are
+// written, the lean one whenever no option it leaves out is set
 template <int TY>
 static void launch_h(const Args &A, const TileMaps &maps, cudaStream_t s) {
   const Grid &g = A.g;
   const dim3 grd((g.nxv + TX - 1) / TX, (g.nyv + TY - 1) / TY), blk(TX, TY);
-  if (A.nflux[0]) pointvalue_kernel<TY, true><<<grd, blk, Tile<TY>::SMEM_NF_BYTES, s>>>(A, maps);
-  else pointvalue_kernel<TY, false><<<grd, blk, Tile<TY>::SMEM_BYTES, s>>>(A, maps);
+  const bool lean = !A.tsw && !A.theta[0] && !A.node_bounds && !A.force_lo && A.lin_mode != 2 && !A.mask[0] &&
+                    !A.mask[1] && !A.mask[2] && !A.tile_flag;
+  if (A.nflux[0]) pointvalue_kernel<TY, PV_NF><<<grd, blk, Tile<TY>::SMEM_NF_BYTES, s>>>(A, maps);
+  else if (lean) pointvalue_kernel<TY, PV_LEAN><<<grd, blk, Tile<TY>::SMEM_BYTES, s>>>(A, maps);
+  else pointvalue_kernel<TY, PV_FULL><<<grd, blk, Tile<TY>::SMEM_BYTES, s>>>(A, maps);
 }
 static cudaError_t launch_single(const Args &A, const TileMaps &maps, int tile_h, cudaStream_t s) {
   switch (tile_h) {
