@@ -214,21 +214,44 @@ def init_params(seed=0):
     return P
 
 
-def forward(P, X):
-    """Outputs (n, 16) and the cache of pre-activations and activations."""
+def bf16_round(a):
+    """Nearest BF16 value (ties to even) of each element, via its FP32 value:
+    the upper 16 bits of the FP32 word after adding half a BF16 unit (0x7FFF)
+    plus the lowest kept bit, the usual round-to-nearest-even on the bits.
+    Returned in FP64."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _keep(a):
+    return a
+
+
+def forward(P, X, rnd=None):
+    """Outputs (n, 16) and the cache of pre-activations and activations.
+    rnd (optional) rounds each hidden activation where a reduced-precision
+    implementation stores it (e.g. bf16_round); the products stay exact."""
+    r = rnd or _keep
     H = [np.asarray(X, dtype=np.float64)]
     Z = []
     for k, (w, b, _, _) in enumerate(LAYERS):
         z = H[-1] @ P[w].T + P[b]
         Z.append(z)
-        H.append(gelu(z) if k < 3 else z)
+        H.append(r(gelu(z)) if k < 3 else z)
     return H[-1], (H, Z)
 
 
-def loss_and_grads(P, X, T):
+def loss_and_grads(P, X, T, rnd=None):
     """Mean squared error over the first 8 outputs and every row, and its
-    gradient with respect to every parameter (reverse-mode, layer by layer)."""
-    Y, (H, Z) = forward(P, X)
+    gradient with respect to every parameter (reverse-mode, layer by layer).
+    rnd (optional) rounds the hidden activations (as in forward) and the
+    operands of the backward products, dY and each dZ, where a
+    reduced-precision implementation stores them; the bias gradients are
+    the sums of the unrounded values."""
+    r = rnd or _keep
+    Y, (H, Z) = forward(P, X, rnd)
     n = X.shape[0]
     R = Y[:, :NOUT] - T
     loss = float(np.mean(R * R))
@@ -238,8 +261,9 @@ def loss_and_grads(P, X, T):
     d = dY
     for k in range(3, -1, -1):
         w, b, _, _ = LAYERS[k]
-        grads[w] = d.T @ H[k]
         grads[b] = d.sum(axis=0)
+        d = r(d)
+        grads[w] = d.T @ H[k]
         if k > 0:
             d = (d @ P[w]) * gelu_grad(Z[k - 1])
     grads["W4"][NOUT:] = 0.0

@@ -778,7 +778,10 @@ static int enqueue_step(af_ctx *h, double dt) {
     collect_stages(h);
     cudaEventRecord(h->ev_stage[0], s);
   }
-  CK(launch_ghost_fill(h->g, h->hi, h->lo, h->lev[0], s), "ghost fill");
+  {
+    NvtxScope st("ghost fill");
+    CK(launch_ghost_fill(h->g, h->hi, h->lo, h->lev[0], s), "ghost fill");
+  }
   h->launches[AF_STAGE_PREP] += 1;
   CK(cudaMemsetAsync(h->d_counters, 0, 4 * sizeof(unsigned long long), s), "memset counters");
   const float *theta[2] = {nullptr, nullptr};
@@ -789,72 +792,76 @@ static int enqueue_step(af_ctx *h, double dt) {
        "shock indicator");
   }
   if (prof) cudaEventRecord(h->ev_stage[1], s);
-  if (h->opt.surrogate) {
-    // network at every node, then the exact operator at the nodes it rejected
-    CK(cudaMemsetAsync(h->surr_tiles, 0, sizeof(int) * h->surr_tiles_x * ((h->g.nyv + h->tile_h - 1) / h->tile_h), s),
-       "memset tiles");
-    CK(launch_ubar(h->g, h->hi, h->lev[0], h->surr_ubar, s), "surrogate cell prep");
-    const unsigned char *mask[3];
-    for (int k = 0; k < 3; k++) {
-      SurrogateArgs A;
-      A.g = h->g;
-      for (int q = 0; q < 3; q++) {
-        A.n0[q] = h->lev[0].k[q];
-        A.n1[q] = h->lev[1].k[q];
-        A.n2[q] = h->lev[2].k[q];
+  {
+    NvtxScope pvr("point values");
+    if (h->opt.surrogate) {
+      // network at every node, then the exact operator at the nodes it rejected
+      CK(cudaMemsetAsync(h->surr_tiles, 0, sizeof(int) * h->surr_tiles_x * ((h->g.nyv + h->tile_h - 1) / h->tile_h), s),
+         "memset tiles");
+      CK(launch_ubar(h->g, h->hi, h->lev[0], h->surr_ubar, s), "surrogate cell prep");
+      const unsigned char *mask[3];
+      for (int k = 0; k < 3; k++) {
+        SurrogateArgs A;
+        A.g = h->g;
+        for (int q = 0; q < 3; q++) {
+          A.n0[q] = h->lev[0].k[q];
+          A.n1[q] = h->lev[1].k[q];
+          A.n2[q] = h->lev[2].k[q];
+        }
+        A.hi = h->hi;
+        A.ubar = h->surr_ubar;
+        A.dt = (float)dt;
+        A.tol = h->opt.surr_tol;
+        A.tol_abs = h->opt.surr_abs;
+        af_mlp *net = h->surr[k == VTX ? 0 : 1];
+        A.wb = net->wb;
+        A.params = net->params;
+        A.mask = h->surr_mask + (size_t)k * h->g.plane;
+        mask[k] = A.mask;
+        A.tile_flag = h->surr_tiles;
+        A.tiles_x = h->surr_tiles_x;
+        A.tile_rows = h->tile_h;
+        A.stats = h->surr_stats;
+        A.status = h->d_status;
+        A.test_no_issue = h->opt.test_timeout != 0;
+        A.wait_limit = h->opt.test_timeout ? kTestWaitLimit : kWaitLimit;
+        CK(launch_surrogate(k, A, h->sms, s), "surrogate");
       }
-      A.hi = h->hi;
-      A.ubar = h->surr_ubar;
-      A.dt = (float)dt;
-      A.tol = h->opt.surr_tol;
-      A.tol_abs = h->opt.surr_abs;
-      af_mlp *net = h->surr[k == VTX ? 0 : 1];
-      A.wb = net->wb;
-      A.params = net->params;
-      A.mask = h->surr_mask + (size_t)k * h->g.plane;
-      mask[k] = A.mask;
-      A.tile_flag = h->surr_tiles;
-      A.tiles_x = h->surr_tiles_x;
-      A.tile_rows = h->tile_h;
-      A.stats = h->surr_stats;
-      A.status = h->d_status;
-      A.test_no_issue = h->opt.test_timeout != 0;
-      A.wait_limit = h->opt.test_timeout ? kTestWaitLimit : kWaitLimit;
-      CK(launch_surrogate(k, A, h->sms, s), "surrogate");
+      CK(launch_pointvalue_masked(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
+                                  h->opt, h->d_status, h->d_counters, mask, h->surr_tiles, theta, h->tile_h, s),
+         "point values (fallback)");
+      h->launches[AF_STAGE_POINTVALUE] += 5;
+      h->half_valid = true;
+    } else if (!h->opt.node_flux) {
+      // plain path: t^{n+1/2} and t^{n+1} written, the flux kernel forms the
+      // node fluxes from three levels
+      CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
+                           h->opt, h->d_status, h->d_counters, theta, h->tile_h, nullptr, s),
+         "point values");
+      h->launches[AF_STAGE_POINTVALUE] += 1;
+      h->half_valid = true;
+    } else {
+      // node-flux path: the point-value kernel writes the node fluxes (and
+      // folds the new point values into the wave speed) for the flux kernel
+      NodeFluxOut nf;
+      for (int q = 0; q < 4; q++) nf.q[q] = h->nflux[q];
+      nf.speed = h->d_speed;
+      nf.speed_bad = h->d_speed_bad;
+      nf.write_half = h->keep_half;
+      CK(cudaMemsetAsync(h->d_speed, 0, sizeof(unsigned), s), "memset speed");
+      CK(cudaMemsetAsync(h->d_speed_bad, 0, sizeof(int), s), "memset speed");
+      CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
+                           h->opt, h->d_status, h->d_counters, theta, h->tile_h, &nf, s),
+         "point values");
+      h->launches[AF_STAGE_POINTVALUE] += 1;
+      h->half_valid = h->keep_half != 0;
     }
-    CK(launch_pointvalue_masked(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
-                                h->opt, h->d_status, h->d_counters, mask, h->surr_tiles, theta, h->tile_h, s),
-       "point values (fallback)");
-    h->launches[AF_STAGE_POINTVALUE] += 5;
-    h->half_valid = true;
-  } else if (!h->opt.node_flux) {
-    // plain path: t^{n+1/2} and t^{n+1} written, the flux kernel forms the
-    // node fluxes from three levels
-    CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
-                         h->opt, h->d_status, h->d_counters, theta, h->tile_h, nullptr, s),
-       "point values");
-    h->launches[AF_STAGE_POINTVALUE] += 1;
-    h->half_valid = true;
-  } else {
-    // node-flux path: the point-value kernel writes the node fluxes (and
-    // folds the new point values into the wave speed) for the flux kernel
-    NodeFluxOut nf;
-    for (int q = 0; q < 4; q++) nf.q[q] = h->nflux[q];
-    nf.speed = h->d_speed;
-    nf.speed_bad = h->d_speed_bad;
-    nf.write_half = h->keep_half;
-    CK(cudaMemsetAsync(h->d_speed, 0, sizeof(unsigned), s), "memset speed");
-    CK(cudaMemsetAsync(h->d_speed_bad, 0, sizeof(int), s), "memset speed");
-    CK(launch_pointvalue(h->g, h->lev[0], h->hi, h->tmaps[h->tmap_cur], h->lev[1], h->lev[2], (float)dt,
-                         h->opt, h->d_status, h->d_counters, theta, h->tile_h, &nf, s),
-       "point values");
-    h->launches[AF_STAGE_POINTVALUE] += 1;
-    h->half_valid = h->keep_half != 0;
   }
   if (prof) {
     cudaEventRecord(h->ev_stage[2], s);
     cudaEventRecord(h->ev_stage[3], s);
   }
+  NvtxScope fl("flux update");
   // the limiter reads t^n averages while the kernel overwrites them: snapshot
   if (h->opt.flux_limiter)
     CK(cudaMemcpyAsync(h->q0, h->hi, sizeof(float) * NV * (size_t)h->g.plane, cudaMemcpyDeviceToDevice, s),
@@ -924,6 +931,7 @@ int af_step(af_ctx *h, double dt) {
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(AF_ERR_ARG, "af_step: dt must be positive%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
   if (h->timed_out) return fail(AF_ERR_STATE, kTimedOut);
+  NvtxScope range("af_step");
   if (h->fp64) {
     DeviceGuard dg(h->device);
     return step64(h, dt);
@@ -977,6 +985,7 @@ int af_run(af_ctx *h, int nsteps, double dt) {
   if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(AF_ERR_ARG, "af_run: bad arguments%s");
   if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
   if (h->timed_out) return fail(AF_ERR_STATE, kTimedOut);
+  NvtxScope range("af_run");
   DeviceGuard dg(h->device);
   if (h->fp64) {
     for (int k = 0; k < nsteps; k++) {
@@ -994,6 +1003,7 @@ int af_run(af_ctx *h, int nsteps, double dt) {
   }
   const int p = h->tmap_cur;
   if (!h->run_exec[p] || h->run_dt[p] != dt || !same_options(h->run_opt[p], h->opt)) {
+    NvtxScope cap("af_run/capture");
     int rc = capture_pair(h, dt);
     if (rc) return rc;
   }

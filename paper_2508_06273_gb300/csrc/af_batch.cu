@@ -520,6 +520,7 @@ int af_batch_run(af_batch *b, int nsteps, double *hist, int hist_steps) {
     return bfail(AF_ERR_STATE, "af_batch_run: a wait for staged data timed out (AF_ST_TIMEOUT): the states are "
                                "invalid and the batch takes no further steps");
   if (nsteps == 0) return AF_OK;
+  NvtxScope range("af_batch_run");
   Dev d(b->device);
   int rc = build_tiles(b);
   if (rc) return rc;

@@ -2,6 +2,7 @@
 // the batch of af_batch.cu holds one per instance).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "af_common.cuh"
 #include "af_kernels.h"
@@ -10,6 +11,16 @@ using af::Grid;
 using af::NodeSet;
 using af::Options;
 using af::TileMaps;
+
+// NVTX range over a scope of a host call (a no-op unless a tool that reads
+// NVTX is attached, e.g. ncu --nvtx with --nvtx-include): names the library
+// call and, inside a step, the stage whose kernels it enqueues
+struct NvtxScope {
+  explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope &) = delete;
+  NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 struct af_ctx {
   Grid g;

@@ -103,3 +103,38 @@ def test_zero_change_has_zero_targets():
     ut = rng.uniform(0.5, 1.5, size=(6, 4))
     s = rng.uniform(0.5, 1.5, size=(6, 4))
     assert np.all(S.targets(U0, U0, U0, ut, s, S.VERTEX) == 0)
+
+
+def test_bf16_rounding_of_the_reference():
+    """bf16_round: ties go to the even BF16 value, other values to the
+    nearest; the result agrees with torch's BF16 conversion element by element
+    and leaves values already in BF16 alone."""
+    one = np.float32(1.0)
+    ulp = np.float32(2.0 ** -7)  # BF16 unit at 1
+    cases = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -8 + 2.0 ** -20, -1.0 - 2.0 ** -8,
+                      3.0, 0.0], dtype=np.float32)
+    want = np.array([1.0, 1.0, 1.0 + 2 * ulp, 1.0 + ulp, -1.0, 3.0, 0.0])
+    assert np.array_equal(S.bf16_round(cases), want)
+    assert one + ulp == np.float32(1.0078125)
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(3).normal(scale=10.0, size=4096).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).double().numpy()
+    assert np.array_equal(S.bf16_round(x), ref)
+    assert np.array_equal(S.bf16_round(ref), ref)
+
+
+def test_rounded_gradients_reduce_to_the_exact_ones():
+    """With rounding switched on but an identity in its place the gradients
+    are the exact ones; with BF16 rounding they stay within a few BF16 units."""
+    rng = np.random.default_rng(9)
+    P = S.init_params(4)
+    X = rng.normal(size=(16, S.NIN))
+    T = rng.normal(size=(16, S.NOUT))
+    l0, g0 = S.loss_and_grads(P, X, T)
+    l1, g1 = S.loss_and_grads(P, X, T, rnd=lambda a: a)
+    assert l0 == l1 and all(np.array_equal(g0[k], g1[k]) for k in g0)
+    _, g2 = S.loss_and_grads(P, X, T, rnd=S.bf16_round)
+    for k in g0:
+        n = np.linalg.norm(g0[k])
+        if n > 0:
+            assert np.linalg.norm(g2[k] - g0[k]) / n < 3e-2, k
