@@ -55,9 +55,9 @@ FLUX_BYTES_PER_CELL = 208
 # otherwise reported as null
 _KSRC = "paper_2508_06273_gb300/csrc/"
 _SHARED = {_KSRC + "af_common.cuh": "49af0eb9318155a23c020300f00bfd3f9cd68738d61f011d7b9bf66f74e1cd97"}
-PV_TRAFFIC = {"bytes_per_cell": 151.0, "profile": "profiles/dram_pointvalue_flux_vortex2048.md",
+PV_TRAFFIC = {"bytes_per_cell": 150.9, "profile": "profiles/dram_pointvalue_flux_vortex2048.md",
               "sha256": dict(_SHARED, **{_KSRC + "af_pointvalue.cu":
-                                         "bac612b803f5017aa254577cf6a20d4dc7593d6e7556bde0a60839add1adf32d"})}
+                                         "fa12b6eaef2aca48a5fd03ec42a8f60dc469bde6fb49fcda0e72c6bb2ef3a0b6"})}
 FLUX_TRAFFIC = {"bytes_per_cell": 206.6, "profile": "profiles/dram_pointvalue_flux_vortex2048.md",
                 "sha256": dict(_SHARED, **{_KSRC + "af_flux.cu":
                                            "70398b018a67b747d998e66f32b926fefc0c64c3c7bd6b4c9036b1caf4e30272"})}
