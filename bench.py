@@ -54,13 +54,13 @@ FLUX_BYTES_PER_CELL = 208
 # code; af_kernels.h, which declares every kernel's launcher, is left out);
 # otherwise reported as null
 _KSRC = "paper_2508_06273_gb300/csrc/"
-_SHARED = {_KSRC + "af_common.cuh": "49af0eb9318155a23c020300f00bfd3f9cd68738d61f011d7b9bf66f74e1cd97"}
-PV_TRAFFIC = {"bytes_per_cell": 150.9, "profile": "profiles/dram_pointvalue_flux_vortex2048.md",
+_SHARED = {_KSRC + "af_common.cuh": "093115c23be2e775d5d20529727a61310b8bf8c4402d8e1bf8500c33560da0aa"}
+PV_TRAFFIC = {"bytes_per_cell": 150.8, "profile": "profiles/dram_pointvalue_flux_vortex2048.md",
               "sha256": dict(_SHARED, **{_KSRC + "af_pointvalue.cu":
-                                         "fa12b6eaef2aca48a5fd03ec42a8f60dc469bde6fb49fcda0e72c6bb2ef3a0b6"})}
+                                         "5dd8c49de21a3549206c6886e2b4104ff62e4ac106776ebf97ec4a8a3fad0121"})}
 FLUX_TRAFFIC = {"bytes_per_cell": 206.6, "profile": "profiles/dram_pointvalue_flux_vortex2048.md",
                 "sha256": dict(_SHARED, **{_KSRC + "af_flux.cu":
-                                           "70398b018a67b747d998e66f32b926fefc0c64c3c7bd6b4c9036b1caf4e30272"})}
+                                           "164c4a83daa94e5a5764bed37528724938990583775d6600124f0663476ded73"})}
 
 
 def measured_traffic(spec, cells):

@@ -210,6 +210,31 @@ int af_run(af_ctx *h, int nsteps, double dt);
 /* Synchronise the handle's stream; return the accumulated AF_ST_* bits
  * (>= 0) and clear them, or a negative AF_ERR_* code. */
 int af_status(af_ctx *h);
+/* Index checks of a checking build (the library compiled with AF_CHECK_BOUNDS,
+ * paper_2508_06273_gb300/build.py check_bounds=True; not a part of the method).
+ * Synchronises the calling thread's current device, then writes to *out the
+ * AF_BD_* bits of every index check that failed in the library's kernels on that
+ * device since the last call, and clears them.  A failed check does not fault:
+ * the access goes to element 0 of the same array and the step goes on, so a
+ * nonzero *out means the results of the steps since the last call are not to be
+ * trusted.  Checking builds also fill a new handle's state with NaN instead of
+ * zero, so that a read of a point that no set call or step wrote shows up as a
+ * non-finite value.  Returns 1 in a checking build, 0 in a normal one (*out is
+ * then 0), AF_ERR_ARG for a NULL out, AF_ERR_CUDA if the synchronisation fails. */
+enum {
+  AF_BD_PLANE = 1,    /* a plane index outside the padded plane (any kernel) */
+  AF_BD_BOX = 2,      /* the point-value kernel's staged t^n box */
+  AF_BD_RECORD = 4,   /* the point-value kernel's shared-memory cell records */
+  AF_BD_RECORD64 = 8  /* the FP64 path's cell records */
+};
+int af_debug_bounds(unsigned *out);
+/* Minimum density (out[0]) and pressure (out[1]) over the current state: the
+ * primitive form of every cell average and every point value of the three node
+ * arrays; both NaN if any of those values is not finite.  A diagnostic for run
+ * logs (the Sec. 3 positivity of the state), computed on the device and
+ * synchronising the handle's stream.  AF_ERR_STATE without a state or in FP64
+ * mode. */
+int af_state_min(af_ctx *h, float out[2]);
 /* Counters of the last step (synchronises): EG1 fallbacks, LF fallbacks,
  * kept values, vertices flagged by Alg. 2. */
 int af_counters(af_ctx *h, int64_t out[4]);

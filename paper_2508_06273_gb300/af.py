@@ -14,7 +14,9 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libaf.so")
+# AF_LIBRARY may name another build of the same library (the checking build of
+# build.py, check_bounds=True); by default the in-tree libaf.so
+LIB_PATH = os.environ.get("AF_LIBRARY") or os.path.join(_HERE, "_build", "libaf.so")
 _LOCK = threading.Lock()
 _LIB = None
 
@@ -28,7 +30,7 @@ EXPORTS = [
     "af_create", "af_destroy", "af_last_error", "af_set_stream", "af_set_option",
     "af_get_option", "af_set_state", "af_set_state_host", "af_get_state", "af_get_state_host",
     "af_set_state_host_async", "af_get_state_host_async", "af_host_sync", "af_set_state_f64", "af_get_state_f64",
-    "af_get_avg_lo", "af_set_avg_lo", "af_get_half", "af_step", "af_run", "af_status",
+    "af_get_avg_lo", "af_set_avg_lo", "af_get_half", "af_step", "af_run", "af_status", "af_debug_bounds", "af_state_min",
     "af_counters", "af_conserved_totals", "af_max_speed", "af_profile",
     "af_conserved_totals_noalloc",
     "af_batch_create", "af_batch_destroy", "af_batch_set_option", "af_batch_set_state",
@@ -58,6 +60,8 @@ def lib():
             vp, i, d, fp = C.c_void_p, C.c_int, C.c_double, C.c_void_p
             sig = {
                 "af_create": (vp, [i, i, d, d, d, C.c_uint32]),
+                "af_debug_bounds": (i, [C.POINTER(C.c_uint)]),
+                "af_state_min": (i, [vp, fp]),
                 "af_destroy": (None, [vp]),
                 "af_last_error": (C.c_char_p, []),
                 "af_set_stream": (i, [vp, vp]),
@@ -123,6 +127,19 @@ def _check(rc):
     if rc < 0:
         raise AFError(f"af error {rc}: {lib().af_last_error().decode()}")
     return rc
+
+
+BD_PLANE, BD_BOX, BD_RECORD, BD_RECORD64 = 1, 2, 4, 8
+
+
+def debug_bounds():
+    """(checking build?, AF_BD_* bits of the index checks that failed since
+    the last call, on the current device); synchronises the device."""
+    out = C.c_uint(0)
+    rc = lib().af_debug_bounds(C.byref(out))
+    if rc < 0:
+        raise AFError(lib().af_last_error().decode())
+    return bool(rc), int(out.value)
 
 
 def bc_code(bc):
@@ -288,6 +305,13 @@ class Solver:
         out = C.c_float()
         _check(self.L.af_max_speed(self.h, C.byref(out)))
         return out.value
+
+    def state_min(self):
+        """(min rho, min p) over the primitive averages and all point values
+        (NaN, NaN if a value is not finite)."""
+        out = (C.c_float * 2)()
+        _check(self.L.af_state_min(self.h, out))
+        return float(out[0]), float(out[1])
 
     def set_surrogate(self, vertex_net, edge_net, tol=None):
         """Attach networks (Mlp) and switch the surrogate on (None, None: off)."""

@@ -15,6 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libaf.so")
+# checking build (index checks in the kernels, NaN-filled new state; see
+# af_debug_bounds in include/af.h): its own directory, never the default library
+CHECK_DIR = os.path.join(HERE, "_build_check")
+CHECK_LIB = os.path.join(CHECK_DIR, "libaf.so")
 SOURCES = ["af_api.cu", "af_misc.cu", "af_pointvalue.cu", "af_flux.cu", "af_noalloc.cu", "af_batch.cu", "af_gemm.cu", "af_mlp.cu", "af_surrogate.cu", "af_fp64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -34,17 +38,19 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(verbose: bool = False, ptxas_info: bool = False, check_bounds: bool = False) -> str:
+    out_dir, lib = (CHECK_DIR, CHECK_LIB) if check_bounds else (OUT_DIR, LIB)
+    flags = FLAGS + (["-DAF_CHECK_BOUNDS"] if check_bounds else [])
+    os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "af.h"))
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if _stale(o, [s] + headers) or ptxas_info:
-            cmd = [nvcc()] + ARCH + FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", s, "-o", o]
+            cmd = [nvcc()] + ARCH + flags + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", s, "-o", o]
             jobs.append(cmd)
 
     def run(cmd):
@@ -57,16 +63,16 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    if jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, ptxas_info="-v" in sys.argv))
+    print(build(verbose=True, ptxas_info="-v" in sys.argv, check_bounds="--check-bounds" in sys.argv))

@@ -249,11 +249,18 @@ af_ctx *af_create(int nx, int ny, double dx, double dy, double gamma, uint32_t b
   h->d_speed = (unsigned *)(sp + 128);
   h->d_speed_bad = (int *)(sp + 160);
   h->d_counters = (unsigned long long *)(sp + 192);
+  h->d_min_keys = (unsigned *)(sp + 224);
   h->d_totals = (double *)(sp + 256);
   h->d_partials = h->d_totals + NV;
   h->stream = h->own_stream;
-  // the whole state starts zeroed, ghosts included
+  // the whole state starts zeroed, ghosts included; checking builds fill it
+  // with NaN instead, so that a read of a point no step or set call wrote
+  // (a ghost layer not filled, padding) shows as a non-finite result
+#ifdef AF_CHECK_BOUNDS
+  cudaMemsetAsync(h->base, 0xFF, state_bytes, h->stream);
+#else
   cudaMemsetAsync(h->base, 0, state_bytes, h->stream);
+#endif
   cudaMemsetAsync(h->small, 0, small, h->stream);
   cudaStreamSynchronize(h->stream);
   return h;
@@ -1018,6 +1025,17 @@ int af_run(af_ctx *h, int nsteps, double dt) {
   return AF_OK;
 }
 
+int af_debug_bounds(unsigned *out) {
+  if (!out) return fail(AF_ERR_ARG, "null argument%s");
+  CK(cudaDeviceSynchronize(), "af_debug_bounds: sync");
+  *out = af::bounds_flux() | af::bounds_fp64() | af::bounds_misc() | af::bounds_pointvalue() | af::bounds_surrogate();
+#ifdef AF_CHECK_BOUNDS
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 int af_status(af_ctx *h) {
   if (!h) return fail(AF_ERR_ARG, "null handle%s");
   DeviceGuard dg(h->device);
@@ -1069,6 +1087,23 @@ static cudaError_t read_speed(af_ctx *h, unsigned &bits, int &bad) {
   bits = w[0];
   bad = (int)w[1];
   return cudaSuccess;
+}
+
+int af_state_min(af_ctx *h, float out[2]) {
+  if (!h || !out) return fail(AF_ERR_ARG, "null argument%s");
+  if (!h->has_state) return fail(AF_ERR_STATE, "no state set%s");
+  if (h->fp64) return fail(AF_ERR_STATE, "af_state_min: the FP64 state has no FP32 minima (use af_get_state_f64)%s");
+  DeviceGuard dg(h->device);
+  CK(launch_state_min(h->g, h->hi, h->lev[0], h->d_min_keys, h->stream), "state minima");
+  unsigned keys[3];
+  CK(cudaMemcpyAsync(keys, h->d_min_keys, sizeof(keys), cudaMemcpyDeviceToHost, h->stream), "state minima");
+  CK(cudaStreamSynchronize(h->stream), "sync");
+  for (int q = 0; q < 2; q++) {
+    const unsigned u = (keys[q] & 0x80000000u) ? (keys[q] & 0x7FFFFFFFu) : ~keys[q];
+    std::memcpy(&out[q], &u, sizeof(float));
+    if (keys[2]) out[q] = NAN;
+  }
+  return AF_OK;
 }
 
 int af_max_speed(af_ctx *h, float *out) {

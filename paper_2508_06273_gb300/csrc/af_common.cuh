@@ -41,7 +41,38 @@ struct Grid {
   int ubar_c2p;
 };
 
+// Checking builds (AF_CHECK_BOUNDS defined, see build.py): index checks on
+// the planes (at), the point-value kernel's staged box and cell records and
+// the FP64 path's records.  A failed check sets the site's bit in the
+// translation unit's bounds word and the access goes to index 0 of the same
+// array instead (in bounds); af_debug_bounds() collects and clears the words
+// of every unit.  Normal builds compile the checks away.
+enum BoundsSite { BD_PLANE = 1, BD_BOX = 2, BD_RECORD = 4, BD_RECORD64 = 8 };
+#ifdef AF_CHECK_BOUNDS
+static __device__ unsigned bounds_word;  // this unit's failed-check sites
+__device__ __forceinline__ bool bounds_ok(bool ok, unsigned site) {
+  if (!ok) atomicOr(&bounds_word, site);
+  return ok;
+}
+// the unit's word, read and cleared (host; after the unit's kernels ended)
+static inline unsigned take_bounds_word() {
+  unsigned v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, bounds_word, sizeof(v)) != cudaSuccess) return ~0u;
+  cudaMemcpyToSymbol(bounds_word, &z, sizeof(z));
+  return v;
+}
+#define AF_BOUNDS_READER(name) \
+  unsigned name() { return take_bounds_word(); }
+#else
+#define AF_BOUNDS_READER(name) \
+  unsigned name() { return 0u; }
+#endif
+
 __host__ __device__ __forceinline__ long long at(const Grid &g, int v, int i, int j) {
+#if defined(AF_CHECK_BOUNDS) && defined(__CUDA_ARCH__)
+  if (!bounds_ok(v >= 0 && v < NV && i + OX >= 0 && i + OX < g.P && j + OY >= 0 && j + OY < g.H, BD_PLANE))
+    return 0;
+#endif
   return (long long)v * g.plane + (long long)(j + OY) * g.P + (i + OX);
 }
 

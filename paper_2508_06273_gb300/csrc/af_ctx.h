@@ -72,6 +72,7 @@ struct af_ctx {
   int *d_bad_async;
   // two words of mapped pinned host memory (host and device addresses) for
   // the small reads (status, max speed)
+  unsigned *d_min_keys;  // state minima (af_state_min): rho, p as ordered keys, non-finite flag
   unsigned *host_words, *host_words_dev;  // a periodic duplicate line differed in an asynchronous upload
   bool has_state;
   // a block's wait for staged data or for the tensor cores ran out (seen by

@@ -548,4 +548,6 @@ cudaError_t launch_flux_batch(const FluxBatch &B, int nplain, int ntiles, cudaSt
   return cudaGetLastError();
 }
 
+AF_BOUNDS_READER(bounds_flux)
+
 }  // namespace af

@@ -29,6 +29,9 @@ constexpr int REC64 = REC64_DOUBLES;  // a cell record: 4 variables x 9 coeffici
 constexpr double PI_D = 3.14159265358979323846;
 
 __host__ __device__ __forceinline__ long long cell_index(const Grid &g, int i, int j) {
+#if defined(AF_CHECK_BOUNDS) && defined(__CUDA_ARCH__)
+  if (!bounds_ok(i + OX >= 0 && i + OX < g.P && j + OY >= 0 && j + OY < g.H, BD_RECORD64)) return 0;
+#endif
   return (long long)(j + OY) * g.P + (i + OX);
 }
 
@@ -664,5 +667,7 @@ cudaError_t launch_pack64(const Grid &g, const double *src, double *dst, int ni,
   pack64_kernel<<<blocks_for(4LL * ni * nj), 256, 0, s>>>(g, src, dst, ni, nj, to_padded ? 1 : 0);
   return cudaGetLastError();
 }
+
+AF_BOUNDS_READER(bounds_fp64)
 
 }  // namespace af

@@ -238,6 +238,10 @@ cudaError_t launch_flux_nf(const Grid &g, const float *const nf[4], float *avg_h
 // clear_a: small results reach the host without a copy engine, so that they
 // do not queue behind a large transfer
 cudaError_t launch_export_words(unsigned *a, unsigned *b, int clear_a, unsigned *dst, cudaStream_t s);
+// minimum rho and p over the primitive averages and the node arrays into
+// keys[0], keys[1] (order-preserving keys of the floats), keys[2] = 1 if a
+// value is not finite
+cudaError_t launch_state_min(const Grid &g, const float *avg_hi, const NodeSet &n, unsigned *keys, cudaStream_t s);
 cudaError_t launch_max_speed(const Grid &g, const float *avg_hi, const NodeSet &n,
                              unsigned *out_bits, int *bad, cudaStream_t s);
 // fixed-order FP64 sums of hi + lo per variable: partials[nblk][4] -> out[4]
@@ -336,5 +340,13 @@ cudaError_t launch_pointvalue_masked(const Grid &g, const NodeSet &n0, const flo
 
 // record a message for af_last_error on this host thread; returns code
 int set_error(int code, const char *msg);
+
+// failed-index-check sites of each unit's kernels since the last call (0 in
+// normal builds; see AF_BOUNDS_READER in af_common.cuh)
+unsigned bounds_flux();
+unsigned bounds_fp64();
+unsigned bounds_misc();
+unsigned bounds_pointvalue();
+unsigned bounds_surrogate();
 
 }  // namespace af

@@ -290,6 +290,67 @@ __global__ void max_speed_kernel(Grid g, const float *__restrict__ avg, const fl
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(badflag, 1);
 }
 
+// order-preserving unsigned key of a float (atomicMin on keys is a min on
+// the floats; -0 and +0 get neighbouring keys)
+__device__ __forceinline__ unsigned float_key(float f) {
+  const unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// minimum density and pressure over the primitive cell averages and the three
+// node arrays of a state (keys[0], keys[1]); keys[2] set if a value is not finite
+__global__ void state_min_kernel(Grid g, const float *__restrict__ avg, const float *__restrict__ V,
+                                 const float *__restrict__ X, const float *__restrict__ Y, unsigned *keys) {
+  const long long nc = (long long)g.nx * g.ny, nv = (long long)g.nxv * g.nyv;
+  const long long nxe = (long long)g.nxv * g.ny, nye = (long long)g.nx * g.nyv;
+  const long long total = nc + nv + nxe + nye;
+  float rmin = __int_as_float(0x7f800000), pmin = __int_as_float(0x7f800000);
+  bool bad = false;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    float U[4];
+    long long r = k;
+    if (r < nc) {
+      const int i = (int)(r % g.nx), j = (int)(r / g.nx);
+      float Q[4];
+#pragma unroll
+      for (int v = 0; v < NV; v++) Q[v] = __ldg(avg + at(g, v, i, j));
+      c2p(Q, g.gamma - 1.0f, U);
+    } else {
+      const float *p;
+      int ni;
+      if ((r -= nc) < nv) {
+        p = V;
+        ni = g.nxv;
+      } else if ((r -= nv) < nxe) {
+        p = X;
+        ni = g.nxv;
+      } else {
+        r -= nxe;
+        p = Y;
+        ni = g.nx;
+      }
+      const int i = (int)(r % ni), j = (int)(r / ni);
+#pragma unroll
+      for (int v = 0; v < NV; v++) U[v] = __ldg(p + at(g, v, i, j));
+    }
+    bad |= !(isfinite(U[0]) && isfinite(U[1]) && isfinite(U[2]) && isfinite(U[3]));
+    rmin = fminf(rmin, U[0]);
+    pmin = fminf(pmin, U[3]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    pmin = fminf(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
+  }
+  const bool anybad = __any_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(keys, float_key(rmin));
+    atomicMin(keys + 1, float_key(pmin));
+    if (anybad) atomicOr(keys + 2, 1u);
+  }
+}
+
 // stage 1: block b sums rows b, b + nblk, ... in a fixed order
 __global__ void totals_stage1(Grid g, const float *__restrict__ hi, const float *__restrict__ lo,
                               double *partials) {
@@ -420,6 +481,16 @@ cudaError_t launch_max_speed(const Grid &g, const float *avg_hi, const NodeSet &
   return cudaGetLastError();
 }
 
+cudaError_t launch_state_min(const Grid &g, const float *avg_hi, const NodeSet &n, unsigned *keys, cudaStream_t s) {
+  cudaMemsetAsync(keys, 0xFF, 2 * sizeof(unsigned), s);
+  cudaMemsetAsync(keys + 2, 0, sizeof(unsigned), s);
+  long long total = 4LL * (g.nx + 1) * (g.ny + 1);
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  state_min_kernel<<<blocks, 256, 0, s>>>(g, avg_hi, n.k[VTX], n.k[XE], n.k[YE], keys);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_totals(const Grid &g, const float *avg_hi, const float *avg_lo, double *partials,
                           double *out, cudaStream_t s) {
   totals_stage1<<<TOTALS_BLOCKS, 256, 0, s>>>(g, avg_hi, avg_lo, partials);
@@ -444,5 +515,7 @@ cudaError_t launch_check_dup(const float *ext, int ni, int nj, int dup_x, int du
 cudaError_t launch_zero(float *p, long long n, cudaStream_t s) {
   return cudaMemsetAsync(p, 0, (size_t)n * sizeof(float), s);
 }
+
+AF_BOUNDS_READER(bounds_misc)
 
 }  // namespace af

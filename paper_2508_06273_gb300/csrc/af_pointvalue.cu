@@ -86,6 +86,12 @@ using Args = PointValueArgs;
 // tile with origin (i0, j0)
 template <int TY>
 __device__ __forceinline__ float raw_at(const float *raw, int arr, int v, int i, int j, int i0, int j0) {
+#ifdef AF_CHECK_BOUNDS
+  if (!bounds_ok(arr >= 0 && arr < 4 && v >= 0 && v < NV && j - j0 + 1 >= 0 && j - j0 + 1 < Tile<TY>::RAW_H &&
+                     i - i0 + 4 >= 0 && i - i0 + 4 < RAW_W,
+                 BD_BOX))
+    return raw[0];
+#endif
   return raw[((arr * NV + v) * Tile<TY>::RAW_H + (j - j0 + 1)) * RAW_W + (i - i0 + 4)];
 }
 template <int TY>
@@ -110,8 +116,15 @@ __device__ __forceinline__ void unpack4(float4 w, float U[4]) {
   U[3] = w.w;
 }
 
+#ifdef AF_CHECK_BOUNDS
+// rows of cell records the running kernel's tile holds (checking builds)
+__shared__ int rec_rows;
+#endif
 // shared-memory cell record of tile-local cell (a, b), a in [0, HX), b in [0, HY)
 __device__ __forceinline__ const float *cell_rec(const float *sm, int a, int b) {
+#ifdef AF_CHECK_BOUNDS
+  if (!bounds_ok(a >= 0 && a < HX && b >= 0 && b < rec_rows, BD_RECORD)) return sm;
+#endif
   return sm + (b * HX + a) * CELL_F;
 }
 
@@ -952,7 +965,7 @@ template <int TY, int W, int H>
 __device__ __forceinline__ void build_records(const Args &A, const float *raw, float *sm, int i0, int j0, int tid) {
   for (int k = tid; k < W * H; k += TX * TY) {
     const int a = k % W, b = k / W, ci = i0 - 1 + a, cj = j0 - 1 + b;
-    if (ci <= A.g.nx && cj <= A.g.ny) build_cell<TY>(A.g, raw, i0, j0, ci, cj, sm + (b * HX + a) * CELL_F);
+    if (ci <= A.g.nx && cj <= A.g.ny) build_cell<TY>(A.g, raw, i0, j0, ci, cj, const_cast<float *>(cell_rec(sm, a, b)));
   }
 }
 template <int TY>
@@ -1065,6 +1078,9 @@ __device__ __forceinline__ void tile_body(const Args &A, const TileMaps &T, floa
                                           int i0, int j0) {
   float *sm = raw + Tile<TY>::RAW_FLOATS;
   const int tid = threadIdx.y * TX + threadIdx.x;
+#ifdef AF_CHECK_BOUNDS
+  if (tid == 0) rec_rows = Tile<TY>::HY;
+#endif
   if (tid == 0) tile_fetch<TY>(T, raw, bar, i0, j0, A.test_no_copy);
   __syncthreads();
   const bool landed = tile_wait(bar, A.wait_limit);
@@ -1262,5 +1278,7 @@ cudaError_t launch_pointvalue_batch(const PointValueBatch &B, int ntiles, int ti
   }
   return cudaGetLastError();
 }
+
+AF_BOUNDS_READER(bounds_pointvalue)
 
 }  // namespace af

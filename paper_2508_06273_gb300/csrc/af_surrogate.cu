@@ -562,4 +562,6 @@ cudaError_t launch_sample_batch(const SampleBatch &B, const int4 *tiles, int nti
   return cudaGetLastError();
 }
 
+AF_BOUNDS_READER(bounds_surrogate)
+
 }  // namespace af

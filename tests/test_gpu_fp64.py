@@ -148,6 +148,19 @@ def test_table1_to_1024_cells(env, col, opts):
     _check64(errs, tab, range(6), col, 0.12, 0.15)
 
 
+@pytest.mark.skipif(os.environ.get("AF_LONG_TESTS") != "1",
+                    reason="the 1024 row takes about 13 GPU minutes: set AF_LONG_TESTS=1")
+def test_table2_row_1024(env):
+    """Example 2's 1024 row of Table 2 (with the correction, CFL 0.3): the
+    error of the 1024^2 run against the restriction of the 2048^2 run at
+    t = 1, and the order from the 512 row."""
+    tab = read_table(os.path.join(GOLDEN, "table2_ex2.txt"))
+    make = lambda n, fine: W.compact_vortex(2 * n if fine else n)  # noqa: E731
+    errs = _table64(env, make, [512, 1024], 1, {"lin_mode": 2, "correction": 1}, per_row=False)
+    print("Table 2 rows 512, 1024 (GPU FP64):", errs, "printed:", tab[4, 1], tab[5, 1], "EOC", np.log2(errs[0] / errs[1]))
+    _check64(errs, tab, [4, 5], 1, 0.12, 0.15)
+
+
 def test_table2_to_512_cells(env):
     """Example 2 (CFL 0.3) in FP64 with the correction, rows 256 and 512
     (the 512 row is below the FP32 floor)."""
