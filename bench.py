@@ -463,10 +463,11 @@ def _oracle_run(af, W, prob, t_end, max_steps=1_000_000):
     return o.get_state(), dts, time.perf_counter() - t0
 
 
-def _gpu_replay(torch, af, W, prob, dts, nets=None):
+def _gpu_replay(torch, af, W, prob, dts, nets=None, surr_opts=None):
     """GPU run of ``prob`` from the same FP32 initial data with the given dt
-    sequence (plain, or the surrogate with exact fallback when nets are
-    given).  Returns (state as float64 arrays, status, fallback fraction)."""
+    sequence (plain, or the surrogate with exact fallback and the options
+    surr_opts when nets are given).  Returns (state as float64 arrays,
+    status, fallback fraction)."""
     import numpy as np
 
     s = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=prob.options)
@@ -474,6 +475,8 @@ def _gpu_replay(torch, af, W, prob, dts, nets=None):
                   for a in W.to_f32(W.discretise(prob))])
     if nets:
         s.set_surrogate(nets[0], nets[1])
+        for k, v in (surr_opts or {}).items():
+            s.set_option(k, v)
     status = 0
     for dt in dts:
         s.step(dt)
@@ -711,7 +714,7 @@ def _train_surrogate(args, af, W, probs, seed):
     return nets, int(Xv.shape[0]), int(Xe.shape[0])
 
 
-def _surrogate_full(args, torch, af, W, prob, nets, t_end):
+def _surrogate_full(args, torch, af, W, prob, nets, t_end, surr_opts=None):
     """Plain path and surrogate + exact fallback on the full-size grid from
     the same state to t_end: the plain run takes dt = cfl h / (its max speed)
     each step (the last one clipped); the surrogate run takes the same dt
@@ -722,6 +725,8 @@ def _surrogate_full(args, torch, af, W, prob, nets, t_end):
     plain = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=prob.options)
     surr = af.Solver(prob.nx, prob.ny, prob.dx, prob.dy, prob.gamma, prob.bc, options=prob.options)
     surr.set_surrogate(nets[0], nets[1])
+    for k, v in (surr_opts or {}).items():
+        surr.set_option(k, v)
     h = min(prob.dx, prob.dy)
     for s in (plain, surr):  # warm-up steps, then the initial state again
         s.set_state(*dev)
@@ -787,12 +792,12 @@ def sst_or_none(runs, name):
     return runs[name][2] if name in runs else None
 
 
-def _surrogate_vs_oracle(torch, af, W, ref, nets, vortex):
+def _surrogate_vs_oracle(torch, af, W, ref, nets, vortex, surr_opts=None):
     """Plain and surrogate GPU runs at the oracle's size, with the oracle's dt
     sequence, against the FP64 oracle at its final time."""
     prob, ora, dts, osec = ref
     plain, pst, _ = _gpu_replay(torch, af, W, prob, dts)
-    surr, sst, frac = _gpu_replay(torch, af, W, prob, dts, nets)
+    surr, sst, frac = _gpu_replay(torch, af, W, prob, dts, nets, surr_opts)
     rp, rs = _rel_l1(plain, ora), _rel_l1(surr, ora)
     out = {"grid": [prob.nx, prob.ny], "final_time": float(sum(dts)), "steps": len(dts),
            "rel_l1_plain_vs_oracle": rp, "rel_l1_surrogate_vs_oracle": rs,
@@ -805,6 +810,12 @@ def _surrogate_vs_oracle(torch, af, W, ref, nets, vortex):
                                   "plain": _vortex_l1_vs_exact(W, prob, plain[0][0], t)[0],
                                   "surrogate": _vortex_l1_vs_exact(W, prob, surr[0][0], t)[0]}
     return out
+
+
+# the Riemann case keeps the network away from shocks and contacts: its value
+# is used only where every variable's range over the node's stencil is at
+# most 0.05 in the features' scaled units (AF_OPT_SURR_SMOOTH)
+RIEMANN_SURR = {"surr_smooth": 0.05}
 
 
 def run_surrogate_leg(args, torch, af, W, refs):
@@ -850,13 +861,15 @@ def run_surrogate_leg(args, torch, af, W, refs):
     train_s = time.perf_counter() - t0
     nr = args.surr_grid // 2
     pair = (nets[0][0], nets[1][0])
-    rie = _surrogate_full(args, torch, af, W, W.four_quadrant(nr, seed=6), pair, args.riemann_t)
+    rie = _surrogate_full(args, torch, af, W, W.four_quadrant(nr, seed=6), pair, args.riemann_t, RIEMANN_SURR)
     if refs:
-        rie["oracle_check"] = _surrogate_vs_oracle(torch, af, W, refs["riemann256"], pair, vortex=False)
+        rie["oracle_check"] = _surrogate_vs_oracle(torch, af, W, refs["riemann256"], pair, vortex=False,
+                                                   surr_opts=RIEMANN_SURR)
     rie.update({
         "workload": f"four-quadrant Riemann problem, transmissive [0,1]^2, {nr}x{nr} cells, states from seed 6, "
                     f"Alg. 2, Alg. 3 with node bounds, Sec. 3.4 blend, flux limiter, Ubar = C2P of the average, "
                     f"CFL 0.3, dt from the max speed every step, to t = {args.riemann_t}",
+        "surrogate_options": RIEMANN_SURR,
         "training": {"samples_vertex": nv, "samples_edge": ne, "seconds_incl_sampling": train_s,
                      "loss_first_last_vertex": [nets[0][1], nets[0][2]],
                      "loss_first_last_edge": [nets[1][1], nets[1][2]],

@@ -84,6 +84,9 @@ enum {
   AF_OPT_SURR_TOL = 7,   /* surrogate check: a new value may leave the range of the node's
                             stencil by at most this fraction of the range's width (default 0.5) */
   AF_OPT_SURR_ABS = 8,   /* ... plus this much in the scaled units of the features (default 2e-3) */
+  AF_OPT_SURR_SMOOTH = 18, /* the network's value is used only where the range of every variable over the
+                              node's stencil, in the same scaled units, is at most this (default: no limit);
+                              elsewhere (at shocks and contacts) the exact operator, as for a failed check */
   AF_OPT_FLUX_LIMITER = 9, /* 1: cell-average flux limiter (Sec. 3.5 names one without printing it): each
                               face flux blended with the Rusanov flux of the two averages by the largest
                               weight that keeps the convex-decomposition face states of both cells
@@ -308,7 +311,8 @@ int af_set_inflow(af_ctx *h, int side, const double U[4]);
  * Outputs: (U^{n+1/2} - U^n) and (U^{n+1} - U^n) in the same scaling and
  * frame.  A node's result is kept if rho, p > 0, it is finite and each
  * scaled variable lies within the stencil's range widened by
- * AF_OPT_SURR_TOL times its width plus AF_OPT_SURR_ABS; otherwise the exact operator (with its
+ * AF_OPT_SURR_TOL times its width plus AF_OPT_SURR_ABS, and (with AF_OPT_SURR_SMOOTH) no
+ * variable's stencil range exceeds that limit; otherwise the exact operator (with its
  * limiter) computes that node.  The networks stay owned by the caller and
  * must outlive their use; square cells only (AF_ERR_ARG otherwise).
  * Passing NULL, NULL removes them. */

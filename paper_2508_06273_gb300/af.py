@@ -23,7 +23,8 @@ _LIB = None
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTING, BC_INFLOW = 0, 1, 2, 3
 OPT = {"lin_mode": 0, "tsw": 1, "limiter": 2, "correction": 3, "force_lo": 4, "profile": 5, "surrogate": 6,
        "surr_tol": 7, "surr_abs": 8,
-       "flux_limiter": 9, "shock_blend": 10, "tile_h": 11, "node_bounds": 12, "ubar": 13, "test_timeout": 14, "keep_half": 15, "node_flux": 16, "fp64": 17}
+       "flux_limiter": 9, "shock_blend": 10, "tile_h": 11, "node_bounds": 12, "ubar": 13, "test_timeout": 14, "keep_half": 15, "node_flux": 16, "fp64": 17,
+       "surr_smooth": 18}
 STAGES = ("prep", "pointvalue", "flux", "reduce")
 ST_CFL, ST_AVG_NONPOS, ST_NONFINITE, ST_KEPT, ST_TIMEOUT, ST_STOPPED, ST_FLUX_LIMITED = 1, 2, 4, 8, 16, 32, 64
 EXPORTS = [

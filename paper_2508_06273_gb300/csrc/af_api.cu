@@ -431,6 +431,10 @@ int af_set_option(af_ctx *h, int key, double value) {
       if (!(value >= 0.0) || !std::isfinite(value)) return fail(AF_ERR_ARG, "surrogate tolerance must be >= 0%s");
       h->opt.surr_abs = (float)value;
       return AF_OK;
+    case AF_OPT_SURR_SMOOTH:
+      if (!(value >= 0.0)) return fail(AF_ERR_ARG, "surrogate stencil limit must be >= 0%s");
+      h->opt.surr_smooth = value > 3.0e38 ? 3.0e38f : (float)value;
+      return AF_OK;
     default: return fail(AF_ERR_ARG, "unknown option%s");
   }
 }
@@ -447,6 +451,7 @@ int af_get_option(af_ctx *h, int key, double *value) {
     case AF_OPT_SURROGATE: *value = h->opt.surrogate; return AF_OK;
     case AF_OPT_SURR_TOL: *value = h->opt.surr_tol; return AF_OK;
     case AF_OPT_SURR_ABS: *value = h->opt.surr_abs; return AF_OK;
+    case AF_OPT_SURR_SMOOTH: *value = h->opt.surr_smooth; return AF_OK;
     case AF_OPT_FLUX_LIMITER: *value = h->opt.flux_limiter; return AF_OK;
     case AF_OPT_SHOCK_BLEND: *value = h->opt.shock_blend; return AF_OK;
     case AF_OPT_NODE_BOUNDS: *value = h->opt.node_bounds; return AF_OK;
@@ -820,6 +825,7 @@ static int enqueue_step(af_ctx *h, double dt) {
         A.dt = (float)dt;
         A.tol = h->opt.surr_tol;
         A.tol_abs = h->opt.surr_abs;
+        A.smooth = h->opt.surr_smooth;
         af_mlp *net = h->surr[k == VTX ? 0 : 1];
         A.wb = net->wb;
         A.params = net->params;
@@ -950,7 +956,8 @@ int af_step(af_ctx *h, double dt) {
 static bool same_options(const Options &a, const Options &b) {
   return a.lin_mode == b.lin_mode && a.tsw == b.tsw && a.limiter == b.limiter &&
          a.correction == b.correction && a.force_lo == b.force_lo && a.surrogate == b.surrogate &&
-         a.surr_tol == b.surr_tol && a.surr_abs == b.surr_abs && a.flux_limiter == b.flux_limiter &&
+         a.surr_tol == b.surr_tol && a.surr_abs == b.surr_abs && a.surr_smooth == b.surr_smooth &&
+         a.flux_limiter == b.flux_limiter &&
          a.shock_blend == b.shock_blend && a.node_bounds == b.node_bounds && a.test_timeout == b.test_timeout &&
          a.node_flux == b.node_flux;
 }

@@ -23,6 +23,7 @@ struct Options {
   int surrogate = 0;   // learned point-value operator with exact fallback
   float surr_tol = 0.5f;
   float surr_abs = 2e-3f;
+  float surr_smooth = 3.0e38f;  // network only where every scaled stencil range is at most this
   int flux_limiter = 0;  // cell-average flux limiter (Sec. 3.5)
   int shock_blend = 0;   // Sec. 3.4 shock-indicator blend of point values
   int node_bounds = 0;   // Alg. 3 also bounds rho, p by the node's cells (see node_update)
@@ -315,6 +316,7 @@ struct SurrogateArgs {
   const float *ubar;  // primitive cell averages Ubar of cells -1 .. n (launch_ubar)
   float *n1[3], *n2[3];
   float dt, tol, tol_abs;
+  float smooth;  // the network's values are used only where every scaled stencil range is <= smooth
   const __nv_bfloat16 *wb;  // network weights (row-major, packed)
   const float *params;      // FP32 parameters (biases, scales)
   unsigned char *mask;      // this kind's fallback bytes

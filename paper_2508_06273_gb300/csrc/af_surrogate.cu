@@ -480,8 +480,8 @@ __global__ void __launch_bounds__(NG *TM, 1) surrogate_kernel(SurrogateArgs A) {
     tc::tmem_ld32(tld, y);
     if (valid) {
       // decode, check (admissible, inside the stencil's range widened by tol
-      // times its width plus tol_abs, finite), store or flag for the exact
-      // operator
+      // times its width plus tol_abs, finite, a stencil no wider than smooth),
+      // store or flag for the exact operator
       bool good = true;
       float Un[2][4];
       float U0[4];
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(NG *TM, 1) surrogate_kernel(SurrogateArgs A) {
           const int v = var_of_slot<K>(q);
           const float d = (y[4 * lev + q] + b4[4 * lev + q]) * outs[4 * lev + q];
           const float x = self[q] + d, w = A.tol * (hi[q] - lo[q]) + A.tol_abs;
-          good = good && (x >= lo[q] - w) && (x <= hi[q] + w);
+          good = good && (x >= lo[q] - w) && (x <= hi[q] + w) && (hi[q] - lo[q] <= A.smooth);
           Un[lev][v] = U0[v] + s[v] * d;
         }
         good = good && Un[lev][0] > 0.0f && Un[lev][3] > 0.0f && isfinite(Un[lev][1]) && isfinite(Un[lev][2]);

@@ -158,3 +158,35 @@ def test_trained_surrogate_beats_the_method_without_it(env):
         s.close()
     for m in nets:
         m.close()
+
+
+def test_the_stencil_limit_sends_wide_stencils_to_the_exact_operator(env):
+    """AF_OPT_SURR_SMOOTH: with a limit of 0 no stencil of smooth nonuniform
+    data qualifies and the step is bit for bit the plain method; a limit no
+    stencil reaches changes nothing against no limit."""
+    torch, af, _ = env
+    prob = W.fourier_smooth(40, 40, seed=9)
+    nets = [af.Mlp(seed=s) for s in (1, 2)]
+    plain, surr = solver(env, prob), solver(env, prob)
+    surr.set_surrogate(*nets)
+    surr.set_option("surr_smooth", 0.0)
+    dt = 0.3 * prob.dx / plain.max_speed()
+    for _ in range(3):
+        plain.step(dt)
+        surr.step(dt)
+    for a, c in zip(plain.get_state(), surr.get_state()):
+        assert torch.equal(a, c)
+    n_net, n_fall = surr.surrogate_stats()
+    assert n_net == 0 and n_fall == 3 * 3 * 40 * 40
+    a, b = solver(env, prob), solver(env, prob)
+    for s in (a, b):
+        s.set_surrogate(*nets)
+    b.set_option("surr_smooth", 1e30)
+    for _ in range(3):
+        a.step(dt)
+        b.step(dt)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert torch.equal(x, y)
+    assert a.surrogate_stats() == b.surrogate_stats()
+    for s in (plain, surr, a, b):
+        s.close()
