@@ -276,7 +276,7 @@ int af_profile(af_ctx *h, double ms[4], int64_t launches[4], int reset);
  * the limit is rejected with AF_ERR_ARG before anything runs.  Set-up on the
  * first call on each device: the call looks the array's device address up
  * (cudaGetSymbolAddress), and with CUDA's default lazy module loading that
- * is when the driver loads this entry point's device code and the array onto
+ * is when the CUDA driver loads this entry point's device code and the array onto
  * the device, which allocates device memory and may synchronise.  Make that
  * first call on every device during set-up, before the region that must not
  * allocate and before any stream capture; later calls allocate nothing.
